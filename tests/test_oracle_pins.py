@@ -1,0 +1,380 @@
+"""Pins for the FP64 oracle against facts fixed independently of its code.
+
+Each pin is something the paper or the mathematics fixes without reference to the oracle:
+a hand-worked example (tests/golden), closed forms derived by substitution, the random
+surfer's stationary distribution (a Markov-chain description of the same quantity,
+solved as an eigenproblem), a library PageRank (networkx), brute force over every
+digraph on up to 4 vertices, and invariants/bounds that any correct solution obeys.
+The last test compiles deliberately broken copies of the oracle and checks that each
+plausible mistake (dropped term, wrong sign, transposed operand) fails a pin.
+"""
+import os
+import re
+import subprocess
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+D85 = 0.85
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------------ helpers --
+
+def surfer_stationary(n, src, dst, d, t=None):
+    """Stationary distribution of the random surfer, written from its description:
+    from page u the surfer teleports with probability 1-d to a page drawn from t
+    (uniform by default); otherwise it follows one of u's out-links chosen uniformly
+    (a repeated link is proportionally more likely) or, if u has none, jumps to a
+    uniformly random page.  Solved as the eigenvector of eigenvalue 1 of P^T."""
+    t = np.full(n, 1.0 / n) if t is None else np.asarray(t, dtype=np.float64) / np.sum(t)
+    P = np.zeros((n, n))
+    links = np.zeros((n, n))
+    for u, v in zip(src, dst):
+        links[u, v] += 1
+    for u in range(n):
+        P[u, :] += (1 - d) * t
+        k = links[u].sum()
+        if k > 0:
+            P[u, :] += d * links[u] / k
+        else:
+            P[u, :] += d / n
+    w, V = np.linalg.eig(P.T)
+    i = np.argmin(np.abs(w - 1.0))
+    pi = np.real(V[:, i])
+    return pi / pi.sum()
+
+
+def load_golden(name):
+    vals = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, *rest = line.split()
+            vals[key] = rest
+    return vals
+
+
+def frac_list(tokens):
+    return [float(Fraction(x)) for x in tokens]
+
+
+# --------------------------------------------------------- worked example --
+
+def test_worked_example_one_step(oracle_lib):
+    g = load_golden("worked_example_4v.txt")
+    n = int(g["n"][0])
+    d = float(Fraction(g["d"][0]))
+    rp, ci = gg.edges_to_in_csr(n, [int(s) for s in g["src"]], [int(s) for s in g["dst"]])
+    x = np.array(frac_list(g["x"]))
+    t = np.array(frac_list(g["t"]))
+    xn, D, l1, _ = oracle.jacobi_step(rp, ci, x, d=d)
+    assert D == pytest.approx(float(Fraction(g["dangling_mass"][0])), abs=1e-15)
+    np.testing.assert_allclose(xn, frac_list(g["x_next"]), rtol=0, atol=1e-15)
+    assert l1 == pytest.approx(float(Fraction(g["l1_change"][0])), abs=1e-15)
+    xl, _, _, _ = oracle.jacobi_step(rp, ci, x, d=d, redistribute=False)
+    np.testing.assert_allclose(xl, frac_list(g["x_next_literal"]), rtol=0, atol=1e-15)
+    xt, _, _, _ = oracle.jacobi_step(rp, ci, x, d=d, t=t)
+    np.testing.assert_allclose(xt, frac_list(g["x_next_teleport"]), rtol=0, atol=1e-15)
+    # the single-vertex form agrees with the whole-vector step
+    for v in range(n):
+        assert oracle.vertex_update(v, rp, ci, x, D, d=d) == pytest.approx(xn[v], abs=1e-16)
+        assert oracle.vertex_update(v, rp, ci, x, D, d=d, t=t) == pytest.approx(xt[v], abs=1e-16)
+
+
+def test_outdeg_counts_multiplicity():
+    rp, ci = gg.edges_to_in_csr(4, [0, 0, 0, 1, 2], [1, 1, 2, 2, 0], dedup=False)
+    assert list(oracle.outdeg(rp, ci)) == [3, 1, 1, 0]
+
+
+# ------------------------------------------------------------ closed forms --
+
+def _both(rp, ci, d, t=None):
+    xs = oracle.dense_solve(rp, ci, d=d, t=t)
+    xj, it, res = oracle.fixed_point(rp, ci, d=d, t=t)
+    return xs, xj
+
+
+@pytest.mark.parametrize("n", [2, 3, 7, 50])
+@pytest.mark.parametrize("d", [0.0, 0.5, 0.85, 0.99])
+def test_closed_forms(n, d):
+    L = n - 1
+    for build, expect in [
+        (gg.cycle, np.full(n, 1.0 / n)),
+        (gg.complete, np.full(n, 1.0 / n)),
+        (gg.empty, np.full(n, 1.0 / n)),
+        (gg.in_star, np.array([(1 + d * L) / (n + d * L)] + [1.0 / (n + d * L)] * L)),
+        (gg.out_star, np.array([1.0 / (n + d)] + [(L + d) / (L * (n + d))] * L)),
+        (gg.bi_star, None),
+    ]:
+        rp, ci = build(n)
+        if expect is None:  # bidirectional star
+            hub = (1 + d * L) / (n * (1 + d))
+            expect = np.array([hub] + [(1 - d) / n + d * hub / L] * L)
+        for x in _both(rp, ci, d):
+            np.testing.assert_allclose(x, expect, rtol=1e-11, atol=1e-14,
+                                       err_msg=f"{build.__name__} n={n} d={d}")
+
+
+def test_literal_eq1_leaks_mass():
+    # single edge 0 -> 1 on two vertices, Eq. 1 without a dangling share:
+    # x0 = (1-d)/2,  x1 = (1-d)/2 + d*x0
+    d = 0.85
+    rp, ci = gg.edges_to_in_csr(2, [0], [1])
+    x = oracle.dense_solve(rp, ci, d=d, redistribute=False)
+    np.testing.assert_allclose(x, [(1 - d) / 2, (1 - d) / 2 + d * (1 - d) / 2], atol=1e-15)
+    xj, _, _ = oracle.fixed_point(rp, ci, d=d, redistribute=False)
+    np.testing.assert_allclose(xj, x, atol=1e-14)
+    assert x.sum() < 1.0
+
+
+def test_literal_equals_redistributed_without_dangling():
+    rp, ci = gg.cycle(9)
+    rp2, ci2 = gg.rmat(9, seed=2)
+    for r, c in [(rp, ci), (rp2, ci2)]:
+        if np.any(oracle.outdeg(r, c) == 0):
+            x1, _, _ = oracle.pagerank_jacobi(r, c, tol=0, max_iter=30)
+            x2, _, _ = oracle.pagerank_jacobi(r, c, tol=0, max_iter=30, redistribute=False)
+            assert x2.sum() < x1.sum()
+        else:
+            x1, _, _ = oracle.pagerank_jacobi(r, c, tol=0, max_iter=30)
+            x2, _, _ = oracle.pagerank_jacobi(r, c, tol=0, max_iter=30, redistribute=False)
+            assert np.array_equal(x1, x2)
+
+
+# ------------------------------------------------------------ random surfer --
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_surfer_stationary_distribution(seed):
+    n = 5 + 7 * seed
+    m = 3 * n
+    multi = seed % 2 == 1
+    rp, ci = gg.random_digraph(n, m, seed=seed, allow_multi=multi, self_loops=multi)
+    src, dst = gg.in_csr_edges(rp, ci)
+    t = gg.uniform(seed, 3, n) if seed >= 3 else None
+    if t is not None:
+        t = t / t.sum()
+    for d in (0.5, 0.85):
+        pi = surfer_stationary(n, src, dst, d, t)
+        xs, xj = _both(rp, ci, d, t)
+        np.testing.assert_allclose(xs, pi, rtol=1e-9, atol=1e-13)
+        np.testing.assert_allclose(xj, pi, rtol=1e-9, atol=1e-13)
+
+
+def test_library_pagerank():
+    nx = pytest.importorskip("networkx")
+    for seed in range(4):
+        rp, ci = gg.rmat(8, edge_factor=4, seed=100 + seed)
+        n = rp.size - 1
+        src, dst = gg.in_csr_edges(rp, ci)
+        G = nx.DiGraph()
+        G.add_nodes_from(range(n))
+        G.add_edges_from(zip(src.tolist(), dst.tolist()))
+        ref = nx.pagerank(G, alpha=D85, tol=1e-15, max_iter=100000)
+        ref = np.array([ref[v] for v in range(n)])
+        x, _, _ = oracle.fixed_point(rp, ci)
+        np.testing.assert_allclose(x, ref, rtol=1e-9, atol=1e-14)
+        # personalised teleport (networkx keeps dangling mass uniform when dangling=None)
+        t = gg.uniform(seed, 5, n)
+        t /= t.sum()
+        ref = nx.pagerank(G, alpha=D85, personalization={v: t[v] for v in range(n)},
+                          dangling={v: 1.0 / n for v in range(n)}, tol=1e-15, max_iter=100000)
+        ref = np.array([ref[v] for v in range(n)])
+        x, _, _ = oracle.fixed_point(rp, ci, t=t)
+        np.testing.assert_allclose(x, ref, rtol=1e-9, atol=1e-14)
+
+
+# -------------------------------------------------------------- brute force --
+
+def _all_digraphs(n):
+    pairs = [(u, v) for u in range(n) for v in range(n) if u != v]
+    for mask in range(1 << len(pairs)):
+        es = [pairs[i] for i in range(len(pairs)) if mask >> i & 1]
+        yield es
+
+
+@pytest.mark.parametrize("n", [2, 3, 4])
+def test_every_digraph(n):
+    worst_j, worst_s = 0.0, 0.0
+    for es in _all_digraphs(n):
+        src = [e[0] for e in es]
+        dst = [e[1] for e in es]
+        rp, ci = gg.edges_to_in_csr(n, src, dst)
+        pi = surfer_stationary(n, src, dst, D85)
+        xs = oracle.dense_solve(rp, ci)
+        xj, _, _ = oracle.fixed_point(rp, ci)
+        worst_s = max(worst_s, np.abs(xs - pi).max())
+        worst_j = max(worst_j, np.abs(xj - pi).max())
+    assert worst_s < 1e-12 and worst_j < 1e-12
+
+
+# --------------------------------------------------- invariants and bounds --
+
+@pytest.mark.parametrize("seed", range(3))
+def test_invariants_and_contraction_bound(seed):
+    rp, ci = gg.rmat(11, seed=seed)
+    n = rp.size - 1
+    t = gg.uniform(seed, 9, n)
+    t = 0.7 * t / t.sum()           # sum(t) = 0.7: the fixed point then sums to 0.7
+    for tt, total in [(None, 1.0), (t, 0.7)]:
+        xstar, _, _ = oracle.fixed_point(rp, ci, t=tt)
+        assert xstar.sum() == pytest.approx(total, rel=1e-12)
+        floor = (1 - D85) * (np.full(n, 1.0 / n) if tt is None else tt)
+        assert np.all(xstar >= floor * (1 - 1e-12))
+        # a-posteriori bound of a contraction with factor d in L1:
+        #   ||x_k - x*||_1 <= d/(1-d) * ||x_k - x_{k-1}||_1
+        x = np.full(n, 1.0 / n) if tt is None else tt.copy()
+        for _ in range(15):
+            xn, _, l1, _ = oracle.jacobi_step(rp, ci, x, t=tt)
+            err = np.abs(xn - xstar).sum()
+            assert err <= D85 / (1 - D85) * l1 * (1 + 1e-9) + 1e-14
+            x = xn
+
+
+def test_permutation_equivariance():
+    rp, ci = gg.rmat(10, seed=4)
+    n = rp.size - 1
+    perm = gg.permutation(4, 1, n)
+    rp2, ci2 = gg.permute_in_csr(rp, ci, perm)
+    x, _, _ = oracle.fixed_point(rp, ci)
+    x2, _, _ = oracle.fixed_point(rp2, ci2)
+    np.testing.assert_allclose(x2[perm], x, rtol=1e-10, atol=1e-15)
+
+
+def test_matching_mode_counts_iterations():
+    rp, ci = gg.rmat(12, seed=1)
+    x, it, res, hist = oracle.pagerank_jacobi(rp, ci, tol=1e-10, max_iter=200, history=True)
+    assert res < 1e-10 and it == hist.size and np.all(hist[:-1] >= 1e-10)
+    x1, it1, _ = oracle.pagerank_jacobi(rp, ci, tol=0, max_iter=1)
+    assert it1 == 1
+    # two single steps equal one two-step run
+    xa, _, _ = oracle.pagerank_jacobi(rp, ci, tol=0, max_iter=2)
+    xb, _, _ = oracle.pagerank_jacobi(rp, ci, tol=0, max_iter=1, x0=x1)
+    assert np.array_equal(xa, xb)
+
+
+# ------------------------------------------------------- No-Sync (Alg. 3) --
+
+@pytest.mark.parametrize("form", ["mass", "complement"])
+@pytest.mark.parametrize("p", [1, 3, 16])
+def test_nosync_reaches_the_same_fixed_point(form, p):
+    """Lemma 2: the lock-free result equals the sequential one within the threshold."""
+    rp, ci = gg.rmat(10, seed=7)
+    xstar, _, _ = oracle.fixed_point(rp, ci)
+    speed = (1 + np.arange(p) % 3).astype(np.int32)  # unequal thread speeds
+    x, sweeps, upd, est = oracle.nosync(rp, ci, p=p, tol=1e-12, max_sweeps=5000, speed=speed,
+                                        dangling=form)
+    assert est <= 1e-12
+    assert np.abs(x - xstar).sum() < 1e-10
+    assert sweeps.min() >= 1
+
+
+def test_nosync_paper_norm_and_literal():
+    rp, ci = gg.rmat(9, seed=8)
+    for redistribute in (True, False):
+        xstar, _, _ = oracle.fixed_point(rp, ci, redistribute=redistribute)
+        x, sweeps, _, est = oracle.nosync(rp, ci, p=4, tol=1e-14, max_sweeps=5000, norm="linf",
+                                          redistribute=redistribute, dangling="mass")
+        assert np.abs(x - xstar).sum() < 1e-11
+
+
+def test_nosync_fewer_sweeps_than_jacobi_iterations():
+    """The paper's iteration-count observation (Fig. 7): in-place updates converge in fewer
+    sweeps than synchronous iterations.  With uniform dangling redistribution this needs
+    the complement form of the dangling share; the running-mass form is slower."""
+    rp, ci = gg.rmat(12, seed=3)
+    _, it, _ = oracle.pagerank_jacobi(rp, ci, tol=1e-12, max_iter=1000)
+    _, sw_c, _, _ = oracle.nosync(rp, ci, p=8, tol=1e-12, dangling="complement")
+    _, sw_m, _, _ = oracle.nosync(rp, ci, p=8, tol=1e-12, dangling="mass")
+    assert sw_c.max() < it < sw_m.max()
+
+
+def test_nosync_single_sweep_on_a_chain():
+    """p=1 on the chain 0 -> 1 -> ... -> n-1 with Eq. 1 literal: an in-place sweep in vertex
+    order sees each predecessor's new value, so one sweep gives the exact fixed point
+    x_k = (1-d)/n * sum_{j<=k} d^j (Jacobi needs n sweeps for the same)."""
+    n, d = 6, 0.85
+    rp, ci = gg.edges_to_in_csr(n, np.arange(n - 1), np.arange(1, n))
+    expect = np.array([(1 - d) / n * sum(d ** j for j in range(k + 1)) for k in range(n)])
+    x, sweeps, upd, est = oracle.nosync(rp, ci, d=d, p=1, tol=1e-300, max_sweeps=1,
+                                        redistribute=False, dangling="mass")
+    np.testing.assert_allclose(x, expect, rtol=1e-14)
+    xj, _, _ = oracle.pagerank_jacobi(rp, ci, d=d, tol=0, max_iter=1, redistribute=False)
+    assert not np.allclose(xj, expect)
+
+
+# ------------------------------------------------------ planted mistakes --
+
+def _pins_pass(lib):
+    """A compact run of the pins above against a given build of the oracle."""
+    g = load_golden("worked_example_4v.txt")
+    n = int(g["n"][0])
+    d = float(Fraction(g["d"][0]))
+    rp, ci = gg.edges_to_in_csr(n, [int(s) for s in g["src"]], [int(s) for s in g["dst"]])
+    x = np.array(frac_list(g["x"]))
+    t = np.array(frac_list(g["t"]))
+    try:
+        xn, _, _, _ = oracle.jacobi_step(rp, ci, x, d=d, lib=lib)
+        if not np.allclose(xn, frac_list(g["x_next"]), atol=1e-15):
+            return False
+        xt, _, _, _ = oracle.jacobi_step(rp, ci, x, d=d, t=t, lib=lib)
+        if not np.allclose(xt, frac_list(g["x_next_teleport"]), atol=1e-15):
+            return False
+        for build in (gg.in_star, gg.out_star):
+            rps, cis = build(7)
+            L = 6
+            expect = (np.array([(1 + d * L) / (7 + d * L)] + [1 / (7 + d * L)] * L)
+                      if build is gg.in_star else
+                      np.array([1 / (7 + d)] + [(L + d) / (L * (7 + d))] * L))
+            if not np.allclose(oracle.dense_solve(rps, cis, d=d, lib=lib), expect, atol=1e-12):
+                return False
+        rp2, ci2 = gg.random_digraph(9, 25, seed=2)
+        src, dst = gg.in_csr_edges(rp2, ci2)
+        pi = surfer_stationary(9, src, dst, d)
+        if not np.allclose(oracle.dense_solve(rp2, ci2, d=d, lib=lib), pi, atol=1e-12):
+            return False
+        xj, _, _ = oracle.fixed_point(rp2, ci2, d=d, lib=lib)
+        if not np.allclose(xj, pi, atol=1e-12):
+            return False
+        xs, _, _, _ = oracle.nosync(rp2, ci2, d=d, p=3, tol=1e-13, lib=lib)
+        if not np.allclose(xs, pi, atol=1e-11):
+            return False
+    except oracle.OracleError:
+        return False
+    return True
+
+
+MUTATIONS = {
+    "drop_dangling_share": ("d * (sum + D / (double)n)", "d * (sum)"),
+    "wrong_damping_sign": ("(1.0 - d) * or_teleport(n, t, v)", "(1.0 + d) * or_teleport(n, t, v)"),
+    "divide_by_target_degree": ("sum += x[u] / (double)outdeg[u];",
+                                "sum += x[u] / (double)(outdeg[v] ? outdeg[v] : 1);"),
+    "teleport_index": ("return t ? t[v] : 1.0 / (double)n;",
+                       "return t ? t[n - 1 - v] : 1.0 / (double)n;"),
+    "transposed_system": ("M[v * n + u] -= d / (double)outdeg[u];",
+                          "M[u * n + v] -= d / (double)outdeg[u];"),
+    "dangling_from_wrong_set": ("if (outdeg[u] == 0) D += x[u];", "if (outdeg[u] == 1) D += x[u];"),
+    "nosync_stale_nondangling_mass": ("else S += tmp - previous;", "else S += 0.0;"),
+}
+
+
+def test_pins_pass_on_the_real_oracle(oracle_lib):
+    assert _pins_pass(oracle_lib)
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_each_planted_mistake_fails_a_pin(name, tmp_path):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "pagerank_oracle.c")).read()
+    old, new = MUTATIONS[name]
+    assert src.count(old) >= 1, f"mutation anchor for {name} not found"
+    mutated = tmp_path / "oracle_mut.c"
+    mutated.write_text(src.replace(old, new))
+    out = oracle.build(force=True, src=str(mutated), out=str(tmp_path / "liboracle_mut.so"))
+    lib = oracle.load(out)
+    assert not _pins_pass(lib), f"planted mistake '{name}' was not caught"
