@@ -1,0 +1,413 @@
+"""Benchmark: PageRank on one GB300 -- synchronous (Jacobi) and barrier-free solves.
+
+Workload (one "step"): R-MAT scale 24 (Graph500 a/b/c = .57/.19/.19, edge factor 16,
+self-loops and duplicates removed, seeded relabelling) and an Erdos-Renyi digraph of
+2^24 vertices with mean out-degree 16 and 20% dangling vertices; each graph solved
+with the synchronous Jacobi iteration and with the barrier-free in-place kernel, to an
+L1 change below 1e-6 (damping 0.85, budget 200 iterations).  Four solves per step.
+
+  value     GTEPS = edges gathered in the timed steps / their device time (CUDA
+            events on the solving stream; graphs already resident in HBM)
+  e2e       the same metric through the C ABI from pinned host buffers: graph
+            creation (H2D copy + set-up), both solves, and the D2H read of every
+            result inside the timed region
+  roofline  one Jacobi iteration (k_heavy_segments + k_rows) on R-MAT-24:
+            algorithmic bytes 4*nnz + 4*(n+1) + 20*n over the measured iteration time
+  cpu_baseline  the FP64 oracle (single thread, as it stands) on a bounded sample:
+            a few synchronous iterations of the same R-MAT-24 graph
+
+``--impl reference`` times the oracle alone (the reference arm for this build).
+Multi-GPU (torchrun): every rank solves its own replica (weak scaling, no collective
+in the data path); the timed region is bracketed by barriers and the max over ranks
+is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PageRank GTEPS/iter and time-to-L1<1e-6 on 1 GB300 vs plain FP32 Jacobi; % HBM peak"
+DAMPING = 0.85
+TOL = 1e-6
+MAX_ITER = 200
+SEED_RMAT = 24
+SEED_ER = 1024
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def make_graphs(scale, er_n):
+    import graphgen as gg
+    t0 = time.time()
+    rmat = gg.rmat(scale, 16, seed=SEED_RMAT)
+    t1 = time.time()
+    er = gg.er_dangling(er_n, 16.0, 0.2, seed=SEED_ER)
+    t2 = time.time()
+    log(f"[bench] generated rmat-{scale} nnz={rmat[1].size} in {t1 - t0:.1f}s, "
+        f"er n={er_n} nnz={er[1].size} in {t2 - t1:.1f}s")
+    return [(f"rmat{scale}", rmat), (f"er{int(round(math.log2(er_n)))}", er)]
+
+
+def algorithmic_bytes(n, nnz, rowptr_bytes=4):
+    return 4 * nnz + rowptr_bytes * (n + 1) + 20 * n
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_sources_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2109_09527_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per iteration from the committed ncu summary, if taken on these sources."""
+    path = os.path.join(ROOT, "profiles", "traffic_rmat24_jacobi.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    if rec.get("source_sha") != kernel_sources_sha():
+        return None
+    return rec.get("dram_bytes_per_iteration")
+
+
+def kernels_executed(info, variant, has_segments, use_graph=True):
+    """Kernels that ran for one pr_solve (graph nodes included)."""
+    per_iter = 2 if has_segments else 1
+    if variant == 0:
+        it = info.iterations
+        body = 2 * math.ceil(it / 2) if use_graph else it
+        return 1 + per_iter * body + 2
+    return info.launches
+
+
+def cpu_baseline(graph, budget_s=20.0):
+    """The oracle as it stands, on a bounded sample of the R-MAT graph: synchronous FP64
+    iterations, one thread.  GTEPS = nnz * iterations / seconds."""
+    import oracle
+    name, (rp, ci) = graph
+    iters, elapsed = 0, 0.0
+    k = 1
+    while elapsed < budget_s and iters < 8:
+        t0 = time.perf_counter()
+        oracle.pagerank_jacobi(rp, ci, d=DAMPING, tol=0, max_iter=k)
+        dt = time.perf_counter() - t0
+        elapsed += dt
+        iters += k
+        if dt * 2 > budget_s - elapsed:
+            break
+    return {"value": ci.size * iters / elapsed / 1e9, "unit": "GTEPS", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{iters} FP64 synchronous iterations (oracle, 1 thread, incl. its out-degree "
+                      f"pass) on {name} (n={rp.size - 1}, nnz={ci.size}), {elapsed:.1f} s"}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    import graphgen  # noqa: F401
+    import oracle
+    graphs = make_graphs(args.scale, 1 << args.er_log2)
+    name, (rp, ci) = graphs[0]
+    oracle.outdeg(rp, ci)  # builds the oracle library before timing
+    for _ in range(args.warmup):
+        oracle.pagerank_jacobi(rp, ci, d=DAMPING, tol=0, max_iter=1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.pagerank_jacobi(rp, ci, d=DAMPING, tol=0, max_iter=1)
+    dt = time.perf_counter() - t0
+    value = ci.size * args.steps / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{name}: one FP64 synchronous iteration per step (oracle)",
+                       "damping": DAMPING},
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} single FP64 synchronous iterations of the "
+                                       f"oracle on {name} (n={rp.size - 1}, nnz={ci.size})"},
+            "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--scale", type=int, default=24)
+    ap.add_argument("--er-log2", type=int, default=24)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import paper_2109_09527_gb300 as pr
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    graphs = make_graphs(args.scale, 1 << args.er_log2)
+    stream = torch.cuda.current_stream()
+
+    # graphs resident in HBM
+    resident = []
+    for name, (rp, ci) in graphs:
+        g = pr.Graph(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev))
+        st = g.stats()
+        resident.append((name, g, st))
+        log(f"[bench] {name}: n={st['n']} nnz={st['nnz']} heavy={st['n_heavy']} "
+            f"segments={st['n_segments']} tiles={st['n_tiles']} dangling={st['n_dangling']} "
+            f"setup={st['setup_ms']:.1f} ms")
+    outs = {name: torch.empty(st["n"], dtype=torch.float32, device=dev) for name, _, st in resident}
+    variants = [(pr.PR_JACOBI, "jacobi"), (pr.PR_NONBLOCKING, "nonblocking")]
+
+    def step(record):
+        visits = 0.0
+        launches = 0
+        for name, g, st in resident:
+            for vid, vname in variants:
+                status, info = pr.pr_solve(g.handle, DAMPING, TOL, MAX_ITER, vid, None, None,
+                                           outs[name])
+                visits += info.edge_visits
+                launches += kernels_executed(info, vid, st["n_segments"] > 0)
+                if record is not None:
+                    record.append({"graph": name, "variant": vname, "iterations": info.iterations,
+                                   "time_to_tol_ms": info.ms_device, "residual_l1": info.residual_l1,
+                                   "converged": bool(info.converged),
+                                   "gteps": info.edge_visits / (info.ms_device * 1e-3) / 1e9})
+        return visits, launches
+
+    for _ in range(args.warmup):
+        step(None)
+
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    records = []
+    ev0.record(stream)
+    visits, launches = 0.0, 0
+    for _ in range(args.steps):
+        v, l = step(records)
+        visits += v
+        launches += l
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        vt = torch.tensor([visits], dtype=torch.float64, device=dev)
+        dist.all_reduce(vt, op=dist.ReduceOp.SUM)
+        visits = float(vt.item())
+    value = visits / (ms * 1e-3) / 1e9
+
+    # roofline: one Jacobi iteration on the R-MAT graph, from the timed solves
+    rname, rg, rst = resident[0]
+    jac = [r for r in records if r["graph"] == rname and r["variant"] == "jacobi"]
+    it_ms = statistics.median(r["time_to_tol_ms"] / r["iterations"] for r in jac)
+    peak, peak_kind = peaks()
+    bytes_iter = algorithmic_bytes(rst["n"], rst["nnz"], rst["rowptr_bytes"])
+    achieved = bytes_iter / (it_ms * 1e-3) / 1e9
+    traffic = recorded_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": f"jacobi iteration (k_heavy_segments + k_rows) on {rname}",
+                "peak_source": f"{peak_kind} hbm_gbs", "bytes_per_iteration": bytes_iter,
+                "ms_per_iteration": it_ms, "frac_of_8tbs_spec": achieved / 8000.0}
+
+    cases = {}
+    for r in records:
+        cases.setdefault((r["graph"], r["variant"]), []).append(r)
+    case_lines = []
+    for (gname, vname), rs in cases.items():
+        case_lines.append({"graph": gname, "variant": vname,
+                           "iterations": rs[0]["iterations"],
+                           "time_to_tol_ms": statistics.median(r["time_to_tol_ms"] for r in rs),
+                           "gteps": statistics.median(r["gteps"] for r in rs),
+                           "residual_l1": rs[-1]["residual_l1"],
+                           "converged": all(r["converged"] for r in rs)})
+
+    # end to end through the C ABI from pinned host buffers
+    pinned = []
+    h2d = 0
+    for name, (rp, ci) in graphs:
+        prp = torch.from_numpy(rp).pin_memory()
+        pci = torch.from_numpy(ci).pin_memory()
+        pinned.append((name, prp, pci))
+        h2d += prp.numel() * 8 + pci.numel() * 4
+    host_out = {name: torch.empty(rp.size - 1, dtype=torch.float32).pin_memory()
+                for name, (rp, ci) in graphs}
+    d2h = sum(2 * 4 * (rp.size - 1) for _, (rp, ci) in graphs)
+
+    def e2e_step():
+        v = 0.0
+        for name, prp, pci in pinned:
+            with pr.Graph(prp, pci) as g:
+                for vid, _ in variants:
+                    _, info = pr.pr_solve(g.handle, DAMPING, TOL, MAX_ITER, vid, None, None,
+                                          host_out[name])
+                    v += info.edge_visits
+        return v
+
+    e2e_step()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ev = 0.0
+    for _ in range(args.e2e_steps):
+        ev += e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+        vt = torch.tensor([ev], dtype=torch.float64, device=dev)
+        dist.all_reduce(vt, op=dist.ReduceOp.SUM)
+        ev = float(vt.item())
+    e2e = {"value": ev / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
+           "ms_per_step": e2e_s * 1e3 / args.e2e_steps,
+           "includes": "pr_create_graph from pinned host CSR (H2D + set-up), Jacobi and "
+                       "barrier-free solves, D2H of each result, pr_destroy_graph"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(graphs[0])
+
+    for _, g, _ in resident:
+        g.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": f"rmat{args.scale} (Graph500 a/b/c .57/.19/.19, ef 16) + "
+                                       f"er{args.er_log2} (mean out-degree 16, 20% dangling); "
+                                       "Jacobi and barrier-free solves to L1<1e-6, d=0.85",
+                           "graphs": [{"name": n, "n": st["n"], "nnz": st["nnz"]}
+                                      for n, _, st in resident],
+                           "tol": TOL, "damping": DAMPING, "max_iter": MAX_ITER,
+                           "parallelism": f"replicas x{world}",
+                           "l2": "inputs larger than L2 (colidx alone 1.07 GB per graph)"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clocks, "cases": case_lines}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

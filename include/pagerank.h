@@ -1,0 +1,195 @@
+/*
+ * pagerank.h -- C ABI of the GB300 (sm_103a) PageRank library.
+ *
+ * The library computes the PageRank vector of a directed graph given as CSR:
+ *
+ *   Eq. 1:  x(v) = (1-d) t(v) + d * ( sum_{(u,v) in E} x(u)/outdeg(u) + D/n )
+ *
+ * where t is the teleport vector (uniform 1/n unless given), D is the rank
+ * held by dangling vertices (outdeg 0), spread uniformly over all n vertices,
+ * and a repeated edge counts with its multiplicity.  Eq. 1 of the paper has
+ * t = 1/n and no dangling term; the dangling share is this library's reading
+ * (mass is conserved: sum(x) = sum(t)).
+ *
+ * Two solvers run the same update:
+ *   PR_JACOBI       the synchronous iteration of Alg. 1 (Barrier baseline):
+ *                   every vertex is recomputed from the previous vector, the
+ *                   dangling mass and the L1 change ||x_k - x_{k-1}||_1 are
+ *                   reduced in the same pass, and the loop stops when that
+ *                   change is below tol or after max_iter iterations.
+ *   PR_NONBLOCKING  the barrier-free form of Alg. 3 (No-Sync): one persistent
+ *                   launch in which warps update ranks in place, with no grid
+ *                   synchronisation and no previous-iteration array; each
+ *                   block stops on its own view of the global change
+ *                   (thread-level convergence, Section 4.3).  The result is
+ *                   then verified with one synchronous update, whose L1
+ *                   change is the reported residual.
+ *
+ * Conventions
+ *   - All functions return a pr_status.  No function aborts or exits; on an
+ *     error the thread-local message from pr_last_error() says what failed.
+ *   - Vertex ids are 0..n-1, int32 (n <= 2^31-1).  Row offsets may be int32
+ *     or int64; the edge count may exceed 2^31 only with int64 offsets.
+ *   - Pointers marked "host or device" are classified with
+ *     cudaPointerGetAttributes; host memory (pinned or pageable) is copied
+ *     in or out by the call, device memory is used in place.
+ *   - Work is enqueued on the given CUDA stream (NULL = the legacy default
+ *     stream).  Calls that fill a pr_info synchronise that stream before
+ *     returning; calls that do not are asynchronous with respect to the host.
+ *   - A pr_graph belongs to the device that was current when it was created;
+ *     use it with that device current.  One pr_graph must not be used by two
+ *     host threads at the same time.
+ */
+#ifndef PAGERANK_GB300_H
+#define PAGERANK_GB300_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PR_API __attribute__((visibility("default")))
+#else
+#define PR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pr_graph pr_graph; /* opaque; owned by the library */
+
+typedef enum pr_status {
+    PR_OK = 0,
+    PR_ERR_INVALID_ARG = 1,    /* a bad argument; nothing was changed           */
+    PR_ERR_CUDA = 2,           /* a CUDA call failed (message in pr_last_error)  */
+    PR_ERR_OOM = 3,            /* device or pinned memory could not be obtained  */
+    PR_NOT_CONVERGED = 4,      /* max_iter reached; outputs are still written    */
+    PR_ERR_UNSUPPORTED = 5,    /* a valid request this build does not implement  */
+    PR_ERR_INVALID_GRAPH = 6,  /* rowptr/colidx failed validation on the device  */
+    PR_ERR_DEVICE_TIMEOUT = 7  /* a bounded device-side wait gave up             */
+} pr_status;
+
+/* layout argument of pr_create_graph */
+#define PR_IN_CSR 0  /* rows are destinations: row v lists the sources u of u -> v */
+#define PR_OUT_CSR 1 /* rows are sources: row u lists the destinations v of u -> v */
+
+/* variant argument of pr_solve */
+#define PR_JACOBI 0
+#define PR_NONBLOCKING 1
+
+typedef struct pr_info {
+    int32_t iterations;    /* Jacobi: iterations run.  Non-blocking: the largest
+                              number of sweeps any block made, summed over
+                              launches, plus the verifying update.            */
+    int32_t converged;     /* 1 if the stopping test was met                  */
+    double residual_l1;    /* L1 change of the last synchronous update         */
+    double sum_x;          /* sum of the final vector before renormalisation   */
+    double dangling_mass;  /* dangling mass of the final vector (before any
+                              renormalisation)                                 */
+    double edge_visits;    /* edges gathered in total (GTEPS numerator)        */
+    float ms_device;       /* device time of the call's work, CUDA events      */
+    int32_t launches;      /* kernel launches the call enqueued                */
+} pr_info;
+
+typedef struct pr_graph_stats {
+    int64_t n;             /* vertices                                         */
+    int64_t nnz;           /* edges (with multiplicity)                        */
+    int64_t n_dangling;    /* vertices without out-edges                       */
+    int64_t n_zero_indeg;  /* vertices without in-edges                        */
+    int64_t n_heavy;       /* rows gathered in segments by whole warps         */
+    int64_t n_segments;    /* edge segments of those rows                      */
+    int64_t n_tiles;       /* row tiles of the per-iteration gather kernel     */
+    int64_t max_indeg;
+    int32_t rowptr_bytes;  /* 4 or 8: width of the row offsets kept on device  */
+    int32_t sm_count;
+    int64_t device_bytes;  /* device memory owned by the graph                 */
+    float setup_ms;        /* device time of pr_create_graph's kernels         */
+} pr_graph_stats;
+
+/* Build a graph on the current device.
+ *   n, nnz        vertex and edge counts (n >= 1, nnz >= 0).
+ *   rowptr        host or device, n+1 offsets, int64 if rowptr_is_64 else
+ *                 int32; rowptr[0] = 0, non-decreasing, rowptr[n] = nnz.
+ *   colidx        host or device, nnz int32 vertex ids in [0, n).
+ *   weights       must be NULL (edge weights are not supported by this
+ *                 build: PR_ERR_UNSUPPORTED).
+ *   layout        PR_IN_CSR (the CSR input of Alg. 1, "G = ConvertCsr(V,E)"
+ *                 in Alg. 2/3, read as in-links).  PR_OUT_CSR returns
+ *                 PR_ERR_UNSUPPORTED in this build.
+ *   stream        CUDA stream for the copies and set-up kernels.
+ *   out           receives the new graph; *out is NULL on failure.
+ * The library copies the arrays into memory it owns; the caller may free or
+ * reuse them when the call returns.  Validation runs on the device: a
+ * malformed CSR returns PR_ERR_INVALID_GRAPH.  The call synchronises the
+ * stream.  Set-up computes out-degrees, bins rows by in-degree and relabels
+ * vertices so that each bin is a contiguous range (outputs are always in the
+ * caller's vertex order). */
+PR_API pr_status pr_create_graph(int64_t n, int64_t nnz, const void* rowptr, int rowptr_is_64,
+                                 const int32_t* colidx, const float* weights, int layout,
+                                 void* stream, pr_graph** out);
+
+/* Free a graph and all device memory it owns.  NULL is accepted. */
+PR_API pr_status pr_destroy_graph(pr_graph* g);
+
+/* Solve for the PageRank vector (Eq. 1 with the uniform dangling share).
+ *   damping       d, 0 <= d < 1 (the paper uses 0.85, Section 1).
+ *   tol           > 0: stop when ||x_k - x_{k-1}||_1 < tol (the paper's
+ *                 threshold, Alg. 1, compared in L1 rather than max-abs).
+ *   max_iter      >= 1: iteration budget (sweep budget for PR_NONBLOCKING).
+ *   variant       PR_JACOBI or PR_NONBLOCKING.
+ *   teleport      host or device, n floats >= 0, or NULL for uniform 1/n.
+ *   x0            host or device, n floats (warm start), or NULL for x0 = t.
+ *   x_out         host or device, n floats: the result, rescaled in FP64 so
+ *                 that sum(x_out) = sum(teleport) (1 when uniform).
+ *   info          may be NULL; filled after the stream is synchronised.
+ * Returns PR_OK, or PR_NOT_CONVERGED when the budget ran out (x_out and info
+ * are written in both cases). */
+PR_API pr_status pr_solve(pr_graph* g, float damping, double tol, int32_t max_iter, int variant,
+                          const float* teleport, const float* x0, float* x_out, pr_info* info,
+                          void* stream);
+
+/* Run exactly n_iter synchronous updates (the loop body of Alg. 1) from x_in,
+ * with no stopping test and no renormalisation.
+ *   x_in, x_out   host or device, n floats each (may be the same buffer).
+ *   teleport      as in pr_solve.
+ *   info          may be NULL; residual_l1 is the L1 change of the last
+ *                 update and dangling_mass the dangling mass of x_out.
+ * n_iter >= 1. */
+PR_API pr_status pr_iterate(pr_graph* g, float damping, const float* teleport, const float* x_in,
+                            int32_t n_iter, float* x_out, pr_info* info, void* stream);
+
+/* Fill *stats with the graph's sizes and set-up figures. */
+PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
+
+/* Tuning knobs, mostly for tests that force one code path at a time.
+ *   PR_OPT_HEAVY_DEGREE   rows with in-degree >= value are gathered in
+ *                         segments (a power of two in [64, 2^30]; default
+ *                         1024).  Takes effect at the next pr_create_graph
+ *                         of the same thread (it changes the layout), so it
+ *                         is a thread-local default, set with g = NULL.
+ *   PR_OPT_USE_GRAPH      1 (default): the Jacobi loop runs as one CUDA
+ *                         graph with a conditional while node; 0: the host
+ *                         enqueues iterations in chunks.
+ *   PR_OPT_CTAS_PER_SM    blocks per SM of the persistent kernels (0 =
+ *                         from occupancy, else 1..8).
+ *   PR_OPT_INDEX64        1: keep 64-bit row offsets on the device even when
+ *                         the edge count fits 32 bits (thread-local default
+ *                         for the next pr_create_graph, set with g = NULL;
+ *                         0 restores the automatic choice).
+ * Unknown keys or values out of range return PR_ERR_INVALID_ARG. */
+#define PR_OPT_HEAVY_DEGREE 1
+#define PR_OPT_USE_GRAPH 2
+#define PR_OPT_CTAS_PER_SM 3
+#define PR_OPT_INDEX64 4
+PR_API pr_status pr_set_option(pr_graph* g, int key, int64_t value);
+
+/* Static text for a status code. */
+PR_API const char* pr_status_string(pr_status s);
+
+/* Message of the last error raised on the calling thread ("" if none). */
+PR_API const char* pr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAGERANK_GB300_H */

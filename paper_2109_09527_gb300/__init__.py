@@ -1,0 +1,275 @@
+"""GB300 (sm_103a) PageRank: Python binding of the C ABI in ``include/pagerank.h``.
+
+This module only marshals arguments: every step of the computation runs in the
+CUDA library ``_build/libpagerank_gb300.so``.  The functions named ``pr_*``
+mirror the C entry points one to one (a non-OK status raises
+:class:`PageRankError`, except ``PR_NOT_CONVERGED`` which is returned); the
+:class:`Graph` class wraps a ``pr_graph`` handle for convenience.
+
+Array arguments may be numpy arrays (host memory), torch tensors (host or
+CUDA), or raw integer addresses.  Device tensors are used in place; host
+arrays are copied by the library.  ``stream=None`` means torch's current CUDA
+stream when torch has initialised CUDA, else the legacy default stream.
+
+If the library is missing or stale it is built with nvcc on first use; if
+that fails, import-time use raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+PR_OK = 0
+PR_ERR_INVALID_ARG = 1
+PR_ERR_CUDA = 2
+PR_ERR_OOM = 3
+PR_NOT_CONVERGED = 4
+PR_ERR_UNSUPPORTED = 5
+PR_ERR_INVALID_GRAPH = 6
+PR_ERR_DEVICE_TIMEOUT = 7
+
+PR_IN_CSR = 0
+PR_OUT_CSR = 1
+PR_JACOBI = 0
+PR_NONBLOCKING = 1
+
+PR_OPT_HEAVY_DEGREE = 1
+PR_OPT_USE_GRAPH = 2
+PR_OPT_CTAS_PER_SM = 3
+PR_OPT_INDEX64 = 4
+
+LIB_PATH = _build.LIB_PATH
+
+
+class PageRankError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_status_name(status)}: {message}")
+        self.status = status
+
+
+class pr_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("residual_l1", ctypes.c_double), ("sum_x", ctypes.c_double),
+                ("dangling_mass", ctypes.c_double), ("edge_visits", ctypes.c_double),
+                ("ms_device", ctypes.c_float), ("launches", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class pr_graph_stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("n_dangling", ctypes.c_int64),
+                ("n_zero_indeg", ctypes.c_int64), ("n_heavy", ctypes.c_int64),
+                ("n_segments", ctypes.c_int64), ("n_tiles", ctypes.c_int64),
+                ("max_indeg", ctypes.c_int64), ("rowptr_bytes", ctypes.c_int32),
+                ("sm_count", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
+                ("setup_ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+# name -> (restype, argtypes) of every entry point declared in include/pagerank.h
+_VP, _I64, _I32, _D, _F = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_float
+SIGNATURES = {
+    "pr_create_graph": (ctypes.c_int, [_I64, _I64, _VP, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP,
+                                       ctypes.POINTER(_VP)]),
+    "pr_destroy_graph": (ctypes.c_int, [_VP]),
+    "pr_solve": (ctypes.c_int, [_VP, _F, _D, _I32, ctypes.c_int, _VP, _VP, _VP,
+                                ctypes.POINTER(pr_info), _VP]),
+    "pr_iterate": (ctypes.c_int, [_VP, _F, _VP, _VP, _I32, _VP, ctypes.POINTER(pr_info), _VP]),
+    "pr_graph_get_stats": (ctypes.c_int, [_VP, ctypes.POINTER(pr_graph_stats)]),
+    "pr_set_option": (ctypes.c_int, [_VP, ctypes.c_int, _I64]),
+    "pr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "pr_last_error": (ctypes.c_char_p, []),
+}
+
+
+def load(path: str | None = None):
+    """The ctypes handle of the CUDA library (built on first use if missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None or path is not None:
+            if path is None:
+                path = _build.build()
+            if not os.path.exists(path):
+                raise ImportError(f"CUDA library not found at {path}")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            if path == LIB_PATH:
+                _lib = lib
+            else:
+                return lib
+    return _lib
+
+
+def _status_name(s: int) -> str:
+    try:
+        return load().pr_status_string(s).decode()
+    except Exception:  # noqa: BLE001 - naming only
+        return f"status {s}"
+
+
+def _check(status: int, allow_not_converged: bool = False) -> int:
+    if status == PR_OK or (allow_not_converged and status == PR_NOT_CONVERGED):
+        return status
+    raise PageRankError(status, load().pr_last_error().decode())
+
+
+def _addr(obj, dtype=None):
+    """Address of an array argument: None, int, numpy array or torch tensor."""
+    if obj is None:
+        return None
+    if isinstance(obj, int):
+        return obj
+    if isinstance(obj, np.ndarray):
+        if dtype is not None and obj.dtype != dtype:
+            raise TypeError(f"expected dtype {np.dtype(dtype)}, got {obj.dtype}")
+        if not obj.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return obj.ctypes.data
+    if hasattr(obj, "data_ptr"):  # torch.Tensor
+        if not obj.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if dtype is not None:
+            want = {np.float32: "torch.float32", np.int32: "torch.int32",
+                    np.int64: "torch.int64"}[np.dtype(dtype).type]
+            if str(obj.dtype) != want:
+                raise TypeError(f"expected {want}, got {obj.dtype}")
+        return obj.data_ptr()
+    raise TypeError(f"unsupported array argument {type(obj)}")
+
+
+def _stream(stream):
+    if stream is not None:
+        return int(stream) if not hasattr(stream, "cuda_stream") else stream.cuda_stream
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return 0
+
+
+# ---------------------------------------------------------------- C entry points --
+
+def pr_create_graph(n, nnz, rowptr, rowptr_is_64, colidx, weights=None, layout=PR_IN_CSR,
+                    stream=None):
+    out = _VP()
+    _check(load().pr_create_graph(int(n), int(nnz), _addr(rowptr), int(bool(rowptr_is_64)),
+                                  _addr(colidx, np.int32), _addr(weights), int(layout),
+                                  _stream(stream), ctypes.byref(out)))
+    return out.value
+
+
+def pr_destroy_graph(g):
+    return _check(load().pr_destroy_graph(g))
+
+
+def pr_solve(g, damping, tol, max_iter, variant, teleport, x0, x_out, stream=None):
+    """Returns (status, pr_info); status is PR_OK or PR_NOT_CONVERGED."""
+    info = pr_info()
+    st = _check(load().pr_solve(g, float(damping), float(tol), int(max_iter), int(variant),
+                                _addr(teleport, np.float32), _addr(x0, np.float32),
+                                _addr(x_out, np.float32), ctypes.byref(info), _stream(stream)),
+                allow_not_converged=True)
+    return st, info
+
+
+def pr_iterate(g, damping, teleport, x_in, n_iter, x_out, stream=None):
+    info = pr_info()
+    _check(load().pr_iterate(g, float(damping), _addr(teleport, np.float32),
+                             _addr(x_in, np.float32), int(n_iter), _addr(x_out, np.float32),
+                             ctypes.byref(info), _stream(stream)))
+    return info
+
+
+def pr_graph_get_stats(g):
+    s = pr_graph_stats()
+    _check(load().pr_graph_get_stats(g, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def pr_set_option(g, key, value):
+    return _check(load().pr_set_option(g, int(key), int(value)))
+
+
+def pr_status_string(status):
+    return load().pr_status_string(int(status)).decode()
+
+
+def pr_last_error():
+    return load().pr_last_error().decode()
+
+
+# ------------------------------------------------------------------- convenience --
+
+class Graph:
+    """Owns a pr_graph built from an in-edge CSR (row v lists the sources of v's in-edges)."""
+
+    def __init__(self, rowptr, colidx, stream=None):
+        n = (rowptr.shape[0] if hasattr(rowptr, "shape") else len(rowptr)) - 1
+        nnz = colidx.shape[0] if hasattr(colidx, "shape") else len(colidx)
+        is64 = str(getattr(rowptr, "dtype", "")) in ("int64", "torch.int64")
+        if not is64 and str(getattr(rowptr, "dtype", "")) not in ("int32", "torch.int32"):
+            raise TypeError("rowptr must be int32 or int64")
+        self.n, self.nnz = int(n), int(nnz)
+        self.handle = pr_create_graph(n, nnz, rowptr, is64, colidx, stream=stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            pr_destroy_graph(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def stats(self):
+        return pr_graph_get_stats(self.handle)
+
+    def solve(self, damping=0.85, tol=1e-6, max_iter=200, variant=PR_JACOBI, teleport=None,
+              x0=None, out=None, stream=None):
+        """PageRank vector; `out` defaults to a host float32 numpy array.  Returns (out, info)."""
+        if out is None:
+            out = np.empty(self.n, dtype=np.float32)
+        if isinstance(variant, str):
+            variant = {"jacobi": PR_JACOBI, "nonblocking": PR_NONBLOCKING}[variant]
+        status, info = pr_solve(self.handle, damping, tol, max_iter, variant, teleport, x0, out,
+                                stream=stream)
+        return out, info
+
+    def iterate(self, x_in, n_iter=1, damping=0.85, teleport=None, out=None, stream=None):
+        """Exactly n_iter synchronous updates from x_in (no stopping test, no rescaling)."""
+        if out is None:
+            out = np.empty(self.n, dtype=np.float32)
+        info = pr_iterate(self.handle, damping, teleport, x_in, n_iter, out, stream=stream)
+        return out, info
+
+    def set_option(self, key, value):
+        pr_set_option(self.handle, key, value)
+
+
+def set_heavy_degree(value: int):
+    """Heavy in-degree threshold for graphs created next on this thread (power of two)."""
+    pr_set_option(None, PR_OPT_HEAVY_DEGREE, value)

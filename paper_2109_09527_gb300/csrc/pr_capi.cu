@@ -1,0 +1,144 @@
+// pr_capi.cu -- error reporting, options, statistics and teardown of the C ABI.
+#include <cstring>
+#include <string>
+
+#include "pr_common.cuh"
+
+namespace prk {
+
+namespace {
+thread_local std::string t_last_error;
+thread_local int t_heavy_degree = kDefaultHeavy;
+thread_local bool t_force_index64 = false;
+}  // namespace
+
+void set_error(const std::string& msg) { t_last_error = msg; }
+
+pr_status fail(pr_status s, const std::string& msg) {
+    set_error(msg);
+    return s;
+}
+
+pr_status cuda_fail(cudaError_t e, const char* what) {
+    std::string msg = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    set_error(msg);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();  // clear the sticky-free allocation error
+        return PR_ERR_OOM;
+    }
+    return PR_ERR_CUDA;
+}
+
+cudaError_t dev_alloc(pr_graph* g, void** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) g->device_bytes += (int64_t)bytes;
+    else *p = nullptr;
+    return e;
+}
+
+bool is_device_pointer(const void* p) {
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int thread_heavy_degree() { return t_heavy_degree; }
+
+void set_thread_heavy_degree(int v) { t_heavy_degree = v; }
+
+bool thread_force_index64() { return t_force_index64; }
+
+}  // namespace prk
+
+using namespace prk;
+
+extern "C" pr_status pr_destroy_graph(pr_graph* g) {
+    if (!g) return PR_OK;
+    void* dev[] = {g->rowptr, g->colidx, g->inv_out, g->order, g->rank, g->x[0], g->x[1],
+                   g->y[0], g->y[1], g->teleport, g->stage, g->seg_row, g->seg_ptr, g->seg_sum,
+                   g->tiles, g->state, g->slots, g->nb_items, g->nb_slots,
+                   g->nb_scalars, g->nb_block_sweeps};
+    cudaError_t first = cudaSuccess;
+    for (void* p : dev)
+        if (p) {
+            cudaError_t e = cudaFree(p);
+            if (first == cudaSuccess) first = e;
+        }
+    for (auto& ex : g->loop_exec)
+        if (ex) cudaGraphExecDestroy(ex);
+    if (g->host_state) cudaFreeHost(g->host_state);
+    if (g->host_flag) cudaFreeHost(g->host_flag);
+    if (g->capture_stream) cudaStreamDestroy(g->capture_stream);
+    if (g->ev_start) cudaEventDestroy(g->ev_start);
+    if (g->ev_stop) cudaEventDestroy(g->ev_stop);
+    delete g;
+    if (first != cudaSuccess) return cuda_fail(first, "pr_destroy_graph: cudaFree");
+    return PR_OK;
+}
+
+extern "C" pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* s) {
+    if (!g || !s) return fail(PR_ERR_INVALID_ARG, "pr_graph_get_stats: NULL argument");
+    memset(s, 0, sizeof(*s));
+    s->n = g->n;
+    s->nnz = g->nnz;
+    s->n_dangling = g->n_dangling;
+    s->n_zero_indeg = g->n_zero_indeg;
+    s->n_heavy = g->n_heavy;
+    s->n_segments = g->n_seg;
+    s->n_tiles = g->n_tiles;
+    s->max_indeg = g->max_indeg;
+    s->rowptr_bytes = g->idx64 ? 8 : 4;
+    s->sm_count = g->sm_count;
+    s->device_bytes = g->device_bytes;
+    s->setup_ms = g->setup_ms;
+    return PR_OK;
+}
+
+extern "C" pr_status pr_set_option(pr_graph* g, int key, int64_t value) {
+    switch (key) {
+        case PR_OPT_HEAVY_DEGREE:
+            if (g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_HEAVY_DEGREE is set with g = NULL (it applies to the next pr_create_graph)");
+            if (value < 64 || value > (1LL << 30) || (value & (value - 1)))
+                return fail(PR_ERR_INVALID_ARG, "PR_OPT_HEAVY_DEGREE must be a power of two in [64, 2^30]");
+            set_thread_heavy_degree((int)value);
+            return PR_OK;
+        case PR_OPT_USE_GRAPH:
+            if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_USE_GRAPH needs a graph");
+            if (value != 0 && value != 1) return fail(PR_ERR_INVALID_ARG, "PR_OPT_USE_GRAPH is 0 or 1");
+            g->use_graph = value == 1;
+            return PR_OK;
+        case PR_OPT_CTAS_PER_SM:
+            if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_CTAS_PER_SM needs a graph");
+            if (value < 0 || value > 8) return fail(PR_ERR_INVALID_ARG, "PR_OPT_CTAS_PER_SM is 0 (automatic) to 8");
+            g->ctas_per_sm = (int)value;
+            return PR_OK;
+        case PR_OPT_INDEX64:
+            if (g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_INDEX64 is set with g = NULL (it applies to the next pr_create_graph)");
+            if (value != 0 && value != 1) return fail(PR_ERR_INVALID_ARG, "PR_OPT_INDEX64 is 0 or 1");
+            t_force_index64 = value == 1;
+            return PR_OK;
+        default:
+            return fail(PR_ERR_INVALID_ARG, "unknown option key");
+    }
+}
+
+extern "C" const char* pr_status_string(pr_status s) {
+    switch (s) {
+        case PR_OK: return "PR_OK";
+        case PR_ERR_INVALID_ARG: return "PR_ERR_INVALID_ARG";
+        case PR_ERR_CUDA: return "PR_ERR_CUDA";
+        case PR_ERR_OOM: return "PR_ERR_OOM";
+        case PR_NOT_CONVERGED: return "PR_NOT_CONVERGED";
+        case PR_ERR_UNSUPPORTED: return "PR_ERR_UNSUPPORTED";
+        case PR_ERR_INVALID_GRAPH: return "PR_ERR_INVALID_GRAPH";
+        case PR_ERR_DEVICE_TIMEOUT: return "PR_ERR_DEVICE_TIMEOUT";
+        default: return "PR_UNKNOWN_STATUS";
+    }
+}
+
+extern "C" const char* pr_last_error(void) { return prk::t_last_error.c_str(); }

@@ -1,0 +1,201 @@
+// pr_common.cuh -- internal definitions shared by the library's CUDA sources.
+//
+// Device data layout of a graph (all in HBM, owned by pr_graph):
+//   Vertices are relabelled at set-up so that rows with similar in-degree are
+//   contiguous: first the heavy rows (in-degree >= heavy threshold, gathered in
+//   fixed-size edge segments), then the light rows in bins of decreasing
+//   power-of-two in-degree class, then the rows without in-edges.  Every
+//   per-vertex vector below is in this "binned" order; order[i] is the caller's
+//   id of binned vertex i and rank[v] the binned id of caller vertex v.
+//
+//   rowptr   IdxT[n+1]   in-edge offsets (IdxT = int32 when nnz < 2^31)
+//   colidx   int32[nnz]  binned source ids, each row in the caller's order
+//   inv_out  float[n]    1/outdeg, 0 for dangling vertices
+//   x[2], y[2] float[n]  rank and rank/outdeg (the quotient vector the gather
+//                        reads), double-buffered for the synchronous update
+//   seg_*                segments of heavy rows and their partial sums
+//   tiles               row ranges of the per-iteration row kernel
+//
+// Every array is allocated with kPad spare elements so that 16-byte vector
+// loads that start inside the array never leave the allocation.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "pagerank.h"
+
+namespace prk {
+
+constexpr int kBlock = 256;              // threads per block of the per-iteration kernels
+constexpr int kWarps = kBlock / 32;
+constexpr int kSegEdges = 2048;          // edges per segment of a heavy row
+constexpr int kDefaultHeavy = 1024;      // default heavy in-degree threshold
+constexpr int kPad = 64;                 // spare elements after every device array
+constexpr int kTileHeavy = -1;           // tile kind: epilogue of heavy rows
+constexpr int kTileZero = -2;            // tile kind: rows without in-edges
+constexpr int kMaxBins = 42;   // degree bins: 40 power-of-two classes + zero + spare
+
+// A tile of the row kernel: rows [row_begin, row_end) of one bin.  kind >= 0
+// is log2 of the lanes that gather one row together.
+struct Tile {
+    int32_t row_begin;
+    int32_t row_end;
+    int32_t kind;
+    int32_t pad;
+};
+
+// Per-solve device state.  Parameters are written by the host before a solve;
+// the running fields are written by the last block of each kernel that
+// reduces (see the "last block" pattern in pr_jacobi.cu).
+struct SolveState {
+    double d;          // damping
+    double tol;        // stop when the L1 change of an iteration is below this
+    double inv_n;      // 1/n
+    double t_sum;      // sum of the teleport vector (1 when uniform)
+    int32_t max_iter;
+    int32_t uniform_t;
+    double D;          // dangling mass of the current input vector
+    double resid;      // L1 change of the last iteration
+    double sum_x;      // sum of the final vector (finalise)
+    double scale;      // t_sum / sum_x (finalise)
+    double edge_visits;
+    int32_t iter;      // iterations completed
+    int32_t done;      // stopping test met or budget spent
+    uint32_t ticket;   // arrival counter of the last-block reductions
+    uint32_t error;    // device-side error bits
+    int32_t sweeps_max;
+    int32_t pad;
+};
+
+// Arguments of the per-iteration kernels (passed by value).
+struct IterArgs {
+    const void* rowptr;          // IdxT*
+    const int32_t* colidx;
+    const float* inv_out;
+    const float* teleport;       // binned order, NULL when uniform
+    const int32_t* seg_row;      // heavy row of each segment
+    const int32_t* seg_ptr;      // first segment of each heavy row, [n_heavy+1]
+    float* seg_sum;              // partial gather sum of each segment
+    const Tile* tiles;
+    int64_t n;
+    int32_t n_seg;
+    int32_t n_tiles;
+    SolveState* state;
+    double* slots;               // two doubles per block of the row kernel
+    cudaGraphConditionalHandle cond;
+    int32_t use_cond;            // 1: the kernel runs inside the while-graph
+    int32_t pad;
+};
+
+}  // namespace prk
+
+// The opaque graph object of the C ABI.
+struct pr_graph {
+    int device = 0;
+    int sm_count = 0;
+    int64_t n = 0;
+    int64_t nnz = 0;
+    bool idx64 = false;          // rowptr kept as int64
+    int heavy_degree = prk::kDefaultHeavy;
+    int ctas_per_sm = 0;         // 0 = from occupancy
+    bool use_graph = true;
+
+    void* rowptr = nullptr;
+    int32_t* colidx = nullptr;
+    float* inv_out = nullptr;
+    int32_t* order = nullptr;    // binned -> caller id
+    int32_t* rank = nullptr;     // caller -> binned id
+    float* x[2] = {nullptr, nullptr};
+    float* y[2] = {nullptr, nullptr};
+    float* teleport = nullptr;   // binned teleport (allocated on first use)
+    float* stage = nullptr;      // staging for host inputs/outputs (first use)
+    int32_t* seg_row = nullptr;
+    int32_t* seg_ptr = nullptr;
+    float* seg_sum = nullptr;
+    prk::Tile* tiles = nullptr;
+    prk::SolveState* state = nullptr;
+    double* slots = nullptr;
+    int slot_capacity = 0;       // blocks the slot array can serve
+    prk::SolveState* host_state = nullptr;  // pinned mirror
+    int32_t* host_flag = nullptr;           // pinned: done flag of the host-driven loop
+
+    // barrier-free solver (built on first use)
+    int32_t* nb_items = nullptr;     // Tile[]: work items of the persistent kernel
+    double* nb_slots = nullptr;      // latest sweep residual of each block
+    double* nb_scalars = nullptr;    // running non-dangling mass, counters
+    int32_t* nb_block_sweeps = nullptr;  // sweeps per block of the last launch (+ diagnostics)
+    int nb_grid = 0;
+    int64_t nb_items_count = 0;
+    std::vector<int64_t> nb_cta_edges;  // edges owned by each block (items dealt round-robin)
+    std::vector<int64_t> bin_start;     // first binned row of each degree bin (+ n)
+    std::vector<prk::Tile> host_tiles;  // copy of tiles
+
+    int64_t n_heavy = 0;
+    int64_t n_seg = 0;
+    int64_t n_tiles = 0;
+    int64_t n_dangling = 0;
+    int64_t n_zero_indeg = 0;
+    int64_t max_indeg = 0;
+    int64_t device_bytes = 0;
+    float setup_ms = 0.f;
+
+    // while-graph of the Jacobi loop, one per teleport kind (uniform / given)
+    cudaGraphExec_t loop_exec[2] = {nullptr, nullptr};
+    cudaStream_t capture_stream = nullptr;
+    cudaEvent_t ev_start = nullptr;
+    cudaEvent_t ev_stop = nullptr;
+};
+
+namespace prk {
+
+// Thread-local error message of the C ABI.
+void set_error(const std::string& msg);
+pr_status fail(pr_status s, const std::string& msg);
+pr_status cuda_fail(cudaError_t e, const char* what);
+
+// Grid size of the persistent per-iteration kernels for graph g.
+int row_grid(const pr_graph* g);
+int seg_grid(const pr_graph* g);
+
+// Device allocation recorded in g->device_bytes.
+cudaError_t dev_alloc(pr_graph* g, void** p, size_t bytes);
+
+bool is_device_pointer(const void* p);
+
+// Heavy in-degree threshold that the next pr_create_graph of this thread uses.
+int thread_heavy_degree();
+void set_thread_heavy_degree(int v);
+bool thread_force_index64();
+
+// Allocate the solver's vectors, state and slots once the layout exists.
+pr_status alloc_solver(pr_graph* g);
+
+// Solver pieces shared by the synchronous and the barrier-free drivers.
+IterArgs make_args(const pr_graph* g, bool uniform);
+int small_grid(const pr_graph* g);
+cudaError_t enqueue_iteration(const pr_graph* g, const IterArgs& a, int src, bool uniform,
+                              cudaStream_t s, int* launches);
+cudaError_t launch_segments(const pr_graph* g, const IterArgs& a, int src, cudaStream_t s, int* launches);
+pr_status stage_input(pr_graph* g, const float* src, int slot, cudaStream_t s, const float** out);
+pr_status ensure_stage(pr_graph* g);
+pr_status ensure_teleport(pr_graph* g);
+void launch_init(const pr_graph* g, const IterArgs& a, const float* t_dev, const float* x0_dev,
+                 cudaStream_t s);
+void launch_finalize(const pr_graph* g, const IterArgs& a, float* out, bool renormalise,
+                     cudaStream_t s, int* launches);
+
+pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_iter,
+                            const float* teleport, const float* x0, float* x_out, pr_info* info,
+                            cudaStream_t s);
+
+}  // namespace prk
+
+#define PRK_CHECK(call)                                                     \
+    do {                                                                    \
+        cudaError_t prk_e_ = (call);                                        \
+        if (prk_e_ != cudaSuccess) return prk::cuda_fail(prk_e_, #call);    \
+    } while (0)

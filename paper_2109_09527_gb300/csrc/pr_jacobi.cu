@@ -1,0 +1,506 @@
+// pr_jacobi.cu -- the synchronous (Jacobi) PageRank iteration on the device.
+//
+// One iteration k (Alg. 1, loop body) computes, from x = x_k and its quotient
+// vector y = x / outdeg (0 for dangling vertices):
+//
+//   s(v)   = sum_{e in row v} y[colidx[e]]                      (gather)
+//   x'(v)  = (1-d) t(v) + d (s(v) + D/n)                        (Eq. 1 + dangling share)
+//   y'(v)  = x'(v) / outdeg(v)                                  (next quotient)
+//   D'     = sum_{outdeg(v)=0} x'(v)                            (next dangling mass)
+//   r      = sum_v |x'(v) - x(v)|                               (L1 change)
+//
+// Two launches per iteration:
+//   k_heavy_segments  a warp per 2048-edge segment of every heavy row: streams
+//                     colidx with 16-byte loads, gathers y, writes the
+//                     segment's partial sum;
+//   k_rows            persistent blocks walk the row tiles round-robin:
+//                     heavy-row epilogues (sum of the segment partials),
+//                     light rows gathered by groups of 1..32 lanes sized to
+//                     the bin's degree class, rows without in-edges; the
+//                     epilogue writes x' and y' and accumulates r and D'.
+//                     The last block to finish (arrival ticket) reduces the
+//                     per-block partials in a fixed order, so D' and r are
+//                     bitwise reproducible, and applies the stopping test.
+//
+// The solve loop is a CUDA graph with a conditional while node whose body
+// holds two iterations (x0 -> x1, x1 -> x0); the last block clears the
+// condition when r < tol or the budget is spent.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include <cstring>
+
+#include "pr_tile.cuh"
+
+namespace prk {
+
+// --------------------------------------------------------- iteration kernels --
+
+template <typename IdxT>
+__global__ void __launch_bounds__(kBlock) k_heavy_segments(IterArgs a, const float* __restrict__ y) {
+    if (*(volatile int32_t*)&a.state->done) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * kBlock) >> 5;
+    for (int64_t s = warp; s < a.n_seg; s += nwarp) {
+        const int32_t h = a.seg_row[s];
+        const int64_t re = row_at<IdxT>(a.rowptr, h + 1);
+        const int64_t e0 = row_at<IdxT>(a.rowptr, h) + (s - a.seg_ptr[h]) * (int64_t)kSegEdges;
+        const int64_t e1 = min(e0 + (int64_t)kSegEdges, re);
+        const int64_t a0 = e0 & ~(int64_t)3;   // 16-byte aligned start
+        float acc = 0.f;
+        for (int64_t base = a0; base < e1; base += 512) {
+            int4 c[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int64_t p = base + 128 * j + 4 * lane;
+                c[j] = p < e1 ? ld_stream4(a.colidx + p) : make_int4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int64_t p = base + 128 * j + 4 * lane;
+                const float v0 = (p + 0 >= e0 && p + 0 < e1) ? __ldg(y + c[j].x) : 0.f;
+                const float v1 = (p + 1 >= e0 && p + 1 < e1) ? __ldg(y + c[j].y) : 0.f;
+                const float v2 = (p + 2 >= e0 && p + 2 < e1) ? __ldg(y + c[j].z) : 0.f;
+                const float v3 = (p + 3 >= e0 && p + 3 < e1) ? __ldg(y + c[j].w) : 0.f;
+                acc += (v0 + v1) + (v2 + v3);
+            }
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) a.seg_sum[s] = acc;
+    }
+}
+
+template <typename IdxT, bool kUniform>
+__global__ void __launch_bounds__(kBlock) k_rows(IterArgs a, const float* __restrict__ x_in,
+                                                 const float* __restrict__ y_in,
+                                                 float* __restrict__ x_out, float* __restrict__ y_out) {
+    SolveState* st = a.state;
+    if (*(volatile int32_t*)&st->done) {
+        // A skipped iteration inside the while-graph keeps the loop closed.
+        if (a.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0);
+        return;
+    }
+    const double d = st->d;
+    const double share = st->D * st->inv_n;   // D/n
+    RowCtx c;
+    c.d = (float)d;
+    c.one_m_d = (float)(1.0 - d);
+    c.d_share = (float)(d * share);
+    c.base = (float)((1.0 - d) * st->inv_n + d * share);
+    Acc acc;
+
+    for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+        const Tile tile = a.tiles[t];
+        if (tile.kind >= 0) {
+            process_light_tile<IdxT, kUniform, false>(tile, a.rowptr, a.colidx, a.inv_out, a.teleport,
+                                                       x_in, y_in, x_out, y_out, c, acc);
+        } else if (tile.kind == kTileZero) {
+            process_zero_tile<kUniform, false>(tile, a.inv_out, a.teleport, x_in, x_out, y_out, c, acc);
+        } else {  // heavy rows: sum of the segment partials
+            for (int64_t r = tile.row_begin + threadIdx.x; r < tile.row_end; r += kBlock) {
+                const float xo = ld_stream(x_in + r);
+                const float inv = ld_stream(a.inv_out + r);
+                const float tv = kUniform ? 0.f : ld_stream(a.teleport + r);
+                float s = 0.f;
+                const int32_t j1 = a.seg_ptr[r + 1];
+                for (int32_t j = a.seg_ptr[r]; j < j1; ++j) s += __ldcg(a.seg_sum + j);
+                row_update<kUniform, false>(r, s, xo, inv, tv, c, x_out, y_out, acc);
+            }
+        }
+    }
+
+    double R, Dn;
+    if (block_pair_to_grid((double)acc.r, acc.mass(), a.slots, &st->ticket, &R, &Dn) &&
+        threadIdx.x == 0) {
+        st->resid = R;
+        st->D = Dn;
+        st->iter += 1;
+        const int done = (R < st->tol) || (st->iter >= st->max_iter);
+        st->done = done;
+        st->ticket = 0;
+        if (done && a.use_cond) cudaGraphSetConditional(a.cond, 0);
+    }
+}
+
+// x = t or x0 (both in the caller's order), y = x/outdeg, D = dangling mass of
+// x, sum(t); resets the running state.
+__global__ void __launch_bounds__(kBlock) k_init(IterArgs a, const float* __restrict__ t_src,
+                                                 const float* __restrict__ x0_src,
+                                                 const int32_t* __restrict__ order,
+                                                 float* __restrict__ t_bin, float* __restrict__ x,
+                                                 float* __restrict__ y) {
+    SolveState* st = a.state;
+    const float tu = (float)st->inv_n;
+    double dsum = 0.0, tsum = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < a.n; i += stride) {
+        const int32_t o = order[i];
+        const float tv = t_src ? t_src[o] : tu;
+        if (t_src) t_bin[i] = tv;
+        const float xv = x0_src ? x0_src[o] : tv;
+        const float inv = a.inv_out[i];
+        x[i] = xv;
+        y[i] = xv * inv;
+        if (inv == 0.f) dsum += (double)xv;
+        tsum += (double)tv;
+    }
+    double D, T;
+    if (block_pair_to_grid(dsum, tsum, a.slots, &st->ticket, &D, &T) && threadIdx.x == 0) {
+        st->D = D;
+        st->t_sum = t_src ? T : 1.0;
+        st->iter = 0;
+        st->done = 0;
+        st->resid = INFINITY;
+        st->error = 0;
+        st->ticket = 0;
+    }
+}
+
+// Sum of the final vector (buffer x[iter & 1]) and the renormalising scale.
+__global__ void __launch_bounds__(kBlock) k_sum_x(IterArgs a, const float* __restrict__ x0,
+                                                  const float* __restrict__ x1) {
+    SolveState* st = a.state;
+    const float* x = (st->iter & 1) ? x1 : x0;
+    double s = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < a.n; i += stride) s += (double)x[i];
+    double S, unused;
+    if (block_pair_to_grid(s, 0.0, a.slots, &st->ticket, &S, &unused) && threadIdx.x == 0) {
+        st->sum_x = S;
+        st->scale = S > 0.0 ? st->t_sum / S : 1.0;
+        st->ticket = 0;
+    }
+}
+
+// out[v] = x[rank[v]] (* scale): back to the caller's vertex order.
+__global__ void __launch_bounds__(kBlock) k_unpermute(IterArgs a, const float* __restrict__ x0,
+                                                      const float* __restrict__ x1,
+                                                      const int32_t* __restrict__ rank,
+                                                      float* __restrict__ out, int apply_scale) {
+    const SolveState* st = a.state;
+    const float* x = (st->iter & 1) ? x1 : x0;
+    const float sc = apply_scale ? (float)st->scale : 1.0f;
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
+    for (int64_t v = (int64_t)blockIdx.x * kBlock + threadIdx.x; v < a.n; v += stride)
+        out[v] = x[rank[v]] * sc;
+}
+
+// ------------------------------------------------------------------ host --
+
+namespace {
+int g_occ_rows = 0;
+}  // namespace
+
+IterArgs make_args(const pr_graph* g, bool uniform) {
+    IterArgs a{};
+    a.rowptr = g->rowptr;
+    a.colidx = g->colidx;
+    a.inv_out = g->inv_out;
+    a.teleport = uniform ? nullptr : g->teleport;
+    a.seg_row = g->seg_row;
+    a.seg_ptr = g->seg_ptr;
+    a.seg_sum = g->seg_sum;
+    a.tiles = g->tiles;
+    a.n = g->n;
+    a.n_seg = (int32_t)g->n_seg;
+    a.n_tiles = (int32_t)g->n_tiles;
+    a.state = g->state;
+    a.slots = g->slots;
+    a.cond = 0;
+    a.use_cond = 0;
+    return a;
+}
+
+int small_grid(const pr_graph* g) {
+    int64_t blocks = (g->n + kBlock - 1) / kBlock;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)g->slot_capacity));
+}
+
+// Enqueue one iteration reading buffer `src` and writing buffer 1-src.
+template <typename IdxT>
+cudaError_t enqueue_iteration_t(const pr_graph* g, const IterArgs& a, int src, bool uniform,
+                                cudaStream_t s, int* launches) {
+    if (g->n_seg > 0) {
+        k_heavy_segments<IdxT><<<seg_grid(g), kBlock, 0, s>>>(a, g->y[src]);
+        ++*launches;
+    }
+    if (uniform)
+        k_rows<IdxT, true><<<row_grid(g), kBlock, 0, s>>>(a, g->x[src], g->y[src], g->x[1 - src], g->y[1 - src]);
+    else
+        k_rows<IdxT, false><<<row_grid(g), kBlock, 0, s>>>(a, g->x[src], g->y[src], g->x[1 - src], g->y[1 - src]);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_segments(const pr_graph* g, const IterArgs& a, int src, cudaStream_t s, int* launches) {
+    if (g->n_seg == 0) return cudaSuccess;
+    if (g->idx64) k_heavy_segments<int64_t><<<seg_grid(g), kBlock, 0, s>>>(a, g->y[src]);
+    else k_heavy_segments<int32_t><<<seg_grid(g), kBlock, 0, s>>>(a, g->y[src]);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue_iteration(const pr_graph* g, const IterArgs& a, int src, bool uniform,
+                              cudaStream_t s, int* launches) {
+    return g->idx64 ? enqueue_iteration_t<int64_t>(g, a, src, uniform, s, launches)
+                    : enqueue_iteration_t<int32_t>(g, a, src, uniform, s, launches);
+}
+
+// The while-graph: body = two iterations, x0 -> x1 and x1 -> x0.
+pr_status build_loop_graph(pr_graph* g, bool uniform) {
+    cudaGraph_t graph = nullptr;
+    PRK_CHECK(cudaGraphCreate(&graph, 0));
+    struct Guard {
+        cudaGraph_t gr;
+        ~Guard() { if (gr) cudaGraphDestroy(gr); }
+    } guard{graph};
+    cudaGraphConditionalHandle handle;
+    PRK_CHECK(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = handle;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    PRK_CHECK(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &p));
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    IterArgs a = make_args(g, uniform);
+    a.cond = handle;
+    a.use_cond = 1;
+    PRK_CHECK(cudaStreamBeginCaptureToGraph(g->capture_stream, body, nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeThreadLocal));
+    int launches = 0;
+    cudaError_t e1 = enqueue_iteration(g, a, 0, uniform, g->capture_stream, &launches);
+    cudaError_t e2 = cudaSuccess;
+    if (e1 == cudaSuccess) e2 = enqueue_iteration(g, a, 1, uniform, g->capture_stream, &launches);
+    cudaGraph_t captured = nullptr;
+    cudaError_t e3 = cudaStreamEndCapture(g->capture_stream, &captured);
+    PRK_CHECK(e1);
+    PRK_CHECK(e2);
+    PRK_CHECK(e3);
+    cudaGraphExec_t exec = nullptr;
+    PRK_CHECK(cudaGraphInstantiate(&exec, graph, 0));
+    g->loop_exec[uniform ? 0 : 1] = exec;
+    return PR_OK;
+}
+
+// Input vector from the caller: device pointers are used in place, host
+// memory is staged through g->stage + offset.
+pr_status stage_input(pr_graph* g, const float* src, int slot, cudaStream_t s, const float** out) {
+    *out = nullptr;
+    if (!src) return PR_OK;
+    if (is_device_pointer(src)) {
+        *out = src;
+        return PR_OK;
+    }
+    float* dst = g->stage + (size_t)slot * (size_t)(g->n + kPad);
+    PRK_CHECK(cudaMemcpyAsync(dst, src, (size_t)g->n * sizeof(float), cudaMemcpyHostToDevice, s));
+    *out = dst;
+    return PR_OK;
+}
+
+pr_status ensure_stage(pr_graph* g) {
+    if (g->stage) return PR_OK;
+    PRK_CHECK(dev_alloc(g, (void**)&g->stage, (size_t)3 * (size_t)(g->n + kPad) * sizeof(float)));
+    return PR_OK;
+}
+
+pr_status ensure_teleport(pr_graph* g) {
+    if (g->teleport) return PR_OK;
+    PRK_CHECK(dev_alloc(g, (void**)&g->teleport, (size_t)(g->n + kPad) * sizeof(float)));
+    return PR_OK;
+}
+
+void launch_init(const pr_graph* g, const IterArgs& a, const float* t_dev, const float* x0_dev,
+                 cudaStream_t s) {
+    k_init<<<small_grid(g), kBlock, 0, s>>>(a, t_dev, x0_dev, g->order, g->teleport, g->x[0], g->y[0]);
+}
+
+void launch_finalize(const pr_graph* g, const IterArgs& a, float* out, bool renormalise, cudaStream_t s,
+                     int* launches) {
+    if (renormalise) {
+        k_sum_x<<<small_grid(g), kBlock, 0, s>>>(a, g->x[0], g->x[1]);
+        ++*launches;
+    }
+    k_unpermute<<<small_grid(g), kBlock, 0, s>>>(a, g->x[0], g->x[1], g->rank, out, renormalise ? 1 : 0);
+    ++*launches;
+}
+
+int row_grid(const pr_graph* g) {
+    int per_sm = g->ctas_per_sm > 0 ? g->ctas_per_sm : std::max(1, std::min(g_occ_rows, 8));
+    int64_t blocks = (int64_t)g->sm_count * per_sm;
+    blocks = std::min<int64_t>(blocks, std::max<int64_t>(1, g->n_tiles));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)g->slot_capacity));
+}
+
+int seg_grid(const pr_graph* g) {
+    int64_t blocks = (g->n_seg + kWarps - 1) / kWarps;
+    int64_t cap = (int64_t)g->sm_count * 8;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, cap));
+}
+
+pr_status alloc_solver(pr_graph* g) {
+    const size_t vec = (size_t)(g->n + kPad) * sizeof(float);
+    for (int i = 0; i < 2; ++i) {
+        PRK_CHECK(dev_alloc(g, (void**)&g->x[i], vec));
+        PRK_CHECK(dev_alloc(g, (void**)&g->y[i], vec));
+        PRK_CHECK(cudaMemset(g->x[i], 0, vec));
+        PRK_CHECK(cudaMemset(g->y[i], 0, vec));
+    }
+    PRK_CHECK(dev_alloc(g, (void**)&g->state, sizeof(SolveState)));
+    PRK_CHECK(cudaMemset(g->state, 0, sizeof(SolveState)));
+    g->slot_capacity = g->sm_count * 8;
+    PRK_CHECK(dev_alloc(g, (void**)&g->slots, (size_t)g->slot_capacity * 2 * sizeof(double)));
+    PRK_CHECK(cudaMallocHost((void**)&g->host_state, sizeof(SolveState)));
+    memset(g->host_state, 0, sizeof(SolveState));
+    PRK_CHECK(cudaMallocHost((void**)&g->host_flag, 4 * sizeof(int32_t)));
+    memset(g->host_flag, 0, 4 * sizeof(int32_t));
+    PRK_CHECK(cudaStreamCreateWithFlags(&g->capture_stream, cudaStreamNonBlocking));
+    if (g_occ_rows == 0) {
+        int occ = 0;
+        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rows<int32_t, true>, kBlock, 0));
+        g_occ_rows = std::max(1, occ);
+    }
+    return PR_OK;
+}
+
+}  // namespace prk
+
+using namespace prk;
+
+namespace {
+
+pr_status check_solve_args(pr_graph* g, float damping, double tol, int32_t max_iter, float* x_out) {
+    if (!g) return fail(PR_ERR_INVALID_ARG, "graph is NULL");
+    if (!(damping >= 0.0f && damping < 1.0f)) return fail(PR_ERR_INVALID_ARG, "damping must be in [0, 1)");
+    if (!(tol > 0.0) || !std::isfinite(tol)) return fail(PR_ERR_INVALID_ARG, "tol must be a positive finite number");
+    if (max_iter < 1) return fail(PR_ERR_INVALID_ARG, "max_iter must be >= 1");
+    if (!x_out) return fail(PR_ERR_INVALID_ARG, "x_out is NULL");
+    return PR_OK;
+}
+
+// Shared body of pr_solve (Jacobi) and pr_iterate.
+pr_status run_jacobi(pr_graph* g, float damping, double tol, int32_t max_iter, const float* teleport,
+                     const float* x0, float* x_out, bool renormalise, bool allow_graph, pr_info* info,
+                     cudaStream_t s) {
+    pr_status rc = ensure_stage(g);
+    if (rc != PR_OK) return rc;
+    const float* t_dev = nullptr;
+    const float* x0_dev = nullptr;
+    if ((rc = stage_input(g, teleport, 0, s, &t_dev)) != PR_OK) return rc;
+    if ((rc = stage_input(g, x0, 1, s, &x0_dev)) != PR_OK) return rc;
+    const bool uniform = teleport == nullptr;
+    if (!uniform && (rc = ensure_teleport(g)) != PR_OK) return rc;
+    const bool out_dev = is_device_pointer(x_out);
+    float* out = out_dev ? x_out : g->stage + (size_t)2 * (size_t)(g->n + kPad);
+
+    SolveState* hs = g->host_state;
+    memset(hs, 0, sizeof(SolveState));
+    hs->d = (double)damping;
+    hs->tol = tol;
+    hs->inv_n = 1.0 / (double)g->n;
+    hs->t_sum = 1.0;
+    hs->max_iter = max_iter;
+    hs->uniform_t = uniform ? 1 : 0;
+    PRK_CHECK(cudaEventRecord(g->ev_start, s));
+    PRK_CHECK(cudaMemcpyAsync(g->state, hs, sizeof(SolveState), cudaMemcpyHostToDevice, s));
+
+    IterArgs a = make_args(g, uniform);
+    int launches = 0;
+    launch_init(g, a, t_dev, x0_dev, s);
+    ++launches;
+    PRK_CHECK(cudaGetLastError());
+
+    if (allow_graph && g->use_graph) {
+        const int kind = uniform ? 0 : 1;
+        if (!g->loop_exec[kind] && (rc = build_loop_graph(g, uniform)) != PR_OK) return rc;
+        PRK_CHECK(cudaGraphLaunch(g->loop_exec[kind], s));
+        ++launches;
+    } else {
+        // Host-driven loop: enqueue chunks of iterations and read the done
+        // flag of the chunk before last, so the device is never idle.
+        const int chunk = 8;
+        int32_t launched = 0;
+        cudaEvent_t ev[2];
+        PRK_CHECK(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+        PRK_CHECK(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+        int pending = -1;
+        pr_status loop_rc = PR_OK;
+        while (launched < max_iter) {
+            const int c = std::min<int32_t>(chunk, max_iter - launched);
+            for (int i = 0; i < c && loop_rc == PR_OK; ++i) {
+                cudaError_t e = enqueue_iteration(g, a, (launched + i) & 1, uniform, s, &launches);
+                if (e != cudaSuccess) loop_rc = cuda_fail(e, "iteration launch");
+            }
+            launched += c;
+            if (loop_rc != PR_OK) break;
+            const int slot = (launched / chunk) & 1;
+            cudaError_t e = cudaMemcpyAsync(&g->host_flag[slot], &g->state->done, sizeof(int32_t),
+                                            cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[slot], s);
+            if (e != cudaSuccess) { loop_rc = cuda_fail(e, "loop bookkeeping"); break; }
+            if (pending >= 0) {
+                e = cudaEventSynchronize(ev[pending]);
+                if (e != cudaSuccess) { loop_rc = cuda_fail(e, "cudaEventSynchronize"); break; }
+                if (*(volatile int32_t*)&g->host_flag[pending]) break;
+            }
+            pending = slot;
+        }
+        cudaEventSynchronize(ev[0]);
+        cudaEventSynchronize(ev[1]);
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+        if (loop_rc != PR_OK) return loop_rc;
+    }
+
+    launch_finalize(g, a, out, renormalise, s, &launches);
+    PRK_CHECK(cudaGetLastError());
+    PRK_CHECK(cudaEventRecord(g->ev_stop, s));
+    if (!out_dev)
+        PRK_CHECK(cudaMemcpyAsync(x_out, out, (size_t)g->n * sizeof(float), cudaMemcpyDeviceToHost, s));
+    PRK_CHECK(cudaMemcpyAsync(hs, g->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+    PRK_CHECK(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    PRK_CHECK(cudaEventElapsedTime(&ms, g->ev_start, g->ev_stop));
+    const bool converged = hs->resid < tol;
+    if (info) {
+        info->iterations = hs->iter;
+        info->converged = converged ? 1 : 0;
+        info->residual_l1 = hs->resid;
+        info->sum_x = renormalise ? hs->sum_x : 0.0;
+        info->dangling_mass = hs->D;
+        info->edge_visits = (double)hs->iter * (double)g->nnz;
+        info->ms_device = ms;
+        info->launches = launches;
+    }
+    return converged ? PR_OK : PR_NOT_CONVERGED;
+}
+
+}  // namespace
+
+extern "C" pr_status pr_solve(pr_graph* g, float damping, double tol, int32_t max_iter, int variant,
+                              const float* teleport, const float* x0, float* x_out, pr_info* info,
+                              void* stream) {
+    pr_status rc = check_solve_args(g, damping, tol, max_iter, x_out);
+    if (rc != PR_OK) return rc;
+    if (variant == PR_JACOBI)
+        return run_jacobi(g, damping, tol, max_iter, teleport, x0, x_out, true, true, info,
+                          (cudaStream_t)stream);
+    if (variant == PR_NONBLOCKING)
+        return solve_nonblocking(g, damping, tol, max_iter, teleport, x0, x_out, info,
+                                 (cudaStream_t)stream);
+    return fail(PR_ERR_INVALID_ARG, "variant must be PR_JACOBI or PR_NONBLOCKING");
+}
+
+extern "C" pr_status pr_iterate(pr_graph* g, float damping, const float* teleport, const float* x_in,
+                                int32_t n_iter, float* x_out, pr_info* info, void* stream) {
+    if (!x_in) return fail(PR_ERR_INVALID_ARG, "x_in is NULL");
+    pr_status rc = check_solve_args(g, damping, 1.0, n_iter, x_out);
+    if (rc != PR_OK) return rc;
+    // tol 0 is never met: exactly n_iter updates, no early stop
+    rc = run_jacobi(g, damping, 0.0, n_iter, teleport, x_in, x_out, false, false, info,
+                    (cudaStream_t)stream);
+    return rc == PR_NOT_CONVERGED ? PR_OK : rc;
+}

@@ -1,0 +1,292 @@
+// pr_tile.cuh -- device code shared by the synchronous and the barrier-free
+// kernels: memory-access policies, the per-row update (epilogue) and the
+// gather over a tile of light rows.
+//
+// Two memory policies:
+//   Jacobi (kInPlace = false): the kernel reads x_k, y_k and writes x_{k+1},
+//     y_{k+1} in other buffers, so the inputs are read-only for the whole
+//     launch and go through the non-coherent path (y gathers may hit L1).
+//   In place (kInPlace = true): y is read by every block while its owner
+//     rewrites it (the read-write races of No-Sync, Alg. 3).  Those accesses
+//     are relaxed gpu-scope atomics -- defined behaviour under the PTX memory
+//     model, served by L2.  x, which only its owner touches, uses the same
+//     relaxed accesses (one per row per sweep), so no cached copy can be stale.
+#pragma once
+
+#include "pr_common.cuh"
+
+namespace prk {
+
+__device__ __forceinline__ float ld_stream(const float* p) {
+    float v;
+    asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ int32_t ld_stream(const int32_t* p) {
+    int32_t v;
+    asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ int4 ld_stream4(const int32_t* p) {
+    int4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.s32 {%0, %1, %2, %3}, [%4];"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ void st_stream(float* p, float v) {
+    asm volatile("st.global.cs.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+
+__device__ __forceinline__ float ld_relaxed(const float* p) {
+    float v;
+    asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(float* p, float v) {
+    asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v));
+}
+
+__device__ __forceinline__ double ld_relaxed(const double* p) {
+    double v;
+    asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(double* p, double v) {
+    asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v));
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename IdxT>
+__device__ __forceinline__ int64_t row_at(const void* rowptr, int64_t r) {
+    return (int64_t)__ldg((const IdxT*)rowptr + r);
+}
+
+template <bool kInPlace>
+struct Mem;
+
+template <>
+struct Mem<false> {
+    static __device__ __forceinline__ float gather(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ float load_x(const float* p) { return ld_stream(p); }
+    static __device__ __forceinline__ void store_x(float* p, float v) { st_stream(p, v); }
+    static __device__ __forceinline__ void store_y(float* p, float v) { st_stream(p, v); }
+};
+
+template <>
+struct Mem<true> {
+    static __device__ __forceinline__ float gather(const float* p) { return ld_relaxed(p); }
+    static __device__ __forceinline__ float load_x(const float* p) { return ld_relaxed(p); }
+    static __device__ __forceinline__ void store_x(float* p, float v) { st_relaxed(p, v); }
+    static __device__ __forceinline__ void store_y(float* p, float v) { st_relaxed(p, v); }
+};
+
+// Constants of the update x' = (1-d) t + d (s + share), share = dangling
+// share of this iteration (D/n, or (T - S)/n in the barrier-free form).
+struct RowCtx {
+    float d;          // damping
+    float one_m_d;    // 1 - d
+    float d_share;    // d * share
+    float base;       // (1-d)/n + d * share (uniform teleport)
+};
+
+// Per-thread accumulators.  r: L1 change.  (m, c): Kahan sum of the mass the
+// kernel tracks -- the new dangling mass (synchronous form) or the change of
+// the non-dangling mass (in-place form).
+struct Acc {
+    float r = 0.f;
+    float m = 0.f;
+    float c = 0.f;
+    float dd = 0.f;   // in-place form: change of the dangling mass (diagnostic form only)
+    __device__ __forceinline__ void kahan(float v) {
+        const float yk = v - c;
+        const float tk = m + yk;
+        c = (tk - m) - yk;
+        m = tk;
+    }
+    __device__ __forceinline__ double mass() const { return (double)m - (double)c; }
+};
+
+template <bool kUniform, bool kInPlace>
+__device__ __forceinline__ void row_update(int64_t r, float s, float xo, float inv, float tv,
+                                           const RowCtx& c, float* x_out, float* y_out, Acc& acc) {
+    const float base = kUniform ? c.base : fmaf(c.one_m_d, tv, c.d_share);
+    const float xn = fmaf(c.d, s, base);
+    Mem<kInPlace>::store_x(x_out + r, xn);
+    Mem<kInPlace>::store_y(y_out + r, xn * inv);
+    acc.r += fabsf(xn - xo);
+    if (kInPlace) {
+        if (inv != 0.f) acc.kahan(xn - xo);
+        else acc.dd += xn - xo;
+    } else {
+        if (inv == 0.f) acc.kahan(xn);
+    }
+}
+
+// Rows without in-edges: thread per row, s = 0.
+template <bool kUniform, bool kInPlace>
+__device__ __forceinline__ void process_zero_tile(const Tile& tile, const float* inv_out,
+                                                  const float* teleport, const float* x_in,
+                                                  float* x_out, float* y_out, const RowCtx& c,
+                                                  Acc& acc) {
+    for (int64_t r = tile.row_begin + threadIdx.x; r < tile.row_end; r += kBlock) {
+        const float tv = kUniform ? 0.f : ld_stream(teleport + r);
+        row_update<kUniform, kInPlace>(r, 0.f, Mem<kInPlace>::load_x(x_in + r), ld_stream(inv_out + r),
+                                       tv, c, x_out, y_out, acc);
+    }
+}
+
+// Light rows of one degree class: groups of g = 2^tile.kind lanes gather one
+// row each (coalesced colidx reads within the group, up to four gathers in
+// flight per lane), reduce with shuffles, and the group's first lane updates
+// the row.
+template <typename IdxT, bool kUniform, bool kInPlace>
+__device__ __forceinline__ void process_light_tile(const Tile& tile, const void* rowptr,
+                                                   const int32_t* colidx, const float* inv_out,
+                                                   const float* teleport, const float* x_in,
+                                                   const float* y_in, float* x_out, float* y_out,
+                                                   const RowCtx& c, Acc& acc) {
+    const int lg = tile.kind;
+    const int g = 1 << lg;
+    const int rpp = kBlock >> lg;  // rows per pass
+    const int grp = threadIdx.x >> lg;
+    const int gl = threadIdx.x & (g - 1);
+    for (int64_t r0 = tile.row_begin; r0 < tile.row_end; r0 += rpp) {
+        const int64_t r = r0 + grp;
+        const bool active = r < tile.row_end;
+        int64_t b = 0, e = 0;
+        float xo = 0.f, inv = 0.f, tv = 0.f;
+        if (active) {
+            b = row_at<IdxT>(rowptr, r);
+            e = row_at<IdxT>(rowptr, r + 1);
+            if (gl == 0) {
+                xo = Mem<kInPlace>::load_x(x_in + r);
+                inv = ld_stream(inv_out + r);
+                if (!kUniform) tv = ld_stream(teleport + r);
+            }
+        }
+        float s = 0.f;
+        for (int64_t k = b + gl; k < e; k += 4 * g) {
+            const int32_t c0 = ld_stream(colidx + k);
+            const int32_t c1 = k + g < e ? ld_stream(colidx + k + g) : -1;
+            const int32_t c2 = k + 2 * g < e ? ld_stream(colidx + k + 2 * g) : -1;
+            const int32_t c3 = k + 3 * g < e ? ld_stream(colidx + k + 3 * g) : -1;
+            const float v0 = Mem<kInPlace>::gather(y_in + c0);
+            const float v1 = c1 >= 0 ? Mem<kInPlace>::gather(y_in + c1) : 0.f;
+            const float v2 = c2 >= 0 ? Mem<kInPlace>::gather(y_in + c2) : 0.f;
+            const float v3 = c3 >= 0 ? Mem<kInPlace>::gather(y_in + c3) : 0.f;
+            s += (v0 + v1) + (v2 + v3);
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1)
+            if (o < g) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (active && gl == 0) row_update<kUniform, kInPlace>(r, s, xo, inv, tv, c, x_out, y_out, acc);
+    }
+}
+
+// Sum (a, b) over the block and write the block's pair to
+// slots[2*blockIdx.x]; returns true in every thread of the block that
+// arrives last.  That block then holds the grid totals -- summed over the
+// slots in slot order, so the result does not depend on arrival order -- in
+// (*ta, *tb) of every thread.
+__device__ __forceinline__ bool block_pair_to_grid(double a, double b, double* slots, uint32_t* ticket,
+                                                   double* ta, double* tb) {
+    __shared__ double sa[kWarps], sb[kWarps];
+    __shared__ int last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (lane == 0) {
+        sa[warp] = a;
+        sb[warp] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double A = 0.0, B = 0.0;
+        for (int w = 0; w < kWarps; ++w) {
+            A += sa[w];
+            B += sb[w];
+        }
+        slots[2 * blockIdx.x] = A;
+        slots[2 * blockIdx.x + 1] = B;
+        __threadfence();
+        const uint32_t t = atomicAdd(ticket, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double A = 0.0, B = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += kBlock) {
+        A += __ldcg(slots + 2 * i);
+        B += __ldcg(slots + 2 * i + 1);
+    }
+    A = warp_sum(A);
+    B = warp_sum(B);
+    __syncthreads();
+    if (lane == 0) {
+        sa[warp] = A;
+        sb[warp] = B;
+    }
+    __syncthreads();
+    A = 0.0;
+    B = 0.0;
+    for (int w = 0; w < kWarps; ++w) {
+        A += sa[w];
+        B += sb[w];
+    }
+    *ta = A;
+    *tb = B;
+    return true;
+}
+
+// Block-wide sum of two doubles; every thread receives the totals.
+__device__ __forceinline__ void block_sum2(double& a, double& b) {
+    __shared__ double sa[kWarps], sb[kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    __syncthreads();
+    if (lane == 0) {
+        sa[warp] = a;
+        sb[warp] = b;
+    }
+    __syncthreads();
+    a = 0.0;
+    b = 0.0;
+    for (int w = 0; w < kWarps; ++w) {
+        a += sa[w];
+        b += sb[w];
+    }
+}
+
+// Block-wide sum of a float; every thread receives the total.
+__device__ __forceinline__ float block_sum(float v) {
+    __shared__ float sv[kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sv[warp] = v;
+    __syncthreads();
+    float t = 0.f;
+    for (int w = 0; w < kWarps; ++w) t += sv[w];
+    return t;
+}
+
+}  // namespace prk

@@ -1,0 +1,91 @@
+"""The C-ABI library builds for sm_103a, loads, and exports exactly what include/pagerank.h
+declares; host-side argument checks return statuses (no GPU needed, no compute calls)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2109_09527_gb300 as pr
+from paper_2109_09527_gb300 import _build
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                      "pagerank.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    return set(re.findall(r"PR_API\s+[\w\s\*]+?\b(pr_\w+)\s*\(", src))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    assert {"pr_create_graph", "pr_destroy_graph", "pr_solve", "pr_iterate", "pr_status_string",
+            "pr_last_error", "pr_graph_get_stats", "pr_set_option"} <= names
+
+
+def test_library_exports_every_declared_symbol():
+    path = _build.build()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    assert declared_functions() <= exported
+    # nothing else leaks out of the library
+    assert {s for s in exported if not s.startswith("_")} == declared_functions()
+    lib = pr.load()
+    for name in declared_functions():
+        assert hasattr(lib, name)
+        assert name in pr.SIGNATURES
+
+
+def test_status_strings_and_no_error_yet():
+    assert pr.pr_status_string(pr.PR_OK) == "PR_OK"
+    assert pr.pr_status_string(pr.PR_NOT_CONVERGED) == "PR_NOT_CONVERGED"
+    assert pr.pr_status_string(99) == "PR_UNKNOWN_STATUS"
+
+
+def test_argument_errors_return_status_without_a_gpu():
+    lib = pr.load()
+    out = ctypes.c_void_p()
+    # out == NULL, n out of range, nnz < 0, missing arrays, bad layout: rejected before any CUDA call
+    assert lib.pr_create_graph(4, 0, None, 0, None, None, 0, None, None) == pr.PR_ERR_INVALID_ARG
+    assert lib.pr_create_graph(0, 0, None, 0, None, None, 0, None, ctypes.byref(out)) == pr.PR_ERR_INVALID_ARG
+    rp = (ctypes.c_int32 * 3)(0, 1, 2)
+    assert lib.pr_create_graph(2, -1, rp, 0, None, None, 0, None, ctypes.byref(out)) == pr.PR_ERR_INVALID_ARG
+    assert lib.pr_create_graph(2, 2, None, 0, None, None, 0, None, ctypes.byref(out)) == pr.PR_ERR_INVALID_ARG
+    assert lib.pr_create_graph(2, 2, rp, 0, None, None, 0, None, ctypes.byref(out)) == pr.PR_ERR_INVALID_ARG
+    ci = (ctypes.c_int32 * 2)(1, 0)
+    assert lib.pr_create_graph(2, 2, rp, 0, ci, None, 7, None, ctypes.byref(out)) == pr.PR_ERR_INVALID_ARG
+    assert lib.pr_create_graph(2, 2, rp, 0, ci, None, pr.PR_OUT_CSR, None,
+                               ctypes.byref(out)) == pr.PR_ERR_UNSUPPORTED
+    w = (ctypes.c_float * 2)(1.0, 1.0)
+    assert lib.pr_create_graph(2, 2, rp, 0, ci, w, 0, None, ctypes.byref(out)) == pr.PR_ERR_UNSUPPORTED
+    assert lib.pr_create_graph(2, 1 << 31, rp, 0, ci, None, 0, None,
+                               ctypes.byref(out)) == pr.PR_ERR_INVALID_ARG
+    assert out.value is None
+    assert "layout" in pr.pr_last_error() or "weights" in pr.pr_last_error() or pr.pr_last_error()
+    # solve on a NULL graph
+    info = pr.pr_info()
+    x = (ctypes.c_float * 2)()
+    assert lib.pr_solve(None, 0.85, 1e-6, 10, 0, None, None, x, ctypes.byref(info), None) == pr.PR_ERR_INVALID_ARG
+    assert lib.pr_iterate(None, 0.85, None, x, 1, x, ctypes.byref(info), None) == pr.PR_ERR_INVALID_ARG
+    assert lib.pr_destroy_graph(None) == pr.PR_OK
+    assert lib.pr_graph_get_stats(None, None) == pr.PR_ERR_INVALID_ARG
+
+
+def test_options_validate_host_side():
+    with pytest.raises(pr.PageRankError):
+        pr.set_heavy_degree(100)          # not a power of two
+    with pytest.raises(pr.PageRankError):
+        pr.set_heavy_degree(32)           # too small
+    pr.set_heavy_degree(1024)
+    with pytest.raises(pr.PageRankError):
+        pr.pr_set_option(None, 99, 1)
+    with pytest.raises(pr.PageRankError):
+        pr.pr_set_option(None, pr.PR_OPT_USE_GRAPH, 1)   # needs a graph
+    pr.pr_set_option(None, pr.PR_OPT_INDEX64, 0)
+
+
+def test_build_targets_sm103a_only():
+    assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -1,0 +1,260 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (FP32 ranks against FP64):
+  * matching mode -- GPU Jacobi and the oracle's Alg. 1 after the same number of
+    iterations from the same start: L1 <= 1e-6 and per-vertex relative error
+    <= 1e-4 (the target stated for FP32 ranks);
+  * one synchronous update from the same input: L1 <= 1e-6, relative <= 1e-4;
+  * any variant against the fixed point x*: ||x - x*||_1 <= r/(1-d) + 2e-7,
+    where r is the L1 change of the verifying synchronous update reported by
+    the library (contraction bound of Eq. 1 with factor d) and 2e-7 covers the
+    FP32 rounding of x itself (about 2^-24 of sum(x) per rounding).
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pr = pytest.importorskip("paper_2109_09527_gb300")
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+D = 0.85
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    yield
+
+
+def l1(a, b):
+    return float(np.abs(np.asarray(a, np.float64) - np.asarray(b, np.float64)).sum())
+
+
+def max_rel(a, b):
+    b = np.asarray(b, np.float64)
+    return float(np.max(np.abs(np.asarray(a, np.float64) - b) / np.abs(b)))
+
+
+def solve(rp, ci, **kw):
+    with pr.Graph(rp, ci) as g:
+        x, info = g.solve(**kw)
+        return x, info, g.stats()
+
+
+def matching(rp, ci, x, info, t=None, x0=None):
+    xo, it, _ = oracle.pagerank_jacobi(rp, ci, d=D, tol=0, max_iter=info.iterations, t=t, x0=x0)
+    return xo
+
+
+# ------------------------------------------------------------------ fixtures --
+
+@pytest.mark.parametrize("n", [1, 2, 5, 64, 300])
+def test_closed_form_graphs(n):
+    L = n - 1
+    cases = [(gg.cycle, np.full(n, 1.0 / n)), (gg.complete, np.full(n, 1.0 / n)),
+             (gg.empty, np.full(n, 1.0 / n))]
+    if n >= 2:
+        cases += [(gg.in_star, np.array([(1 + D * L) / (n + D * L)] + [1.0 / (n + D * L)] * L)),
+                  (gg.out_star, np.array([1.0 / (n + D)] + [(L + D) / (L * (n + D))] * L))]
+    for build, expect in cases:
+        if n == 1 and build is not gg.empty:
+            continue
+        rp, ci = build(n)
+        for variant in ("jacobi", "nonblocking"):
+            x, info, _ = solve(rp, ci, tol=1e-6, max_iter=500, variant=variant)
+            assert info.converged == 1, (build.__name__, variant)
+            np.testing.assert_allclose(x, expect, rtol=2e-5, err_msg=f"{build.__name__} {variant}")
+
+
+# ---------------------------------------------------- R-MAT, matching mode --
+
+@pytest.mark.parametrize("scale,heavy,index64", [(10, 1024, 0), (12, 64, 0), (14, 1024, 0),
+                                                 (14, 64, 1), (12, 1 << 20, 0)])
+def test_rmat_jacobi_matches_oracle(scale, heavy, index64):
+    """Each layout path in turn: default bins; heavy threshold 64 (segments for most edges);
+    64-bit row offsets on device; threshold 2^20 (no heavy rows at all)."""
+    rp, ci = gg.rmat(scale, seed=scale)
+    pr.set_heavy_degree(heavy)
+    pr.pr_set_option(None, pr.PR_OPT_INDEX64, index64)
+    try:
+        x, info, st = solve(rp, ci, tol=1e-6, max_iter=200)
+    finally:
+        pr.set_heavy_degree(1024)
+        pr.pr_set_option(None, pr.PR_OPT_INDEX64, 0)
+    assert st["rowptr_bytes"] == (8 if index64 else 4)
+    if heavy == 64:
+        assert st["n_heavy"] > 0 and st["n_segments"] > 0
+    if heavy == 1 << 20:
+        assert st["n_heavy"] == 0
+    xo = matching(rp, ci, x, info)
+    _, it_oracle, _ = oracle.pagerank_jacobi(rp, ci, d=D, tol=1e-6, max_iter=200)
+    assert abs(info.iterations - it_oracle) <= 1
+    assert info.converged == 1 and info.residual_l1 < 1e-6
+    assert l1(x, xo) <= 1e-6
+    assert max_rel(x, xo) <= 1e-4
+    assert abs(np.sum(x, dtype=np.float64) - 1.0) < 1e-5
+
+
+def test_er_dangling_jacobi_matches_oracle():
+    rp, ci = gg.er_dangling(20000, seed=3)
+    x, info, st = solve(rp, ci, tol=1e-6, max_iter=200)
+    assert st["n_dangling"] == 4000
+    xo = matching(rp, ci, x, info)
+    assert l1(x, xo) <= 1e-6 and max_rel(x, xo) <= 1e-4
+
+
+def test_small_config_scale16_budget():
+    """R-MAT scale 16, tol 1e-10 or 200 iterations: 1e-10 is below the FP32 floor of the
+    L1 change, so the budget ends the run; the vector still matches the oracle's 200th
+    iterate."""
+    rp, ci = gg.rmat(16, seed=1)
+    with pr.Graph(rp, ci) as g:
+        x = np.empty(rp.size - 1, np.float32)
+        status, info = pr.pr_solve(g.handle, D, 1e-10, 200, pr.PR_JACOBI, None, None, x)
+    assert status in (pr.PR_NOT_CONVERGED, pr.PR_OK)
+    if status == pr.PR_NOT_CONVERGED:
+        assert info.iterations == 200 and info.converged == 0
+    assert np.isfinite(info.residual_l1) and info.residual_l1 < 1e-6
+    xo = matching(rp, ci, x, info)
+    assert l1(x, xo) <= 1e-6 and max_rel(x, xo) <= 1e-4
+
+
+# ------------------------------------------------------------ one update --
+
+@pytest.mark.parametrize("scale,heavy", [(13, 1024), (13, 64)])
+def test_one_synchronous_update(scale, heavy):
+    rp, ci = gg.rmat(scale, seed=21)
+    n = rp.size - 1
+    x_in = gg.uniform(5, 1, n) + 0.1
+    x_in = (x_in / x_in.sum()).astype(np.float32)
+    t = gg.uniform(6, 1, n).astype(np.float32)
+    t /= t.sum()
+    pr.set_heavy_degree(heavy)
+    try:
+        with pr.Graph(rp, ci) as g:
+            for tt in (None, t):
+                x1, info = g.iterate(x_in, n_iter=1, teleport=tt)
+                xo, Dm, l1o, _ = oracle.jacobi_step(rp, ci, x_in.astype(np.float64), d=D,
+                                                    t=None if tt is None else tt.astype(np.float64))
+                assert l1(x1, xo) <= 1e-6 and max_rel(x1, xo) <= 1e-4
+                assert info.residual_l1 == pytest.approx(l1o, rel=1e-3, abs=1e-9)
+                assert info.dangling_mass == pytest.approx(
+                    oracle.dangling_mass(rp, ci, xo), rel=1e-5)
+            # three updates equal three oracle steps
+            x3, _ = g.iterate(x_in, n_iter=3)
+            xo3, _, _ = oracle.pagerank_jacobi(rp, ci, d=D, tol=0, max_iter=3, x0=x_in)
+            assert l1(x3, xo3) <= 1e-6
+    finally:
+        pr.set_heavy_degree(1024)
+
+
+def test_personalised_teleport_and_warm_start():
+    rp, ci = gg.rmat(12, seed=8)
+    n = rp.size - 1
+    t = np.zeros(n, np.float32)
+    seeds = gg.permutation(8, 3, n)[:8]
+    t[seeds] = 1.0 / 8
+    x, info, _ = solve(rp, ci, tol=1e-7, max_iter=300, teleport=t)
+    xo = matching(rp, ci, x, info, t=t.astype(np.float64))
+    assert l1(x, xo) <= 1e-6
+    assert abs(np.sum(x, dtype=np.float64) - 1.0) < 1e-5
+    # warm start from the answer: converges at once
+    x2, info2, _ = solve(rp, ci, tol=1e-6, max_iter=300, teleport=t, x0=x)
+    assert info2.iterations <= 3 and l1(x2, x) < 1e-6
+
+
+def test_host_and_device_buffers_agree_and_runs_are_bitwise_reproducible():
+    rp, ci = gg.rmat(13, seed=4)
+    n = rp.size - 1
+    dev = torch.device("cuda:0")
+    with pr.Graph(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)) as g:
+        out_d = torch.empty(n, dtype=torch.float32, device=dev)
+        g.solve(tol=1e-6, out=out_d)
+        torch.cuda.synchronize()
+        out_h, _ = g.solve(tol=1e-6)
+        out_h2, _ = g.solve(tol=1e-6)
+        g.set_option(pr.PR_OPT_USE_GRAPH, 0)
+        out_h3, info3 = g.solve(tol=1e-6)
+    assert np.array_equal(out_d.cpu().numpy(), out_h)
+    assert np.array_equal(out_h, out_h2)
+    assert np.array_equal(out_h, out_h3)          # host-driven loop, same iterates
+
+
+# ---------------------------------------------------------- barrier-free --
+
+@pytest.mark.parametrize("build", ["rmat12", "rmat14_heavy64", "er"])
+def test_nonblocking_reaches_the_fixed_point(build):
+    if build == "er":
+        rp, ci = gg.er_dangling(30000, seed=9)
+    elif build == "rmat12":
+        rp, ci = gg.rmat(12, seed=2)
+    else:
+        rp, ci = gg.rmat(14, seed=3)
+        pr.set_heavy_degree(64)
+    try:
+        xstar, _, _ = oracle.fixed_point(rp, ci, d=D)
+        for tol in (1e-6, 2e-7):
+            x, info, _ = solve(rp, ci, tol=tol, max_iter=500, variant="nonblocking")
+            assert info.converged == 1 and info.residual_l1 < tol
+            err = l1(x, xstar)
+            assert err <= info.residual_l1 / (1 - D) + 2e-7, (tol, err, info.residual_l1)
+            assert max_rel(x, xstar) <= 1e-4
+            xj, infoj, _ = solve(rp, ci, tol=tol, max_iter=500, variant="jacobi")
+            assert l1(x, xj) <= (info.residual_l1 + infoj.residual_l1) / (1 - D) + 4e-7
+    finally:
+        pr.set_heavy_degree(1024)
+
+
+def test_nonblocking_budget_of_one_sweep_returns():
+    rp, ci = gg.rmat(12, seed=5)
+    with pr.Graph(rp, ci) as g:
+        x = np.empty(rp.size - 1, np.float32)
+        status, info = pr.pr_solve(g.handle, D, 1e-9, 1, pr.PR_NONBLOCKING, None, None, x)
+    assert status == pr.PR_NOT_CONVERGED and info.converged == 0
+    assert np.isfinite(info.residual_l1) and np.all(np.isfinite(x))
+
+
+# ------------------------------------------------------------- boundary --
+
+def test_invalid_graphs_are_rejected():
+    ci = np.array([1, 0], np.int32)
+    for rp, why in [(np.array([0, 2, 1], np.int64), "decreasing"),
+                    (np.array([1, 1, 2], np.int64), "rowptr[0]"),
+                    (np.array([0, 1, 2], np.int64), None)]:
+        if why is None:
+            bad = np.array([1, 5], np.int32)   # colidx out of range
+            with pytest.raises(pr.PageRankError) as e:
+                pr.Graph(rp, bad)
+        else:
+            with pytest.raises(pr.PageRankError) as e:
+                pr.Graph(rp, ci)
+        assert e.value.status == pr.PR_ERR_INVALID_GRAPH
+    rp = np.array([0, 1, 3], np.int64)   # rowptr[n] != nnz
+    with pytest.raises(pr.PageRankError) as e:
+        pr.pr_create_graph(2, 2, rp, True, ci)
+    assert e.value.status == pr.PR_ERR_INVALID_GRAPH
+
+
+def test_invalid_solve_arguments():
+    rp, ci = gg.cycle(8)
+    with pr.Graph(rp, ci) as g:
+        x = np.empty(8, np.float32)
+        for damping, tol, it, var in [(1.0, 1e-6, 10, 0), (-0.1, 1e-6, 10, 0), (0.85, 0.0, 10, 0),
+                                      (0.85, 1e-6, 0, 0), (0.85, 1e-6, 10, 7)]:
+            with pytest.raises(pr.PageRankError) as e:
+                pr.pr_solve(g.handle, damping, tol, it, var, None, None, x)
+            assert e.value.status == pr.PR_ERR_INVALID_ARG
+        status, info = pr.pr_solve(g.handle, 0.85, 1e-12, 1, pr.PR_JACOBI, None, None, x)
+        assert info.iterations == 1 and np.isfinite(info.residual_l1)
+
+
+def test_damping_zero_is_the_teleport():
+    rp, ci = gg.rmat(10, seed=1)
+    x, info, _ = solve(rp, ci, damping=0.0, tol=1e-9, max_iter=10)
+    np.testing.assert_allclose(x, 1.0 / (rp.size - 1), rtol=1e-6)
