@@ -171,6 +171,12 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
  *                         enqueues iterations in chunks.
  *   PR_OPT_CTAS_PER_SM    blocks per SM of the persistent kernels (0 =
  *                         from occupancy, else 1..8).
+ *   PR_OPT_HOT_VERTICES   L1 policy of the rank gathers: bits 0..27 count
+ *                         the first vertices in the library's degree order
+ *                         that are gathered with L1 evict_last; bits 28..31
+ *                         pick what the other gathers use (0: everything is
+ *                         a plain cached load -- the default; 1: plain;
+ *                         2: evict_first; 3: no L1 allocation).
  *   PR_OPT_INDEX64        1: keep 64-bit row offsets on the device even when
  *                         the edge count fits 32 bits (thread-local default
  *                         for the next pr_create_graph, set with g = NULL;
@@ -180,6 +186,7 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
 #define PR_OPT_USE_GRAPH 2
 #define PR_OPT_CTAS_PER_SM 3
 #define PR_OPT_INDEX64 4
+#define PR_OPT_HOT_VERTICES 5
 PR_API pr_status pr_set_option(pr_graph* g, int key, int64_t value);
 
 /* Static text for a status code. */

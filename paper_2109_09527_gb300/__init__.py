@@ -42,6 +42,7 @@ PR_OPT_HEAVY_DEGREE = 1
 PR_OPT_USE_GRAPH = 2
 PR_OPT_CTAS_PER_SM = 3
 PR_OPT_INDEX64 = 4
+PR_OPT_HOT_VERTICES = 5
 
 LIB_PATH = _build.LIB_PATH
 

@@ -117,6 +117,17 @@ extern "C" pr_status pr_set_option(pr_graph* g, int key, int64_t value) {
             if (value < 0 || value > 8) return fail(PR_ERR_INVALID_ARG, "PR_OPT_CTAS_PER_SM is 0 (automatic) to 8");
             g->ctas_per_sm = (int)value;
             return PR_OK;
+        case PR_OPT_HOT_VERTICES:
+            if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_HOT_VERTICES needs a graph");
+            if (value < 0 || value > 0x7fffffffLL) return fail(PR_ERR_INVALID_ARG, "PR_OPT_HOT_VERTICES out of range");
+            if ((value >> 28) > 3) return fail(PR_ERR_INVALID_ARG, "PR_OPT_HOT_VERTICES: policy (bits 28..31) must be 0..3");
+            g->hot_vertices = value;
+            for (auto& ex : g->loop_exec)
+                if (ex) {
+                    cudaGraphExecDestroy(ex);
+                    ex = nullptr;
+                }
+            return PR_OK;
         case PR_OPT_INDEX64:
             if (g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_INDEX64 is set with g = NULL (it applies to the next pr_create_graph)");
             if (value != 0 && value != 1) return fail(PR_ERR_INVALID_ARG, "PR_OPT_INDEX64 is 0 or 1");

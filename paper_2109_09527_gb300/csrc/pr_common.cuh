@@ -37,7 +37,8 @@ constexpr int kDefaultHeavy = 1024;      // default heavy in-degree threshold
 constexpr int kPad = 64;                 // spare elements after every device array
 constexpr int kTileHeavy = -1;           // tile kind: epilogue of heavy rows
 constexpr int kTileZero = -2;            // tile kind: rows without in-edges
-constexpr int kMaxBins = 42;   // degree bins: 40 power-of-two classes + zero + spare
+constexpr int kMaxBins = 42;
+constexpr int64_t kDefaultHot = 0;       // gather L1 policy and hot-vertex count (see ld_gather)   // degree bins: 40 power-of-two classes + zero + spare
 
 // A tile of the row kernel: rows [row_begin, row_end) of one bin.  kind >= 0
 // is log2 of the lanes that gather one row together.
@@ -88,7 +89,7 @@ struct IterArgs {
     double* slots;               // two doubles per block of the row kernel
     cudaGraphConditionalHandle cond;
     int32_t use_cond;            // 1: the kernel runs inside the while-graph
-    int32_t pad;
+    int32_t hot;                 // binned ids gathered through L1 (ld_gather)
 };
 
 }  // namespace prk
@@ -103,6 +104,7 @@ struct pr_graph {
     int heavy_degree = prk::kDefaultHeavy;
     int ctas_per_sm = 0;         // 0 = from occupancy
     bool use_graph = true;
+    int64_t hot_vertices = prk::kDefaultHot;  // see ld_gather
 
     void* rowptr = nullptr;
     int32_t* colidx = nullptr;

@@ -60,10 +60,10 @@ __global__ void __launch_bounds__(kBlock) k_heavy_segments(IterArgs a, const flo
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int64_t p = base + 128 * j + 4 * lane;
-                const float v0 = (p + 0 >= e0 && p + 0 < e1) ? __ldg(y + c[j].x) : 0.f;
-                const float v1 = (p + 1 >= e0 && p + 1 < e1) ? __ldg(y + c[j].y) : 0.f;
-                const float v2 = (p + 2 >= e0 && p + 2 < e1) ? __ldg(y + c[j].z) : 0.f;
-                const float v3 = (p + 3 >= e0 && p + 3 < e1) ? __ldg(y + c[j].w) : 0.f;
+                const float v0 = (p + 0 >= e0 && p + 0 < e1) ? ld_gather(y, c[j].x, a.hot) : 0.f;
+                const float v1 = (p + 1 >= e0 && p + 1 < e1) ? ld_gather(y, c[j].y, a.hot) : 0.f;
+                const float v2 = (p + 2 >= e0 && p + 2 < e1) ? ld_gather(y, c[j].z, a.hot) : 0.f;
+                const float v3 = (p + 3 >= e0 && p + 3 < e1) ? ld_gather(y, c[j].w, a.hot) : 0.f;
                 acc += (v0 + v1) + (v2 + v3);
             }
         }
@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(kBlock) k_rows(IterArgs a, const float* __rest
     c.one_m_d = (float)(1.0 - d);
     c.d_share = (float)(d * share);
     c.base = (float)((1.0 - d) * st->inv_n + d * share);
+    c.hot = a.hot;
     Acc acc;
 
     for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
@@ -210,6 +211,8 @@ IterArgs make_args(const pr_graph* g, bool uniform) {
     a.slots = g->slots;
     a.cond = 0;
     a.use_cond = 0;
+    a.hot = (int32_t)(((g->hot_vertices >> 28) << 28) |
+                      std::min<int64_t>(g->hot_vertices & 0x0fffffff, g->n));
     return a;
 }
 

@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(kBlock) k_nonblocking(NbArgs a) {
         RowCtx c;
         c.d = (float)d;
         c.one_m_d = (float)(1.0 - d);
+        c.hot = 0;
         float r_sweep = 0.f;
         int since = kPublishEvery;
         for (int32_t it = i0; it < i1 || since > 0; it += istep) {

@@ -37,6 +37,29 @@ __device__ __forceinline__ int4 ld_stream4(const int32_t* p) {
     return v;
 }
 
+// Gathers of the quotient vector through the non-coherent path.  `hot` packs
+// an L1 policy (bits 28..31) and a vertex count (bits 0..27): the first
+// `count` binned ids -- the rows with the highest in-degree classes, which in
+// power-law graphs are also the sources of most edges -- may be given a
+// different L1 eviction priority from the rest.  Policy 0 (default) is the
+// plain cached load for every id.
+__device__ __forceinline__ float ld_gather(const float* y, int32_t c, int32_t hot) {
+    float v;
+    const int policy = (int)((uint32_t)hot >> 28);
+    const int32_t count = hot & 0x0fffffff;
+    if (policy == 0) return __ldg(y + c);
+    if (c < count) {
+        asm("ld.global.nc.L1::evict_last.f32 %0, [%1];" : "=f"(v) : "l"(y + c));
+    } else if (policy == 1) {
+        v = __ldg(y + c);
+    } else if (policy == 2) {
+        asm("ld.global.nc.L1::evict_first.f32 %0, [%1];" : "=f"(v) : "l"(y + c));
+    } else {
+        asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(y + c));
+    }
+    return v;
+}
+
 __device__ __forceinline__ void st_stream(float* p, float v) {
     asm volatile("st.global.cs.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
 }
@@ -83,7 +106,9 @@ struct Mem;
 
 template <>
 struct Mem<false> {
-    static __device__ __forceinline__ float gather(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ float gather(const float* y, int32_t c, int32_t hot) {
+        return ld_gather(y, c, hot);
+    }
     static __device__ __forceinline__ float load_x(const float* p) { return ld_stream(p); }
     static __device__ __forceinline__ void store_x(float* p, float v) { st_stream(p, v); }
     static __device__ __forceinline__ void store_y(float* p, float v) { st_stream(p, v); }
@@ -91,7 +116,9 @@ struct Mem<false> {
 
 template <>
 struct Mem<true> {
-    static __device__ __forceinline__ float gather(const float* p) { return ld_relaxed(p); }
+    static __device__ __forceinline__ float gather(const float* y, int32_t c, int32_t) {
+        return ld_relaxed(y + c);
+    }
     static __device__ __forceinline__ float load_x(const float* p) { return ld_relaxed(p); }
     static __device__ __forceinline__ void store_x(float* p, float v) { st_relaxed(p, v); }
     static __device__ __forceinline__ void store_y(float* p, float v) { st_relaxed(p, v); }
@@ -104,6 +131,7 @@ struct RowCtx {
     float one_m_d;    // 1 - d
     float d_share;    // d * share
     float base;       // (1-d)/n + d * share (uniform teleport)
+    int32_t hot;      // binned ids below this are gathered through L1 (see ld_gather)
 };
 
 // Per-thread accumulators.  r: L1 change.  (m, c): Kahan sum of the mass the
@@ -187,10 +215,10 @@ __device__ __forceinline__ void process_light_tile(const Tile& tile, const void*
             const int32_t c1 = k + g < e ? ld_stream(colidx + k + g) : -1;
             const int32_t c2 = k + 2 * g < e ? ld_stream(colidx + k + 2 * g) : -1;
             const int32_t c3 = k + 3 * g < e ? ld_stream(colidx + k + 3 * g) : -1;
-            const float v0 = Mem<kInPlace>::gather(y_in + c0);
-            const float v1 = c1 >= 0 ? Mem<kInPlace>::gather(y_in + c1) : 0.f;
-            const float v2 = c2 >= 0 ? Mem<kInPlace>::gather(y_in + c2) : 0.f;
-            const float v3 = c3 >= 0 ? Mem<kInPlace>::gather(y_in + c3) : 0.f;
+            const float v0 = Mem<kInPlace>::gather(y_in, c0, c.hot);
+            const float v1 = c1 >= 0 ? Mem<kInPlace>::gather(y_in, c1, c.hot) : 0.f;
+            const float v2 = c2 >= 0 ? Mem<kInPlace>::gather(y_in, c2, c.hot) : 0.f;
+            const float v3 = c3 >= 0 ? Mem<kInPlace>::gather(y_in, c3, c.hot) : 0.f;
             s += (v0 + v1) + (v2 + v3);
         }
 #pragma unroll
