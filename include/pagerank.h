@@ -189,6 +189,33 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
 #define PR_OPT_HOT_VERTICES 5
 PR_API pr_status pr_set_option(pr_graph* g, int key, int64_t value);
 
+/* One synchronous PageRank update that allocates no memory -- for callers
+ * that cannot call cudaMalloc (or anything that allocates) where they need an
+ * update: code running inside a fixed memory pool or arena, under another
+ * framework's allocator, or in a latency-bound loop where an allocation may
+ * not happen.  The paper has no counterpart; it is a deployment convenience.
+ *
+ * It works directly on the caller's plain in-edge CSR (no pr_graph, no
+ * relabelling) and computes
+ *   x_out(v) = (1-d)/n + d * ( sum_{(u,v) in E} x_in(u) * inv_outdeg(u) + D/n )
+ * with D the dangling mass of x_in (the vertices with inv_outdeg = 0).
+ *   n            1 <= n <= 16,777,216 (the fixed scratch holds 8192 blocks of
+ *                2048 rows); larger n returns PR_ERR_INVALID_ARG.
+ *   rowptr       device, n+1 int32 offsets; colidx device, int32 sources.
+ *   inv_outdeg   device, n floats: 1/outdeg(u), or 0 for dangling u.
+ *   x_in, x_out  device, n floats each; must be different buffers.
+ *   sums_out     device, 3 doubles: [0] dangling mass of x_in, [1] dangling
+ *                mass of x_out, [2] ||x_out - x_in||_1.
+ * The call is asynchronous on `stream` and does not validate the CSR.
+ * Scratch lives in one fixed device array (about 128 KiB) that the library
+ * keeps on every GPU that loads it, until the process exits; all calls share
+ * it, so calls that overlap on the GPU race -- serialise them.  The first call
+ * on a device looks up that array's address (cudaGetSymbolAddress); make it
+ * before any stream capture. */
+PR_API pr_status pr_step_noalloc(int64_t n, const int32_t* rowptr, const int32_t* colidx,
+                                 const float* inv_outdeg, float damping, const float* x_in,
+                                 float* x_out, double* sums_out, void* stream);
+
 /* Static text for a status code. */
 PR_API const char* pr_status_string(pr_status s);
 

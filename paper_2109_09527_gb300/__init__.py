@@ -89,6 +89,7 @@ SIGNATURES = {
     "pr_iterate": (ctypes.c_int, [_VP, _F, _VP, _VP, _I32, _VP, ctypes.POINTER(pr_info), _VP]),
     "pr_graph_get_stats": (ctypes.c_int, [_VP, ctypes.POINTER(pr_graph_stats)]),
     "pr_set_option": (ctypes.c_int, [_VP, ctypes.c_int, _I64]),
+    "pr_step_noalloc": (ctypes.c_int, [_I64, _VP, _VP, _VP, _F, _VP, _VP, _VP, _VP]),
     "pr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pr_last_error": (ctypes.c_char_p, []),
 }
@@ -205,6 +206,15 @@ def pr_graph_get_stats(g):
 
 def pr_set_option(g, key, value):
     return _check(load().pr_set_option(g, int(key), int(value)))
+
+
+def pr_step_noalloc(n, rowptr, colidx, inv_outdeg, damping, x_in, x_out, sums_out, stream=None):
+    """One synchronous update on a caller-owned plain CSR without any allocation (all
+    arrays device memory; sums_out holds 3 doubles).  Asynchronous on the stream."""
+    return _check(load().pr_step_noalloc(int(n), _addr(rowptr, np.int32), _addr(colidx, np.int32),
+                                         _addr(inv_outdeg, np.float32), float(damping),
+                                         _addr(x_in, np.float32), _addr(x_out, np.float32),
+                                         _addr(sums_out), _stream(stream)))
 
 
 def pr_status_string(status):
