@@ -162,7 +162,7 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
 
 /* Tuning knobs, mostly for tests that force one code path at a time.
  *   PR_OPT_HEAVY_DEGREE   rows with in-degree >= value are gathered in
- *                         segments (a power of two in [64, 2^30]; default
+ *                         segments (a power of two in [64, 4096]; default
  *                         1024).  Takes effect at the next pr_create_graph
  *                         of the same thread (it changes the layout), so it
  *                         is a thread-local default, set with g = NULL.
@@ -173,10 +173,17 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
  *                         from occupancy, else 1..8).
  *   PR_OPT_HOT_VERTICES   L1 policy of the rank gathers: bits 0..27 count
  *                         the first vertices in the library's degree order
- *                         that are gathered with L1 evict_last; bits 28..31
- *                         pick what the other gathers use (0: everything is
- *                         a plain cached load -- the default; 1: plain;
- *                         2: evict_first; 3: no L1 allocation).
+ *                         (the hubs); bits 28..31 pick the policy: 0 every
+ *                         gather is a plain cached load; 1/2/3 the hubs use
+ *                         L1 evict_last and the others plain / evict_first /
+ *                         no L1 allocation; 4 (default, with 49152 hubs) the
+ *                         hubs are plain cached loads and all others are read
+ *                         from L2 only, so they cannot evict the hubs.
+ *   PR_OPT_HOT_CACHE      vertices at the front of the library's degree
+ *                         order whose quotient values each block of the
+ *                         synchronous kernels copies into shared memory and
+ *                         gathers from there (0..40960, default 0: off --
+ *                         measured slower than letting L1 cache them).
  *   PR_OPT_INDEX64        1: keep 64-bit row offsets on the device even when
  *                         the edge count fits 32 bits (thread-local default
  *                         for the next pr_create_graph, set with g = NULL;
@@ -187,6 +194,7 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
 #define PR_OPT_CTAS_PER_SM 3
 #define PR_OPT_INDEX64 4
 #define PR_OPT_HOT_VERTICES 5
+#define PR_OPT_HOT_CACHE 6
 PR_API pr_status pr_set_option(pr_graph* g, int key, int64_t value);
 
 /* One synchronous PageRank update that allocates no memory -- for callers

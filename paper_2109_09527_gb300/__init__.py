@@ -43,6 +43,7 @@ PR_OPT_USE_GRAPH = 2
 PR_OPT_CTAS_PER_SM = 3
 PR_OPT_INDEX64 = 4
 PR_OPT_HOT_VERTICES = 5
+PR_OPT_HOT_CACHE = 6
 
 LIB_PATH = _build.LIB_PATH
 

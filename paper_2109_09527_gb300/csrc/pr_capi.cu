@@ -103,8 +103,8 @@ extern "C" pr_status pr_set_option(pr_graph* g, int key, int64_t value) {
     switch (key) {
         case PR_OPT_HEAVY_DEGREE:
             if (g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_HEAVY_DEGREE is set with g = NULL (it applies to the next pr_create_graph)");
-            if (value < 64 || value > (1LL << 30) || (value & (value - 1)))
-                return fail(PR_ERR_INVALID_ARG, "PR_OPT_HEAVY_DEGREE must be a power of two in [64, 2^30]");
+            if (value < 64 || value > 4096 || (value & (value - 1)))
+                return fail(PR_ERR_INVALID_ARG, "PR_OPT_HEAVY_DEGREE must be a power of two in [64, 4096]");
             set_thread_heavy_degree((int)value);
             return PR_OK;
         case PR_OPT_USE_GRAPH:
@@ -120,8 +120,19 @@ extern "C" pr_status pr_set_option(pr_graph* g, int key, int64_t value) {
         case PR_OPT_HOT_VERTICES:
             if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_HOT_VERTICES needs a graph");
             if (value < 0 || value > 0x7fffffffLL) return fail(PR_ERR_INVALID_ARG, "PR_OPT_HOT_VERTICES out of range");
-            if ((value >> 28) > 3) return fail(PR_ERR_INVALID_ARG, "PR_OPT_HOT_VERTICES: policy (bits 28..31) must be 0..3");
+            if ((value >> 28) > 4) return fail(PR_ERR_INVALID_ARG, "PR_OPT_HOT_VERTICES: policy (bits 28..31) must be 0..4");
             g->hot_vertices = value;
+            for (auto& ex : g->loop_exec)
+                if (ex) {
+                    cudaGraphExecDestroy(ex);
+                    ex = nullptr;
+                }
+            return PR_OK;
+        case PR_OPT_HOT_CACHE:
+            if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_HOT_CACHE needs a graph");
+            if (value < 0 || value > kHotCacheMax)
+                return fail(PR_ERR_INVALID_ARG, "PR_OPT_HOT_CACHE must be in [0, 40960]");
+            g->hot_cache = value;
             for (auto& ex : g->loop_exec)
                 if (ex) {
                     cudaGraphExecDestroy(ex);

@@ -30,15 +30,19 @@
 
 namespace prk {
 
-constexpr int kBlock = 256;              // threads per block of the per-iteration kernels
+constexpr int kBlock = 256;              // threads of a tile group (and of the small kernels)
 constexpr int kWarps = kBlock / 32;
+constexpr int kIterBlock = 256;          // threads per block of the Jacobi iteration kernels
+constexpr int kHotCacheMax = 40960;      // largest shared-memory copy of y's hot prefix (160 KB)
+constexpr int kTileEdgesMax = 6144;      // edges of a light tile
+constexpr int kTileRowsMax = 2048;       // rows of a light tile
 constexpr int kSegEdges = 2048;          // edges per segment of a heavy row
 constexpr int kDefaultHeavy = 1024;      // default heavy in-degree threshold
 constexpr int kPad = 64;                 // spare elements after every device array
 constexpr int kTileHeavy = -1;           // tile kind: epilogue of heavy rows
 constexpr int kTileZero = -2;            // tile kind: rows without in-edges
 constexpr int kMaxBins = 42;
-constexpr int64_t kDefaultHot = 0;       // gather L1 policy and hot-vertex count (see ld_gather)   // degree bins: 40 power-of-two classes + zero + spare
+constexpr int64_t kDefaultHot = (4LL << 28) | 49152;  // gather L1 policy 4, 48K hot ids (see ld_gather)   // degree bins: 40 power-of-two classes + zero + spare
 
 // A tile of the row kernel: rows [row_begin, row_end) of one bin.  kind >= 0
 // is log2 of the lanes that gather one row together.
@@ -89,7 +93,9 @@ struct IterArgs {
     double* slots;               // two doubles per block of the row kernel
     cudaGraphConditionalHandle cond;
     int32_t use_cond;            // 1: the kernel runs inside the while-graph
-    int32_t hot;                 // binned ids gathered through L1 (ld_gather)
+    int32_t hot;                 // L1 policy of the global gathers (ld_gather)
+    int32_t hot_n;               // ids [0, hot_n) of y are cached in shared memory
+    int32_t pad2;
 };
 
 }  // namespace prk
@@ -105,6 +111,7 @@ struct pr_graph {
     int ctas_per_sm = 0;         // 0 = from occupancy
     bool use_graph = true;
     int64_t hot_vertices = prk::kDefaultHot;  // see ld_gather
+    int64_t hot_cache = 0;                    // size of the shared-memory copy of y's prefix (off)
 
     void* rowptr = nullptr;
     int32_t* colidx = nullptr;

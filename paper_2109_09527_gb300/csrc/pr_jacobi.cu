@@ -37,12 +37,27 @@ namespace prk {
 
 // --------------------------------------------------------- iteration kernels --
 
+// Copy y[0, hot_n) -- the sources of most edges in a power-law graph, which
+// the degree binning puts first -- into shared memory with 16-byte loads.
+__device__ __forceinline__ void load_hot(const float* __restrict__ y, int32_t hot_n, float* sm) {
+    const float4* src = reinterpret_cast<const float4*>(y);
+    float4* dst = reinterpret_cast<float4*>(sm);
+    for (int i = threadIdx.x; i < (hot_n >> 2); i += blockDim.x) dst[i] = __ldg(src + i);
+    __syncthreads();
+}
+
 template <typename IdxT>
-__global__ void __launch_bounds__(kBlock) k_heavy_segments(IterArgs a, const float* __restrict__ y) {
+__global__ void __launch_bounds__(kIterBlock) k_heavy_segments(IterArgs a, const float* __restrict__ y) {
+    extern __shared__ __align__(16) float hot_sm[];
     if (*(volatile int32_t*)&a.state->done) return;
+    load_hot(y, a.hot_n, hot_sm);
+    RowCtx c{};
+    c.hot = a.hot;
+    c.hot_n = a.hot_n;
+    c.hot_sm = hot_sm;
     const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
-    const int64_t nwarp = ((int64_t)gridDim.x * kBlock) >> 5;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t s = warp; s < a.n_seg; s += nwarp) {
         const int32_t h = a.seg_row[s];
         const int64_t re = row_at<IdxT>(a.rowptr, h + 1);
@@ -51,19 +66,19 @@ __global__ void __launch_bounds__(kBlock) k_heavy_segments(IterArgs a, const flo
         const int64_t a0 = e0 & ~(int64_t)3;   // 16-byte aligned start
         float acc = 0.f;
         for (int64_t base = a0; base < e1; base += 512) {
-            int4 c[4];
+            int4 cv[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int64_t p = base + 128 * j + 4 * lane;
-                c[j] = p < e1 ? ld_stream4(a.colidx + p) : make_int4(0, 0, 0, 0);
+                cv[j] = p < e1 ? ld_stream4(a.colidx + p) : make_int4(0, 0, 0, 0);
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int64_t p = base + 128 * j + 4 * lane;
-                const float v0 = (p + 0 >= e0 && p + 0 < e1) ? ld_gather(y, c[j].x, a.hot) : 0.f;
-                const float v1 = (p + 1 >= e0 && p + 1 < e1) ? ld_gather(y, c[j].y, a.hot) : 0.f;
-                const float v2 = (p + 2 >= e0 && p + 2 < e1) ? ld_gather(y, c[j].z, a.hot) : 0.f;
-                const float v3 = (p + 3 >= e0 && p + 3 < e1) ? ld_gather(y, c[j].w, a.hot) : 0.f;
+                const float v0 = (p + 0 >= e0 && p + 0 < e1) ? Mem<false>::gather(y, cv[j].x, c) : 0.f;
+                const float v1 = (p + 1 >= e0 && p + 1 < e1) ? Mem<false>::gather(y, cv[j].y, c) : 0.f;
+                const float v2 = (p + 2 >= e0 && p + 2 < e1) ? Mem<false>::gather(y, cv[j].z, c) : 0.f;
+                const float v3 = (p + 3 >= e0 && p + 3 < e1) ? Mem<false>::gather(y, cv[j].w, c) : 0.f;
                 acc += (v0 + v1) + (v2 + v3);
             }
         }
@@ -72,16 +87,21 @@ __global__ void __launch_bounds__(kBlock) k_heavy_segments(IterArgs a, const flo
     }
 }
 
+// One block of kIterBlock threads per SM; each 256-thread group walks its own
+// tiles (round-robin over all groups of the grid) and shares the block's copy
+// of the hot prefix of y.
 template <typename IdxT, bool kUniform>
-__global__ void __launch_bounds__(kBlock) k_rows(IterArgs a, const float* __restrict__ x_in,
-                                                 const float* __restrict__ y_in,
-                                                 float* __restrict__ x_out, float* __restrict__ y_out) {
+__global__ void __launch_bounds__(kIterBlock) k_rows(IterArgs a, const float* __restrict__ x_in,
+                                                     const float* __restrict__ y_in,
+                                                     float* __restrict__ x_out, float* __restrict__ y_out) {
+    extern __shared__ __align__(16) float hot_sm[];
     SolveState* st = a.state;
     if (*(volatile int32_t*)&st->done) {
         // A skipped iteration inside the while-graph keeps the loop closed.
         if (a.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0);
         return;
     }
+    load_hot(y_in, a.hot_n, hot_sm);
     const double d = st->d;
     const double share = st->D * st->inv_n;   // D/n
     RowCtx c;
@@ -90,17 +110,22 @@ __global__ void __launch_bounds__(kBlock) k_rows(IterArgs a, const float* __rest
     c.d_share = (float)(d * share);
     c.base = (float)((1.0 - d) * st->inv_n + d * share);
     c.hot = a.hot;
+    c.hot_n = a.hot_n;
+    c.hot_sm = hot_sm;
     Acc acc;
+    const int groups = blockDim.x / kBlock;
+    const int tid = threadIdx.x & (kBlock - 1);
+    const int group = blockIdx.x * groups + threadIdx.x / kBlock;
 
-    for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+    for (int t = group; t < a.n_tiles; t += gridDim.x * groups) {
         const Tile tile = a.tiles[t];
         if (tile.kind >= 0) {
             process_light_tile<IdxT, kUniform, false>(tile, a.rowptr, a.colidx, a.inv_out, a.teleport,
-                                                       x_in, y_in, x_out, y_out, c, acc);
+                                                       x_in, y_in, x_out, y_out, c, acc, tid);
         } else if (tile.kind == kTileZero) {
-            process_zero_tile<kUniform, false>(tile, a.inv_out, a.teleport, x_in, x_out, y_out, c, acc);
+            process_zero_tile<kUniform, false>(tile, a.inv_out, a.teleport, x_in, x_out, y_out, c, acc, tid);
         } else {  // heavy rows: sum of the segment partials
-            for (int64_t r = tile.row_begin + threadIdx.x; r < tile.row_end; r += kBlock) {
+            for (int64_t r = tile.row_begin + tid; r < tile.row_end; r += kBlock) {
                 const float xo = ld_stream(x_in + r);
                 const float inv = ld_stream(a.inv_out + r);
                 const float tv = kUniform ? 0.f : ld_stream(a.teleport + r);
@@ -192,6 +217,7 @@ __global__ void __launch_bounds__(kBlock) k_unpermute(IterArgs a, const float* _
 
 namespace {
 int g_occ_rows = 0;
+int g_occ_seg = 0;
 }  // namespace
 
 IterArgs make_args(const pr_graph* g, bool uniform) {
@@ -213,6 +239,7 @@ IterArgs make_args(const pr_graph* g, bool uniform) {
     a.use_cond = 0;
     a.hot = (int32_t)(((g->hot_vertices >> 28) << 28) |
                       std::min<int64_t>(g->hot_vertices & 0x0fffffff, g->n));
+    a.hot_n = (int32_t)(std::min<int64_t>(g->hot_cache, g->n) & ~(int64_t)3);
     return a;
 }
 
@@ -225,22 +252,26 @@ int small_grid(const pr_graph* g) {
 template <typename IdxT>
 cudaError_t enqueue_iteration_t(const pr_graph* g, const IterArgs& a, int src, bool uniform,
                                 cudaStream_t s, int* launches) {
+    const size_t hot = (size_t)a.hot_n * sizeof(float);
     if (g->n_seg > 0) {
-        k_heavy_segments<IdxT><<<seg_grid(g), kBlock, 0, s>>>(a, g->y[src]);
+        k_heavy_segments<IdxT><<<seg_grid(g), kIterBlock, hot, s>>>(a, g->y[src]);
         ++*launches;
     }
     if (uniform)
-        k_rows<IdxT, true><<<row_grid(g), kBlock, 0, s>>>(a, g->x[src], g->y[src], g->x[1 - src], g->y[1 - src]);
+        k_rows<IdxT, true><<<row_grid(g), kIterBlock, hot, s>>>(a, g->x[src], g->y[src], g->x[1 - src],
+                                                                g->y[1 - src]);
     else
-        k_rows<IdxT, false><<<row_grid(g), kBlock, 0, s>>>(a, g->x[src], g->y[src], g->x[1 - src], g->y[1 - src]);
+        k_rows<IdxT, false><<<row_grid(g), kIterBlock, hot, s>>>(a, g->x[src], g->y[src], g->x[1 - src],
+                                                                 g->y[1 - src]);
     ++*launches;
     return cudaGetLastError();
 }
 
 cudaError_t launch_segments(const pr_graph* g, const IterArgs& a, int src, cudaStream_t s, int* launches) {
     if (g->n_seg == 0) return cudaSuccess;
-    if (g->idx64) k_heavy_segments<int64_t><<<seg_grid(g), kBlock, 0, s>>>(a, g->y[src]);
-    else k_heavy_segments<int32_t><<<seg_grid(g), kBlock, 0, s>>>(a, g->y[src]);
+    const size_t smem = (size_t)a.hot_n * sizeof(float);
+    if (g->idx64) k_heavy_segments<int64_t><<<seg_grid(g), kIterBlock, smem, s>>>(a, g->y[src]);
+    else k_heavy_segments<int32_t><<<seg_grid(g), kIterBlock, smem, s>>>(a, g->y[src]);
     ++*launches;
     return cudaGetLastError();
 }
@@ -332,15 +363,15 @@ void launch_finalize(const pr_graph* g, const IterArgs& a, float* out, bool reno
 }
 
 int row_grid(const pr_graph* g) {
-    int per_sm = g->ctas_per_sm > 0 ? g->ctas_per_sm : std::max(1, std::min(g_occ_rows, 8));
+    int per_sm = g->ctas_per_sm > 0 ? std::min(g->ctas_per_sm, g_occ_rows) : g_occ_rows;
     int64_t blocks = (int64_t)g->sm_count * per_sm;
     blocks = std::min<int64_t>(blocks, std::max<int64_t>(1, g->n_tiles));
     return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)g->slot_capacity));
 }
 
 int seg_grid(const pr_graph* g) {
-    int64_t blocks = (g->n_seg + kWarps - 1) / kWarps;
-    int64_t cap = (int64_t)g->sm_count * 8;
+    int64_t blocks = (g->n_seg + (kIterBlock / 32) - 1) / (kIterBlock / 32);
+    int64_t cap = (int64_t)g->sm_count * g_occ_seg;
     return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, cap));
 }
 
@@ -354,7 +385,7 @@ pr_status alloc_solver(pr_graph* g) {
     }
     PRK_CHECK(dev_alloc(g, (void**)&g->state, sizeof(SolveState)));
     PRK_CHECK(cudaMemset(g->state, 0, sizeof(SolveState)));
-    g->slot_capacity = g->sm_count * 8;
+    g->slot_capacity = g->sm_count * 8;   // also bounds every grid that reduces through slots
     PRK_CHECK(dev_alloc(g, (void**)&g->slots, (size_t)g->slot_capacity * 2 * sizeof(double)));
     PRK_CHECK(cudaMallocHost((void**)&g->host_state, sizeof(SolveState)));
     memset(g->host_state, 0, sizeof(SolveState));
@@ -362,9 +393,27 @@ pr_status alloc_solver(pr_graph* g) {
     memset(g->host_flag, 0, 4 * sizeof(int32_t));
     PRK_CHECK(cudaStreamCreateWithFlags(&g->capture_stream, cudaStreamNonBlocking));
     if (g_occ_rows == 0) {
+        const int hot = (int)(kHotCacheMax * sizeof(float));
+        PRK_CHECK(cudaFuncSetAttribute(k_rows<int32_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, hot));
+        PRK_CHECK(cudaFuncSetAttribute(k_rows<int32_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, hot));
+        PRK_CHECK(cudaFuncSetAttribute(k_rows<int64_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, hot));
+        PRK_CHECK(cudaFuncSetAttribute(k_rows<int64_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, hot));
+        PRK_CHECK(cudaFuncSetAttribute(k_heavy_segments<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, hot));
+        PRK_CHECK(cudaFuncSetAttribute(k_heavy_segments<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, hot));
+        // These kernels need almost no shared memory: give the SRAM to L1, which
+        // caches the gathered ranks of the hub vertices.
+        PRK_CHECK(cudaFuncSetAttribute(k_rows<int32_t, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
+        PRK_CHECK(cudaFuncSetAttribute(k_rows<int32_t, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
+        PRK_CHECK(cudaFuncSetAttribute(k_rows<int64_t, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
+        PRK_CHECK(cudaFuncSetAttribute(k_rows<int64_t, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
+        PRK_CHECK(cudaFuncSetAttribute(k_heavy_segments<int32_t>, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
+        PRK_CHECK(cudaFuncSetAttribute(k_heavy_segments<int64_t>, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
         int occ = 0;
-        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rows<int32_t, true>, kBlock, 0));
+        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rows<int32_t, false>, kIterBlock, 0));
         g_occ_rows = std::max(1, occ);
+        int occ_seg = 0;
+        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_seg, k_heavy_segments<int32_t>, kIterBlock, 0));
+        g_occ_seg = std::max(1, occ_seg);
     }
     return PR_OK;
 }
@@ -465,6 +514,8 @@ pr_status run_jacobi(pr_graph* g, float damping, double tol, int32_t max_iter, c
         PRK_CHECK(cudaMemcpyAsync(x_out, out, (size_t)g->n * sizeof(float), cudaMemcpyDeviceToHost, s));
     PRK_CHECK(cudaMemcpyAsync(hs, g->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
     PRK_CHECK(cudaStreamSynchronize(s));
+    if (hs->error)
+        return fail(PR_ERR_CUDA, "internal error: a row tile exceeded its shared-memory staging area");
     float ms = 0.f;
     PRK_CHECK(cudaEventElapsedTime(&ms, g->ev_start, g->ev_stop));
     const bool converged = hs->resid < tol;

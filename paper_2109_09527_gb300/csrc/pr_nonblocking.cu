@@ -135,6 +135,8 @@ __global__ void __launch_bounds__(kBlock) k_nonblocking(NbArgs a) {
         c.d = (float)d;
         c.one_m_d = (float)(1.0 - d);
         c.hot = 0;
+        c.hot_n = 0;
+        c.hot_sm = nullptr;
         float r_sweep = 0.f;
         int since = kPublishEvery;
         for (int32_t it = i0; it < i1 || since > 0; it += istep) {
@@ -160,9 +162,9 @@ __global__ void __launch_bounds__(kBlock) k_nonblocking(NbArgs a) {
             const Tile item = a.items[it];
             if (item.kind >= 0)
                 process_light_tile<IdxT, kUniform, true>(item, a.rowptr, a.colidx, a.inv_out, a.teleport,
-                                                          a.x, a.y, a.x, a.y, c, acc);
+                                                          a.x, a.y, a.x, a.y, c, acc, threadIdx.x);
             else if (item.kind == kTileZero)
-                process_zero_tile<kUniform, true>(item, a.inv_out, a.teleport, a.x, a.x, a.y, c, acc);
+                process_zero_tile<kUniform, true>(item, a.inv_out, a.teleport, a.x, a.x, a.y, c, acc, threadIdx.x);
             else
                 heavy_segment<IdxT, kUniform>(item, a, c, acc);
             ++since;
@@ -247,6 +249,7 @@ namespace {
 
 int g_occ_nb = 0;
 
+
 template <typename IdxT, bool kUniform>
 void* nb_kernel() {
     return (void*)k_nonblocking<IdxT, kUniform>;
@@ -261,11 +264,17 @@ void* pick_kernel(const pr_graph* g, bool uniform) {
 pr_status build_items(pr_graph* g, cudaStream_t s) {
     if (g->nb_items) return PR_OK;
     if (g_occ_nb == 0) {
-        int occ = 0;
-        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_nonblocking<int32_t, true>, kBlock, 0));
-        int occ64 = 0;
-        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ64, k_nonblocking<int64_t, false>, kBlock, 0));
-        g_occ_nb = std::max(1, std::min(occ, occ64));
+        int occ = 1 << 30;
+        int o = 0;
+        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_nonblocking<int32_t, true>, kBlock, 0));
+        occ = std::min(occ, o);
+        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_nonblocking<int32_t, false>, kBlock, 0));
+        occ = std::min(occ, o);
+        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_nonblocking<int64_t, true>, kBlock, 0));
+        occ = std::min(occ, o);
+        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_nonblocking<int64_t, false>, kBlock, 0));
+        occ = std::min(occ, o);
+        g_occ_nb = std::max(1, occ);
     }
     // heavy rows [0, n_heavy): one item per segment (the Jacobi segments)
     std::vector<int32_t> seg_ptr((size_t)g->n_heavy + 1, 0);
@@ -463,6 +472,8 @@ pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_
     PRK_CHECK(cudaStreamSynchronize(s));
     float ms = 0.f;
     PRK_CHECK(cudaEventElapsedTime(&ms, g->ev_start, g->ev_stop));
+    if (hs->error)
+        return fail(PR_ERR_CUDA, "internal error: a row tile exceeded its shared-memory staging area");
     if (info) {
         info->iterations = iterations;
         info->converged = converged ? 1 : 0;

@@ -309,11 +309,11 @@ std::vector<Tile> make_tiles(const std::vector<int64_t>& bin_start, int lh) {
     for (int b = first_light; b <= kTopClass; ++b) {
         const int k = kTopClass - b;             // degree class [2^k, 2^(k+1))
         const int lg = std::min(k, 5);           // lanes per row = 2^lg
-        const int64_t rows_per_pass = kBlock >> lg;
-        const double edges_per_pass = (double)rows_per_pass * 1.5 * (double)(1LL << k);
-        int64_t passes = (int64_t)std::lround(4096.0 / edges_per_pass);
-        passes = std::max<int64_t>(1, std::min<int64_t>(16, passes));
-        add(bin_start[b], bin_start[b + 1], rows_per_pass * passes, lg);
+        // every row of the class has at most 2^(k+1)-1 edges, so this many rows
+        // always fit the shared-memory staging area of a tile
+        const int64_t rows = std::max<int64_t>(
+            1, std::min<int64_t>(kTileRowsMax, kTileEdgesMax / ((1LL << (k + 1)) - 1)));
+        add(bin_start[b], bin_start[b + 1], rows, lg);
     }
     add(bin_start[kZeroBin], bin_start[kNumBins], 16 * kBlock, kTileZero);
     return tiles;

@@ -42,12 +42,14 @@ __device__ __forceinline__ int4 ld_stream4(const int32_t* p) {
 // `count` binned ids -- the rows with the highest in-degree classes, which in
 // power-law graphs are also the sources of most edges -- may be given a
 // different L1 eviction priority from the rest.  Policy 0 (default) is the
-// plain cached load for every id.
+// plain cached load for every id; policy 4 caches only the first `count` ids
+// in L1 and reads every other id from L2 (ld.global.cg).
 __device__ __forceinline__ float ld_gather(const float* y, int32_t c, int32_t hot) {
     float v;
     const int policy = (int)((uint32_t)hot >> 28);
     const int32_t count = hot & 0x0fffffff;
     if (policy == 0) return __ldg(y + c);
+    if (policy == 4) return c < count ? __ldg(y + c) : __ldcg(y + c);
     if (c < count) {
         asm("ld.global.nc.L1::evict_last.f32 %0, [%1];" : "=f"(v) : "l"(y + c));
     } else if (policy == 1) {
@@ -101,13 +103,25 @@ __device__ __forceinline__ int64_t row_at(const void* rowptr, int64_t r) {
     return (int64_t)__ldg((const IdxT*)rowptr + r);
 }
 
+// Constants of the update x' = (1-d) t + d (s + share), share = dangling
+// share of this iteration (D/n, or (T - S)/n in the barrier-free form).
+struct RowCtx {
+    float d;          // damping
+    float one_m_d;    // 1 - d
+    float d_share;    // d * share
+    float base;       // (1-d)/n + d * share (uniform teleport)
+    int32_t hot;      // L1 policy of the global gathers (see ld_gather)
+    int32_t hot_n;    // binned ids [0, hot_n) are read from hot_sm (shared memory)
+    const float* hot_sm;
+};
+
 template <bool kInPlace>
 struct Mem;
 
 template <>
 struct Mem<false> {
-    static __device__ __forceinline__ float gather(const float* y, int32_t c, int32_t hot) {
-        return ld_gather(y, c, hot);
+    static __device__ __forceinline__ float gather(const float* y, int32_t c, const RowCtx& x) {
+        return c < x.hot_n ? x.hot_sm[c] : ld_gather(y, c, x.hot);
     }
     static __device__ __forceinline__ float load_x(const float* p) { return ld_stream(p); }
     static __device__ __forceinline__ void store_x(float* p, float v) { st_stream(p, v); }
@@ -116,22 +130,12 @@ struct Mem<false> {
 
 template <>
 struct Mem<true> {
-    static __device__ __forceinline__ float gather(const float* y, int32_t c, int32_t) {
-        return ld_relaxed(y + c);
+    static __device__ __forceinline__ float gather(const float* y, int32_t c, const RowCtx& x) {
+        return c < x.hot_n ? x.hot_sm[c] : ld_relaxed(y + c);
     }
     static __device__ __forceinline__ float load_x(const float* p) { return ld_relaxed(p); }
     static __device__ __forceinline__ void store_x(float* p, float v) { st_relaxed(p, v); }
     static __device__ __forceinline__ void store_y(float* p, float v) { st_relaxed(p, v); }
-};
-
-// Constants of the update x' = (1-d) t + d (s + share), share = dangling
-// share of this iteration (D/n, or (T - S)/n in the barrier-free form).
-struct RowCtx {
-    float d;          // damping
-    float one_m_d;    // 1 - d
-    float d_share;    // d * share
-    float base;       // (1-d)/n + d * share (uniform teleport)
-    int32_t hot;      // binned ids below this are gathered through L1 (see ld_gather)
 };
 
 // Per-thread accumulators.  r: L1 change.  (m, c): Kahan sum of the mass the
@@ -172,59 +176,83 @@ template <bool kUniform, bool kInPlace>
 __device__ __forceinline__ void process_zero_tile(const Tile& tile, const float* inv_out,
                                                   const float* teleport, const float* x_in,
                                                   float* x_out, float* y_out, const RowCtx& c,
-                                                  Acc& acc) {
-    for (int64_t r = tile.row_begin + threadIdx.x; r < tile.row_end; r += kBlock) {
+                                                  Acc& acc, int tid) {
+    for (int64_t r = tile.row_begin + tid; r < tile.row_end; r += kBlock) {
         const float tv = kUniform ? 0.f : ld_stream(teleport + r);
         row_update<kUniform, kInPlace>(r, 0.f, Mem<kInPlace>::load_x(x_in + r), ld_stream(inv_out + r),
                                        tv, c, x_out, y_out, acc);
     }
 }
 
+// Tile functions run on a 256-thread (kBlock) group of whole warps; tid is
+// the thread's index in that group.
+//
 // Light rows of one degree class: groups of g = 2^tile.kind lanes gather one
-// row each (coalesced colidx reads within the group, up to four gathers in
-// flight per lane), reduce with shuffles, and the group's first lane updates
-// the row.
+// row each, two rows per group at a time (rows r and r + 256/g), so that a lane
+// has up to four colidx loads and four gathers in flight; coalesced colidx
+// reads within the group; shuffle reduction; the group's first lane updates
+// both rows.
 template <typename IdxT, bool kUniform, bool kInPlace>
 __device__ __forceinline__ void process_light_tile(const Tile& tile, const void* rowptr,
                                                    const int32_t* colidx, const float* inv_out,
                                                    const float* teleport, const float* x_in,
                                                    const float* y_in, float* x_out, float* y_out,
-                                                   const RowCtx& c, Acc& acc) {
+                                                   const RowCtx& c, Acc& acc, int tid) {
     const int lg = tile.kind;
     const int g = 1 << lg;
-    const int rpp = kBlock >> lg;  // rows per pass
-    const int grp = threadIdx.x >> lg;
-    const int gl = threadIdx.x & (g - 1);
-    for (int64_t r0 = tile.row_begin; r0 < tile.row_end; r0 += rpp) {
-        const int64_t r = r0 + grp;
-        const bool active = r < tile.row_end;
-        int64_t b = 0, e = 0;
-        float xo = 0.f, inv = 0.f, tv = 0.f;
-        if (active) {
-            b = row_at<IdxT>(rowptr, r);
-            e = row_at<IdxT>(rowptr, r + 1);
-            if (gl == 0) {
-                xo = Mem<kInPlace>::load_x(x_in + r);
-                inv = ld_stream(inv_out + r);
-                if (!kUniform) tv = ld_stream(teleport + r);
+    const int rpp = kBlock >> lg;  // rows per pass of the whole group set
+    const int grp = tid >> lg;
+    const int gl = tid & (g - 1);
+    for (int64_t r0 = tile.row_begin; r0 < tile.row_end; r0 += 2 * rpp) {
+        int64_t rr[2];
+        bool act[2];
+        int64_t b[2], e[2];
+        float xo[2], inv[2], tv[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            rr[q] = r0 + q * rpp + grp;
+            act[q] = rr[q] < tile.row_end;
+            b[q] = e[q] = 0;
+            xo[q] = inv[q] = tv[q] = 0.f;
+            if (act[q]) {
+                b[q] = row_at<IdxT>(rowptr, rr[q]);
+                e[q] = row_at<IdxT>(rowptr, rr[q] + 1);
+                if (gl == 0) {
+                    xo[q] = Mem<kInPlace>::load_x(x_in + rr[q]);
+                    inv[q] = ld_stream(inv_out + rr[q]);
+                    if (!kUniform) tv[q] = ld_stream(teleport + rr[q]);
+                }
             }
         }
-        float s = 0.f;
-        for (int64_t k = b + gl; k < e; k += 4 * g) {
-            const int32_t c0 = ld_stream(colidx + k);
-            const int32_t c1 = k + g < e ? ld_stream(colidx + k + g) : -1;
-            const int32_t c2 = k + 2 * g < e ? ld_stream(colidx + k + 2 * g) : -1;
-            const int32_t c3 = k + 3 * g < e ? ld_stream(colidx + k + 3 * g) : -1;
-            const float v0 = Mem<kInPlace>::gather(y_in, c0, c.hot);
-            const float v1 = c1 >= 0 ? Mem<kInPlace>::gather(y_in, c1, c.hot) : 0.f;
-            const float v2 = c2 >= 0 ? Mem<kInPlace>::gather(y_in, c2, c.hot) : 0.f;
-            const float v3 = c3 >= 0 ? Mem<kInPlace>::gather(y_in, c3, c.hot) : 0.f;
-            s += (v0 + v1) + (v2 + v3);
+        float s[2] = {0.f, 0.f};
+        const int64_t len = max(e[0] - b[0], e[1] - b[1]);
+        for (int64_t k = gl; k < len; k += 2 * g) {
+            int32_t cc[2][2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                cc[q][0] = b[q] + k < e[q] ? ld_stream(colidx + b[q] + k) : -1;
+                cc[q][1] = b[q] + k + g < e[q] ? ld_stream(colidx + b[q] + k + g) : -1;
+            }
+            float v[2][2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                v[q][0] = cc[q][0] >= 0 ? Mem<kInPlace>::gather(y_in, cc[q][0], c) : 0.f;
+                v[q][1] = cc[q][1] >= 0 ? Mem<kInPlace>::gather(y_in, cc[q][1], c) : 0.f;
+            }
+            s[0] += v[0][0] + v[0][1];
+            s[1] += v[1][0] + v[1][1];
         }
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1)
-            if (o < g) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (active && gl == 0) row_update<kUniform, kInPlace>(r, s, xo, inv, tv, c, x_out, y_out, acc);
+            if (o < g) {
+                s[0] += __shfl_xor_sync(0xffffffffu, s[0], o);
+                s[1] += __shfl_xor_sync(0xffffffffu, s[1], o);
+            }
+        if (gl == 0) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+                if (act[q]) row_update<kUniform, kInPlace>(rr[q], s[q], xo[q], inv[q], tv[q], c, x_out, y_out, acc);
+        }
     }
 }
 
@@ -235,7 +263,8 @@ __device__ __forceinline__ void process_light_tile(const Tile& tile, const void*
 // (*ta, *tb) of every thread.
 __device__ __forceinline__ bool block_pair_to_grid(double a, double b, double* slots, uint32_t* ticket,
                                                    double* ta, double* tb) {
-    __shared__ double sa[kWarps], sb[kWarps];
+    __shared__ double sa[32], sb[32];
+    const int nw = blockDim.x >> 5;
     __shared__ int last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     a = warp_sum(a);
@@ -247,7 +276,7 @@ __device__ __forceinline__ bool block_pair_to_grid(double a, double b, double* s
     __syncthreads();
     if (threadIdx.x == 0) {
         double A = 0.0, B = 0.0;
-        for (int w = 0; w < kWarps; ++w) {
+        for (int w = 0; w < nw; ++w) {
             A += sa[w];
             B += sb[w];
         }
@@ -261,7 +290,7 @@ __device__ __forceinline__ bool block_pair_to_grid(double a, double b, double* s
     if (!last) return false;
     __threadfence();
     double A = 0.0, B = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += kBlock) {
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
         A += __ldcg(slots + 2 * i);
         B += __ldcg(slots + 2 * i + 1);
     }
@@ -275,7 +304,7 @@ __device__ __forceinline__ bool block_pair_to_grid(double a, double b, double* s
     __syncthreads();
     A = 0.0;
     B = 0.0;
-    for (int w = 0; w < kWarps; ++w) {
+    for (int w = 0; w < nw; ++w) {
         A += sa[w];
         B += sb[w];
     }
@@ -286,7 +315,8 @@ __device__ __forceinline__ bool block_pair_to_grid(double a, double b, double* s
 
 // Block-wide sum of two doubles; every thread receives the totals.
 __device__ __forceinline__ void block_sum2(double& a, double& b) {
-    __shared__ double sa[kWarps], sb[kWarps];
+    __shared__ double sa[32], sb[32];
+    const int nw = blockDim.x >> 5;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     a = warp_sum(a);
     b = warp_sum(b);
@@ -298,7 +328,7 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
     __syncthreads();
     a = 0.0;
     b = 0.0;
-    for (int w = 0; w < kWarps; ++w) {
+    for (int w = 0; w < nw; ++w) {
         a += sa[w];
         b += sb[w];
     }
@@ -306,14 +336,15 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
 
 // Block-wide sum of a float; every thread receives the total.
 __device__ __forceinline__ float block_sum(float v) {
-    __shared__ float sv[kWarps];
+    __shared__ float sv[32];
+    const int nw = blockDim.x >> 5;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     v = warp_sum(v);
     __syncthreads();
     if (lane == 0) sv[warp] = v;
     __syncthreads();
     float t = 0.f;
-    for (int w = 0; w < kWarps; ++w) t += sv[w];
+    for (int w = 0; w < nw; ++w) t += sv[w];
     return t;
 }
 

@@ -79,6 +79,8 @@ def test_options_validate_host_side():
         pr.set_heavy_degree(100)          # not a power of two
     with pytest.raises(pr.PageRankError):
         pr.set_heavy_degree(32)           # too small
+    with pytest.raises(pr.PageRankError):
+        pr.set_heavy_degree(8192)         # light tiles must fit their staging area
     pr.set_heavy_degree(1024)
     with pytest.raises(pr.PageRankError):
         pr.pr_set_option(None, 99, 1)
