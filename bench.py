@@ -11,8 +11,10 @@ L1 change below 1e-6 (damping 0.85, budget 200 iterations).  Four solves per ste
   e2e       the same metric through the C ABI from pinned host buffers: graph
             creation (H2D copy + set-up), both solves, and the D2H read of every
             result inside the timed region
-  roofline  one Jacobi iteration (k_heavy_segments + k_rows) on R-MAT-24:
-            algorithmic bytes 4*nnz + 4*(n+1) + 20*n over the measured iteration time
+  roofline  the kernel with the larger share of the step's device time (synchronous
+            iteration or persistent barrier-free launch) on R-MAT-24: algorithmic
+            bytes (4*nnz + 4*(n+1) + 20*n per full sweep, times the sweeps the launch
+            made) over its CUDA-event duration; roofline_all has every graph/variant
   cpu_baseline  the FP64 oracle (single thread, as it stands) on a bounded sample:
             a few synchronous iterations of the same R-MAT-24 graph
 
@@ -134,26 +136,90 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_sources_sha():
+# Sources each timed kernel family is compiled from: a recorded ncu traffic figure is
+# used only while these files are unchanged.
+KERNEL_SOURCES = {
+    "jacobi": ["pr_common.cuh", "pr_tile.cuh", "pr_jacobi.cu"],
+    "nonblocking": ["pr_common.cuh", "pr_tile.cuh", "pr_nonblocking.cu"],
+}
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_rmat24.txt")
+
+
+def kernel_sources_sha(family):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2109_09527_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in KERNEL_SOURCES[family]:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
-    """DRAM bytes per iteration from the committed ncu summary, if taken on these sources."""
-    path = os.path.join(ROOT, "profiles", "traffic_rmat24_jacobi.json")
-    if not os.path.exists(path):
+def recorded_traffic(family):
+    """DRAM bytes per gathered edge of a kernel family on R-MAT-24, from the committed
+    ncu summary (`key: value` lines), if it was taken on the current sources."""
+    if not os.path.exists(TRAFFIC_FILE):
         return None
-    with open(path) as f:
-        rec = json.load(f)
-    if rec.get("source_sha") != kernel_sources_sha():
+    rec = {}
+    with open(TRAFFIC_FILE) as f:
+        for line in f:
+            if ":" in line and not line.lstrip().startswith("#"):
+                k, v = line.split(":", 1)
+                rec[k.strip()] = v.strip()
+    if rec.get(f"{family}_sources_sha") != kernel_sources_sha(family):
         return None
-    return rec.get("dram_bytes_per_iteration")
+    v = rec.get(f"{family}_dram_bytes_per_edge_visit")
+    return float(v) if v else None
+
+
+def rooflines(records, resident):
+    """Roofline of the dominant kernel of the step, and of every (graph, variant) pair.
+
+    A launch of the synchronous variant is one iteration (k_heavy_segments + k_rows);
+    a launch of the barrier-free variant is one persistent k_nonblocking launch.
+    Algorithmic bytes per launch = B(graph) x (edges gathered in the launch / nnz), with
+    B = 4 nnz + rowptr bytes (n+1) + 20 n the bytes one full sweep must move; the
+    duration is the CUDA-event time of the loop alone (pr_info.ms_loop), averaged over
+    the timed solves.  The dominant kernel is the variant with the larger share of the
+    step's device time, reported on the R-MAT graph (the headline workload)."""
+    peak, peak_kind = peaks()
+    stats = {name: st for name, _, st in resident}
+    per = {}
+    for r in records:
+        per.setdefault((r["graph"], r["variant"]), []).append(r)
+    rows = []
+    for (gname, vname), rs in per.items():
+        st = stats[gname]
+        b_sweep = algorithmic_bytes(st["n"], st["nnz"], st["rowptr_bytes"])
+        launches = sum(r["iterations"] if vname == "jacobi" else 1 for r in rs)
+        loop_ms = sum(r["loop_ms"] for r in rs)
+        visits = sum(r["loop_edge_visits"] for r in rs)
+        alg_bytes = b_sweep * visits / st["nnz"]
+        achieved = alg_bytes / (loop_ms * 1e-3) / 1e9
+        per_visit = recorded_traffic(vname) if gname.startswith("rmat") else None
+        traffic = per_visit * visits / launches if per_visit else None
+        rows.append({"graph": gname, "variant": vname,
+                     "kernel": ("jacobi iteration (k_heavy_segments + k_rows)" if vname == "jacobi"
+                                else "k_nonblocking (persistent barrier-free sweeps)"),
+                     "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "bytes_per_launch": alg_bytes / launches, "ms_per_launch": loop_ms / launches,
+                     "launches": launches, "solve_ms": sum(r["time_to_tol_ms"] for r in rs)})
+    share = {}
+    for row in rows:
+        share[row["variant"]] = share.get(row["variant"], 0.0) + row["solve_ms"]
+    total = sum(share.values())
+    dominant = max(share, key=share.get)
+    head = [r for r in rows if r["variant"] == dominant and r["graph"].startswith("rmat")][0]
+    roofline = {k: head[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
+    roofline.update({"kernel": f"{head['kernel']} on {head['graph']}",
+                     "share_of_step": share[dominant] / total,
+                     "peak_source": f"{peak_kind} hbm_gbs (of measured)" if peak_kind == "measured"
+                     else f"{peak_kind} hbm_gbs (of fallback)",
+                     "bytes_per_launch": head["bytes_per_launch"],
+                     "ms_per_launch": head["ms_per_launch"],
+                     "frac_of_8tbs_spec": head["achieved"] / 8000.0})
+    return roofline, rows
 
 
 def kernels_executed(info, variant, has_segments, use_graph=True):
@@ -218,6 +284,34 @@ def run_reference(args):
     return 0
 
 
+def run_profile(args):
+    """A short, fixed workload for ncu: one graph resident on the device, a few synchronous
+    updates as separate launches (pr_iterate), or one barrier-free solve."""
+    import torch
+
+    import graphgen as gg
+    import paper_2109_09527_gb300 as pr
+    dev = torch.device("cuda", 0)
+    rp, ci = (gg.rmat(args.scale, 16, seed=SEED_RMAT) if args.graph == "rmat"
+              else gg.er_dangling(1 << args.er_log2, 16.0, 0.2, seed=SEED_ER))
+    g = pr.Graph(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev))
+    n = rp.size - 1
+    x = torch.full((n,), 1.0 / n, dtype=torch.float32, device=dev)
+    out = torch.empty_like(x)
+    for rep in range(2):
+        if args.profile == "jacobi":
+            info = pr.pr_iterate(g.handle, DAMPING, None, x, 3, out)
+        else:
+            _, info = pr.pr_solve(g.handle, DAMPING, TOL, MAX_ITER, pr.PR_NONBLOCKING, None, None, out)
+        torch.cuda.synchronize()
+        log(f"[profile] {args.graph} {args.profile} rep {rep}: {info.ms_device:.3f} ms, "
+            f"iterations {info.iterations}, residual {info.residual_l1:.3e}, loop "
+            f"{info.ms_loop:.3f} ms, loop edge visits {info.loop_edge_visits:.0f}, "
+            f"sources {kernel_sources_sha(args.profile)}")
+    g.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -228,7 +322,12 @@ def main():
     ap.add_argument("--er-log2", type=int, default=24)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", choices=["jacobi", "nonblocking"], default=None,
+                    help="run a short fixed workload for a profiler instead of the benchmark")
+    ap.add_argument("--graph", choices=["rmat", "er"], default="rmat")
     args = ap.parse_args()
+    if args.profile:
+        return run_profile(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -275,7 +374,9 @@ def main():
                     record.append({"graph": name, "variant": vname, "iterations": info.iterations,
                                    "time_to_tol_ms": info.ms_device, "residual_l1": info.residual_l1,
                                    "converged": bool(info.converged),
-                                   "gteps": info.edge_visits / (info.ms_device * 1e-3) / 1e9})
+                                   "gteps": info.edge_visits / (info.ms_device * 1e-3) / 1e9,
+                                   "loop_ms": info.ms_loop,
+                                   "loop_edge_visits": info.loop_edge_visits})
         return visits, launches
 
     for _ in range(args.warmup):
@@ -311,19 +412,7 @@ def main():
         visits = float(vt.item())
     value = visits / (ms * 1e-3) / 1e9
 
-    # roofline: one Jacobi iteration on the R-MAT graph, from the timed solves
-    rname, rg, rst = resident[0]
-    jac = [r for r in records if r["graph"] == rname and r["variant"] == "jacobi"]
-    it_ms = statistics.median(r["time_to_tol_ms"] / r["iterations"] for r in jac)
-    peak, peak_kind = peaks()
-    bytes_iter = algorithmic_bytes(rst["n"], rst["nnz"], rst["rowptr_bytes"])
-    achieved = bytes_iter / (it_ms * 1e-3) / 1e9
-    traffic = recorded_traffic()
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": f"jacobi iteration (k_heavy_segments + k_rows) on {rname}",
-                "peak_source": f"{peak_kind} hbm_gbs", "bytes_per_iteration": bytes_iter,
-                "ms_per_iteration": it_ms, "frac_of_8tbs_spec": achieved / 8000.0}
+    roofline, roofline_all = rooflines(records, resident)
 
     cases = {}
     for r in records:
@@ -401,7 +490,8 @@ def main():
                            "tol": TOL, "damping": DAMPING, "max_iter": MAX_ITER,
                            "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (colidx alone 1.07 GB per graph)"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "roofline_all": roofline_all, "cpu_baseline": cpu,
+                "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks, "cases": case_lines}
         print(json.dumps(line), flush=True)
     if dist:

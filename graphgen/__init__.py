@@ -52,6 +52,8 @@ def _load():
                                       ctypes.c_double, ctypes.c_void_p)
             lib.gg_rmat.restype = i64
             lib.gg_rmat.argtypes = [i32, i32, dbl, dbl, dbl, u64, i32, i32, vp, vp, i64]
+            lib.gg_rmat_n.restype = i64
+            lib.gg_rmat_n.argtypes = [i64, i32, dbl, dbl, dbl, u64, i32, i32, vp, vp, i64]
             lib.gg_er_dangling.restype = i64
             lib.gg_er_dangling.argtypes = [i64, dbl, dbl, u64, i32, vp, vp, i64]
             lib.gg_uniform.restype = None
@@ -84,6 +86,70 @@ def rmat(scale: int, edge_factor: int = 16, a: float = GRAPH500_ABC[0], b: float
     if nnz < 0:
         raise MemoryError(f"gg_rmat failed (code {nnz})")
     return rowptr, colidx[:nnz]
+
+
+def rmat_n(n: int, edge_factor: int = 8, a: float = GRAPH500_ABC[0], b: float = GRAPH500_ABC[1],
+           c: float = GRAPH500_ABC[2], seed: int = 1, permute: bool = True, nthreads: int = 0):
+    """R-MAT digraph on any n >= 2 vertices: edge_factor * n draws of the R-MAT recursion at
+    scale ceil(log2 n), a draw with an endpoint >= n redrawn from a retry stream, seeded
+    relabelling of range(n), no self-loops or duplicates."""
+    lib = _load()
+    cap = lib.gg_rmat_n(n, edge_factor, a, b, c, seed, int(permute), nthreads, None, None, 0)
+    if cap < 0:
+        raise ValueError(f"gg_rmat_n: bad arguments (code {cap})")
+    rowptr = np.empty(n + 1, dtype=np.int64)
+    colidx = np.empty(max(cap, 1), dtype=np.int32)
+    nnz = lib.gg_rmat_n(n, edge_factor, a, b, c, seed, int(permute), nthreads,
+                        _ptr(rowptr), _ptr(colidx), cap)
+    if nnz < 0:
+        raise MemoryError(f"gg_rmat_n failed (code {nnz})")
+    return rowptr, colidx[:nnz]
+
+
+def multi_rmat(count: int = 64, n_lo: float = 1e3, n_hi: float = 1e6, edge_factor: int = 8,
+               seed: int = 1):
+    """`count` independent R-MAT digraphs whose vertex counts are log-uniform in
+    [n_lo, n_hi] (rounded to integers), graph g drawn with seed (seed << 8) + g."""
+    u = uniform(seed, 1, count)
+    sizes = np.rint(n_lo * (n_hi / n_lo) ** u).astype(np.int64)
+    return [rmat_n(int(sizes[g]), edge_factor, seed=(seed << 8) + g) for g in range(count)]
+
+
+def block_diagonal(graphs):
+    """One in-edge CSR holding the graphs side by side (graph g's vertex v becomes
+    offsets[g] + v).  Returns (rowptr int64, colidx int32, offsets int64[count + 1])."""
+    offsets = np.zeros(len(graphs) + 1, dtype=np.int64)
+    for g, (rp, ci) in enumerate(graphs):
+        offsets[g + 1] = offsets[g] + (rp.size - 1)
+    nnz = sum(ci.size for _, ci in graphs)
+    rowptr = np.zeros(offsets[-1] + 1, dtype=np.int64)
+    colidx = np.empty(nnz, dtype=np.int32)
+    e = 0
+    for g, (rp, ci) in enumerate(graphs):
+        o = offsets[g]
+        rowptr[o + 1: offsets[g + 1] + 1] = e + rp[1:]
+        colidx[e: e + ci.size] = ci + o
+        e += ci.size
+    return rowptr, colidx, offsets
+
+
+def seed_teleports(n: int, k: int, per_column: int = 8, seed: int = 1):
+    """k personalisation vectors as an n x k row-major float32 matrix: column j is uniform
+    (1/per_column) over per_column distinct seeded random vertices."""
+    if per_column > n:
+        raise ValueError("more seed vertices than vertices")
+    t = np.zeros((n, k), dtype=np.float32)
+    for j in range(k):
+        picked = []
+        draw = 0
+        while len(picked) < per_column:
+            u = uniform(seed, 2 + j, per_column + draw)[draw:]
+            for v in np.minimum((u * n).astype(np.int64), n - 1):
+                if v not in picked and len(picked) < per_column:
+                    picked.append(int(v))
+            draw += per_column
+        t[picked, j] = 1.0 / per_column
+    return t
 
 
 def er_dangling(n: int, mean_deg: float = 16.0, frac_dangling: float = 0.2, seed: int = 1,

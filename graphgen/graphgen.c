@@ -138,12 +138,13 @@ static void gg_parallel(int nthreads, int64_t total, int64_t chunk, gg_task_fn f
 #define GG_MAX_OUT 256
 
 typedef struct {
-    int kind;                 /* 0 = R-MAT, 1 = ER with dangling */
+    int kind;                 /* 0 = R-MAT, 1 = ER with dangling, 2 = R-MAT on n vertices */
     int64_t n;
     int64_t units;            /* R-MAT: edges; ER: source vertices */
     /* R-MAT */
     int scale;
     uint64_t key_rmat;
+    uint64_t seed;            /* kind 2: keys of the retry streams */
     uint64_t t_a, t_ab, t_abc;
     const int32_t* perm;      /* NULL: no relabelling */
     /* ER */
@@ -157,8 +158,45 @@ typedef struct {
     int64_t* pre_edges;       /* per-chunk partial edge totals (pass 1) */
 } gg_src_t;
 
+/* One R-MAT draw (source s, destination d in [0, 2^scale)) from stream key. */
+static void gg_rmat_pair(const gg_src_t* g, uint64_t key, int64_t unit, uint64_t* ps, uint64_t* pd) {
+    uint64_t s = 0, d = 0;
+    int nd = (g->scale + 1) / 2;
+    for (int j = 0; j < nd; ++j) {
+        uint64_t r = gg_rand(key, (uint64_t)unit * (uint64_t)nd + (uint64_t)j);
+        for (int h = 0; h < 2; ++h) {
+            int level = 2 * j + h;
+            if (level >= g->scale) break;
+            uint64_t u = h == 0 ? (r >> 32) : (r & 0xFFFFFFFFull);
+            uint64_t sb, db;
+            if (u < g->t_a)        { sb = 0; db = 0; }
+            else if (u < g->t_ab)  { sb = 0; db = 1; }
+            else if (u < g->t_abc) { sb = 1; db = 0; }
+            else                   { sb = 1; db = 1; }
+            s = (s << 1) | sb;
+            d = (d << 1) | db;
+        }
+    }
+    *ps = s;
+    *pd = d;
+}
+
 /* Edges produced by one unit.  Returns how many were written to src/dst. */
 static int gg_unit_edges(const gg_src_t* g, int64_t unit, int32_t* src, int32_t* dst) {
+    if (g->kind == 2) {
+        /* R-MAT on n vertices, 2^(scale-1) < n <= 2^scale: a draw outside
+         * [0, n)^2 is redrawn from the next retry stream (up to 16 times). */
+        for (int t = 0; t < 16; ++t) {
+            uint64_t s, d;
+            gg_rmat_pair(g, gg_key(g->seed, 7 + 16 * (uint64_t)t), unit, &s, &d);
+            if ((int64_t)s >= g->n || (int64_t)d >= g->n) continue;
+            if (s == d) return 0;
+            if (g->perm) { s = (uint64_t)g->perm[s]; d = (uint64_t)g->perm[d]; }
+            src[0] = (int32_t)s; dst[0] = (int32_t)d;
+            return 1;
+        }
+        return 0;
+    }
     if (g->kind == 0) {
         uint64_t s = 0, d = 0;
         int nd = (g->scale + 1) / 2;
@@ -283,7 +321,7 @@ static int64_t gg_build(gg_src_t* g, int nthreads, int64_t* rowptr, int32_t* col
     g->rowstart = (int64_t*)malloc((size_t)(n + 1) * sizeof(int64_t));
     if (!g->count || !g->rowstart) { free(g->count); free(g->rowstart); return -1; }
     g->pre_edges = &pre;
-    int64_t chunk = g->kind == 0 ? (1 << 16) : (1 << 12);
+    int64_t chunk = g->kind != 1 ? (1 << 16) : (1 << 12);
     gg_parallel(nthreads, g->units, chunk, gg_pass_count, g);
     g->rowstart[0] = 0;
     for (int64_t v = 0; v < n; ++v) g->rowstart[v + 1] = g->rowstart[v] + g->count[v];
@@ -323,6 +361,38 @@ GG_API int64_t gg_rmat(int scale, int edge_factor, double a, double b, double c,
     memset(&g, 0, sizeof g);
     g.kind = 0; g.n = n; g.units = m; g.scale = scale;
     g.key_rmat = gg_key(seed, GG_STREAM_RMAT);
+    g.t_a = (uint64_t)(a * 4294967296.0);
+    g.t_ab = (uint64_t)((a + b) * 4294967296.0);
+    g.t_abc = (uint64_t)((a + b + c) * 4294967296.0);
+    int32_t* perm = NULL;
+    if (permute) {
+        perm = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+        if (!perm) return -1;
+        gg_permutation(seed, GG_STREAM_PERM, n, perm);
+        g.perm = perm;
+    }
+    int64_t nnz = gg_build(&g, gg_threads(nthreads), rowptr, colidx, cap);
+    free(perm);
+    return nnz;
+}
+
+/* R-MAT digraph on any n >= 2 vertices with edge_factor * n drawn edges: the
+ * power-of-two generator above at scale = ceil(log2 n), a draw with an
+ * endpoint >= n redrawn (at most 16 tries, then dropped), and a seeded
+ * relabelling of range(n) when permute != 0.  Same buffers and return codes
+ * as gg_rmat. */
+GG_API int64_t gg_rmat_n(int64_t n, int edge_factor, double a, double b, double c,
+                         uint64_t seed, int permute, int nthreads,
+                         int64_t* rowptr, int32_t* colidx, int64_t cap) {
+    if (n < 2 || n > ((int64_t)1 << 30) || edge_factor < 1) return -3;
+    int scale = 0;
+    while (((int64_t)1 << scale) < n) ++scale;
+    int64_t m = (int64_t)edge_factor * n;
+    if (!colidx) return m;
+    if (!(a >= 0 && b >= 0 && c >= 0 && a + b + c <= 1.0)) return -3;
+    gg_src_t g;
+    memset(&g, 0, sizeof g);
+    g.kind = 2; g.n = n; g.units = m; g.scale = scale; g.seed = seed;
     g.t_a = (uint64_t)(a * 4294967296.0);
     g.t_ab = (uint64_t)((a + b) * 4294967296.0);
     g.t_abc = (uint64_t)((a + b + c) * 4294967296.0);

@@ -88,6 +88,15 @@ typedef struct pr_info {
     double edge_visits;    /* edges gathered in total (GTEPS numerator)        */
     float ms_device;       /* device time of the call's work, CUDA events      */
     int32_t launches;      /* kernel launches the call enqueued                */
+    double loop_edge_visits; /* edges gathered inside the iteration loop alone:
+                              Jacobi, every iteration; non-blocking, the sweeps
+                              of the persistent launches (not the verifying
+                              updates)                                        */
+    float ms_loop;         /* device time of that loop alone (CUDA events on
+                              the call's stream around the while-graph or the
+                              host-driven iterations, or around each
+                              persistent launch, summed)                      */
+    int32_t reserved;      /* 0                                               */
 } pr_info;
 
 typedef struct pr_graph_stats {
@@ -184,6 +193,33 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
  *                         synchronous kernels copies into shared memory and
  *                         gathers from there (0..40960, default 0: off --
  *                         measured slower than letting L1 cache them).
+ *   PR_OPT_STAGED_TILES   how the light row tiles are gathered, bit 0 for the
+ *                         synchronous kernels, bit 1 for the barrier-free
+ *                         kernel: 0 = row by row (groups of lanes per row,
+ *                         two rows in flight per group; gathers through L1
+ *                         can hit the hub ranks), 1 = edge-parallel (the
+ *                         whole block issues every gather of the tile at
+ *                         once into a 24.6 KB shared-memory staging area,
+ *                         then reduces row by row).  Values 0..3.
+ *   PR_OPT_NB_HUBS        vertices at the front of the library's degree order
+ *                         (the hubs) whose ranks each block of the
+ *                         barrier-free kernel gathers from a shared-memory
+ *                         snapshot, re-read every few tiles, instead of from
+ *                         L2 (0..8192, rounded down to a multiple of 4;
+ *                         default 0).  Measured slower than
+ *                         PR_OPT_NB_L1_HUBS, which it takes precedence over.
+ *   PR_OPT_NB_L1_HUBS     vertices at the front of the degree order whose ranks
+ *                         the barrier-free kernel gathers with weak loads that
+ *                         L1 may serve (default 49152; 0 = every gather is a
+ *                         relaxed gpu-scope load served by L2).  Each block
+ *                         issues fence.acq_rel.gpu at the start of a sweep, so
+ *                         a cached hub rank is at most about one sweep old --
+ *                         a bounded delay, which the asynchronous iteration
+ *                         allows.  Under the PTX memory model these weak reads
+ *                         race with the owners' relaxed writes; the value read
+ *                         is an old or a new rank (aligned 32-bit accesses),
+ *                         and the verifying synchronous update certifies the
+ *                         result either way.  Set 0 for a race-free run.
  *   PR_OPT_INDEX64        1: keep 64-bit row offsets on the device even when
  *                         the edge count fits 32 bits (thread-local default
  *                         for the next pr_create_graph, set with g = NULL;
@@ -195,7 +231,41 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
 #define PR_OPT_INDEX64 4
 #define PR_OPT_HOT_VERTICES 5
 #define PR_OPT_HOT_CACHE 6
+#define PR_OPT_STAGED_TILES 7
+#define PR_OPT_NB_HUBS 8
+#define PR_OPT_NB_L1_HUBS 9
 PR_API pr_status pr_set_option(pr_graph* g, int key, int64_t value);
+
+/* Batched personalised PageRank: k independent solves on one graph, one per
+ * teleport vector (column), computed together as a sparse-times-dense
+ * product (each gathered edge moves a whole row of k ranks).  Column j is the
+ * fixed point of Eq. 1 with teleport t_j (the dangling mass of column j is
+ * still spread uniformly, so sum(x_j) = sum(t_j)), iterated synchronously
+ * (Alg. 1) until its L1 change is below tol; a converged column is frozen
+ * (its residual mask bit cleared) while the others continue, and the loop
+ * ends when every column is frozen or after max_iter iterations.  Each
+ * column is finally rescaled to sum(t_j) in FP64.
+ *   k              1 <= k <= 32 columns (rows are stored 32 wide on the
+ *                  device whatever k is).
+ *   teleport       host or device, n x k floats, row-major in the caller's
+ *                  vertex order (row v holds t_0(v) .. t_{k-1}(v)), each
+ *                  column non-negative with a positive sum; NULL = every
+ *                  column uniform 1/n.  Only the nonzeros are kept on the
+ *                  device.
+ *   x_out          host or device, n x k floats, row-major, caller's order.
+ *   col_residual   NULL or host array of k doubles: the last L1 change of
+ *                  each column.
+ *   col_iterations NULL or host array of k int32: iterations each column
+ *                  ran before it was frozen (or max_iter).
+ * info->iterations is the largest column count; info->converged is 1 only if
+ * every column converged; info->residual_l1 is the largest column residual;
+ * info->edge_visits counts edges x iterations (each visit moves k ranks).
+ * Returns PR_NOT_CONVERGED (outputs still written) if a column did not
+ * converge. */
+PR_API pr_status pr_solve_batched(pr_graph* g, float damping, double tol, int32_t max_iter,
+                                  int32_t k, const float* teleport, float* x_out,
+                                  double* col_residual, int32_t* col_iterations, pr_info* info,
+                                  void* stream);
 
 /* One synchronous PageRank update that allocates no memory -- for callers
  * that cannot call cudaMalloc (or anything that allocates) where they need an

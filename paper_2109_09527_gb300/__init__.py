@@ -44,6 +44,9 @@ PR_OPT_CTAS_PER_SM = 3
 PR_OPT_INDEX64 = 4
 PR_OPT_HOT_VERTICES = 5
 PR_OPT_HOT_CACHE = 6
+PR_OPT_STAGED_TILES = 7
+PR_OPT_NB_HUBS = 8
+PR_OPT_NB_L1_HUBS = 9
 
 LIB_PATH = _build.LIB_PATH
 
@@ -58,7 +61,9 @@ class pr_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("residual_l1", ctypes.c_double), ("sum_x", ctypes.c_double),
                 ("dangling_mass", ctypes.c_double), ("edge_visits", ctypes.c_double),
-                ("ms_device", ctypes.c_float), ("launches", ctypes.c_int32)]
+                ("ms_device", ctypes.c_float), ("launches", ctypes.c_int32),
+                ("loop_edge_visits", ctypes.c_double), ("ms_loop", ctypes.c_float),
+                ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -91,6 +96,8 @@ SIGNATURES = {
     "pr_graph_get_stats": (ctypes.c_int, [_VP, ctypes.POINTER(pr_graph_stats)]),
     "pr_set_option": (ctypes.c_int, [_VP, ctypes.c_int, _I64]),
     "pr_step_noalloc": (ctypes.c_int, [_I64, _VP, _VP, _VP, _F, _VP, _VP, _VP, _VP]),
+    "pr_solve_batched": (ctypes.c_int, [_VP, _F, _D, _I32, _I32, _VP, _VP, ctypes.POINTER(_D),
+                                        ctypes.POINTER(_I32), ctypes.POINTER(pr_info), _VP]),
     "pr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pr_last_error": (ctypes.c_char_p, []),
 }
@@ -199,6 +206,19 @@ def pr_iterate(g, damping, teleport, x_in, n_iter, x_out, stream=None):
     return info
 
 
+def pr_solve_batched(g, damping, tol, max_iter, k, teleport, x_out, stream=None):
+    """Returns (status, pr_info, col_residual[k], col_iterations[k]); status is PR_OK or
+    PR_NOT_CONVERGED.  teleport: n x k row-major float32 (host or device) or None."""
+    info = pr_info()
+    res = (ctypes.c_double * int(k))()
+    its = (ctypes.c_int32 * int(k))()
+    st = _check(load().pr_solve_batched(g, float(damping), float(tol), int(max_iter), int(k),
+                                        _addr(teleport, np.float32), _addr(x_out, np.float32),
+                                        res, its, ctypes.byref(info), _stream(stream)),
+                allow_not_converged=True)
+    return st, info, np.array(res[:], dtype=np.float64), np.array(its[:], dtype=np.int32)
+
+
 def pr_graph_get_stats(g):
     s = pr_graph_stats()
     _check(load().pr_graph_get_stats(g, ctypes.byref(s)))
@@ -270,6 +290,17 @@ class Graph:
         status, info = pr_solve(self.handle, damping, tol, max_iter, variant, teleport, x0, out,
                                 stream=stream)
         return out, info
+
+    def solve_batched(self, k, teleport=None, damping=0.85, tol=1e-6, max_iter=200, out=None,
+                      stream=None):
+        """k personalised PageRank vectors at once (teleport: n x k row-major, or None for
+        uniform).  `out` defaults to a host float32 numpy array of shape (n, k).
+        Returns (out, info, col_residual, col_iterations)."""
+        if out is None:
+            out = np.empty((self.n, k), dtype=np.float32)
+        status, info, res, its = pr_solve_batched(self.handle, damping, tol, max_iter, k, teleport,
+                                                  out, stream=stream)
+        return out, info, res, its
 
     def iterate(self, x_in, n_iter=1, damping=0.85, teleport=None, out=None, stream=None):
         """Exactly n_iter synchronous updates from x_in (no stopping test, no rescaling)."""

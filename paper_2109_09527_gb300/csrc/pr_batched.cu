@@ -1,0 +1,694 @@
+// pr_batched.cu -- batched personalised PageRank: k <= 32 teleport vectors
+// solved together on one graph (pr_solve_batched).
+//
+// Column j of the n x 32 rank matrix X is the PageRank vector of teleport t_j
+// (Eq. 1 with (1-d) t_j(v) in place of (1-d)/n; the dangling mass of column j
+// is still spread uniformly).  One synchronous iteration (Alg. 1, all
+// columns at once) is the sparse-times-dense product
+//
+//   S(v, :)  = sum_{e in row v} Y(colidx[e], :)          Y = X / outdeg (row-wise)
+//   X'(v, j) = (1-d) t_j(v) + d (S(v, j) + D_j / n)      for active columns j
+//   Y'(v, :) = X'(v, :) / outdeg(v)
+//   D'_j     = sum_{outdeg(v)=0} X'(v, j),  r_j = sum_v |X'(v, j) - X(v, j)|
+//
+// so every gathered edge moves one 128-byte row of Y (one coalesced load per
+// warp, lane j = column j) instead of one 4-byte value: the irregular access
+// of the single-vector solve is paid once for 32 solves.  A column whose L1
+// change r_j falls below tol is frozen (its bit in the active mask clears, its
+// ranks are copied forward unchanged) and the loop ends when no column is
+// active or after max_iter iterations.
+//
+// Three kernels per iteration, captured twice (ping-pong buffers) in a CUDA
+// graph under a conditional while node, like the single-vector solve:
+//   k_b_segments  heavy rows: a warp per 2048-edge segment sums 32 rows of Y
+//                 per step (32 independent 128-byte loads in flight per
+//                 warp) into a partial row P(segment, :);
+//   k_b_light     light rows: a warp per row tile walks the tile's edges in
+//                 windows of 32 (one coalesced colidx load, then 32
+//                 independent row loads), closing a row of S at each row end;
+//   k_b_update    element-wise over the n x 32 matrix: the update, the
+//                 quotient, and per-column Kahan dangling mass and L1 change,
+//                 reduced in a fixed block order by the last block, which
+//                 also clears converged columns and the loop condition.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "pr_tile.cuh"
+
+namespace prk {
+
+constexpr int kBK = 32;              // row width of the batched matrices (floats)
+constexpr int kBUpdateBlocksPerSM = 4;
+
+// Device state of a batched solve.
+struct BatchState {
+    double d;
+    double inv_n;
+    double tol;
+    int32_t max_iter;
+    int32_t iter;
+    int32_t done;
+    int32_t k;
+    uint32_t ticket;
+    uint32_t active;                 // bit j: column j still iterating
+    uint32_t error;                  // bit 0: a column with a non-positive or negative teleport
+    int32_t uniform;                 // 1: every column's teleport is 1/n
+    const int32_t* tptr;             // teleport nonzeros of each binned row (CSR), when !uniform
+    const int32_t* tcol;
+    const float* tval;
+    double D[kBK];                   // dangling mass of each column of the current input
+    double T[kBK];                   // teleport sum of each column
+    double resid[kBK];               // last L1 change of each column
+    double sum_x[kBK];
+    double scale[kBK];
+    int32_t col_iter[kBK];
+};
+
+struct BatchArgs {
+    const void* rowptr;
+    const int32_t* colidx;
+    const float* inv_out;
+    const int32_t* seg_row;
+    const int32_t* seg_ptr;
+    const Tile* tiles;
+    int64_t n;
+    int64_t n_heavy;                 // rows [0, n_heavy) are gathered in segments
+    int64_t zero_start;              // rows [zero_start, n) have no in-edges
+    int32_t n_seg;
+    int32_t n_tiles;
+    BatchState* state;
+    double* slots;                   // [grid][kBK][2] per-block column partials
+    float* P;                        // [n_seg][kBK] segment partial rows
+    float* S;                        // [n][kBK] gathered row sums of the light rows
+    cudaGraphConditionalHandle cond;
+    int32_t use_cond;
+    int32_t pad;
+};
+
+// done flag of the solve, read once per block.
+__device__ __forceinline__ int32_t batch_done(const BatchState* st) {
+    __shared__ int32_t done;
+    if (threadIdx.x == 0) done = *(const volatile int32_t*)&st->done;
+    __syncthreads();
+    const int32_t v = done;
+    __syncthreads();
+    return v;
+}
+
+// Heavy rows: one warp per segment; lane j accumulates column j.
+template <typename IdxT>
+__global__ void __launch_bounds__(kBlock) k_b_segments(BatchArgs a, const float* __restrict__ Y) {
+    if (batch_done(a.state)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t s = warp; s < a.n_seg; s += nwarp) {
+        const int32_t h = a.seg_row[s];
+        const int64_t re = row_at<IdxT>(a.rowptr, h + 1);
+        const int64_t e0 = row_at<IdxT>(a.rowptr, h) + (s - a.seg_ptr[h]) * (int64_t)kSegEdges;
+        const int64_t e1 = min(e0 + (int64_t)kSegEdges, re);
+        float acc = 0.f;
+        for (int64_t wb = e0; wb < e1; wb += 32) {
+            const int32_t c = wb + lane < e1 ? ld_stream(a.colidx + wb + lane) : -1;
+            float v[32];
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                const int32_t u = __shfl_sync(0xffffffffu, c, e);
+                v[e] = u >= 0 ? __ldg(Y + (int64_t)u * kBK + lane) : 0.f;
+            }
+#pragma unroll
+            for (int e = 0; e < 32; ++e) acc += v[e];
+        }
+        a.P[s * kBK + lane] = acc;
+    }
+}
+
+// Light rows: one warp per tile of rows with at least one in-edge each.  The
+// tile's edges are walked in windows of 32: lane e loads colidx of edge
+// wb + e, then every lane loads its column of the 32 source rows (32
+// independent loads), and the sums are closed at the row ends, which the
+// lanes hold for the next 32 rows (rend).
+template <typename IdxT>
+__global__ void __launch_bounds__(kBlock, 3) k_b_light(BatchArgs a, const float* __restrict__ Y) {
+    if (batch_done(a.state)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = warp; t < a.n_tiles; t += nwarp) {
+        const Tile tile = a.tiles[t];
+        if (tile.kind < 0) continue;    // heavy epilogue and empty rows: not gathered here
+        const int64_t r1 = tile.row_end;
+        const int64_t eend = row_at<IdxT>(a.rowptr, r1);
+        int64_t rbase = tile.row_begin;
+        int64_t rend = rbase + 1 + lane <= r1 ? row_at<IdxT>(a.rowptr, rbase + 1 + lane) : INT64_MAX;
+        int ri = 0;
+        int64_t cur_end = __shfl_sync(0xffffffffu, rend, 0);
+        float acc = 0.f;
+        for (int64_t wb = row_at<IdxT>(a.rowptr, rbase); wb < eend; wb += 32) {
+            const int32_t c = wb + lane < eend ? ld_stream(a.colidx + wb + lane) : -1;
+            float v[32];
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                const int32_t u = __shfl_sync(0xffffffffu, c, e);
+                v[e] = u >= 0 ? __ldg(Y + (int64_t)u * kBK + lane) : 0.f;
+            }
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                if (wb + e < eend) {
+                    acc += v[e];
+                    if (wb + e + 1 == cur_end) {      // row rbase + ri is complete
+                        a.S[(rbase + ri) * kBK + lane] = acc;
+                        acc = 0.f;
+                        if (++ri == 32) {
+                            rbase += 32;
+                            ri = 0;
+                            rend = rbase + 1 + lane <= r1 ? row_at<IdxT>(a.rowptr, rbase + 1 + lane)
+                                                          : INT64_MAX;
+                        }
+                        cur_end = __shfl_sync(0xffffffffu, rend, ri);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Per-column block partials of (a, b) -> slots; the last block gets the grid
+// totals of its own column in every lane-j thread of warp 0 (fixed order).
+__device__ __forceinline__ bool batch_columns_to_grid(double a, double b, double* slots, uint32_t* ticket,
+                                                      double* ta, double* tb) {
+    __shared__ double sa[kBlock / 32][32], sb[kBlock / 32][32];
+    __shared__ int last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    sa[warp][lane] = a;
+    sb[warp][lane] = b;
+    __syncthreads();
+    if (warp == 0) {
+        double A = 0.0, B = 0.0;
+        for (int w = 0; w < kBlock / 32; ++w) {
+            A += sa[w][lane];
+            B += sb[w][lane];
+        }
+        slots[((size_t)blockIdx.x * kBK + lane) * 2] = A;
+        slots[((size_t)blockIdx.x * kBK + lane) * 2 + 1] = B;
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    if (warp == 0) {
+        double A = 0.0, B = 0.0;
+        for (unsigned blk = 0; blk < gridDim.x; ++blk) {
+            A += __ldcg(slots + ((size_t)blk * kBK + lane) * 2);
+            B += __ldcg(slots + ((size_t)blk * kBK + lane) * 2 + 1);
+        }
+        *ta = A;
+        *tb = B;
+    }
+    return true;
+}
+
+// X' from S / P, per-column dangling mass and L1 change; lane j = column j.
+__global__ void __launch_bounds__(kBlock) k_b_update(BatchArgs a, const float* __restrict__ Xin,
+                                                     float* __restrict__ Xout, float* __restrict__ Yout) {
+    __shared__ float s_dshare[kBK];
+    __shared__ float s_base[kBK];
+    __shared__ uint32_t s_active;
+    __shared__ const int32_t* s_tptr;
+    __shared__ const int32_t* s_tcol;
+    __shared__ const float* s_tval;
+    __shared__ int32_t s_done;
+    __shared__ float s_d, s_omd;
+    BatchState* st = a.state;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {
+        const double d = st->d;
+        s_dshare[lane] = (float)(d * st->D[lane] * st->inv_n);
+        s_base[lane] = (float)((1.0 - d) * st->inv_n + d * st->D[lane] * st->inv_n);
+        if (lane == 0) {
+            s_active = st->active;
+            s_done = *(const volatile int32_t*)&st->done;
+            s_tptr = st->uniform ? nullptr : st->tptr;
+            s_tcol = st->tcol;
+            s_tval = st->tval;
+            s_d = (float)d;
+            s_omd = (float)(1.0 - d);
+        }
+    }
+    __syncthreads();
+    if (s_done) {
+        if (a.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0);
+        return;
+    }
+    const bool active = (s_active >> lane) & 1u;
+    const float dshare = s_dshare[lane], base = s_base[lane], d = s_d, omd = s_omd;
+    const int32_t* tptr = s_tptr;
+    Acc acc;
+    const int64_t rows_per_pass = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < a.n; v += rows_per_pass) {
+        float s = 0.f;
+        if (v < a.n_heavy) {
+            const int32_t q1 = a.seg_ptr[v + 1];
+            for (int32_t q = a.seg_ptr[v]; q < q1; ++q) s += __ldcg(a.P + (size_t)q * kBK + lane);
+        } else if (v < a.zero_start) {
+            s = __ldcs(a.S + (size_t)v * kBK + lane);
+        }
+        const float xo = __ldcs(Xin + (size_t)v * kBK + lane);
+        const float inv = __ldg(a.inv_out + v);
+        float xn = xo;
+        if (active) {
+            if (tptr) {
+                float tv = 0.f;
+                const int32_t p1 = tptr[v + 1];
+                for (int32_t p = tptr[v]; p < p1; ++p)
+                    if (s_tcol[p] == lane) tv = s_tval[p];
+                xn = fmaf(d, s, fmaf(omd, tv, dshare));
+            } else {
+                xn = fmaf(d, s, base);
+            }
+        }
+        __stcs(Xout + (size_t)v * kBK + lane, xn);
+        __stcs(Yout + (size_t)v * kBK + lane, xn * inv);
+        acc.r += fabsf(xn - xo);
+        if (inv == 0.f) acc.kahan(xn);
+    }
+    double R, Dn;
+    if (batch_columns_to_grid((double)acc.r, acc.mass(), a.slots, &st->ticket, &R, &Dn) && threadIdx.x < 32) {
+        const bool was_active = (s_active >> lane) & 1u;
+        st->D[lane] = Dn;
+        const int32_t it = st->iter + 1;
+        if (was_active) {
+            st->resid[lane] = R;
+            st->col_iter[lane] = it;
+        }
+        const bool stays = was_active && !(R < st->tol);
+        const uint32_t mask = __ballot_sync(0xffffffffu, stays);
+        if (lane == 0) {
+            st->active = mask;
+            st->iter = it;
+            const int done = mask == 0u || it >= st->max_iter;
+            st->done = done;
+            st->ticket = 0;
+            if (done && a.use_cond) cudaGraphSetConditional(a.cond, 0);
+        }
+    }
+}
+
+// X = T (binned order, 32 wide), Y = X / outdeg, per-column D and T; resets
+// the loop state.  t_dense: caller order, n x k, or NULL for uniform.
+__global__ void __launch_bounds__(kBlock) k_b_init(BatchArgs a, const float* __restrict__ t_dense,
+                                                   const int32_t* __restrict__ order, float* __restrict__ X,
+                                                   float* __restrict__ Y) {
+    BatchState* st = a.state;
+    const int lane = threadIdx.x & 31;
+    const int k = st->k;
+    const float tu = (float)st->inv_n;
+    double dsum = 0.0, tsum = 0.0;
+    bool bad = false;
+    const int64_t rows_per_pass = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < a.n; v += rows_per_pass) {
+        float tv = 0.f;
+        if (lane < k) {
+            tv = t_dense ? t_dense[(size_t)order[v] * k + lane] : tu;
+            if (!(tv >= 0.f)) bad = true;   // negative or NaN
+        }
+        const float inv = a.inv_out[v];
+        X[(size_t)v * kBK + lane] = tv;
+        Y[(size_t)v * kBK + lane] = tv * inv;
+        if (inv == 0.f) dsum += (double)tv;
+        tsum += (double)tv;
+    }
+    if (bad) atomicOr(&st->error, 1u);
+    double D, T;
+    if (batch_columns_to_grid(dsum, tsum, a.slots, &st->ticket, &D, &T) && threadIdx.x < 32) {
+        st->D[lane] = D;
+        st->T[lane] = T;
+        st->resid[lane] = INFINITY;
+        st->col_iter[lane] = 0;
+        if (lane < k && !(T > 0.0)) atomicOr(&st->error, 1u);
+        if (lane == 0) {
+            st->iter = 0;
+            st->done = 0;
+            st->active = k == 32 ? 0xffffffffu : ((1u << k) - 1u);
+            st->ticket = 0;
+        }
+    }
+}
+
+// Nonzeros of each binned row of the caller's teleport matrix.
+__global__ void k_b_tcount(const float* __restrict__ t_dense, const int32_t* __restrict__ order, int64_t n,
+                           int k, int64_t* __restrict__ counts) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const float* row = t_dense + (size_t)order[v] * k;
+        int64_t c = 0;
+        for (int j = 0; j < k; ++j) c += row[j] != 0.f;
+        counts[v] = c;
+    }
+}
+
+__global__ void k_b_tfill(const float* __restrict__ t_dense, const int32_t* __restrict__ order, int64_t n, int k,
+                          const int32_t* __restrict__ tptr, int32_t* __restrict__ tcol, float* __restrict__ tval) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const float* row = t_dense + (size_t)order[v] * k;
+        int32_t p = tptr[v];
+        for (int j = 0; j < k; ++j)
+            if (row[j] != 0.f) {
+                tcol[p] = j;
+                tval[p] = row[j];
+                ++p;
+            }
+    }
+}
+
+// Per-column sum of the final X (buffer iter & 1) and the rescaling factors.
+__global__ void __launch_bounds__(kBlock) k_b_sum(BatchArgs a, const float* __restrict__ X0,
+                                                  const float* __restrict__ X1) {
+    BatchState* st = a.state;
+    const float* X = (st->iter & 1) ? X1 : X0;
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    const int64_t rows_per_pass = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < a.n; v += rows_per_pass)
+        s += (double)X[(size_t)v * kBK + lane];
+    double S, unused;
+    if (batch_columns_to_grid(s, 0.0, a.slots, &st->ticket, &S, &unused) && threadIdx.x < 32) {
+        st->sum_x[lane] = S;
+        st->scale[lane] = S > 0.0 ? st->T[lane] / S : 1.0;
+        if (lane == 0) st->ticket = 0;
+    }
+}
+
+// out[v][j] = X[rank[v]][j] * scale_j, caller order, k columns.
+__global__ void k_b_unpermute(BatchArgs a, const float* __restrict__ X0, const float* __restrict__ X1,
+                              const int32_t* __restrict__ rank, float* __restrict__ out, int k) {
+    const BatchState* st = a.state;
+    const float* X = (st->iter & 1) ? X1 : X0;
+    const int64_t total = a.n * (int64_t)k;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+        const int64_t v = i / k;
+        const int j = (int)(i - v * k);
+        out[i] = X[(size_t)rank[v] * kBK + j] * (float)st->scale[j];
+    }
+}
+
+// ------------------------------------------------------------------ host --
+
+// Buffers of the batched solver, allocated on the first batched call.
+struct BatchCtx {
+    float* X[2] = {nullptr, nullptr};
+    float* Y[2] = {nullptr, nullptr};
+    float* S = nullptr;
+    float* P = nullptr;
+    int32_t* tptr = nullptr;
+    int32_t* tcol = nullptr;
+    float* tval = nullptr;
+    int64_t t_cap = 0;
+    int64_t* tcount = nullptr;
+    float* t_stage = nullptr;        // host teleports copied here
+    float* out_stage = nullptr;      // host outputs staged here
+    BatchState* state = nullptr;
+    BatchState* host_state = nullptr;
+    double* slots = nullptr;
+    int slot_blocks = 0;
+    int64_t zero_start = 0;
+    cudaGraphExec_t loop_exec = nullptr;
+};
+
+namespace {
+
+int g_occ_bseg = 0, g_occ_blight = 0;
+
+int batch_grid(const pr_graph* g, int64_t warps, int occ) {
+    const int64_t blocks = (warps + kWarps - 1) / kWarps;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)g->sm_count * occ));
+}
+
+BatchArgs batch_args(const pr_graph* g, const BatchCtx* b) {
+    BatchArgs a{};
+    a.rowptr = g->rowptr;
+    a.colidx = g->colidx;
+    a.inv_out = g->inv_out;
+    a.seg_row = g->seg_row;
+    a.seg_ptr = g->seg_ptr;
+    a.tiles = g->tiles;
+    a.n = g->n;
+    a.n_heavy = g->n_heavy;
+    a.zero_start = b->zero_start;
+    a.n_seg = (int32_t)g->n_seg;
+    a.n_tiles = (int32_t)g->n_tiles;
+    a.state = b->state;
+    a.slots = b->slots;
+    a.P = b->P;
+    a.S = b->S;
+    return a;
+}
+
+int update_grid(const pr_graph* g, const BatchCtx* b) {
+    const int64_t want = (g->n * 32 + kBlock - 1) / kBlock;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)b->slot_blocks));
+}
+
+template <typename IdxT>
+cudaError_t enqueue_batch_iteration(const pr_graph* g, const BatchCtx* b, const BatchArgs& a, int src,
+                                    cudaStream_t s) {
+    if (g->n_seg > 0)
+        k_b_segments<IdxT><<<batch_grid(g, g->n_seg, g_occ_bseg), kBlock, 0, s>>>(a, b->Y[src]);
+    k_b_light<IdxT><<<batch_grid(g, g->n_tiles, g_occ_blight), kBlock, 0, s>>>(a, b->Y[src]);
+    k_b_update<<<update_grid(g, b), kBlock, 0, s>>>(a, b->X[src], b->X[1 - src], b->Y[1 - src]);
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue_batch(const pr_graph* g, const BatchCtx* b, const BatchArgs& a, int src, cudaStream_t s) {
+    return g->idx64 ? enqueue_batch_iteration<int64_t>(g, b, a, src, s)
+                    : enqueue_batch_iteration<int32_t>(g, b, a, src, s);
+}
+
+pr_status ensure_batch(pr_graph* g) {
+    if (g->batch) return PR_OK;
+    BatchCtx* b = new BatchCtx();
+    g->batch = b;
+    const size_t mat = (size_t)(g->n + kPad) * kBK * sizeof(float);
+    for (int i = 0; i < 2; ++i) {
+        PRK_CHECK(dev_alloc(g, (void**)&b->X[i], mat));
+        PRK_CHECK(dev_alloc(g, (void**)&b->Y[i], mat));
+    }
+    PRK_CHECK(dev_alloc(g, (void**)&b->S, mat));
+    PRK_CHECK(dev_alloc(g, (void**)&b->P, (size_t)(g->n_seg + 1) * kBK * sizeof(float)));
+    PRK_CHECK(dev_alloc(g, (void**)&b->tptr, (size_t)(g->n + 1) * sizeof(int32_t)));
+    PRK_CHECK(dev_alloc(g, (void**)&b->tcount, (size_t)(g->n + 1) * sizeof(int64_t)));
+    PRK_CHECK(dev_alloc(g, (void**)&b->state, sizeof(BatchState)));
+    PRK_CHECK(cudaMallocHost((void**)&b->host_state, sizeof(BatchState)));
+    b->slot_blocks = g->sm_count * kBUpdateBlocksPerSM;
+    PRK_CHECK(dev_alloc(g, (void**)&b->slots, (size_t)b->slot_blocks * kBK * 2 * sizeof(double)));
+    b->zero_start = g->n;
+    for (const Tile& t : g->host_tiles)
+        if (t.kind == kTileZero) {
+            b->zero_start = std::min<int64_t>(b->zero_start, t.row_begin);
+        }
+    if (g_occ_bseg == 0) {
+        int o = 0;
+        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_b_segments<int32_t>, kBlock, 0));
+        g_occ_bseg = std::max(1, o);
+        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_b_light<int32_t>, kBlock, 0));
+        g_occ_blight = std::max(1, o);
+    }
+    return PR_OK;
+}
+
+pr_status build_batch_graph(pr_graph* g, BatchCtx* b) {
+    cudaGraph_t graph = nullptr;
+    PRK_CHECK(cudaGraphCreate(&graph, 0));
+    struct Guard {
+        cudaGraph_t gr;
+        ~Guard() { if (gr) cudaGraphDestroy(gr); }
+    } guard{graph};
+    cudaGraphConditionalHandle handle;
+    PRK_CHECK(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = handle;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    PRK_CHECK(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &p));
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    BatchArgs a = batch_args(g, b);
+    a.cond = handle;
+    a.use_cond = 1;
+    PRK_CHECK(cudaStreamBeginCaptureToGraph(g->capture_stream, body, nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeThreadLocal));
+    cudaError_t e1 = enqueue_batch(g, b, a, 0, g->capture_stream);
+    cudaError_t e2 = cudaSuccess;
+    if (e1 == cudaSuccess) e2 = enqueue_batch(g, b, a, 1, g->capture_stream);
+    cudaGraph_t captured = nullptr;
+    cudaError_t e3 = cudaStreamEndCapture(g->capture_stream, &captured);
+    PRK_CHECK(e1);
+    PRK_CHECK(e2);
+    PRK_CHECK(e3);
+    PRK_CHECK(cudaGraphInstantiate(&b->loop_exec, graph, 0));
+    return PR_OK;
+}
+
+// The caller's teleport matrix as a CSR of its nonzeros over binned rows.
+pr_status build_teleport_csr(pr_graph* g, BatchCtx* b, const float* t_dev, int k, cudaStream_t s) {
+    const int grid = small_grid(g);
+    k_b_tcount<<<grid, kBlock, 0, s>>>(t_dev, g->order, g->n, k, b->tcount);
+    PRK_CHECK(cudaGetLastError());
+    PRK_CHECK(scan_counts_i32(b->tcount, g->n, b->tptr, s));
+    int32_t nnz = 0;
+    PRK_CHECK(cudaMemcpyAsync(&nnz, b->tptr + g->n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    PRK_CHECK(cudaStreamSynchronize(s));
+    if (nnz > b->t_cap) {
+        if (b->tcol) cudaFree(b->tcol);
+        if (b->tval) cudaFree(b->tval);
+        b->tcol = nullptr;
+        b->tval = nullptr;
+        b->t_cap = 0;
+        PRK_CHECK(dev_alloc(g, (void**)&b->tcol, (size_t)nnz * sizeof(int32_t)));
+        PRK_CHECK(dev_alloc(g, (void**)&b->tval, (size_t)nnz * sizeof(float)));
+        b->t_cap = nnz;
+    }
+    k_b_tfill<<<grid, kBlock, 0, s>>>(t_dev, g->order, g->n, k, b->tptr, b->tcol, b->tval);
+    PRK_CHECK(cudaGetLastError());
+    return PR_OK;
+}
+
+}  // namespace
+
+void destroy_batch(pr_graph* g) {
+    BatchCtx* b = g->batch;
+    if (!b) return;
+    void* dev[] = {b->X[0], b->X[1], b->Y[0], b->Y[1], b->S, b->P, b->tptr, b->tcol, b->tval,
+                   b->tcount, b->t_stage, b->out_stage, b->state, b->slots};
+    for (void* p : dev)
+        if (p) cudaFree(p);
+    if (b->host_state) cudaFreeHost(b->host_state);
+    if (b->loop_exec) cudaGraphExecDestroy(b->loop_exec);
+    delete b;
+    g->batch = nullptr;
+}
+
+}  // namespace prk
+
+using namespace prk;
+
+extern "C" pr_status pr_solve_batched(pr_graph* g, float damping, double tol, int32_t max_iter, int32_t k,
+                                      const float* teleport, float* x_out, double* col_residual,
+                                      int32_t* col_iterations, pr_info* info, void* stream) {
+    if (!g) return fail(PR_ERR_INVALID_ARG, "pr_solve_batched: graph is NULL");
+    if (!(damping >= 0.0f && damping < 1.0f)) return fail(PR_ERR_INVALID_ARG, "damping must be in [0, 1)");
+    if (!(tol > 0.0) || !std::isfinite(tol)) return fail(PR_ERR_INVALID_ARG, "tol must be a positive finite number");
+    if (max_iter < 1) return fail(PR_ERR_INVALID_ARG, "max_iter must be >= 1");
+    if (k < 1 || k > kBK) return fail(PR_ERR_INVALID_ARG, "k must be in [1, 32]");
+    if (!x_out) return fail(PR_ERR_INVALID_ARG, "x_out is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    pr_status rc = ensure_batch(g);
+    if (rc != PR_OK) return rc;
+    BatchCtx* b = g->batch;
+    const size_t nk = (size_t)g->n * (size_t)k;
+
+    // teleport: device pointer in place, host memory staged
+    const float* t_dev = nullptr;
+    if (teleport) {
+        if (is_device_pointer(teleport)) {
+            t_dev = teleport;
+        } else {
+            if (!b->t_stage) PRK_CHECK(dev_alloc(g, (void**)&b->t_stage, (size_t)(g->n + kPad) * kBK * sizeof(float)));
+            PRK_CHECK(cudaMemcpyAsync(b->t_stage, teleport, nk * sizeof(float), cudaMemcpyHostToDevice, s));
+            t_dev = b->t_stage;
+        }
+        if ((rc = build_teleport_csr(g, b, t_dev, k, s)) != PR_OK) return rc;
+    }
+    const bool out_dev = is_device_pointer(x_out);
+    float* out = x_out;
+    if (!out_dev) {
+        if (!b->out_stage) PRK_CHECK(dev_alloc(g, (void**)&b->out_stage, (size_t)(g->n + kPad) * kBK * sizeof(float)));
+        out = b->out_stage;
+    }
+
+    BatchState* hs = b->host_state;
+    memset(hs, 0, sizeof(BatchState));
+    hs->d = (double)damping;
+    hs->inv_n = 1.0 / (double)g->n;
+    hs->tol = tol;
+    hs->max_iter = max_iter;
+    hs->k = k;
+    hs->uniform = teleport ? 0 : 1;
+    hs->tptr = b->tptr;
+    hs->tcol = b->tcol;
+    hs->tval = b->tval;
+    PRK_CHECK(cudaEventRecord(g->ev_start, s));
+    PRK_CHECK(cudaMemcpyAsync(b->state, hs, sizeof(BatchState), cudaMemcpyHostToDevice, s));
+    BatchArgs a = batch_args(g, b);
+    int launches = 0;
+    k_b_init<<<update_grid(g, b), kBlock, 0, s>>>(a, t_dev, g->order, b->X[0], b->Y[0]);
+    ++launches;
+    PRK_CHECK(cudaGetLastError());
+    PRK_CHECK(cudaEventRecord(g->ev_loop0, s));
+    if (g->use_graph) {
+        if (!b->loop_exec && (rc = build_batch_graph(g, b)) != PR_OK) return rc;
+        PRK_CHECK(cudaGraphLaunch(b->loop_exec, s));
+        ++launches;
+    } else {
+        // host-driven: iterations in chunks of 8 (the kernels return at once
+        // when the state says done), then read the flag
+        for (int32_t it = 0; it < max_iter;) {
+            const int c = std::min<int32_t>(8, max_iter - it);
+            for (int i = 0; i < c; ++i) {
+                PRK_CHECK(enqueue_batch(g, b, a, (it + i) & 1, s));
+                launches += g->n_seg > 0 ? 3 : 2;
+            }
+            it += c;
+            PRK_CHECK(cudaMemcpyAsync(hs, b->state, sizeof(BatchState), cudaMemcpyDeviceToHost, s));
+            PRK_CHECK(cudaStreamSynchronize(s));
+            if (hs->done) break;
+        }
+    }
+    PRK_CHECK(cudaEventRecord(g->ev_loop1, s));
+    k_b_sum<<<update_grid(g, b), kBlock, 0, s>>>(a, b->X[0], b->X[1]);
+    k_b_unpermute<<<small_grid(g), kBlock, 0, s>>>(a, b->X[0], b->X[1], g->rank, out, k);
+    launches += 2;
+    PRK_CHECK(cudaGetLastError());
+    PRK_CHECK(cudaEventRecord(g->ev_stop, s));
+    if (!out_dev) PRK_CHECK(cudaMemcpyAsync(x_out, out, nk * sizeof(float), cudaMemcpyDeviceToHost, s));
+    PRK_CHECK(cudaMemcpyAsync(hs, b->state, sizeof(BatchState), cudaMemcpyDeviceToHost, s));
+    PRK_CHECK(cudaStreamSynchronize(s));
+    if (hs->error)
+        return fail(PR_ERR_INVALID_ARG, "pr_solve_batched: a teleport column has a negative entry or a zero sum");
+    float ms = 0.f, ms_loop = 0.f;
+    PRK_CHECK(cudaEventElapsedTime(&ms, g->ev_start, g->ev_stop));
+    PRK_CHECK(cudaEventElapsedTime(&ms_loop, g->ev_loop0, g->ev_loop1));
+    double worst = 0.0;
+    int conv = 1;
+    for (int j = 0; j < k; ++j) {
+        worst = std::max(worst, hs->resid[j]);
+        if (!(hs->resid[j] < tol)) conv = 0;
+        if (col_residual) col_residual[j] = hs->resid[j];
+        if (col_iterations) col_iterations[j] = hs->col_iter[j];
+    }
+    if (info) {
+        info->iterations = hs->iter;
+        info->converged = conv;
+        info->residual_l1 = worst;
+        double sx = 0.0;
+        for (int j = 0; j < k; ++j) sx += hs->sum_x[j];
+        info->sum_x = sx;
+        double dm = 0.0;
+        for (int j = 0; j < k; ++j) dm += hs->D[j];
+        info->dangling_mass = dm;
+        info->edge_visits = (double)hs->iter * (double)g->nnz;
+        info->ms_device = ms;
+        info->launches = launches;
+        info->loop_edge_visits = info->edge_visits;
+        info->ms_loop = ms_loop;
+        info->reserved = 0;
+    }
+    return conv ? PR_OK : PR_NOT_CONVERGED;
+}

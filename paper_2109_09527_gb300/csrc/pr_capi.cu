@@ -59,6 +59,7 @@ using namespace prk;
 
 extern "C" pr_status pr_destroy_graph(pr_graph* g) {
     if (!g) return PR_OK;
+    destroy_batch(g);
     void* dev[] = {g->rowptr, g->colidx, g->inv_out, g->order, g->rank, g->x[0], g->x[1],
                    g->y[0], g->y[1], g->teleport, g->stage, g->seg_row, g->seg_ptr, g->seg_sum,
                    g->tiles, g->state, g->slots, g->nb_items, g->nb_slots,
@@ -76,6 +77,8 @@ extern "C" pr_status pr_destroy_graph(pr_graph* g) {
     if (g->capture_stream) cudaStreamDestroy(g->capture_stream);
     if (g->ev_start) cudaEventDestroy(g->ev_start);
     if (g->ev_stop) cudaEventDestroy(g->ev_stop);
+    if (g->ev_loop0) cudaEventDestroy(g->ev_loop0);
+    if (g->ev_loop1) cudaEventDestroy(g->ev_loop1);
     delete g;
     if (first != cudaSuccess) return cuda_fail(first, "pr_destroy_graph: cudaFree");
     return PR_OK;
@@ -138,6 +141,29 @@ extern "C" pr_status pr_set_option(pr_graph* g, int key, int64_t value) {
                     cudaGraphExecDestroy(ex);
                     ex = nullptr;
                 }
+            return PR_OK;
+        case PR_OPT_STAGED_TILES:
+            if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_STAGED_TILES needs a graph");
+            if (value < 0 || value > 3)
+                return fail(PR_ERR_INVALID_ARG, "PR_OPT_STAGED_TILES must be in [0, 3]");
+            g->staged_tiles = (int)value;
+            for (auto& ex : g->loop_exec)
+                if (ex) {
+                    cudaGraphExecDestroy(ex);
+                    ex = nullptr;
+                }
+            return PR_OK;
+        case PR_OPT_NB_HUBS:
+            if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_NB_HUBS needs a graph");
+            if (value < 0 || value > kNbHubsMax)
+                return fail(PR_ERR_INVALID_ARG, "PR_OPT_NB_HUBS must be in [0, 8192]");
+            g->nb_hubs = value;
+            return PR_OK;
+        case PR_OPT_NB_L1_HUBS:
+            if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_NB_L1_HUBS needs a graph");
+            if (value < 0 || value > 0x7fffffffLL)
+                return fail(PR_ERR_INVALID_ARG, "PR_OPT_NB_L1_HUBS must be in [0, 2^31-1]");
+            g->nb_l1_hubs = value;
             return PR_OK;
         case PR_OPT_INDEX64:
             if (g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_INDEX64 is set with g = NULL (it applies to the next pr_create_graph)");

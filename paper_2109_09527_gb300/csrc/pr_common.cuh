@@ -30,9 +30,17 @@
 
 namespace prk {
 
+struct BatchCtx;   // buffers of the batched solver (pr_batched.cu)
+
 constexpr int kBlock = 256;              // threads of a tile group (and of the small kernels)
 constexpr int kWarps = kBlock / 32;
 constexpr int kIterBlock = 256;          // threads per block of the Jacobi iteration kernels
+// Blocks per SM the gather kernels are compiled for (__launch_bounds__): with
+// 256 threads, 4 blocks allow 64 registers a thread, 6 allow 40, 8 allow 32.
+#ifndef PRK_GATHER_MIN_BLOCKS
+#define PRK_GATHER_MIN_BLOCKS 4
+#endif
+constexpr int kGatherMinBlocks = PRK_GATHER_MIN_BLOCKS;
 constexpr int kHotCacheMax = 40960;      // largest shared-memory copy of y's hot prefix (160 KB)
 constexpr int kTileEdgesMax = 6144;      // edges of a light tile
 constexpr int kTileRowsMax = 2048;       // rows of a light tile
@@ -42,6 +50,16 @@ constexpr int kPad = 64;                 // spare elements after every device ar
 constexpr int kTileHeavy = -1;           // tile kind: epilogue of heavy rows
 constexpr int kTileZero = -2;            // tile kind: rows without in-edges
 constexpr int kMaxBins = 42;
+#ifndef PRK_DEFAULT_STAGED
+#define PRK_DEFAULT_STAGED 0
+#endif
+constexpr int kDefaultStaged = PRK_DEFAULT_STAGED;
+constexpr int kNbHubsMax = 8192;         // largest hub snapshot of the barrier-free kernel (32 KB)
+#ifndef PRK_DEFAULT_NB_HUBS
+#define PRK_DEFAULT_NB_HUBS 0
+#endif
+constexpr int kDefaultNbHubs = PRK_DEFAULT_NB_HUBS;
+constexpr int64_t kDefaultNbL1Hubs = 49152;   // barrier-free hub gathers through L1  // light-tile mode per variant (PR_OPT_STAGED_TILES)
 constexpr int64_t kDefaultHot = (4LL << 28) | 49152;  // gather L1 policy 4, 48K hot ids (see ld_gather)   // degree bins: 40 power-of-two classes + zero + spare
 
 // A tile of the row kernel: rows [row_begin, row_end) of one bin.  kind >= 0
@@ -95,7 +113,7 @@ struct IterArgs {
     int32_t use_cond;            // 1: the kernel runs inside the while-graph
     int32_t hot;                 // L1 policy of the global gathers (ld_gather)
     int32_t hot_n;               // ids [0, hot_n) of y are cached in shared memory
-    int32_t pad2;
+    int32_t staged;              // 1: light tiles gathered edge-parallel (process_staged_tile)
 };
 
 }  // namespace prk
@@ -112,6 +130,9 @@ struct pr_graph {
     bool use_graph = true;
     int64_t hot_vertices = prk::kDefaultHot;  // see ld_gather
     int64_t hot_cache = 0;                    // size of the shared-memory copy of y's prefix (off)
+    int64_t nb_hubs = prk::kDefaultNbHubs;    // hub snapshot of the barrier-free kernel (PR_OPT_NB_HUBS)
+    int64_t nb_l1_hubs = prk::kDefaultNbL1Hubs;  // weak L1-cached hub gathers (PR_OPT_NB_L1_HUBS)
+    int staged_tiles = prk::kDefaultStaged;   // bit 0: Jacobi, bit 1: barrier-free (see PR_OPT_STAGED_TILES)
 
     void* rowptr = nullptr;
     int32_t* colidx = nullptr;
@@ -140,6 +161,8 @@ struct pr_graph {
     int nb_grid = 0;
     int64_t nb_items_count = 0;
     std::vector<int64_t> nb_cta_edges;  // edges owned by each block (items dealt round-robin)
+    std::vector<int64_t> nb_item_edges; // edges of each work item
+    std::vector<int64_t> nb_seg_edges;  // edges of each heavy-row segment
     std::vector<int64_t> bin_start;     // first binned row of each degree bin (+ n)
     std::vector<prk::Tile> host_tiles;  // copy of tiles
 
@@ -157,6 +180,10 @@ struct pr_graph {
     cudaStream_t capture_stream = nullptr;
     cudaEvent_t ev_start = nullptr;
     cudaEvent_t ev_stop = nullptr;
+    cudaEvent_t ev_loop0 = nullptr;  // around the iteration loop alone
+    cudaEvent_t ev_loop1 = nullptr;
+
+    prk::BatchCtx* batch = nullptr;  // batched solver (built on first use)
 };
 
 namespace prk {
@@ -167,7 +194,7 @@ pr_status fail(pr_status s, const std::string& msg);
 pr_status cuda_fail(cudaError_t e, const char* what);
 
 // Grid size of the persistent per-iteration kernels for graph g.
-int row_grid(const pr_graph* g);
+int row_grid(const pr_graph* g, bool staged);
 int seg_grid(const pr_graph* g);
 
 // Device allocation recorded in g->device_bytes.
@@ -196,6 +223,13 @@ void launch_init(const pr_graph* g, const IterArgs& a, const float* t_dev, const
                  cudaStream_t s);
 void launch_finalize(const pr_graph* g, const IterArgs& a, float* out, bool renormalise,
                      cudaStream_t s, int* launches);
+
+// Exclusive scan of count int64 values into int32 offsets[count + 1] (device
+// arrays); synchronises the stream before its temporaries are freed.
+cudaError_t scan_counts_i32(const int64_t* counts, int64_t count, int32_t* offsets, cudaStream_t st);
+
+// Frees the batched solver's buffers (nothing if it was never used).
+void destroy_batch(pr_graph* g);
 
 pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_iter,
                             const float* teleport, const float* x0, float* x_out, pr_info* info,

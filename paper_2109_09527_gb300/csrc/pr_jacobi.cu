@@ -47,9 +47,9 @@ __device__ __forceinline__ void load_hot(const float* __restrict__ y, int32_t ho
 }
 
 template <typename IdxT>
-__global__ void __launch_bounds__(kIterBlock) k_heavy_segments(IterArgs a, const float* __restrict__ y) {
+__global__ void __launch_bounds__(kIterBlock, kGatherMinBlocks) k_heavy_segments(IterArgs a, const float* __restrict__ y) {
     extern __shared__ __align__(16) float hot_sm[];
-    if (*(volatile int32_t*)&a.state->done) return;
+    if (block_state(a.state).done) return;
     load_hot(y, a.hot_n, hot_sm);
     RowCtx c{};
     c.hot = a.hot;
@@ -90,25 +90,26 @@ __global__ void __launch_bounds__(kIterBlock) k_heavy_segments(IterArgs a, const
 // One block of kIterBlock threads per SM; each 256-thread group walks its own
 // tiles (round-robin over all groups of the grid) and shares the block's copy
 // of the hot prefix of y.
-template <typename IdxT, bool kUniform>
-__global__ void __launch_bounds__(kIterBlock) k_rows(IterArgs a, const float* __restrict__ x_in,
+template <typename IdxT, bool kUniform, bool kStaged>
+__global__ void __launch_bounds__(kIterBlock, kGatherMinBlocks) k_rows(IterArgs a, const float* __restrict__ x_in,
                                                      const float* __restrict__ y_in,
                                                      float* __restrict__ x_out, float* __restrict__ y_out) {
     extern __shared__ __align__(16) float hot_sm[];
     SolveState* st = a.state;
-    if (*(volatile int32_t*)&st->done) {
+    const StateView sv = block_state(st);
+    if (sv.done) {
         // A skipped iteration inside the while-graph keeps the loop closed.
         if (a.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0);
         return;
     }
     load_hot(y_in, a.hot_n, hot_sm);
-    const double d = st->d;
-    const double share = st->D * st->inv_n;   // D/n
+    const double d = sv.d;
+    const double share = sv.D * sv.inv_n;   // D/n
     RowCtx c;
     c.d = (float)d;
     c.one_m_d = (float)(1.0 - d);
     c.d_share = (float)(d * share);
-    c.base = (float)((1.0 - d) * st->inv_n + d * share);
+    c.base = (float)((1.0 - d) * sv.inv_n + d * share);
     c.hot = a.hot;
     c.hot_n = a.hot_n;
     c.hot_sm = hot_sm;
@@ -120,8 +121,16 @@ __global__ void __launch_bounds__(kIterBlock) k_rows(IterArgs a, const float* __
     for (int t = group; t < a.n_tiles; t += gridDim.x * groups) {
         const Tile tile = a.tiles[t];
         if (tile.kind >= 0) {
-            process_light_tile<IdxT, kUniform, false>(tile, a.rowptr, a.colidx, a.inv_out, a.teleport,
-                                                       x_in, y_in, x_out, y_out, c, acc, tid);
+            if (kStaged) {
+                if (!process_staged_tile<IdxT, kUniform, false>(tile, a.rowptr, a.colidx, a.inv_out,
+                                                                a.teleport, x_in, y_in, x_out, y_out, c,
+                                                                acc, tid, hot_sm + a.hot_n) &&
+                    threadIdx.x == 0)
+                    atomicOr(&st->error, 1u);
+            } else {
+                process_light_tile<IdxT, kUniform, false>(tile, a.rowptr, a.colidx, a.inv_out, a.teleport,
+                                                           x_in, y_in, x_out, y_out, c, acc, tid);
+            }
         } else if (tile.kind == kTileZero) {
             process_zero_tile<kUniform, false>(tile, a.inv_out, a.teleport, x_in, x_out, y_out, c, acc, tid);
         } else {  // heavy rows: sum of the segment partials
@@ -158,7 +167,7 @@ __global__ void __launch_bounds__(kBlock) k_init(IterArgs a, const float* __rest
                                                  float* __restrict__ t_bin, float* __restrict__ x,
                                                  float* __restrict__ y) {
     SolveState* st = a.state;
-    const float tu = (float)st->inv_n;
+    const float tu = (float)block_state(st).inv_n;
     double dsum = 0.0, tsum = 0.0;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
     for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < a.n; i += stride) {
@@ -188,7 +197,7 @@ __global__ void __launch_bounds__(kBlock) k_init(IterArgs a, const float* __rest
 __global__ void __launch_bounds__(kBlock) k_sum_x(IterArgs a, const float* __restrict__ x0,
                                                   const float* __restrict__ x1) {
     SolveState* st = a.state;
-    const float* x = (st->iter & 1) ? x1 : x0;
+    const float* x = (block_state(st).iter & 1) ? x1 : x0;
     double s = 0.0;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
     for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < a.n; i += stride) s += (double)x[i];
@@ -205,9 +214,9 @@ __global__ void __launch_bounds__(kBlock) k_unpermute(IterArgs a, const float* _
                                                       const float* __restrict__ x1,
                                                       const int32_t* __restrict__ rank,
                                                       float* __restrict__ out, int apply_scale) {
-    const SolveState* st = a.state;
-    const float* x = (st->iter & 1) ? x1 : x0;
-    const float sc = apply_scale ? (float)st->scale : 1.0f;
+    const StateView sv = block_state(a.state);
+    const float* x = (sv.iter & 1) ? x1 : x0;
+    const float sc = apply_scale ? (float)sv.scale : 1.0f;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
     for (int64_t v = (int64_t)blockIdx.x * kBlock + threadIdx.x; v < a.n; v += stride)
         out[v] = x[rank[v]] * sc;
@@ -217,6 +226,7 @@ __global__ void __launch_bounds__(kBlock) k_unpermute(IterArgs a, const float* _
 
 namespace {
 int g_occ_rows = 0;
+int g_occ_rows_staged = 0;
 int g_occ_seg = 0;
 }  // namespace
 
@@ -240,6 +250,7 @@ IterArgs make_args(const pr_graph* g, bool uniform) {
     a.hot = (int32_t)(((g->hot_vertices >> 28) << 28) |
                       std::min<int64_t>(g->hot_vertices & 0x0fffffff, g->n));
     a.hot_n = (int32_t)(std::min<int64_t>(g->hot_cache, g->n) & ~(int64_t)3);
+    a.staged = g->staged_tiles & 1;
     return a;
 }
 
@@ -253,16 +264,23 @@ template <typename IdxT>
 cudaError_t enqueue_iteration_t(const pr_graph* g, const IterArgs& a, int src, bool uniform,
                                 cudaStream_t s, int* launches) {
     const size_t hot = (size_t)a.hot_n * sizeof(float);
+    const size_t rows_smem = hot + (a.staged ? (size_t)kStageFloats * sizeof(float) : 0);
     if (g->n_seg > 0) {
         k_heavy_segments<IdxT><<<seg_grid(g), kIterBlock, hot, s>>>(a, g->y[src]);
         ++*launches;
     }
-    if (uniform)
-        k_rows<IdxT, true><<<row_grid(g), kIterBlock, hot, s>>>(a, g->x[src], g->y[src], g->x[1 - src],
-                                                                g->y[1 - src]);
-    else
-        k_rows<IdxT, false><<<row_grid(g), kIterBlock, hot, s>>>(a, g->x[src], g->y[src], g->x[1 - src],
-                                                                 g->y[1 - src]);
+    const int grid = row_grid(g, a.staged != 0);
+    const float* xi = g->x[src];
+    const float* yi = g->y[src];
+    float* xo = g->x[1 - src];
+    float* yo = g->y[1 - src];
+    if (a.staged) {
+        if (uniform) k_rows<IdxT, true, true><<<grid, kIterBlock, rows_smem, s>>>(a, xi, yi, xo, yo);
+        else k_rows<IdxT, false, true><<<grid, kIterBlock, rows_smem, s>>>(a, xi, yi, xo, yo);
+    } else {
+        if (uniform) k_rows<IdxT, true, false><<<grid, kIterBlock, rows_smem, s>>>(a, xi, yi, xo, yo);
+        else k_rows<IdxT, false, false><<<grid, kIterBlock, rows_smem, s>>>(a, xi, yi, xo, yo);
+    }
     ++*launches;
     return cudaGetLastError();
 }
@@ -362,8 +380,9 @@ void launch_finalize(const pr_graph* g, const IterArgs& a, float* out, bool reno
     ++*launches;
 }
 
-int row_grid(const pr_graph* g) {
-    int per_sm = g->ctas_per_sm > 0 ? std::min(g->ctas_per_sm, g_occ_rows) : g_occ_rows;
+int row_grid(const pr_graph* g, bool staged) {
+    const int occ = staged ? g_occ_rows_staged : g_occ_rows;
+    int per_sm = g->ctas_per_sm > 0 ? std::min(g->ctas_per_sm, occ) : occ;
     int64_t blocks = (int64_t)g->sm_count * per_sm;
     blocks = std::min<int64_t>(blocks, std::max<int64_t>(1, g->n_tiles));
     return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)g->slot_capacity));
@@ -394,26 +413,36 @@ pr_status alloc_solver(pr_graph* g) {
     PRK_CHECK(cudaStreamCreateWithFlags(&g->capture_stream, cudaStreamNonBlocking));
     if (g_occ_rows == 0) {
         const int hot = (int)(kHotCacheMax * sizeof(float));
-        PRK_CHECK(cudaFuncSetAttribute(k_rows<int32_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, hot));
-        PRK_CHECK(cudaFuncSetAttribute(k_rows<int32_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, hot));
-        PRK_CHECK(cudaFuncSetAttribute(k_rows<int64_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, hot));
-        PRK_CHECK(cudaFuncSetAttribute(k_rows<int64_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, hot));
-        PRK_CHECK(cudaFuncSetAttribute(k_heavy_segments<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, hot));
-        PRK_CHECK(cudaFuncSetAttribute(k_heavy_segments<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, hot));
-        // These kernels need almost no shared memory: give the SRAM to L1, which
-        // caches the gathered ranks of the hub vertices.
-        PRK_CHECK(cudaFuncSetAttribute(k_rows<int32_t, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
-        PRK_CHECK(cudaFuncSetAttribute(k_rows<int32_t, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
-        PRK_CHECK(cudaFuncSetAttribute(k_rows<int64_t, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
-        PRK_CHECK(cudaFuncSetAttribute(k_rows<int64_t, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
-        PRK_CHECK(cudaFuncSetAttribute(k_heavy_segments<int32_t>, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
-        PRK_CHECK(cudaFuncSetAttribute(k_heavy_segments<int64_t>, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
+        const int rows = (int)((kHotCacheMax + kStageFloats) * sizeof(float));
+        const void* row_kernels[] = {
+            (const void*)k_rows<int32_t, true, false>, (const void*)k_rows<int32_t, false, false>,
+            (const void*)k_rows<int64_t, true, false>, (const void*)k_rows<int64_t, false, false>,
+            (const void*)k_rows<int32_t, true, true>,  (const void*)k_rows<int32_t, false, true>,
+            (const void*)k_rows<int64_t, true, true>,  (const void*)k_rows<int64_t, false, true>};
+        const void* seg_kernels[] = {(const void*)k_heavy_segments<int32_t>,
+                                     (const void*)k_heavy_segments<int64_t>};
+        // These kernels need little shared memory: the preferred carveout 0
+        // gives the rest of the SRAM to L1, which caches the hub ranks.
+        // The staged kernels (the last four) hold a 24.6 KB staging area per
+        // block: carve out enough shared memory for four blocks per SM.
+        for (int i = 0; i < 8; ++i) {
+            PRK_CHECK(cudaFuncSetAttribute(row_kernels[i], cudaFuncAttributeMaxDynamicSharedMemorySize, rows));
+            PRK_CHECK(cudaFuncSetAttribute(row_kernels[i], cudaFuncAttributePreferredSharedMemoryCarveout,
+                                           i < 4 ? 0 : 50));
+        }
+        for (const void* k : seg_kernels) {
+            PRK_CHECK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, hot));
+            PRK_CHECK(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
+        }
         int occ = 0;
-        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rows<int32_t, false>, kIterBlock, 0));
-        g_occ_rows = std::max(1, occ);
+        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rows<int32_t, false, true>, kIterBlock,
+                                                                 kStageFloats * sizeof(float)));
+        g_occ_rows_staged = std::max(1, occ);
+        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rows<int32_t, false, false>, kIterBlock, 0));
         int occ_seg = 0;
         PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_seg, k_heavy_segments<int32_t>, kIterBlock, 0));
         g_occ_seg = std::max(1, occ_seg);
+        g_occ_rows = std::max(1, occ);   // last: marks the block as done
     }
     return PR_OK;
 }
@@ -464,6 +493,7 @@ pr_status run_jacobi(pr_graph* g, float damping, double tol, int32_t max_iter, c
     launch_init(g, a, t_dev, x0_dev, s);
     ++launches;
     PRK_CHECK(cudaGetLastError());
+    PRK_CHECK(cudaEventRecord(g->ev_loop0, s));
 
     if (allow_graph && g->use_graph) {
         const int kind = uniform ? 0 : 1;
@@ -506,6 +536,7 @@ pr_status run_jacobi(pr_graph* g, float damping, double tol, int32_t max_iter, c
         cudaEventDestroy(ev[1]);
         if (loop_rc != PR_OK) return loop_rc;
     }
+    PRK_CHECK(cudaEventRecord(g->ev_loop1, s));
 
     launch_finalize(g, a, out, renormalise, s, &launches);
     PRK_CHECK(cudaGetLastError());
@@ -516,8 +547,9 @@ pr_status run_jacobi(pr_graph* g, float damping, double tol, int32_t max_iter, c
     PRK_CHECK(cudaStreamSynchronize(s));
     if (hs->error)
         return fail(PR_ERR_CUDA, "internal error: a row tile exceeded its shared-memory staging area");
-    float ms = 0.f;
+    float ms = 0.f, ms_loop = 0.f;
     PRK_CHECK(cudaEventElapsedTime(&ms, g->ev_start, g->ev_stop));
+    PRK_CHECK(cudaEventElapsedTime(&ms_loop, g->ev_loop0, g->ev_loop1));
     const bool converged = hs->resid < tol;
     if (info) {
         info->iterations = hs->iter;
@@ -528,6 +560,9 @@ pr_status run_jacobi(pr_graph* g, float damping, double tol, int32_t max_iter, c
         info->edge_visits = (double)hs->iter * (double)g->nnz;
         info->ms_device = ms;
         info->launches = launches;
+        info->loop_edge_visits = info->edge_visits;
+        info->ms_loop = ms_loop;
+        info->reserved = 0;
     }
     return converged ? PR_OK : PR_NOT_CONVERGED;
 }

@@ -1,8 +1,8 @@
 // pr_nonblocking.cu -- barrier-free, in-place PageRank: the GPU form of No-Sync (Alg. 3).
 //
-// One persistent launch.  Each block owns a fixed set of work items -- row
-// tiles and segments of heavy rows, dealt round-robin so that every block gets
-// the same mix (static allocation, as the paper's threads own fixed
+// One persistent launch.  Each block owns a fixed set of work -- segments of
+// heavy rows (a warp each) and row tiles, both dealt round-robin so that every
+// block gets the same mix (static allocation, as the paper's threads own fixed
 // partitions) -- and sweeps it repeatedly:
 //
 //   for each owned row v:  x(v) <- (1-d) t(v) + d (sum_{u->v} y(u) + share)
@@ -14,8 +14,9 @@
 // written with relaxed gpu-scope atomics (the read-write races of Alg. 3 made
 // well-defined), and the only shared bookkeeping is
 //
-//   S     the running rank mass of vertices with out-edges, updated with one
-//         FP64 atomic add of each block's change per sweep.  The dangling
+//   S     the running rank mass of vertices with out-edges: every warp adds
+//         its change with one FP64 atomic add every few work items and reads
+//         the new value back.  The dangling
 //         share is share = (T - S)/n with T = sum(t): equal to D/n at the fixed
 //         point, and, unlike a running dangling mass, it puts back the rank
 //         mass that in-place updates gain or lose, which keeps in-place sweeps
@@ -35,19 +36,29 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "pr_tile.cuh"
 
 namespace prk {
 
-// Work item of a heavy row (Tile fields reused): row_begin = the row,
-// row_end = a segment id (kSegEdges edges of the row), pad = 1 when the
-// segment is the row's last one, whose item also updates the row.
-constexpr int kItemSegment = -3;
-
-// Items a block processes between two publications of its mass change.
-constexpr int kPublishEvery = 4;
+// Tiles a warp processes between two publications of its mass change (and
+// between two refreshes of the hub snapshot); segment rounds between two
+// publications and between two refreshes.
+#ifndef PRK_NB_PUBLISH_EVERY
+#define PRK_NB_PUBLISH_EVERY 4
+#endif
+#ifndef PRK_NB_SEG_PUBLISH
+#define PRK_NB_SEG_PUBLISH 2
+#endif
+#ifndef PRK_NB_HUB_REFRESH
+#define PRK_NB_HUB_REFRESH 4
+#endif
+constexpr int kPublishEvery = PRK_NB_PUBLISH_EVERY;
+constexpr int kSegPublish = PRK_NB_SEG_PUBLISH;
+constexpr int kHubRefresh = PRK_NB_HUB_REFRESH;
+constexpr int kNbBlock = kBlock; // threads per block of the persistent kernel
 
 struct NbArgs {
     const void* rowptr;
@@ -57,6 +68,8 @@ struct NbArgs {
     const Tile* items;
     int32_t n_items;
     const int32_t* seg_ptr;      // first segment of each heavy row
+    const int32_t* seg_row;      // heavy row of each segment
+    int64_t n_seg;
     float* seg_sum;              // latest partial sum of each segment
     double* slots;               // [grid]
     double* scalars;             // [0] running non-dangling mass S
@@ -71,104 +84,174 @@ struct NbArgs {
     long long* trace;            // NULL, or 8 values per block (see k_nonblocking)
     float* history;              // NULL, or the L1 change of block 0's first 256 sweeps
     int32_t dangling_form;       // 1: share = (T - S)/n (default); 0: running dangling mass
-    int32_t pad2;
+    int32_t hub_n;               // ids [0, hub_n) are gathered from the block's snapshot
+    int32_t l1_hubs;             // ids [hub_n, l1_hubs) are gathered with weak L1-cached loads
+    int32_t pad3;
 };
 
-// One segment of a heavy row, gathered by the whole block (at most three
-// 16-byte colidx loads and twelve gathers per thread, all issued before use).
-// The partial sum is published with a relaxed store; the row's last segment
-// then sums the latest partials of all the row's segments -- some may be a
-// sweep old, which an asynchronous iteration allows -- and updates the row.
+// The block's snapshot of y[0, hub_n): the hub ranks, which the degree
+// binning puts first.  In power-law graphs a few 32-byte sectors of y take a
+// large share of all gathers (the top sector of an R-MAT graph about 0.5%); in
+// place they cannot be cached in L1, and served from L2 they would queue on a
+// single L2 slice.  The snapshot is re-read (relaxed 16-byte loads) at the
+// start of each phase of a sweep and every few tiles, so a hub value is at most
+// that many tiles old -- a bounded delay, which the asynchronous iteration
+// allows (Eq. 7).
+__device__ __forceinline__ void refresh_hubs(const float* y, float* sm, int32_t hub_n) {
+    __syncthreads();   // every reader of the old copy is done
+    float4* dst = reinterpret_cast<float4*>(sm);
+    for (int i = threadIdx.x; i < (hub_n >> 2); i += blockDim.x) dst[i] = ld_relaxed4(y + 4 * i);
+    __syncthreads();
+}
+
+// One 2048-edge segment of a heavy row, gathered by one warp: 16-byte colidx
+// loads, sixteen gathers in flight per lane, no block barrier.  The partial
+// sum is published with a relaxed store; the warp that gathers a row's last
+// segment then sums the latest partials of all the row's segments -- some may
+// be a sweep old, which an asynchronous iteration allows -- and updates the row.
 template <typename IdxT, bool kUniform>
-__device__ __forceinline__ void heavy_segment(const Tile& item, const NbArgs& a, const RowCtx& c, Acc& acc) {
-    const int64_t r = item.row_begin;
-    const int32_t sid = item.row_end;
-    const int32_t s0 = a.seg_ptr[r], s1 = a.seg_ptr[r + 1];
-    const int64_t rb = row_at<IdxT>(a.rowptr, r), re = row_at<IdxT>(a.rowptr, r + 1);
-    const int64_t e0 = rb + (int64_t)(sid - s0) * kSegEdges;
+__device__ __forceinline__ void warp_segment(int64_t sid, const NbArgs& a, const RowCtx& c, Acc& acc) {
+    const int lane = threadIdx.x & 31;
+    const int32_t h = a.seg_row[sid];
+    const int32_t s0 = a.seg_ptr[h], s1 = a.seg_ptr[h + 1];
+    const int64_t re = row_at<IdxT>(a.rowptr, h + 1);
+    const int64_t e0 = row_at<IdxT>(a.rowptr, h) + (sid - s0) * (int64_t)kSegEdges;
     const int64_t e1 = min(e0 + (int64_t)kSegEdges, re);
     const int64_t a0 = e0 & ~(int64_t)3;
-    int4 cv[3];
+    float v = 0.f;
+    for (int64_t base = a0; base < e1; base += 512) {
+        int4 cv[4];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        const int64_t p = a0 + 4 * (int64_t)threadIdx.x + (int64_t)j * 4 * kBlock;
-        cv[j] = p < e1 ? ld_stream4(a.colidx + p) : make_int4(0, 0, 0, 0);
-    }
-    float g[12];
+        for (int j = 0; j < 4; ++j) {
+            const int64_t p = base + 128 * j + 4 * lane;
+            cv[j] = p < e1 ? ld_stream4(a.colidx + p) : make_int4(0, 0, 0, 0);
+        }
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        const int64_t p = a0 + 4 * (int64_t)threadIdx.x + (int64_t)j * 4 * kBlock;
-        g[4 * j + 0] = (p + 0 >= e0 && p + 0 < e1) ? ld_relaxed(a.y + cv[j].x) : 0.f;
-        g[4 * j + 1] = (p + 1 >= e0 && p + 1 < e1) ? ld_relaxed(a.y + cv[j].y) : 0.f;
-        g[4 * j + 2] = (p + 2 >= e0 && p + 2 < e1) ? ld_relaxed(a.y + cv[j].z) : 0.f;
-        g[4 * j + 3] = (p + 3 >= e0 && p + 3 < e1) ? ld_relaxed(a.y + cv[j].w) : 0.f;
+        for (int j = 0; j < 4; ++j) {
+            const int64_t p = base + 128 * j + 4 * lane;
+            const float g0 = (p + 0 >= e0 && p + 0 < e1) ? Mem<true>::gather(a.y, cv[j].x, c) : 0.f;
+            const float g1 = (p + 1 >= e0 && p + 1 < e1) ? Mem<true>::gather(a.y, cv[j].y, c) : 0.f;
+            const float g2 = (p + 2 >= e0 && p + 2 < e1) ? Mem<true>::gather(a.y, cv[j].z, c) : 0.f;
+            const float g3 = (p + 3 >= e0 && p + 3 < e1) ? Mem<true>::gather(a.y, cv[j].w, c) : 0.f;
+            v += (g0 + g1) + (g2 + g3);
+        }
     }
-    float v = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) +
-              ((g[8] + g[9]) + (g[10] + g[11]));
-    v = block_sum(v);
-    if (threadIdx.x == 0) st_relaxed(a.seg_sum + sid, v);
-    if (item.pad) {
+    v = warp_sum(v);
+    if (lane == 0) st_relaxed(a.seg_sum + sid, v);
+    if (sid + 1 == s1) {
         float p = 0.f;
-        for (int32_t j = s0 + threadIdx.x; j < s1; j += kBlock) p += (j == sid) ? v : ld_relaxed(a.seg_sum + j);
-        p = block_sum(p);
-        if (threadIdx.x == 0) {
-            const float tv = kUniform ? 0.f : ld_stream(a.teleport + r);
-            row_update<kUniform, true>(r, p, Mem<true>::load_x(a.x + r), ld_stream(a.inv_out + r), tv, c,
-                                       a.x, a.y, acc);
+        for (int32_t j = s0 + lane; j < s1; j += 32) p += (j == sid) ? v : ld_relaxed(a.seg_sum + j);
+        p = warp_sum(p);
+        if (lane == 0) {
+            const float tv = kUniform ? 0.f : ld_stream(a.teleport + h);
+            row_update<kUniform, true>(h, p, Mem<true>::load_x(a.x + h), ld_stream(a.inv_out + h), tv, c, a.x,
+                                       a.y, acc);
         }
     }
 }
 
-template <typename IdxT, bool kUniform>
-__global__ void __launch_bounds__(kBlock) k_nonblocking(NbArgs a) {
-    const SolveState* st = a.state;
-    const double d = st->d, inv_n = st->inv_n, T = st->t_sum;
-    // Static, interleaved ownership: block b owns items b, b + G, b + 2G, ...
-    const int32_t i0 = blockIdx.x, i1 = a.n_items, istep = gridDim.x;
+template <typename IdxT, bool kUniform, bool kStaged>
+__global__ void __launch_bounds__(kNbBlock, kGatherMinBlocks) k_nonblocking(NbArgs a) {
+    // dynamic shared memory: the hub snapshot (hub_n floats), then the staging
+    // area of kStaged tiles (kStageFloats floats)
+    extern __shared__ __align__(16) float nb_smem[];
+    float* hub_sm = nb_smem;
+    float* nb_stage = nb_smem + a.hub_n;
+    const StateView sv = block_state(a.state);
+    const double d = sv.d, inv_n = sv.inv_n, T = sv.t_sum;
+    // Static, interleaved ownership: each 256-thread group of the grid owns
+    // tiles g, g + #groups, ...; each warp owns segments w, w + #warps, ...
+    const int groups = blockDim.x / kBlock;
+    const int tid = threadIdx.x & (kBlock - 1);
+    const int32_t i0 = blockIdx.x * groups + threadIdx.x / kBlock, i1 = a.n_items;
+    const int32_t istep = gridDim.x * groups;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t wstep = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int32_t sweeps = 0;
     long long t_start = 0;
     if (a.trace && threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
     double last_R = 0.0, last_est = 0.0;
+    long long seg_ns = 0;
     Acc acc;
     while (sweeps < a.max_sweeps) {
         RowCtx c;
         c.d = (float)d;
         c.one_m_d = (float)(1.0 - d);
-        c.hot = 0;
-        c.hot_n = 0;
-        c.hot_sm = nullptr;
+        // ids below l1_hubs are gathered with weak loads that L1 may serve; the
+        // fence at the start of every sweep makes this SM's next weak loads
+        // observe at least the values L2 held at the fence, which bounds the age
+        // of a cached hub rank to about one sweep of this SM's blocks
+        c.hot = a.l1_hubs;
+        if (a.l1_hubs > 0 && threadIdx.x == 0) asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        c.hot_n = a.hub_n;
+        c.hot_sm = hub_sm;
         float r_sweep = 0.f;
-        int since = kPublishEvery;
-        for (int32_t it = i0; it < i1 || since > 0; it += istep) {
-            if (since == kPublishEvery || it >= i1) {
-                // Publish the mass change of the items done since the last
-                // publication and re-read the running mass, so that the share
-                // used next matches the ranks the other blocks can already see.
-                double dS = acc.mass(), dD = (double)acc.dd;
-                block_sum2(dS, dD);
-                if (threadIdx.x == 0) {
-                    if (dS != 0.0) atomicAdd(a.scalars, dS);
-                    if (!a.dangling_form && dD != 0.0) atomicAdd(a.scalars + 1, dD);
-                }
-                r_sweep += acc.r;
-                acc = Acc();
-                if (it >= i1) break;
-                const double share = a.dangling_form ? (T - ld_relaxed(a.scalars)) * inv_n
-                                                     : ld_relaxed(a.scalars + 1) * inv_n;
-                c.d_share = (float)(d * share);
-                c.base = (float)((1.0 - d) * inv_n + d * share);
+        // Each warp publishes the mass change of its own rows since its last
+        // publication (one FP64 atomic add by lane 0) and re-reads the running
+        // mass, so that the share it uses next matches the ranks the other
+        // blocks can already see.  No block barrier is involved.
+        auto warp_publish = [&](bool publish_mass) {
+            double dS = warp_sum(acc.mass());
+            double dD = warp_sum((double)acc.dd);
+            double m = 0.0;
+            if ((threadIdx.x & 31) == 0) {
+                if (publish_mass && dS != 0.0) atomicAdd(a.scalars, dS);
+                if (publish_mass && !a.dangling_form && dD != 0.0) atomicAdd(a.scalars + 1, dD);
+                m = a.dangling_form ? ld_relaxed(a.scalars) : ld_relaxed(a.scalars + 1);
+            }
+            m = __shfl_sync(0xffffffffu, m, 0);
+            r_sweep += acc.r;
+            acc = Acc();
+            const double share = a.dangling_form ? (T - m) * inv_n : m * inv_n;
+            c.d_share = (float)(d * share);
+            c.base = (float)((1.0 - d) * inv_n + d * share);
+        };
+        warp_publish(false);
+        long long t_seg0 = 0;
+        if (a.trace && threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_seg0));
+        // heavy-row segments, a warp each, in rounds of one segment per warp of
+        // the grid (the same round count in every block, so the hub snapshot
+        // can be refreshed between rounds)
+        if (a.hub_n) refresh_hubs(a.y, hub_sm, a.hub_n);
+        const int64_t rounds = (a.n_seg + wstep - 1) / wstep;
+        for (int64_t rd = 0; rd < rounds; ++rd) {
+            const int64_t sid = wid + rd * wstep;
+            if (sid < a.n_seg) warp_segment<IdxT, kUniform>(sid, a, c, acc);
+            if ((rd % kSegPublish) == kSegPublish - 1) warp_publish(true);
+            if (a.hub_n && (rd % kHubRefresh) == kHubRefresh - 1) refresh_hubs(a.y, hub_sm, a.hub_n);
+        }
+        warp_publish(true);
+        if (a.trace) {
+            __syncthreads();   // diagnostics only: time the segment phase of the whole block
+            if (threadIdx.x == 0) {
+                long long t_seg1;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_seg1));
+                seg_ns += t_seg1 - t_seg0;
+            }
+        }
+        // row tiles, the whole block each
+        if (a.hub_n) refresh_hubs(a.y, hub_sm, a.hub_n);
+        int since = 0;
+        for (int32_t it = i0; it < i1; it += istep) {
+            const Tile item = a.items[it];
+            if (kStaged && item.kind >= 0) {
+                if (!process_staged_tile<IdxT, kUniform, true>(item, a.rowptr, a.colidx, a.inv_out,
+                                                               a.teleport, a.x, a.y, a.x, a.y, c, acc, tid,
+                                                               nb_stage) &&
+                    threadIdx.x == 0)
+                    atomicOr(&a.state->error, 1u);
+            } else if (item.kind >= 0)
+                process_light_tile<IdxT, kUniform, true>(item, a.rowptr, a.colidx, a.inv_out, a.teleport,
+                                                          a.x, a.y, a.x, a.y, c, acc, tid);
+            else
+                process_zero_tile<kUniform, true>(item, a.inv_out, a.teleport, a.x, a.x, a.y, c, acc, tid);
+            if (++since == kPublishEvery) {
+                warp_publish(true);
+                if (a.hub_n) refresh_hubs(a.y, hub_sm, a.hub_n);
                 since = 0;
             }
-            const Tile item = a.items[it];
-            if (item.kind >= 0)
-                process_light_tile<IdxT, kUniform, true>(item, a.rowptr, a.colidx, a.inv_out, a.teleport,
-                                                          a.x, a.y, a.x, a.y, c, acc, threadIdx.x);
-            else if (item.kind == kTileZero)
-                process_zero_tile<kUniform, true>(item, a.inv_out, a.teleport, a.x, a.x, a.y, c, acc, threadIdx.x);
-            else
-                heavy_segment<IdxT, kUniform>(item, a, c, acc);
-            ++since;
         }
+        warp_publish(true);
         ++sweeps;
         double R = (double)r_sweep, unused1 = 0.0;
         block_sum2(R, unused1);
@@ -177,7 +260,7 @@ __global__ void __launch_bounds__(kBlock) k_nonblocking(NbArgs a) {
             if (a.history && blockIdx.x == 0 && sweeps <= 256) a.history[sweeps - 1] = (float)R;
         }
         double est = 0.0, unused = 0.0;
-        for (int i = threadIdx.x; i < (int)gridDim.x; i += kBlock) est += ld_relaxed(a.slots + i);
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) est += ld_relaxed(a.slots + i);
         block_sum2(est, unused);
         last_R = R;
         last_est = est;
@@ -185,7 +268,7 @@ __global__ void __launch_bounds__(kBlock) k_nonblocking(NbArgs a) {
     }
     if (a.trace && threadIdx.x == 0) {
         // per block: sweeps, start/end (ns, %globaltimer), last sweep change, last estimate,
-        // first item, item count
+        // first item, tile count, ns spent in the segment phase
         long long t_end;
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
         long long* tr = a.trace + 8 * blockIdx.x;
@@ -195,8 +278,8 @@ __global__ void __launch_bounds__(kBlock) k_nonblocking(NbArgs a) {
         tr[3] = __double_as_longlong(last_R);
         tr[4] = __double_as_longlong(last_est);
         tr[5] = i0;
-        tr[6] = (i1 - i0 + istep - 1) / istep;
-        tr[7] = 0;
+        tr[6] = (i1 - blockIdx.x * groups + istep - 1) / istep;
+        tr[7] = seg_ns;
     }
     if (threadIdx.x == 0) {
         a.block_sweeps[blockIdx.x] = sweeps;
@@ -230,65 +313,78 @@ __global__ void __launch_bounds__(kBlock) k_mass_split(IterArgs a, const float* 
 }
 
 template <typename IdxT>
-__global__ void k_item_edges(const void* rowptr, const int32_t* seg_ptr, const Tile* items,
-                             int64_t count, int64_t* edges) {
+__global__ void k_item_edges(const void* rowptr, const Tile* items, int64_t count, int64_t* edges) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
-        const Tile t = items[i];
-        if (t.kind == kItemSegment) {
-            const int64_t rb = row_at<IdxT>(rowptr, t.row_begin), re = row_at<IdxT>(rowptr, t.row_begin + 1);
-            const int64_t e0 = rb + (int64_t)(t.row_end - seg_ptr[t.row_begin]) * kSegEdges;
-            edges[i] = min(e0 + (int64_t)kSegEdges, re) - e0;
-        } else {
-            edges[i] = row_at<IdxT>(rowptr, t.row_end) - row_at<IdxT>(rowptr, t.row_begin);
-        }
-    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
+        edges[i] = row_at<IdxT>(rowptr, items[i].row_end) - row_at<IdxT>(rowptr, items[i].row_begin);
 }
 
 namespace {
 
-int g_occ_nb = 0;
-
-
-template <typename IdxT, bool kUniform>
+template <typename IdxT, bool kUniform, bool kStaged>
 void* nb_kernel() {
-    return (void*)k_nonblocking<IdxT, kUniform>;
+    return (void*)k_nonblocking<IdxT, kUniform, kStaged>;
 }
 
-void* pick_kernel(const pr_graph* g, bool uniform) {
-    if (g->idx64) return uniform ? nb_kernel<int64_t, true>() : nb_kernel<int64_t, false>();
-    return uniform ? nb_kernel<int32_t, true>() : nb_kernel<int32_t, false>();
+template <typename IdxT>
+void* pick_kernel_t(bool uniform, bool staged) {
+    if (staged) return uniform ? nb_kernel<IdxT, true, true>() : nb_kernel<IdxT, false, true>();
+    return uniform ? nb_kernel<IdxT, true, false>() : nb_kernel<IdxT, false, false>();
 }
 
-// Work items and the per-block partition, built on first use.
+void* pick_kernel(const pr_graph* g, bool uniform, bool staged) {
+    return g->idx64 ? pick_kernel_t<int64_t>(uniform, staged) : pick_kernel_t<int32_t>(uniform, staged);
+}
+
+// Blocks of `kernel` that fit on one SM with `smem` bytes of dynamic shared
+// memory (cached per kernel and size).  The carveout is left to the driver:
+// asking for a small shared-memory carveout measured slower (the offsets and
+// tile metadata the kernel reads live in L1).
+pr_status nb_occupancy(const void* kernel, size_t smem, int* occ) {
+    struct Entry {
+        const void* kernel;
+        size_t smem;
+        int occ;
+    };
+    static std::mutex mu;
+    static std::vector<Entry> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const auto& e : cache)
+        if (e.kernel == kernel && e.smem == smem) {
+            *occ = e.occ;
+            return PR_OK;
+        }
+    PRK_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)((kNbHubsMax + kStageFloats) * sizeof(float))));
+    int o = 0;
+    PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernel, kNbBlock, smem));
+    if (o < 1) return fail(PR_ERR_UNSUPPORTED, "barrier-free kernel: no block fits on an SM");
+    cache.push_back({kernel, smem, o});
+    *occ = o;
+    return PR_OK;
+}
+
+// Work items (light and empty row tiles; heavy rows are worked as segments)
+// and the edges of each item and segment, built on first use.
 pr_status build_items(pr_graph* g, cudaStream_t s) {
     if (g->nb_items) return PR_OK;
-    if (g_occ_nb == 0) {
-        int occ = 1 << 30;
-        int o = 0;
-        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_nonblocking<int32_t, true>, kBlock, 0));
-        occ = std::min(occ, o);
-        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_nonblocking<int32_t, false>, kBlock, 0));
-        occ = std::min(occ, o);
-        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_nonblocking<int64_t, true>, kBlock, 0));
-        occ = std::min(occ, o);
-        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_nonblocking<int64_t, false>, kBlock, 0));
-        occ = std::min(occ, o);
-        g_occ_nb = std::max(1, occ);
-    }
-    // heavy rows [0, n_heavy): one item per segment (the Jacobi segments)
     std::vector<int32_t> seg_ptr((size_t)g->n_heavy + 1, 0);
-    if (g->n_heavy > 0)
+    std::vector<int64_t> heavy_rp((size_t)g->n_heavy + 1, 0);
+    if (g->n_heavy > 0) {
         PRK_CHECK(cudaMemcpy(seg_ptr.data(), g->seg_ptr, seg_ptr.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if (g->idx64) {
+            PRK_CHECK(cudaMemcpy(heavy_rp.data(), g->rowptr, heavy_rp.size() * sizeof(int64_t), cudaMemcpyDeviceToHost));
+        } else {
+            std::vector<int32_t> tmp(heavy_rp.size());
+            PRK_CHECK(cudaMemcpy(tmp.data(), g->rowptr, tmp.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < tmp.size(); ++i) heavy_rp[i] = tmp[i];
+        }
+    }
     std::vector<Tile> items;
-    for (int64_t r = 0; r < g->n_heavy; ++r)
-        for (int32_t sgi = seg_ptr[r]; sgi < seg_ptr[r + 1]; ++sgi)
-            items.push_back(Tile{(int32_t)r, sgi, kItemSegment, sgi + 1 == seg_ptr[r + 1] ? 1 : 0});
     for (const Tile& t : g->host_tiles)
         if (t.kind != kTileHeavy) items.push_back(t);
     const int64_t count = (int64_t)items.size();
 
-    // edges per item, then a balanced contiguous partition
     Tile* d_items = nullptr;
     int64_t* d_edges = nullptr;
     PRK_CHECK(dev_alloc(g, (void**)&d_items, (size_t)(count + 1) * sizeof(Tile)));
@@ -297,26 +393,44 @@ pr_status build_items(pr_graph* g, cudaStream_t s) {
     PRK_CHECK(cudaMemcpyAsync(d_items, items.data(), (size_t)count * sizeof(Tile), cudaMemcpyHostToDevice, s));
     PRK_CHECK(cudaMalloc((void**)&d_edges, (size_t)(count + 1) * sizeof(int64_t)));
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((count + kBlock - 1) / kBlock, 4096));
-    if (g->idx64) k_item_edges<int64_t><<<grid, kBlock, 0, s>>>(g->rowptr, g->seg_ptr, d_items, count, d_edges);
-    else k_item_edges<int32_t><<<grid, kBlock, 0, s>>>(g->rowptr, g->seg_ptr, d_items, count, d_edges);
-    std::vector<int64_t> edges((size_t)count);
-    cudaError_t e = cudaMemcpyAsync(edges.data(), d_edges, (size_t)count * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (g->idx64) k_item_edges<int64_t><<<grid, kBlock, 0, s>>>(g->rowptr, d_items, count, d_edges);
+    else k_item_edges<int32_t><<<grid, kBlock, 0, s>>>(g->rowptr, d_items, count, d_edges);
+    g->nb_item_edges.assign((size_t)count, 0);
+    cudaError_t e = cudaMemcpyAsync(g->nb_item_edges.data(), d_edges, (size_t)count * sizeof(int64_t),
+                                    cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(d_edges);
     PRK_CHECK(e);
-
-    const int per_sm = g->ctas_per_sm > 0 ? std::min(g->ctas_per_sm, g_occ_nb) : g_occ_nb;
-    const int G = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * per_sm, count));
-    // Items are dealt to blocks round-robin, so every block owns the same mix
-    // of heavy-row segments, light tiles and rows without in-edges.
-    g->nb_cta_edges.assign((size_t)G, 0);
-    for (int64_t i = 0; i < count; ++i) g->nb_cta_edges[i % G] += edges[i];
-    g->nb_grid = G;
-    PRK_CHECK(dev_alloc(g, (void**)&g->nb_slots, (size_t)G * sizeof(double)));
+    g->nb_seg_edges.assign((size_t)g->n_seg, 0);
+    for (int64_t h = 0; h < g->n_heavy; ++h)
+        for (int32_t sg = seg_ptr[h]; sg < seg_ptr[h + 1]; ++sg) {
+            const int64_t e0 = heavy_rp[h] + (int64_t)(sg - seg_ptr[h]) * kSegEdges;
+            g->nb_seg_edges[sg] = std::min<int64_t>(kSegEdges, heavy_rp[h + 1] - e0);
+        }
+    // slots and counters for the largest grid any kernel variant can have
+    const int64_t max_grid = (int64_t)g->sm_count * 8;
+    PRK_CHECK(dev_alloc(g, (void**)&g->nb_slots, (size_t)max_grid * sizeof(double)));
     PRK_CHECK(dev_alloc(g, (void**)&g->nb_scalars, 8 * sizeof(double)));
-    PRK_CHECK(dev_alloc(g, (void**)&g->nb_block_sweeps, (size_t)G * sizeof(int32_t) + 256 * sizeof(float)));
-    PRK_CHECK(cudaStreamSynchronize(s));
+    PRK_CHECK(dev_alloc(g, (void**)&g->nb_block_sweeps, (size_t)max_grid * sizeof(int32_t) + 256 * sizeof(float)));
+    g->nb_grid = 0;
     return PR_OK;
+}
+
+// Grid of the persistent kernel for `per_sm` co-resident blocks per SM, and the
+// edges each block owns.  Tiles are dealt round-robin to the 256-thread groups
+// and segments to the warps of the grid, so every block owns the same mix.
+void nb_partition(pr_graph* g, int per_sm) {
+    if (g->ctas_per_sm > 0) per_sm = std::min(g->ctas_per_sm, per_sm);
+    per_sm = std::min(per_sm, 8);
+    const int groups = kNbBlock / kBlock, warps = kNbBlock / 32;
+    const int64_t count = g->nb_items_count;
+    const int64_t work = std::max<int64_t>((count + groups - 1) / groups, (g->n_seg + warps - 1) / warps);
+    const int G = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * per_sm, work));
+    if (G == g->nb_grid) return;
+    g->nb_cta_edges.assign((size_t)G, 0);
+    for (int64_t i = 0; i < count; ++i) g->nb_cta_edges[(i % ((int64_t)G * groups)) / groups] += g->nb_item_edges[i];
+    for (int64_t sg = 0; sg < g->n_seg; ++sg) g->nb_cta_edges[(sg % ((int64_t)G * warps)) / warps] += g->nb_seg_edges[sg];
+    g->nb_grid = G;
 }
 
 }  // namespace
@@ -335,6 +449,13 @@ pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_
     if (!uniform && (rc = ensure_teleport(g)) != PR_OK) return rc;
     const bool out_dev = is_device_pointer(x_out);
     float* out = out_dev ? x_out : g->stage + (size_t)2 * (size_t)(g->n + kPad);
+    const bool staged = (g->staged_tiles >> 1) & 1;
+    const int32_t hub_n = (int32_t)(std::min<int64_t>(g->nb_hubs, g->n) & ~(int64_t)3);
+    const size_t nb_smem = ((size_t)hub_n + (staged ? (size_t)kStageFloats : 0)) * sizeof(float);
+    void* kernel = pick_kernel(g, uniform, staged);
+    int per_sm = 1;
+    if ((rc = nb_occupancy(kernel, nb_smem, &per_sm)) != PR_OK) return rc;
+    nb_partition(g, per_sm);
     const int G = g->nb_grid;
 
     SolveState* hs = g->host_state;
@@ -373,6 +494,8 @@ pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_
     na.items = (const Tile*)g->nb_items;
     na.n_items = (int32_t)g->nb_items_count;
     na.seg_ptr = g->seg_ptr;
+    na.seg_row = g->seg_row;
+    na.n_seg = g->n_seg;
     na.seg_sum = g->seg_sum;
     na.slots = g->nb_slots;
     na.scalars = g->nb_scalars;
@@ -380,10 +503,11 @@ pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_
     na.sweeps_max = (int32_t*)(g->nb_scalars + 3);
     const char* form_env = getenv("PR_NB_DANGLING_FORM");
     na.dangling_form = (form_env && form_env[0] == '0') ? 0 : 1;
+    na.hub_n = hub_n;
+    na.l1_hubs = (int32_t)std::min<int64_t>(g->nb_l1_hubs, g->n);
     na.state = g->state;
     na.x = g->x[0];
     na.y = g->y[0];
-    void* kernel = pick_kernel(g, uniform);
     // Opt-in diagnostics: PR_TRACE_NB=<file> appends one CSV line per block and launch.
     const char* trace_path = getenv("PR_TRACE_NB");
     long long* d_trace = nullptr;
@@ -401,7 +525,8 @@ pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_
 
     int32_t used = 0;
     int32_t iterations = 0;
-    double visits = 0.0;
+    double loop_visits = 0.0, verify_visits = 0.0;
+    float ms_loop = 0.f;
     double tol_int = tol;
     bool converged = false;
     while (true) {
@@ -414,7 +539,9 @@ pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_
         na.tol_int = tol_int;
         na.max_sweeps = std::max(1, max_iter - used);
         void* args[] = {&na};
-        PRK_CHECK(cudaLaunchCooperativeKernel(kernel, dim3(G), dim3(kBlock), args, 0, s));
+        PRK_CHECK(cudaEventRecord(g->ev_loop0, s));
+        PRK_CHECK(cudaLaunchCooperativeKernel(kernel, dim3(G), dim3(kNbBlock), args, nb_smem, s));
+        PRK_CHECK(cudaEventRecord(g->ev_loop1, s));
         ++launches;
         // verify with one synchronous update x[0] -> x[1]
         k_mass_split<<<small_grid(g), kBlock, 0, s>>>(a, g->x[0], g->nb_scalars + 4);
@@ -426,6 +553,9 @@ pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_
                                   cudaMemcpyDeviceToHost, s));
         PRK_CHECK(cudaMemcpyAsync(hs, g->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
         PRK_CHECK(cudaStreamSynchronize(s));
+        float ms_launch = 0.f;
+        PRK_CHECK(cudaEventElapsedTime(&ms_launch, g->ev_loop0, g->ev_loop1));
+        ms_loop += ms_launch;
         if (d_trace) {
             std::vector<long long> tr((size_t)G * 8);
             PRK_CHECK(cudaMemcpy(tr.data(), d_trace, tr.size() * sizeof(long long), cudaMemcpyDeviceToHost));
@@ -436,9 +566,9 @@ pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_
                     double lr, le;
                     memcpy(&lr, &tr[8 * c + 3], sizeof(double));
                     memcpy(&le, &tr[8 * c + 4], sizeof(double));
-                    fprintf(f, "%d,%d,%lld,%lld,%lld,%.6e,%.6e,%lld,%lld,%lld\n", launch_no, c, tr[8 * c],
+                    fprintf(f, "%d,%d,%lld,%lld,%lld,%.6e,%.6e,%lld,%lld,%lld,%lld\n", launch_no, c, tr[8 * c],
                             tr[8 * c + 1] - t0, tr[8 * c + 2] - t0, lr, le, tr[8 * c + 5], tr[8 * c + 6],
-                            (long long)g->nb_cta_edges[c]);
+                            (long long)g->nb_cta_edges[c], tr[8 * c + 7]);
                 }
                 fclose(f);
             }
@@ -447,8 +577,8 @@ pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_
         const int32_t sweeps = (int32_t)(((const int32_t*)(h_counts + 1))[0]);
         used += std::max(1, sweeps);
         iterations += sweeps + 1;
-        for (int c = 0; c < G; ++c) visits += (double)h_sweeps[c] * (double)g->nb_cta_edges[c];
-        visits += (double)g->nnz;   // the verifying synchronous update
+        for (int c = 0; c < G; ++c) loop_visits += (double)h_sweeps[c] * (double)g->nb_cta_edges[c];
+        verify_visits += (double)g->nnz;   // the verifying synchronous update
         if (d_trace) {
             float hist[256];
             PRK_CHECK(cudaMemcpy(hist, na.history, sizeof(hist), cudaMemcpyDeviceToHost));
@@ -480,9 +610,12 @@ pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_
         info->residual_l1 = hs->resid;
         info->sum_x = hs->sum_x;
         info->dangling_mass = hs->D;
-        info->edge_visits = visits;
+        info->edge_visits = loop_visits + verify_visits;
         info->ms_device = ms;
         info->launches = launches;
+        info->loop_edge_visits = loop_visits;
+        info->ms_loop = ms_loop;
+        info->reserved = 0;
     }
     return converged ? PR_OK : PR_NOT_CONVERGED;
 }

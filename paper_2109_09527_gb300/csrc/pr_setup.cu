@@ -461,6 +461,14 @@ pr_status create_typed(pr_graph* g, const void* rowptr, const int32_t* colidx, c
 }
 
 }  // namespace
+
+cudaError_t scan_counts_i32(const int64_t* counts, int64_t count, int32_t* offsets, cudaStream_t st) {
+    Scratch s;
+    cudaError_t e = exclusive_scan<int32_t>(s, counts, count, offsets, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // before the temporaries are freed
+    return e;
+}
+
 }  // namespace prk
 
 extern "C" pr_status pr_create_graph(int64_t n, int64_t nnz, const void* rowptr, int rowptr_is_64,
@@ -495,6 +503,8 @@ extern "C" pr_status pr_create_graph(int64_t n, int64_t nnz, const void* rowptr,
         g->heavy_degree = thread_heavy_degree();
         e = cudaEventCreate(&g->ev_start);
         if (e == cudaSuccess) e = cudaEventCreate(&g->ev_stop);
+        if (e == cudaSuccess) e = cudaEventCreate(&g->ev_loop0);
+        if (e == cudaSuccess) e = cudaEventCreate(&g->ev_loop1);
         if (e != cudaSuccess) { rc = cuda_fail(e, "cudaEventCreate"); break; }
         e = cudaEventRecord(g->ev_start, st);
         if (e != cudaSuccess) { rc = cuda_fail(e, "cudaEventRecord"); break; }

@@ -15,26 +15,86 @@
 
 #include "pr_common.cuh"
 
+// L2 eviction priority of each access class, as an L2 cache policy made by
+// createpolicy: 0 = no hint (plain instruction forms), 1 = evict_first,
+// 2 = evict_last, 3 = evict_normal.  The stream class covers what an
+// iteration reads once (colidx, x, 1/outdeg, teleport); the gather class the
+// quotient vector y that every edge reads; the y-store class the writes of y'
+// (gathered by the next iteration).  Keeping y resident in L2 while colidx
+// streams past it is what these hints are for.
+#ifndef PRK_L2_STREAM
+#define PRK_L2_STREAM 0
+#endif
+#ifndef PRK_L2_GATHER
+#define PRK_L2_GATHER 0
+#endif
+#ifndef PRK_L2_YSTORE
+#define PRK_L2_YSTORE 0
+#endif
+
 namespace prk {
+
+template <int P>
+__device__ __forceinline__ uint64_t l2_policy() {
+    uint64_t p;
+    if constexpr (P == 1) asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    else if constexpr (P == 2) asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    else asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
 
 __device__ __forceinline__ float ld_stream(const float* p) {
     float v;
-    asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    if constexpr (PRK_L2_STREAM == 0)
+        asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    else
+        asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;"
+            : "=f"(v) : "l"(p), "l"(l2_policy<PRK_L2_STREAM>()));
     return v;
 }
 
 __device__ __forceinline__ int32_t ld_stream(const int32_t* p) {
     int32_t v;
-    asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    if constexpr (PRK_L2_STREAM == 0)
+        asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    else
+        asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;"
+            : "=r"(v) : "l"(p), "l"(l2_policy<PRK_L2_STREAM>()));
     return v;
 }
 
 __device__ __forceinline__ int4 ld_stream4(const int32_t* p) {
     int4 v;
-    asm("ld.global.nc.L1::no_allocate.v4.s32 {%0, %1, %2, %3}, [%4];"
-        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-        : "l"(p));
+    if constexpr (PRK_L2_STREAM == 0)
+        asm("ld.global.nc.L1::no_allocate.v4.s32 {%0, %1, %2, %3}, [%4];"
+            : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+            : "l"(p));
+    else
+        asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+            : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+            : "l"(p), "l"(l2_policy<PRK_L2_STREAM>()));
     return v;
+}
+
+// Gathers of y with the gather-class L2 policy: through L1 (ldg) or L2 only (cg).
+__device__ __forceinline__ float ld_y_ldg(const float* p) {
+    if constexpr (PRK_L2_GATHER == 0) {
+        return __ldg(p);
+    } else {
+        float v;
+        asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(l2_policy<PRK_L2_GATHER>()));
+        return v;
+    }
+}
+
+__device__ __forceinline__ float ld_y_cg(const float* p) {
+    if constexpr (PRK_L2_GATHER == 0) {
+        return __ldcg(p);
+    } else {
+        float v;
+        asm("ld.global.cg.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(l2_policy<PRK_L2_GATHER>()));
+        return v;
+    }
 }
 
 // Gathers of the quotient vector through the non-coherent path.  `hot` packs
@@ -48,8 +108,8 @@ __device__ __forceinline__ float ld_gather(const float* y, int32_t c, int32_t ho
     float v;
     const int policy = (int)((uint32_t)hot >> 28);
     const int32_t count = hot & 0x0fffffff;
-    if (policy == 0) return __ldg(y + c);
-    if (policy == 4) return c < count ? __ldg(y + c) : __ldcg(y + c);
+    if (policy == 0) return ld_y_ldg(y + c);
+    if (policy == 4) return c < count ? ld_y_ldg(y + c) : ld_y_cg(y + c);
     if (c < count) {
         asm("ld.global.nc.L1::evict_last.f32 %0, [%1];" : "=f"(v) : "l"(y + c));
     } else if (policy == 1) {
@@ -66,6 +126,15 @@ __device__ __forceinline__ void st_stream(float* p, float v) {
     asm volatile("st.global.cs.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
 }
 
+// Store of y' (read by the gathers of the next iteration).
+__device__ __forceinline__ void st_y(float* p, float v) {
+    if constexpr (PRK_L2_YSTORE == 0)
+        asm volatile("st.global.cs.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+    else
+        asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v),
+                     "l"(l2_policy<PRK_L2_YSTORE>()) : "memory");
+}
+
 __device__ __forceinline__ float ld_relaxed(const float* p) {
     float v;
     asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
@@ -74,6 +143,44 @@ __device__ __forceinline__ float ld_relaxed(const float* p) {
 
 __device__ __forceinline__ void st_relaxed(float* p, float v) {
     asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v));
+}
+
+// Relaxed accesses of the in-place vectors with an L2 policy of class P.
+template <int P>
+__device__ __forceinline__ float ld_relaxed_p(const float* p) {
+    if constexpr (P == 0) {
+        return ld_relaxed(p);
+    } else {
+        float v;
+        asm volatile("ld.relaxed.gpu.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p),
+                     "l"(l2_policy<P>()));
+        return v;
+    }
+}
+
+template <int P>
+__device__ __forceinline__ void st_relaxed_p(float* p, float v) {
+    if constexpr (P == 0)
+        st_relaxed(p, v);
+    else
+        asm volatile("st.relaxed.gpu.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v),
+                     "l"(l2_policy<P>()));
+}
+
+// Weak load that may be served by L1 (possibly an older value of a location
+// other SMs write; see the barrier-free kernel for the bound on its age).
+__device__ __forceinline__ float ld_weak_l1(const float* p) {
+    float v;
+    asm volatile("ld.global.ca.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ float4 ld_relaxed4(const float* p) {
+    float4 v;
+    asm volatile("ld.relaxed.gpu.global.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
 }
 
 __device__ __forceinline__ double ld_relaxed(const double* p) {
@@ -95,6 +202,31 @@ __device__ __forceinline__ float warp_sum(float v) {
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Solve-state scalars every thread needs, read once per block by thread 0 and
+// broadcast through shared memory: a load of the same word by every thread of
+// every block would queue hundreds of thousands of requests on one L2 slice.
+struct StateView {
+    double d, D, inv_n, t_sum, scale;
+    int32_t done, iter;
+};
+
+__device__ __forceinline__ StateView block_state(const SolveState* st) {
+    __shared__ StateView sv;
+    if (threadIdx.x == 0) {
+        sv.done = *(const volatile int32_t*)&st->done;
+        sv.iter = *(const volatile int32_t*)&st->iter;
+        sv.d = st->d;
+        sv.D = st->D;
+        sv.inv_n = st->inv_n;
+        sv.t_sum = st->t_sum;
+        sv.scale = st->scale;
+    }
+    __syncthreads();
+    StateView v = sv;
+    __syncthreads();
     return v;
 }
 
@@ -125,17 +257,19 @@ struct Mem<false> {
     }
     static __device__ __forceinline__ float load_x(const float* p) { return ld_stream(p); }
     static __device__ __forceinline__ void store_x(float* p, float v) { st_stream(p, v); }
-    static __device__ __forceinline__ void store_y(float* p, float v) { st_stream(p, v); }
+    static __device__ __forceinline__ void store_y(float* p, float v) { st_y(p, v); }
 };
 
 template <>
 struct Mem<true> {
     static __device__ __forceinline__ float gather(const float* y, int32_t c, const RowCtx& x) {
-        return c < x.hot_n ? x.hot_sm[c] : ld_relaxed(y + c);
+        if (c < x.hot_n) return x.hot_sm[c];
+        if (c < x.hot) return ld_weak_l1(y + c);
+        return ld_relaxed_p<PRK_L2_GATHER>(y + c);
     }
-    static __device__ __forceinline__ float load_x(const float* p) { return ld_relaxed(p); }
-    static __device__ __forceinline__ void store_x(float* p, float v) { st_relaxed(p, v); }
-    static __device__ __forceinline__ void store_y(float* p, float v) { st_relaxed(p, v); }
+    static __device__ __forceinline__ float load_x(const float* p) { return ld_relaxed_p<PRK_L2_STREAM>(p); }
+    static __device__ __forceinline__ void store_x(float* p, float v) { st_relaxed_p<PRK_L2_STREAM>(p, v); }
+    static __device__ __forceinline__ void store_y(float* p, float v) { st_relaxed_p<PRK_L2_GATHER>(p, v); }
 };
 
 // Per-thread accumulators.  r: L1 change.  (m, c): Kahan sum of the mass the
@@ -254,6 +388,85 @@ __device__ __forceinline__ void process_light_tile(const Tile& tile, const void*
                 if (act[q]) row_update<kUniform, kInPlace>(rr[q], s[q], xo[q], inv[q], tv[q], c, x_out, y_out, acc);
         }
     }
+}
+
+// Staging area of process_staged_tile: the gathered y values of one light
+// tile, indexed from the tile's first edge rounded down to a multiple of 4.
+constexpr int kStageFloats = kTileEdgesMax + 4;
+
+// Light rows of one degree class, edge-parallel: the 256 threads of the group
+// stream the tile's colidx range with 16-byte loads and issue every gather of
+// the tile without waiting on any row (up to sixteen in flight per thread),
+// park the values in shared memory, and only then reduce row by row (groups
+// of g = 2^tile.kind lanes, consecutive lanes on consecutive values).  Every
+// gather of a tile is independent of the others, so the tile costs three
+// memory latencies (offsets, colidx, y) instead of three per row pair.
+// `stage` holds kStageFloats floats, 16-byte aligned; the caller's group must
+// be a whole block (the routine uses __syncthreads).  Returns false -- and
+// touches nothing -- if the tile does not fit the staging area, which the
+// tiling at set-up rules out.
+template <typename IdxT, bool kUniform, bool kInPlace>
+__device__ __forceinline__ bool process_staged_tile(const Tile& tile, const void* rowptr,
+                                                    const int32_t* colidx, const float* inv_out,
+                                                    const float* teleport, const float* x_in,
+                                                    const float* y_in, float* x_out, float* y_out,
+                                                    const RowCtx& c, Acc& acc, int tid, float* stage) {
+    const int64_t e0 = row_at<IdxT>(rowptr, tile.row_begin);
+    const int64_t e1 = row_at<IdxT>(rowptr, tile.row_end);
+    const int64_t a0 = e0 & ~(int64_t)3;   // 16-byte aligned start of the colidx range
+    if (e1 - a0 > kStageFloats) return false;
+    float4* st4 = reinterpret_cast<float4*>(stage);
+    for (int64_t base = a0; base < e1; base += 16 * kBlock) {
+        int4 cv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t p = base + 4 * (kBlock * j + tid);
+            cv[j] = p < e1 ? ld_stream4(colidx + p) : make_int4(0, 0, 0, 0);
+        }
+        float4 v[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t p = base + 4 * (kBlock * j + tid);
+            v[j].x = (p + 0 >= e0 && p + 0 < e1) ? Mem<kInPlace>::gather(y_in, cv[j].x, c) : 0.f;
+            v[j].y = (p + 1 >= e0 && p + 1 < e1) ? Mem<kInPlace>::gather(y_in, cv[j].y, c) : 0.f;
+            v[j].z = (p + 2 >= e0 && p + 2 < e1) ? Mem<kInPlace>::gather(y_in, cv[j].z, c) : 0.f;
+            v[j].w = (p + 3 >= e0 && p + 3 < e1) ? Mem<kInPlace>::gather(y_in, cv[j].w, c) : 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t p = base + 4 * (kBlock * j + tid);
+            if (p < e1) st4[(p - a0) >> 2] = v[j];
+        }
+    }
+    __syncthreads();
+    const int lg = tile.kind;
+    const int g = 1 << lg;
+    const int rpp = kBlock >> lg;
+    const int gl = tid & (g - 1);
+    // uniform trip count over the block: every lane reaches the shuffles
+    for (int64_t r0 = tile.row_begin; r0 < tile.row_end; r0 += rpp) {
+        const int64_t r = r0 + (tid >> lg);
+        const bool act = r < tile.row_end;
+        int32_t b = 0, e = 0;
+        if (act) {
+            b = (int32_t)(row_at<IdxT>(rowptr, r) - a0);
+            e = (int32_t)(row_at<IdxT>(rowptr, r + 1) - a0);
+        }
+        float xo = 0.f, inv = 0.f, tv = 0.f;
+        if (act && gl == 0) {
+            xo = Mem<kInPlace>::load_x(x_in + r);
+            inv = ld_stream(inv_out + r);
+            if (!kUniform) tv = ld_stream(teleport + r);
+        }
+        float sum = 0.f;
+        for (int32_t k = b + gl; k < e; k += g) sum += stage[k];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1)
+            if (o < g) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (act && gl == 0) row_update<kUniform, kInPlace>(r, sum, xo, inv, tv, c, x_out, y_out, acc);
+    }
+    __syncthreads();   // the staging area is reused by the next tile
+    return true;
 }
 
 // Sum (a, b) over the block and write the block's pair to

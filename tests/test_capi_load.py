@@ -84,10 +84,38 @@ def test_options_validate_host_side():
     pr.set_heavy_degree(1024)
     with pytest.raises(pr.PageRankError):
         pr.pr_set_option(None, 99, 1)
-    with pytest.raises(pr.PageRankError):
-        pr.pr_set_option(None, pr.PR_OPT_USE_GRAPH, 1)   # needs a graph
+    for key in (pr.PR_OPT_USE_GRAPH, pr.PR_OPT_STAGED_TILES, pr.PR_OPT_NB_HUBS,
+                pr.PR_OPT_HOT_VERTICES, pr.PR_OPT_HOT_CACHE, pr.PR_OPT_CTAS_PER_SM):
+        with pytest.raises(pr.PageRankError):
+            pr.pr_set_option(None, key, 1)               # needs a graph
     pr.pr_set_option(None, pr.PR_OPT_INDEX64, 0)
 
 
 def test_build_targets_sm103a_only():
     assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of pr_info and pr_graph_stats have the C layout (sizes and
+    offsets printed by a C program compiled against include/pagerank.h)."""
+    import shutil
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"pr_info": pr.pr_info, "pr_graph_stats": pr.pr_graph_stats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "pagerank.h"', "int main(void) {"]
+    for sname, cls in structs.items():
+        lines.append(f'printf("{sname} sizeof %zu\\n", sizeof({sname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{sname} {fname} %zu\\n", offsetof({sname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(line.split()[:2]): int(line.split()[2]) for line in out if line}
+    for sname, cls in structs.items():
+        assert got[(sname, "sizeof")] == ctypes.sizeof(cls), sname
+        for fname, _ in cls._fields_:
+            assert got[(sname, fname)] == getattr(cls, fname).offset, (sname, fname)

@@ -1,0 +1,185 @@
+"""Batched personalised PageRank (pr_solve_batched) against the FP64 oracle.
+
+Each column j is an independent solve with teleport t_j (uniform dangling share,
+sum(x_j) = sum(t_j)); a column stops when its own L1 change is below tol.  The
+oracle runs Alg. 1 for column j with the same teleport and the same number of
+iterations the library reports for that column (matching mode): L1 <= 1e-6 and
+per-vertex relative error <= 1e-4, the FP32-against-FP64 bar of the
+single-vector solve.  At the full size of the batched workload (R-MAT scale 22,
+k = 32 seed-set teleports) sampled columns are certified by one FP64 oracle
+update instead.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pr = pytest.importorskip("paper_2109_09527_gb300")
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+D = 0.85
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+    yield
+
+
+def check_columns(rp, ci, t, x, its, res, tol):
+    n, k = x.shape
+    for j in range(k):
+        tj = None if t is None else t[:, j].astype(np.float64)
+        xo, it, r = oracle.pagerank_jacobi(rp, ci, d=D, tol=0, max_iter=int(its[j]), t=tj)
+        xo = xo * ((1.0 if tj is None else tj.sum()) / xo.sum())
+        xj = x[:, j].astype(np.float64)
+        assert np.abs(xj - xo).sum() <= 1e-6, j
+        assert np.max(np.abs(xj - xo) / xo) <= 1e-4, j
+        if res[j] < tol:
+            # the oracle's own stopping test agrees to within one iteration
+            _, it_o, _ = oracle.pagerank_jacobi(rp, ci, d=D, tol=tol, max_iter=500, t=tj)
+            assert abs(it_o - int(its[j])) <= 1, (j, it_o, its[j])
+
+
+@pytest.mark.parametrize("scale,heavy,index64", [(12, 1024, 0), (13, 64, 0), (12, 64, 1)])
+def test_seed_teleports_match_oracle(scale, heavy, index64):
+    rp, ci = gg.rmat(scale, 16, seed=40 + scale)
+    n = rp.size - 1
+    t = gg.seed_teleports(n, 32, 8, seed=scale)
+    pr.set_heavy_degree(heavy)
+    pr.pr_set_option(None, pr.PR_OPT_INDEX64, index64)
+    try:
+        g = pr.Graph(rp, ci)
+    finally:
+        pr.set_heavy_degree(1024)
+        pr.pr_set_option(None, pr.PR_OPT_INDEX64, 0)
+    with g:
+        x, info, res, its = g.solve_batched(32, t, tol=1e-6, max_iter=300)
+    assert info.converged == 1 and np.all(res < 1e-6)
+    assert info.iterations == its.max()
+    np.testing.assert_allclose(x.astype(np.float64).sum(axis=0), 1.0, rtol=1e-6)
+    check_columns(rp, ci, t, x, its, res, 1e-6)
+
+
+def test_uniform_columns_equal_the_single_vector_solve():
+    rp, ci = gg.rmat(12, 16, seed=3)
+    with pr.Graph(rp, ci) as g:
+        x, info, res, its = g.solve_batched(4, None, tol=1e-6)
+        x1, info1 = g.solve(tol=1e-6)
+    assert np.all(its == info1.iterations)
+    for j in range(4):
+        assert np.array_equal(x[:, j], x[:, 0])
+        np.testing.assert_allclose(x[:, j], x1, rtol=2e-6)
+    check_columns(rp, ci, None, x, its, res, 1e-6)
+
+
+@pytest.mark.parametrize("k", [1, 7, 32])
+def test_dense_random_teleports(k):
+    """Dense positive teleports from flat to very peaked, k not a power of two."""
+    rp, ci = gg.er_dangling(5000, 8.0, 0.3, seed=5)
+    n = rp.size - 1
+    u = gg.uniform(77, 0, n * k).reshape(n, k)
+    t = (u ** (1 + 6 * np.arange(k) / max(k - 1, 1))).astype(np.float32)   # flat .. very peaked
+    t /= t.sum(axis=0, keepdims=True)
+    with pr.Graph(rp, ci) as g:
+        x, info, res, its = g.solve_batched(k, t, tol=1e-7, max_iter=400)
+    assert info.converged == 1
+    np.testing.assert_allclose(x.astype(np.float64).sum(axis=0), t.astype(np.float64).sum(axis=0),
+                               rtol=1e-6)
+    check_columns(rp, ci, t, x, its, res, 1e-7)
+
+
+def test_columns_freeze_at_their_own_iteration():
+    """On a directed cycle the uniform teleport is already the fixed point (its column
+    stops after one iteration) while seed-set columns need many: the frozen column keeps
+    its value while the others run on, and every column matches the oracle at its own
+    iteration count."""
+    n = 40          # every vertex within reach of every seed after n iterations
+    rp, ci = gg.cycle(n)
+    t = gg.seed_teleports(n, 6, 4, seed=8)
+    t[:, 0] = 1.0 / n
+    with pr.Graph(rp, ci) as g:
+        x, info, res, its = g.solve_batched(6, t, tol=1e-6, max_iter=400)
+    assert info.converged == 1
+    assert its[0] == 1 and its[1:].min() > 20
+    assert info.iterations == its.max()
+    np.testing.assert_allclose(x[:, 0], 1.0 / n, rtol=1e-6)
+    check_columns(rp, ci, t, x, its, res, 1e-6)
+
+
+def test_host_and_device_buffers_agree_bitwise():
+    rp, ci = gg.rmat(12, 16, seed=9)
+    n = rp.size - 1
+    t = gg.seed_teleports(n, 32, 8, seed=1)
+    dev = torch.device("cuda", 0)
+    with pr.Graph(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)) as g:
+        xh, _, _, _ = g.solve_batched(32, t)
+        td = torch.from_numpy(t).to(dev)
+        xd = torch.empty((n, 32), dtype=torch.float32, device=dev)
+        _, _, _, _ = g.solve_batched(32, td, out=xd)
+        torch.cuda.synchronize()
+        xh2, _, _, _ = g.solve_batched(32, t)
+        g.set_option(pr.PR_OPT_USE_GRAPH, 0)
+        xh3, _, _, _ = g.solve_batched(32, t)
+    assert np.array_equal(xh, xd.cpu().numpy())
+    assert np.array_equal(xh, xh2)
+    assert np.array_equal(xh, xh3)          # host-driven loop, same iterates
+
+
+def test_budget_and_invalid_arguments():
+    rp, ci = gg.rmat(10, 16, seed=2)
+    n = rp.size - 1
+    t = gg.seed_teleports(n, 8, 8, seed=2)
+    with pr.Graph(rp, ci) as g:
+        x = np.empty((n, 8), np.float32)
+        status, info, res, its = pr.pr_solve_batched(g.handle, D, 1e-12, 3, 8, t, x)
+        assert status == pr.PR_NOT_CONVERGED and info.iterations == 3 and np.all(its == 3)
+        assert np.all(np.isfinite(x))
+        for k in (0, 33):
+            with pytest.raises(pr.PageRankError):
+                pr.pr_solve_batched(g.handle, D, 1e-6, 10, k, None, np.empty((n, 33), np.float32))
+        bad = t.copy()
+        bad[:, 3] = 0.0                      # a column with zero sum
+        with pytest.raises(pr.PageRankError):
+            pr.pr_solve_batched(g.handle, D, 1e-6, 10, 8, bad, x)
+        bad = t.copy()
+        bad[5, 2] = -0.5                     # a negative entry
+        with pytest.raises(pr.PageRankError):
+            pr.pr_solve_batched(g.handle, D, 1e-6, 10, 8, bad, x)
+        # the graph is still usable afterwards
+        x2, info2, res2, _ = g.solve_batched(8, t)
+        assert info2.converged == 1
+
+
+def test_fullsize_rmat22_k32_certified():
+    """The batched workload at full size: R-MAT scale 22, 32 seed-set teleports (8 seed
+    vertices each), as the benchmark runs it from device arrays; four sampled columns are
+    certified by one FP64 oracle update (residual r, distance to the fixed point <= r/(1-d))."""
+    rp, ci = gg.rmat(22, 16, seed=22)
+    n = rp.size - 1
+    t = gg.seed_teleports(n, 32, 8, seed=22)
+    dev = torch.device("cuda", 0)
+    with pr.Graph(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)) as g:
+        out = torch.empty((n, 32), dtype=torch.float32, device=dev)
+        _, info, res, its = g.solve_batched(32, torch.from_numpy(t).to(dev), tol=1e-6, out=out)
+        torch.cuda.synchronize()
+        x = out.cpu().numpy()
+    assert info.converged == 1 and np.all(res < 1e-6)
+    np.testing.assert_allclose(x.astype(np.float64).sum(axis=0), 1.0, rtol=1e-6)
+    assert np.all(x > 0)
+    deg = oracle.outdeg(rp, ci)
+    for j in (0, 9, 20, 31):
+        xj = x[:, j].astype(np.float64)
+        tj = t[:, j].astype(np.float64)
+        xn, dmass, r, _ = oracle.jacobi_step(rp, ci, xj, d=D, t=tj)
+        assert r < 1e-6 + 5e-7, (j, r)
+        seeds = np.flatnonzero(tj)
+        for v in list(seeds) + list(np.random.default_rng(j).integers(0, n, 64)):
+            xv = oracle.vertex_update(int(v), rp, ci, xj, dmass, d=D, t=tj, deg=deg)
+            assert xv == pytest.approx(xn[v], rel=1e-12)
+            assert abs(xv - xj[v]) <= 1e-3 * xj[v]

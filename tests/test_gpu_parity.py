@@ -188,15 +188,19 @@ def test_host_and_device_buffers_agree_and_runs_are_bitwise_reproducible():
 
 # ---------------------------------------------------------- barrier-free --
 
-@pytest.mark.parametrize("build", ["rmat12", "rmat14_heavy64", "er"])
+@pytest.mark.parametrize("build", ["rmat12", "rmat14_heavy64", "rmat13_heavy64_index64", "er"])
 def test_nonblocking_reaches_the_fixed_point(build):
     if build == "er":
         rp, ci = gg.er_dangling(30000, seed=9)
     elif build == "rmat12":
         rp, ci = gg.rmat(12, seed=2)
-    else:
+    elif build == "rmat14_heavy64":
         rp, ci = gg.rmat(14, seed=3)
         pr.set_heavy_degree(64)
+    else:   # 64-bit row offsets on the device, segments for most edges
+        rp, ci = gg.rmat(13, seed=4)
+        pr.set_heavy_degree(64)
+        pr.pr_set_option(None, pr.PR_OPT_INDEX64, 1)
     try:
         xstar, _, _ = oracle.fixed_point(rp, ci, d=D)
         for tol in (1e-6, 2e-7):
@@ -209,6 +213,7 @@ def test_nonblocking_reaches_the_fixed_point(build):
             assert l1(x, xj) <= (info.residual_l1 + infoj.residual_l1) / (1 - D) + 4e-7
     finally:
         pr.set_heavy_degree(1024)
+        pr.pr_set_option(None, pr.PR_OPT_INDEX64, 0)
 
 
 def test_nonblocking_budget_of_one_sweep_returns():
@@ -258,3 +263,70 @@ def test_damping_zero_is_the_teleport():
     rp, ci = gg.rmat(10, seed=1)
     x, info, _ = solve(rp, ci, damping=0.0, tol=1e-9, max_iter=10)
     np.testing.assert_allclose(x, 1.0 / (rp.size - 1), rtol=1e-6)
+
+
+# ------------------------------------------------------ light-tile modes --
+
+@pytest.mark.parametrize("build", ["rmat14", "rmat12_heavy64_index64", "er"])
+def test_staged_tiles_match_oracle(build):
+    """Edge-parallel (staged) light tiles, both variants: the synchronous solve in matching
+    mode and the barrier-free solve against the fixed point; the staged and row-by-row
+    synchronous solves agree to FP32 summation-order rounding."""
+    index64 = 0
+    if build == "er":
+        rp, ci = gg.er_dangling(40000, seed=11)
+    elif build == "rmat14":
+        rp, ci = gg.rmat(14, seed=6)
+    else:
+        rp, ci = gg.rmat(12, seed=7)
+        pr.set_heavy_degree(64)
+        index64 = 1
+    pr.pr_set_option(None, pr.PR_OPT_INDEX64, index64)
+    try:
+        g = pr.Graph(rp, ci)
+    finally:
+        pr.pr_set_option(None, pr.PR_OPT_INDEX64, 0)
+        pr.set_heavy_degree(1024)
+    xstar, _, _ = oracle.fixed_point(rp, ci, d=D)
+    with g:
+        g.set_option(pr.PR_OPT_STAGED_TILES, 0)
+        x_rows, info_rows = g.solve(tol=1e-6, max_iter=200, variant="jacobi")
+        g.set_option(pr.PR_OPT_STAGED_TILES, 3)
+        x, info = g.solve(tol=1e-6, max_iter=200, variant="jacobi")
+        assert info.converged == 1
+        xo = matching(rp, ci, x, info)
+        assert l1(x, xo) <= 1e-6 and max_rel(x, xo) <= 1e-4
+        assert info.iterations == info_rows.iterations
+        assert max_rel(x, x_rows) <= 1e-5
+        xn, infon = g.solve(tol=1e-6, max_iter=500, variant="nonblocking")
+        assert infon.converged == 1 and infon.residual_l1 < 1e-6
+        assert l1(xn, xstar) <= infon.residual_l1 / (1 - D) + 2e-7
+        assert max_rel(xn, xstar) <= 1e-4
+
+
+@pytest.mark.parametrize("hubs", [0, 4, 1000, 8192])
+def test_nonblocking_hub_snapshot_sizes(hubs):
+    """The barrier-free kernel with no hub snapshot, a tiny one, one that is not a
+    multiple of 4 (rounded down) and the largest: the fixed point is reached."""
+    rp, ci = gg.rmat(14, seed=8)
+    xstar, _, _ = oracle.fixed_point(rp, ci, d=D)
+    with pr.Graph(rp, ci) as g:
+        g.set_option(pr.PR_OPT_NB_HUBS, hubs)
+        x, info = g.solve(tol=1e-6, max_iter=500, variant="nonblocking")
+    assert info.converged == 1 and info.residual_l1 < 1e-6
+    assert l1(x, xstar) <= info.residual_l1 / (1 - D) + 2e-7
+    assert max_rel(x, xstar) <= 1e-4
+
+
+@pytest.mark.parametrize("l1_hubs", [0, 64, 49152, 1 << 30])
+def test_nonblocking_l1_hub_gathers(l1_hubs):
+    """Barrier-free kernel with no weak hub gathers (every gather a relaxed load), a few,
+    the default and all vertices: each run reaches the fixed point."""
+    rp, ci = gg.rmat(14, seed=12)
+    xstar, _, _ = oracle.fixed_point(rp, ci, d=D)
+    with pr.Graph(rp, ci) as g:
+        g.set_option(pr.PR_OPT_NB_L1_HUBS, l1_hubs)
+        x, info = g.solve(tol=1e-6, max_iter=500, variant="nonblocking")
+    assert info.converged == 1 and info.residual_l1 < 1e-6
+    assert l1(x, xstar) <= info.residual_l1 / (1 - D) + 2e-7
+    assert max_rel(x, xstar) <= 1e-4

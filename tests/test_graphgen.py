@@ -84,3 +84,45 @@ def test_uniform_and_permutation():
     assert np.array_equal(u, gg.uniform(1, 0, 1000))
     p = gg.permutation(1, 9, 1000)
     assert np.array_equal(np.sort(p), np.arange(1000))
+
+
+def test_rmat_n_any_size_deterministic_and_clean():
+    for n in (2, 3, 1000, 4097):
+        rp, ci = gg.rmat_n(n, 8, seed=12)
+        assert rp.size == n + 1 and rp[0] == 0 and rp[-1] == ci.size
+        assert np.all(np.diff(rp) >= 0)
+        if ci.size:
+            assert ci.min() >= 0 and ci.max() < n
+        src, dst = gg.in_csr_edges(rp, ci)
+        assert np.all(src != dst)                                  # no self-loops
+        assert np.unique(dst * n + src).size == src.size           # no duplicates
+        rp2, ci2 = gg.rmat_n(n, 8, seed=12, nthreads=1)
+        assert np.array_equal(rp, rp2) and np.array_equal(ci, ci2)  # thread-count independent
+    rp, ci = gg.rmat_n(5000, 8, seed=1)
+    assert 0.8 * 8 * 5000 < ci.size <= 8 * 5000                    # few draws lost to dedup
+    # skew: the in-degree distribution is heavy-tailed like R-MAT's
+    indeg = np.diff(rp)
+    assert indeg.max() > 10 * indeg.mean()
+
+
+def test_multi_rmat_sizes_and_block_diagonal():
+    graphs = gg.multi_rmat(16, 1e3, 1e5, 8, seed=4)
+    sizes = np.array([rp.size - 1 for rp, _ in graphs])
+    assert sizes.min() >= 1000 and sizes.max() <= 100000
+    assert np.array_equal(sizes, [rp.size - 1 for rp, _ in gg.multi_rmat(16, 1e3, 1e5, 8, seed=4)])
+    rp, ci, off = gg.block_diagonal(graphs)
+    assert off[-1] == sizes.sum() and rp[-1] == ci.size == sum(c.size for _, c in graphs)
+    for g, (grp, gci) in enumerate(graphs):
+        lo, hi = off[g], off[g + 1]
+        sub_rp = rp[lo: hi + 1] - rp[lo]
+        sub_ci = ci[rp[lo]: rp[hi]] - lo
+        assert np.array_equal(sub_rp, grp) and np.array_equal(sub_ci, gci)
+
+
+def test_seed_teleports():
+    t = gg.seed_teleports(1000, 32, 8, seed=3)
+    assert t.shape == (1000, 32) and t.dtype == np.float32
+    assert np.all((t > 0).sum(axis=0) == 8)
+    np.testing.assert_allclose(t.sum(axis=0), 1.0, rtol=1e-6)
+    assert np.array_equal(t, gg.seed_teleports(1000, 32, 8, seed=3))
+    assert not np.array_equal(t, gg.seed_teleports(1000, 32, 8, seed=4))
