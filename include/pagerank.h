@@ -267,6 +267,38 @@ PR_API pr_status pr_solve_batched(pr_graph* g, float damping, double tol, int32_
                                   double* col_residual, int32_t* col_iterations, pr_info* info,
                                   void* stream);
 
+/* Many independent graphs solved together.  Build one pr_graph from the
+ * block-diagonal CSR of `count` graphs -- graph i owns the caller ids
+ * [offsets[i], offsets[i+1]) and no edge joins two graphs -- then declare the
+ * partition once:
+ *   offsets    host, count+1 int64, offsets[0] = 0, strictly increasing,
+ *              offsets[count] = n (every graph has at least one vertex).
+ *   count      1 .. 2^20.
+ * The partition is checked on the device: an edge between two graphs returns
+ * PR_ERR_INVALID_GRAPH (and no partition is kept).  A new call replaces the
+ * previous partition.  Synchronises `stream`. */
+PR_API pr_status pr_graph_set_partition(pr_graph* g, int32_t count, const int64_t* offsets,
+                                        void* stream);
+
+/* PageRank of every graph of the partition (Eq. 1 per graph: teleport 1/n_i,
+ * graph i's dangling mass spread over graph i only), by the synchronous
+ * iteration of Alg. 1 run on all graphs at once -- each launch covers every
+ * graph and the whole loop is one CUDA graph launch.  Graph i stops, and is
+ * frozen, when its own L1 change falls below tol; the loop ends when all are
+ * frozen or after max_iter iterations.  Each graph's ranks are rescaled to
+ * sum 1 in FP64.
+ *   x_out            host or device, n floats, caller's vertex order.
+ *   graph_residual   NULL or host array of count doubles: last L1 change.
+ *   graph_iterations NULL or host array of count int32: iterations run.
+ * info->iterations is the largest count, info->converged is 1 only if every
+ * graph converged, info->residual_l1 the largest residual, and
+ * info->edge_visits = iterations x nnz (frozen graphs' rows are copied, not
+ * gathered, after they stop).  Returns PR_NOT_CONVERGED (outputs written) if
+ * some graph did not converge. */
+PR_API pr_status pr_solve_set(pr_graph* g, float damping, double tol, int32_t max_iter, float* x_out,
+                              double* graph_residual, int32_t* graph_iterations, pr_info* info,
+                              void* stream);
+
 /* One synchronous PageRank update that allocates no memory -- for callers
  * that cannot call cudaMalloc (or anything that allocates) where they need an
  * update: code running inside a fixed memory pool or arena, under another

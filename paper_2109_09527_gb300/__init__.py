@@ -98,6 +98,9 @@ SIGNATURES = {
     "pr_step_noalloc": (ctypes.c_int, [_I64, _VP, _VP, _VP, _F, _VP, _VP, _VP, _VP]),
     "pr_solve_batched": (ctypes.c_int, [_VP, _F, _D, _I32, _I32, _VP, _VP, ctypes.POINTER(_D),
                                         ctypes.POINTER(_I32), ctypes.POINTER(pr_info), _VP]),
+    "pr_graph_set_partition": (ctypes.c_int, [_VP, _I32, _VP, _VP]),
+    "pr_solve_set": (ctypes.c_int, [_VP, _F, _D, _I32, _VP, ctypes.POINTER(_D), ctypes.POINTER(_I32),
+                                    ctypes.POINTER(pr_info), _VP]),
     "pr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pr_last_error": (ctypes.c_char_p, []),
 }
@@ -219,6 +222,24 @@ def pr_solve_batched(g, damping, tol, max_iter, k, teleport, x_out, stream=None)
     return st, info, np.array(res[:], dtype=np.float64), np.array(its[:], dtype=np.int32)
 
 
+def pr_graph_set_partition(g, offsets, stream=None):
+    """Declare g as the disjoint union of graphs on caller-id ranges offsets[i]..offsets[i+1]."""
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    return _check(load().pr_graph_set_partition(g, int(off.size - 1), off.ctypes.data, _stream(stream)))
+
+
+def pr_solve_set(g, count, damping, tol, max_iter, x_out, stream=None):
+    """Returns (status, pr_info, graph_residual[count], graph_iterations[count])."""
+    info = pr_info()
+    res = (ctypes.c_double * int(count))()
+    its = (ctypes.c_int32 * int(count))()
+    st = _check(load().pr_solve_set(g, float(damping), float(tol), int(max_iter),
+                                    _addr(x_out, np.float32), res, its, ctypes.byref(info),
+                                    _stream(stream)),
+                allow_not_converged=True)
+    return st, info, np.array(res[:], dtype=np.float64), np.array(its[:], dtype=np.int32)
+
+
 def pr_graph_get_stats(g):
     s = pr_graph_stats()
     _check(load().pr_graph_get_stats(g, ctypes.byref(s)))
@@ -300,6 +321,19 @@ class Graph:
             out = np.empty((self.n, k), dtype=np.float32)
         status, info, res, its = pr_solve_batched(self.handle, damping, tol, max_iter, k, teleport,
                                                   out, stream=stream)
+        return out, info, res, its
+
+    def set_partition(self, offsets, stream=None):
+        """Treat the graph as independent graphs on caller-id ranges [offsets[i], offsets[i+1])."""
+        pr_graph_set_partition(self.handle, offsets, stream=stream)
+        self.set_count = len(offsets) - 1
+
+    def solve_set(self, damping=0.85, tol=1e-6, max_iter=200, out=None, stream=None):
+        """PageRank of every graph of the partition.  Returns (out, info, residuals, iterations)."""
+        if out is None:
+            out = np.empty(self.n, dtype=np.float32)
+        status, info, res, its = pr_solve_set(self.handle, self.set_count, damping, tol, max_iter,
+                                              out, stream=stream)
         return out, info, res, its
 
     def iterate(self, x_in, n_iter=1, damping=0.85, teleport=None, out=None, stream=None):

@@ -24,9 +24,9 @@
 //                 per step (32 independent 128-byte loads in flight per
 //                 warp) into a partial row P(segment, :);
 //   k_b_light     light rows: a warp per row tile walks the tile's edges in
-//                 windows of 32 (one coalesced colidx load, then 32
-//                 independent row loads), closing a row of S at each row end;
-//   k_b_update    element-wise over the n x 32 matrix: the update, the
+//                 windows of 16 (one colidx load, then 16 independent row
+//                 loads), closing a row of S at each row end;
+//   k_b_update    four rows per warp over the n x 32 matrix: the update, the
 //                 quotient, and per-column Kahan dangling mass and L1 change,
 //                 reduced in a fixed block order by the last block, which
 //                 also clears converged columns and the loop condition.
@@ -126,12 +126,17 @@ __global__ void __launch_bounds__(kBlock) k_b_segments(BatchArgs a, const float*
 }
 
 // Light rows: one warp per tile of rows with at least one in-edge each.  The
-// tile's edges are walked in windows of 32: lane e loads colidx of edge
-// wb + e, then every lane loads its column of the 32 source rows (32
-// independent loads), and the sums are closed at the row ends, which the
-// lanes hold for the next 32 rows (rend).
+// tile's edges are walked in windows of kBW = 16: lane e loads colidx of edge
+// wb + e, every lane then loads its column of the 16 source rows (16
+// independent 128-byte row loads per warp), and the sums are closed at the
+// row ends.  The lanes hold the end offsets of 32 rows starting at rbase; a
+// window closes at most 16 rows, so while row - rbase < 16 every end inside
+// the window is described, and one warp-wide OR of (1 << position of a row's
+// last edge in the window) gives all of them as a bit mask.
+constexpr int kBW = 16;
+
 template <typename IdxT>
-__global__ void __launch_bounds__(kBlock, 3) k_b_light(BatchArgs a, const float* __restrict__ Y) {
+__global__ void __launch_bounds__(kBlock, 4) k_b_light(BatchArgs a, const float* __restrict__ Y) {
     if (batch_done(a.state)) return;
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -141,35 +146,32 @@ __global__ void __launch_bounds__(kBlock, 3) k_b_light(BatchArgs a, const float*
         if (tile.kind < 0) continue;    // heavy epilogue and empty rows: not gathered here
         const int64_t r1 = tile.row_end;
         const int64_t eend = row_at<IdxT>(a.rowptr, r1);
-        int64_t rbase = tile.row_begin;
+        int64_t row = tile.row_begin;   // row being summed
+        int64_t rbase = row;            // first row whose end offset the lanes hold
         int64_t rend = rbase + 1 + lane <= r1 ? row_at<IdxT>(a.rowptr, rbase + 1 + lane) : INT64_MAX;
-        int ri = 0;
-        int64_t cur_end = __shfl_sync(0xffffffffu, rend, 0);
         float acc = 0.f;
-        for (int64_t wb = row_at<IdxT>(a.rowptr, rbase); wb < eend; wb += 32) {
-            const int32_t c = wb + lane < eend ? ld_stream(a.colidx + wb + lane) : -1;
-            float v[32];
+        for (int64_t wb = row_at<IdxT>(a.rowptr, row); wb < eend; wb += kBW) {
+            const int32_t c = (lane < kBW && wb + lane < eend) ? ld_stream(a.colidx + wb + lane) : -1;
+            float v[kBW];
 #pragma unroll
-            for (int e = 0; e < 32; ++e) {
+            for (int e = 0; e < kBW; ++e) {
                 const int32_t u = __shfl_sync(0xffffffffu, c, e);
                 v[e] = u >= 0 ? __ldg(Y + (int64_t)u * kBK + lane) : 0.f;
             }
+            const int64_t pos = rend - 1 - wb;
+            const unsigned ends = __reduce_or_sync(0xffffffffu, (pos >= 0 && pos < kBW) ? (1u << pos) : 0u);
 #pragma unroll
-            for (int e = 0; e < 32; ++e) {
-                if (wb + e < eend) {
-                    acc += v[e];
-                    if (wb + e + 1 == cur_end) {      // row rbase + ri is complete
-                        a.S[(rbase + ri) * kBK + lane] = acc;
-                        acc = 0.f;
-                        if (++ri == 32) {
-                            rbase += 32;
-                            ri = 0;
-                            rend = rbase + 1 + lane <= r1 ? row_at<IdxT>(a.rowptr, rbase + 1 + lane)
-                                                          : INT64_MAX;
-                        }
-                        cur_end = __shfl_sync(0xffffffffu, rend, ri);
-                    }
+            for (int e = 0; e < kBW; ++e) {
+                acc += v[e];   // v[e] = 0 past the tile's last edge
+                if ((ends >> e) & 1u) {
+                    a.S[row * kBK + lane] = acc;
+                    acc = 0.f;
+                    ++row;
                 }
+            }
+            if (row - rbase >= kBW && row < r1) {
+                rbase = row;
+                rend = rbase + 1 + lane <= r1 ? row_at<IdxT>(a.rowptr, rbase + 1 + lane) : INT64_MAX;
             }
         }
     }
@@ -248,33 +250,51 @@ __global__ void __launch_bounds__(kBlock) k_b_update(BatchArgs a, const float* _
     const float dshare = s_dshare[lane], base = s_base[lane], d = s_d, omd = s_omd;
     const int32_t* tptr = s_tptr;
     Acc acc;
-    const int64_t rows_per_pass = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < a.n; v += rows_per_pass) {
-        float s = 0.f;
-        if (v < a.n_heavy) {
-            const int32_t q1 = a.seg_ptr[v + 1];
-            for (int32_t q = a.seg_ptr[v]; q < q1; ++q) s += __ldcg(a.P + (size_t)q * kBK + lane);
-        } else if (v < a.zero_start) {
-            s = __ldcs(a.S + (size_t)v * kBK + lane);
-        }
-        const float xo = __ldcs(Xin + (size_t)v * kBK + lane);
-        const float inv = __ldg(a.inv_out + v);
-        float xn = xo;
-        if (active) {
-            if (tptr) {
-                float tv = 0.f;
-                const int32_t p1 = tptr[v + 1];
-                for (int32_t p = tptr[v]; p < p1; ++p)
-                    if (s_tcol[p] == lane) tv = s_tval[p];
-                xn = fmaf(d, s, fmaf(omd, tv, dshare));
-            } else {
-                xn = fmaf(d, s, base);
+    // four rows per warp per pass: their loads are independent, so a warp has
+    // four 128-byte rows of S, X (and the segment partials of heavy rows) in flight
+    constexpr int kRows = 4;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t step = (((int64_t)gridDim.x * blockDim.x) >> 5) * kRows;
+    for (int64_t v0 = warp * kRows; v0 < a.n; v0 += step) {
+        float sv[kRows], xo[kRows], inv[kRows];
+#pragma unroll
+        for (int q = 0; q < kRows; ++q) {
+            const int64_t v = v0 + q;
+            sv[q] = 0.f;
+            xo[q] = 0.f;
+            inv[q] = 0.f;
+            if (v < a.n) {
+                if (v < a.n_heavy) {
+                    const int32_t q1 = a.seg_ptr[v + 1];
+                    for (int32_t j = a.seg_ptr[v]; j < q1; ++j) sv[q] += __ldcg(a.P + (size_t)j * kBK + lane);
+                } else if (v < a.zero_start) {
+                    sv[q] = __ldcs(a.S + (size_t)v * kBK + lane);
+                }
+                xo[q] = __ldcs(Xin + (size_t)v * kBK + lane);
+                inv[q] = __ldg(a.inv_out + v);
             }
         }
-        __stcs(Xout + (size_t)v * kBK + lane, xn);
-        __stcs(Yout + (size_t)v * kBK + lane, xn * inv);
-        acc.r += fabsf(xn - xo);
-        if (inv == 0.f) acc.kahan(xn);
+#pragma unroll
+        for (int q = 0; q < kRows; ++q) {
+            const int64_t v = v0 + q;
+            if (v >= a.n) break;
+            float xn = xo[q];
+            if (active) {
+                if (tptr) {
+                    float tv = 0.f;
+                    const int32_t p1 = tptr[v + 1];
+                    for (int32_t p = tptr[v]; p < p1; ++p)
+                        if (s_tcol[p] == lane) tv = s_tval[p];
+                    xn = fmaf(d, sv[q], fmaf(omd, tv, dshare));
+                } else {
+                    xn = fmaf(d, sv[q], base);
+                }
+            }
+            __stcs(Xout + (size_t)v * kBK + lane, xn);
+            __stcs(Yout + (size_t)v * kBK + lane, xn * inv[q]);
+            acc.r += fabsf(xn - xo[q]);
+            if (inv[q] == 0.f) acc.kahan(xn);
+        }
     }
     double R, Dn;
     if (batch_columns_to_grid((double)acc.r, acc.mass(), a.slots, &st->ticket, &R, &Dn) && threadIdx.x < 32) {
@@ -561,6 +581,13 @@ pr_status build_teleport_csr(pr_graph* g, BatchCtx* b, const float* t_dev, int k
 }
 
 }  // namespace
+
+void drop_batch_graph(pr_graph* g) {
+    if (g->batch && g->batch->loop_exec) {
+        cudaGraphExecDestroy(g->batch->loop_exec);
+        g->batch->loop_exec = nullptr;
+    }
+}
 
 void destroy_batch(pr_graph* g) {
     BatchCtx* b = g->batch;

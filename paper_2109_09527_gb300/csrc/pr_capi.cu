@@ -60,6 +60,7 @@ using namespace prk;
 extern "C" pr_status pr_destroy_graph(pr_graph* g) {
     if (!g) return PR_OK;
     destroy_batch(g);
+    destroy_set(g);
     void* dev[] = {g->rowptr, g->colidx, g->inv_out, g->order, g->rank, g->x[0], g->x[1],
                    g->y[0], g->y[1], g->teleport, g->stage, g->seg_row, g->seg_ptr, g->seg_sum,
                    g->tiles, g->state, g->slots, g->nb_items, g->nb_slots,
@@ -102,7 +103,21 @@ extern "C" pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* s) {
     return PR_OK;
 }
 
-extern "C" pr_status pr_set_option(pr_graph* g, int key, int64_t value) {
+namespace {
+
+void drop_loop_graphs(pr_graph* g) {
+    for (auto& ex : g->loop_exec)
+        if (ex) {
+            cudaGraphExecDestroy(ex);
+            ex = nullptr;
+        }
+    drop_batch_graph(g);
+    drop_set_graph(g);
+}
+
+}  // namespace
+
+static pr_status set_option_impl(pr_graph* g, int key, int64_t value) {
     switch (key) {
         case PR_OPT_HEAVY_DEGREE:
             if (g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_HEAVY_DEGREE is set with g = NULL (it applies to the next pr_create_graph)");
@@ -125,33 +140,18 @@ extern "C" pr_status pr_set_option(pr_graph* g, int key, int64_t value) {
             if (value < 0 || value > 0x7fffffffLL) return fail(PR_ERR_INVALID_ARG, "PR_OPT_HOT_VERTICES out of range");
             if ((value >> 28) > 4) return fail(PR_ERR_INVALID_ARG, "PR_OPT_HOT_VERTICES: policy (bits 28..31) must be 0..4");
             g->hot_vertices = value;
-            for (auto& ex : g->loop_exec)
-                if (ex) {
-                    cudaGraphExecDestroy(ex);
-                    ex = nullptr;
-                }
             return PR_OK;
         case PR_OPT_HOT_CACHE:
             if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_HOT_CACHE needs a graph");
             if (value < 0 || value > kHotCacheMax)
                 return fail(PR_ERR_INVALID_ARG, "PR_OPT_HOT_CACHE must be in [0, 40960]");
             g->hot_cache = value;
-            for (auto& ex : g->loop_exec)
-                if (ex) {
-                    cudaGraphExecDestroy(ex);
-                    ex = nullptr;
-                }
             return PR_OK;
         case PR_OPT_STAGED_TILES:
             if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_STAGED_TILES needs a graph");
             if (value < 0 || value > 3)
                 return fail(PR_ERR_INVALID_ARG, "PR_OPT_STAGED_TILES must be in [0, 3]");
             g->staged_tiles = (int)value;
-            for (auto& ex : g->loop_exec)
-                if (ex) {
-                    cudaGraphExecDestroy(ex);
-                    ex = nullptr;
-                }
             return PR_OK;
         case PR_OPT_NB_HUBS:
             if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_NB_HUBS needs a graph");
@@ -174,6 +174,14 @@ extern "C" pr_status pr_set_option(pr_graph* g, int key, int64_t value) {
             return fail(PR_ERR_INVALID_ARG, "unknown option key");
     }
 }
+
+extern "C" pr_status pr_set_option(pr_graph* g, int key, int64_t value) {
+    pr_status rc = set_option_impl(g, key, value);
+    // captured loop graphs bake the options in: rebuild them on next use
+    if (rc == PR_OK && g) drop_loop_graphs(g);
+    return rc;
+}
+
 
 extern "C" const char* pr_status_string(pr_status s) {
     switch (s) {

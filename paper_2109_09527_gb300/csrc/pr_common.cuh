@@ -31,6 +31,7 @@
 namespace prk {
 
 struct BatchCtx;   // buffers of the batched solver (pr_batched.cu)
+struct SetCtx;     // partition and buffers of the graph-set solver (pr_set.cu)
 
 constexpr int kBlock = 256;              // threads of a tile group (and of the small kernels)
 constexpr int kWarps = kBlock / 32;
@@ -184,6 +185,7 @@ struct pr_graph {
     cudaEvent_t ev_loop1 = nullptr;
 
     prk::BatchCtx* batch = nullptr;  // batched solver (built on first use)
+    prk::SetCtx* set = nullptr;      // graph-set partition (pr_graph_set_partition)
 };
 
 namespace prk {
@@ -228,8 +230,12 @@ void launch_finalize(const pr_graph* g, const IterArgs& a, float* out, bool reno
 // arrays); synchronises the stream before its temporaries are freed.
 cudaError_t scan_counts_i32(const int64_t* counts, int64_t count, int32_t* offsets, cudaStream_t st);
 
-// Frees the batched solver's buffers (nothing if it was never used).
+// Free the batched / graph-set solvers' buffers (nothing if never used), or
+// only their captured loop graphs.
 void destroy_batch(pr_graph* g);
+void destroy_set(pr_graph* g);
+void drop_batch_graph(pr_graph* g);
+void drop_set_graph(pr_graph* g);
 
 pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_iter,
                             const float* teleport, const float* x0, float* x_out, pr_info* info,
