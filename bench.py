@@ -315,6 +315,7 @@ def run_profile(args):
 BATCH_SCALE = 22
 BATCH_K = 32
 BATCH_SEEDS = 8
+BATCH_BF16_SWITCH = 2
 
 
 def batched_bytes(n, nnz, k_stride=32, rowptr_bytes=4):
@@ -407,6 +408,18 @@ def run_batched(args):
     achieved = b_iter * iters / (loop_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
 
+    # BF16 storage of Y for the early iterations (PR_OPT_BATCH_BF16), same tol
+    g.set_option(pr.PR_OPT_BATCH_BF16, BATCH_BF16_SWITCH)
+    step()
+    torch.cuda.synchronize()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record(stream)
+    bf_runs = [step() for _ in range(args.steps)]
+    b1.record(stream)
+    torch.cuda.synchronize()
+    bf_ms = b0.elapsed_time(b1) / args.steps
+    g.set_option(pr.PR_OPT_BATCH_BF16, 0)
+
     # the same 32 personalised solves one at a time (plain FP32 Jacobi)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -448,6 +461,12 @@ def run_batched(args):
                              "kernel": "batched iteration (k_b_segments + k_b_light + k_b_update)",
                              "bytes_per_iteration": b_iter, "ms_per_iteration": loop_ms / iters,
                              "peak_source": f"{peak_kind} hbm_gbs"},
+                "bf16_variant": {"ms_per_step": bf_ms, "speedup_vs_fp32": (ms / steps) / bf_ms,
+                                 "iterations": bf_runs[-1][0].iterations,
+                                 "max_residual_l1": bf_runs[-1][0].residual_l1,
+                                 "converged": bool(bf_runs[-1][0].converged),
+                                 "switch": f"BF16 Y until every active column's L1 change < "
+                                           f"1e-{BATCH_BF16_SWITCH}, then FP32"},
                 "vs_single_vector_jacobi": {"batched_ms": ms / steps, "single_ms_total": single_ms,
                                             "speedup": single_ms / (ms / steps),
                                             "single_iterations_total": single_iters,

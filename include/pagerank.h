@@ -220,6 +220,14 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
  *                         is an old or a new rank (aligned 32-bit accesses),
  *                         and the verifying synchronous update certifies the
  *                         result either way.  Set 0 for a race-free run.
+ *   PR_OPT_BATCH_BF16     batched solver only: 0 (default) keeps the quotient
+ *                         matrix Y in FP32; m in 1..8 also keeps a BF16 copy
+ *                         and gathers from it (half the bytes per gathered
+ *                         row, FP32 accumulation) until every active column's
+ *                         L1 change is below 10^-m, then gathers from the FP32
+ *                         copy to the end.  X stays FP32 throughout, so the
+ *                         result meets the same tol; BF16's 2^-9 rounding
+ *                         limits how far the BF16 phase can go (m ~ 2..3).
  *   PR_OPT_INDEX64        1: keep 64-bit row offsets on the device even when
  *                         the edge count fits 32 bits (thread-local default
  *                         for the next pr_create_graph, set with g = NULL;
@@ -234,6 +242,7 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
 #define PR_OPT_STAGED_TILES 7
 #define PR_OPT_NB_HUBS 8
 #define PR_OPT_NB_L1_HUBS 9
+#define PR_OPT_BATCH_BF16 10
 PR_API pr_status pr_set_option(pr_graph* g, int key, int64_t value);
 
 /* Batched personalised PageRank: k independent solves on one graph, one per

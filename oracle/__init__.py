@@ -62,6 +62,12 @@ def _declare(lib):
                                        vp, vp, vp]
     lib.or_dense_solve.restype = ctypes.c_int
     lib.or_dense_solve.argtypes = [i64, vp, vp, dbl, vp, ctypes.c_int, vp]
+    lib.or_w_outweight.restype = ctypes.c_int
+    lib.or_w_outweight.argtypes = [i64, vp, vp, vp, vp]
+    lib.or_w_jacobi.restype = ctypes.c_int
+    lib.or_w_jacobi.argtypes = [i64, vp, vp, vp, dbl, vp, dbl, i32, vp, vp, vp, vp]
+    lib.or_w_adjoint.restype = ctypes.c_int
+    lib.or_w_adjoint.argtypes = [i64, vp, vp, vp, dbl, vp, vp, dbl, i32, vp, vp, vp, vp, vp, vp]
     lib.or_nosync.restype = ctypes.c_int
     lib.or_nosync.argtypes = [i64, vp, vp, dbl, vp, ctypes.c_int, ctypes.c_int, i32, vp,
                               ctypes.c_int, dbl, i32, vp, vp, vp, vp, vp]
@@ -218,3 +224,87 @@ def nosync(rowptr, colidx, d=0.85, p=4, tol=1e-10, max_sweeps=1000, t=None, x0=N
                          0 if norm == "l1" else 1, tol, max_sweeps, _p(x0), _p(x), _p(sweeps),
                          ctypes.byref(upd), ctypes.byref(est)), "or_nosync")
     return x, sweeps, upd.value, est.value
+
+
+# ------------------------------------------------------------ weighted graphs --
+
+def _weights(w, nnz):
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    if w.shape != (nnz,):
+        raise ValueError(f"expected {nnz} edge weights")
+    if nnz == 0:
+        w = np.ones(1, dtype=np.float64)
+    return w
+
+
+def w_outweight(rowptr, colidx, w, lib=None):
+    """W(u) = sum of the weights of u's out-edges (edges given as an in-edge CSR)."""
+    lib = lib or load()
+    rowptr, colidx = _csr(rowptr, colidx)
+    n = rowptr.size - 1
+    W = np.empty(n, dtype=np.float64)
+    _check(lib.or_w_outweight(n, _p(rowptr), _p(colidx), _p(_weights(w, int(rowptr[-1]))), _p(W)),
+           "or_w_outweight")
+    return W
+
+
+def w_pagerank(rowptr, colidx, w, d=0.85, t=None, tol=1e-13, max_iter=5000, x0=None, lib=None):
+    """Alg. 1 on the weighted graph (P(u,v) = w(u,v)/W(u)).  Returns (x, iterations, last_l1)."""
+    lib = lib or load()
+    rowptr, colidx = _csr(rowptr, colidx)
+    n = rowptr.size - 1
+    x = np.empty(n, dtype=np.float64)
+    it, res = ctypes.c_int32(), ctypes.c_double()
+    _check(lib.or_w_jacobi(n, _p(rowptr), _p(colidx), _p(_weights(w, int(rowptr[-1]))), d,
+                           _p(_vec(t, n)), tol, max_iter, _p(_vec(x0, n)), _p(x), ctypes.byref(it),
+                           ctypes.byref(res)), "or_w_jacobi")
+    return x, it.value, res.value
+
+
+def w_adjoint(rowptr, colidx, w, x, c, d=0.85, tol=1e-14, max_iter=5000, lib=None):
+    """Adjoint of L = c^T x at the weighted fixed point x.  Returns a dict with lambda, mu,
+    grad_t (dL/dt) and grad_w (dL/dw per edge, aligned with colidx), iterations, residual."""
+    lib = lib or load()
+    rowptr, colidx = _csr(rowptr, colidx)
+    n = rowptr.size - 1
+    nnz = int(rowptr[-1])
+    lam, mu, gt = (np.empty(n, dtype=np.float64) for _ in range(3))
+    gw = np.empty(max(nnz, 1), dtype=np.float64)
+    it, res = ctypes.c_int32(), ctypes.c_double()
+    _check(lib.or_w_adjoint(n, _p(rowptr), _p(colidx), _p(_weights(w, nnz)), d, _p(_vec(x, n)),
+                            _p(_vec(c, n)), tol, max_iter, _p(lam), _p(mu), _p(gt), _p(gw),
+                            ctypes.byref(it), ctypes.byref(res)), "or_w_adjoint")
+    return {"lambda": lam, "mu": mu, "grad_t": gt, "grad_w": gw[:nnz], "iterations": it.value,
+            "residual": res.value}
+
+
+def dense_adjoint(rowptr, colidx, w, c, d=0.85, t=None):
+    """The same gradients by dense linear algebra (small n): M = I - d P^T - (d/n) 1 a^T is
+    assembled explicitly, x = (1-d) M^-1 t and lambda = M^-T c by numpy's solver, and each
+    edge weight's gradient is -lambda^T (dM/dw_e) x with dM/dw_e assembled from the
+    quotient rule on P(u,.) = w(u,.)/W(u).  Returns (x, lambda, grad_t, grad_w)."""
+    rowptr = np.asarray(rowptr, dtype=np.int64)
+    colidx = np.asarray(colidx, dtype=np.int64)
+    w = np.asarray(w, dtype=np.float64)
+    n = rowptr.size - 1
+    t = np.full(n, 1.0 / n) if t is None else np.asarray(t, dtype=np.float64)
+    dst = np.repeat(np.arange(n), np.diff(rowptr))
+    W = np.zeros(n)
+    np.add.at(W, colidx, w)
+    P = np.zeros((n, n))                      # P[u, v]
+    for e in range(colidx.size):
+        P[colidx[e], dst[e]] += w[e] / W[colidx[e]]
+    a = (W == 0.0).astype(np.float64)
+    M = np.eye(n) - d * P.T - (d / n) * np.outer(np.ones(n), a)
+    x = np.linalg.solve(M, (1.0 - d) * t)
+    lam = np.linalg.solve(M.T, np.asarray(c, dtype=np.float64))
+    grad_t = (1.0 - d) * lam
+    grad_w = np.empty(colidx.size)
+    for e in range(colidx.size):
+        u, v = colidx[e], dst[e]
+        dP = np.zeros((n, n))                 # d P / d w_e: row u only
+        dP[u, :] = -P[u, :] / W[u]
+        dP[u, v] += 1.0 / W[u]
+        dM = -d * dP.T
+        grad_w[e] = -lam @ dM @ x
+    return x, lam, grad_t, grad_w

@@ -30,6 +30,17 @@
  *   or_dense_solve     the fixed point as the solution of the linear system
  *                      (I - d*A - (d/n)*1*a^T) x = (1-d)*t by Gaussian
  *                      elimination with partial pivoting (small n only).
+ *   or_w_outweight     weighted graphs: W(u) = sum of the weights of u's
+ *                      out-edges (the row normaliser of the transition
+ *                      matrix P(u,v) = w(u,v)/W(u)).
+ *   or_w_jacobi        Alg. 1 on a weighted graph: x(v) = (1-d) t(v) + d *
+ *                      ( sum_{(u,v)} x(u) w(u,v)/W(u) + D/n ).
+ *   or_w_adjoint       the adjoint of the weighted fixed point for a loss
+ *                      L = c^T x: the solution lambda of M^T lambda = c with
+ *                      M = I - d P^T - (d/n) 1 a^T (Jacobi iteration on the
+ *                      transposed system), then dL/dt = (1-d) lambda and, for
+ *                      an edge e = (u, v), dL/dw(e) = d x(u)/W(u) *
+ *                      (lambda(v) - sum_{v'} P(u,v') lambda(v')).
  *   or_nosync          the lock-free No-Sync scheme, Alg. 3: p simulated
  *                      threads, static equal partitions, in-place updates,
  *                      thread-level convergence; two forms of the dangling
@@ -40,7 +51,12 @@
  * or_vertex_update and or_dense_solve are pinned by closed forms, by the
  * random-surfer stationary distribution and by a library PageRank in the
  * CPU test suite; or_nosync is pinned by Lemma 2 (same fixed point) and by
- * its single-thread case, Gauss-Seidel.
+ * its single-thread case, Gauss-Seidel.  or_w_jacobi is pinned by unit
+ * weights (the unweighted oracle), by invariance under scaling one vertex's
+ * out-weights, and by a dense solve; or_w_adjoint by the dense adjoint
+ * (numpy linear algebra on explicit dM/dw matrices, n <= 12), by central
+ * finite differences of or_w_jacobi, and by the identities
+ * (1-d) lambda^T t = c^T x and sum_{e out of u} w(e) dL/dw(e) = 0.
  */
 #include <math.h>
 #include <stdint.h>
@@ -309,5 +325,125 @@ OR_API int or_nosync(int64_t n, const int64_t* rowptr, const int32_t* colidx, do
     if (updates) *updates = total_updates;
     if (est) *est = combined;
     free(outdeg); free(thread_err); free(local_err); free(pos); free(stopped);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------ weighted graphs -- */
+
+/* W(u) = sum of w(e) over the edges e = (u, v), read from the in-edge CSR
+ * (weights w[e] are aligned with colidx). */
+OR_API int or_w_outweight(int64_t n, const int64_t* rowptr, const int32_t* colidx, const double* w,
+                          double* W) {
+    int rc = or_check_csr(n, rowptr, colidx);
+    if (rc) return rc;
+    for (int64_t u = 0; u < n; ++u) W[u] = 0.0;
+    for (int64_t e = 0; e < rowptr[n]; ++e) {
+        if (!(w[e] > 0.0)) return OR_BAD_ARG;
+        W[colidx[e]] += w[e];
+    }
+    return OR_OK;
+}
+
+/* Alg. 1 on the weighted graph from x0 (default t) until the L1 change of an
+ * iteration is below tol or max_iter iterations.  A vertex with W(u) = 0 is
+ * dangling; its rank is spread uniformly. */
+OR_API int or_w_jacobi(int64_t n, const int64_t* rowptr, const int32_t* colidx, const double* w, double d,
+                       const double* t, double tol, int32_t max_iter, const double* x0, double* x,
+                       int32_t* iterations, double* residual) {
+    int rc = or_check_csr(n, rowptr, colidx);
+    if (rc) return rc;
+    if (!(d >= 0.0 && d < 1.0) || max_iter < 0) return OR_BAD_ARG;
+    double* W = (double*)malloc((size_t)n * sizeof(double));
+    double* xn = (double*)malloc((size_t)n * sizeof(double));
+    if (!W || !xn) { free(W); free(xn); return OR_NO_MEM; }
+    rc = or_w_outweight(n, rowptr, colidx, w, W);
+    if (rc) { free(W); free(xn); return rc; }
+    for (int64_t v = 0; v < n; ++v) x[v] = x0 ? x0[v] : or_teleport(n, t, v);
+    int32_t it = 0;
+    double r = INFINITY;
+    while (it < max_iter) {
+        double D = 0.0;
+        for (int64_t u = 0; u < n; ++u)
+            if (W[u] == 0.0) D += x[u];
+        r = 0.0;
+        for (int64_t v = 0; v < n; ++v) {
+            double s = 0.0;
+            for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+                int64_t u = colidx[e];
+                s += x[u] * w[e] / W[u];
+            }
+            xn[v] = (1.0 - d) * or_teleport(n, t, v) + d * (s + D / (double)n);
+            r += fabs(xn[v] - x[v]);
+        }
+        memcpy(x, xn, (size_t)n * sizeof(double));
+        ++it;
+        if (r < tol) break;
+    }
+    if (iterations) *iterations = it;
+    if (residual) *residual = r;
+    free(W);
+    free(xn);
+    return OR_OK;
+}
+
+/* The adjoint of L = c^T x at the weighted fixed point x: lambda solves
+ *   lambda(u) = c(u) + d * ( sum_{(u,v)} P(u,v) lambda(v) + a(u) * sum(lambda)/n ),
+ * a(u) = 1 for dangling u (M^T lambda = c), iterated synchronously until the
+ * L1 change is below tol * ||c||_1 or max_iter.  Outputs lambda, mu(u) =
+ * sum_v P(u,v) lambda(v), dL/dt = (1-d) lambda, and dL/dw for every edge. */
+OR_API int or_w_adjoint(int64_t n, const int64_t* rowptr, const int32_t* colidx, const double* w, double d,
+                        const double* x, const double* c, double tol, int32_t max_iter, double* lambda,
+                        double* mu, double* grad_t, double* grad_w, int32_t* iterations, double* residual) {
+    int rc = or_check_csr(n, rowptr, colidx);
+    if (rc) return rc;
+    if (!(d >= 0.0 && d < 1.0) || max_iter < 0) return OR_BAD_ARG;
+    double* W = (double*)malloc((size_t)n * sizeof(double));
+    double* ln = (double*)malloc((size_t)n * sizeof(double));
+    if (!W || !ln) { free(W); free(ln); return OR_NO_MEM; }
+    rc = or_w_outweight(n, rowptr, colidx, w, W);
+    if (rc) { free(W); free(ln); return rc; }
+    double cnorm = 0.0;
+    for (int64_t u = 0; u < n; ++u) {
+        lambda[u] = c[u];
+        cnorm += fabs(c[u]);
+    }
+    int32_t it = 0;
+    double r = INFINITY;
+    while (it < max_iter) {
+        double L = 0.0;
+        for (int64_t u = 0; u < n; ++u) L += lambda[u];
+        for (int64_t u = 0; u < n; ++u) mu[u] = 0.0;
+        /* the in-edge (u, v) of row v pushes P(u,v) lambda(v) to u */
+        for (int64_t v = 0; v < n; ++v)
+            for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+                int64_t u = colidx[e];
+                mu[u] += w[e] / W[u] * lambda[v];
+            }
+        r = 0.0;
+        for (int64_t u = 0; u < n; ++u) {
+            ln[u] = c[u] + d * (mu[u] + (W[u] == 0.0 ? L / (double)n : 0.0));
+            r += fabs(ln[u] - lambda[u]);
+        }
+        memcpy(lambda, ln, (size_t)n * sizeof(double));
+        ++it;
+        if (r < tol * cnorm) break;
+    }
+    /* mu of the final lambda, then the gradients */
+    for (int64_t u = 0; u < n; ++u) mu[u] = 0.0;
+    for (int64_t v = 0; v < n; ++v)
+        for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+            int64_t u = colidx[e];
+            mu[u] += w[e] / W[u] * lambda[v];
+        }
+    for (int64_t u = 0; u < n; ++u) grad_t[u] = (1.0 - d) * lambda[u];
+    for (int64_t v = 0; v < n; ++v)
+        for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+            int64_t u = colidx[e];
+            grad_w[e] = d * x[u] / W[u] * (lambda[v] - mu[u]);
+        }
+    if (iterations) *iterations = it;
+    if (residual) *residual = r;
+    free(W);
+    free(ln);
     return OR_OK;
 }

@@ -35,6 +35,8 @@
 #include <cstring>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "pr_tile.cuh"
 
 namespace prk {
@@ -55,6 +57,9 @@ struct BatchState {
     uint32_t active;                 // bit j: column j still iterating
     uint32_t error;                  // bit 0: a column with a non-positive or negative teleport
     int32_t uniform;                 // 1: every column's teleport is 1/n
+    int32_t bf16;                    // 1 while the gathers read the BF16 copy of Y
+    int32_t pad0;
+    double bf16_switch;              // leave BF16 once every active column's change is below this
     const int32_t* tptr;             // teleport nonzeros of each binned row (CSR), when !uniform
     const int32_t* tcol;
     const float* tval;
@@ -87,6 +92,33 @@ struct BatchArgs {
     int32_t pad;
 };
 
+// A quotient of Y as float, from FP32 or BF16 storage.
+__device__ __forceinline__ float ld_q(const float* Y, int64_t i) { return __ldg(Y + i); }
+__device__ __forceinline__ float ld_q(const __nv_bfloat16* Y, int64_t i) {
+    return __bfloat162float(__ldg(Y + i));
+}
+
+template <typename T>
+constexpr int kIsBf16 = 0;
+template <>
+constexpr int kIsBf16<__nv_bfloat16> = 1;
+
+// True if this launch has nothing to do: the solve is done, or the gathers
+// read the other storage type of Y in this phase.
+template <typename T>
+__device__ __forceinline__ bool batch_skip(const BatchState* st) {
+    __shared__ int32_t skip;
+    if (threadIdx.x == 0) {
+        const int32_t done = *(const volatile int32_t*)&st->done;
+        const int32_t bf = *(const volatile int32_t*)&st->bf16;
+        skip = done || (bf != kIsBf16<T>);
+    }
+    __syncthreads();
+    const bool v = skip;
+    __syncthreads();
+    return v;
+}
+
 // done flag of the solve, read once per block.
 __device__ __forceinline__ int32_t batch_done(const BatchState* st) {
     __shared__ int32_t done;
@@ -98,9 +130,9 @@ __device__ __forceinline__ int32_t batch_done(const BatchState* st) {
 }
 
 // Heavy rows: one warp per segment; lane j accumulates column j.
-template <typename IdxT>
-__global__ void __launch_bounds__(kBlock) k_b_segments(BatchArgs a, const float* __restrict__ Y) {
-    if (batch_done(a.state)) return;
+template <typename IdxT, typename T>
+__global__ void __launch_bounds__(kBlock) k_b_segments(BatchArgs a, const T* __restrict__ Y) {
+    if (batch_skip<T>(a.state)) return;
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -116,7 +148,7 @@ __global__ void __launch_bounds__(kBlock) k_b_segments(BatchArgs a, const float*
 #pragma unroll
             for (int e = 0; e < 32; ++e) {
                 const int32_t u = __shfl_sync(0xffffffffu, c, e);
-                v[e] = u >= 0 ? __ldg(Y + (int64_t)u * kBK + lane) : 0.f;
+                v[e] = u >= 0 ? ld_q(Y, (int64_t)u * kBK + lane) : 0.f;
             }
 #pragma unroll
             for (int e = 0; e < 32; ++e) acc += v[e];
@@ -135,9 +167,9 @@ __global__ void __launch_bounds__(kBlock) k_b_segments(BatchArgs a, const float*
 // last edge in the window) gives all of them as a bit mask.
 constexpr int kBW = 16;
 
-template <typename IdxT>
-__global__ void __launch_bounds__(kBlock, 4) k_b_light(BatchArgs a, const float* __restrict__ Y) {
-    if (batch_done(a.state)) return;
+template <typename IdxT, typename T>
+__global__ void __launch_bounds__(kBlock, 4) k_b_light(BatchArgs a, const T* __restrict__ Y) {
+    if (batch_skip<T>(a.state)) return;
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -156,7 +188,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_b_light(BatchArgs a, const float*
 #pragma unroll
             for (int e = 0; e < kBW; ++e) {
                 const int32_t u = __shfl_sync(0xffffffffu, c, e);
-                v[e] = u >= 0 ? __ldg(Y + (int64_t)u * kBK + lane) : 0.f;
+                v[e] = u >= 0 ? ld_q(Y, (int64_t)u * kBK + lane) : 0.f;
             }
             const int64_t pos = rend - 1 - wb;
             const unsigned ends = __reduce_or_sync(0xffffffffu, (pos >= 0 && pos < kBW) ? (1u << pos) : 0u);
@@ -216,7 +248,9 @@ __device__ __forceinline__ bool batch_columns_to_grid(double a, double b, double
 
 // X' from S / P, per-column dangling mass and L1 change; lane j = column j.
 __global__ void __launch_bounds__(kBlock) k_b_update(BatchArgs a, const float* __restrict__ Xin,
-                                                     float* __restrict__ Xout, float* __restrict__ Yout) {
+                                                     float* __restrict__ Xout, float* __restrict__ Yout,
+                                                     __nv_bfloat16* __restrict__ Yout16) {
+    __shared__ int32_t s_bf16;
     __shared__ float s_dshare[kBK];
     __shared__ float s_base[kBK];
     __shared__ uint32_t s_active;
@@ -233,6 +267,7 @@ __global__ void __launch_bounds__(kBlock) k_b_update(BatchArgs a, const float* _
         s_base[lane] = (float)((1.0 - d) * st->inv_n + d * st->D[lane] * st->inv_n);
         if (lane == 0) {
             s_active = st->active;
+            s_bf16 = st->bf16;
             s_done = *(const volatile int32_t*)&st->done;
             s_tptr = st->uniform ? nullptr : st->tptr;
             s_tcol = st->tcol;
@@ -292,6 +327,7 @@ __global__ void __launch_bounds__(kBlock) k_b_update(BatchArgs a, const float* _
             }
             __stcs(Xout + (size_t)v * kBK + lane, xn);
             __stcs(Yout + (size_t)v * kBK + lane, xn * inv[q]);
+            if (s_bf16) Yout16[(size_t)v * kBK + lane] = __float2bfloat16_rn(xn * inv[q]);
             acc.r += fabsf(xn - xo[q]);
             if (inv[q] == 0.f) acc.kahan(xn);
         }
@@ -299,15 +335,26 @@ __global__ void __launch_bounds__(kBlock) k_b_update(BatchArgs a, const float* _
     double R, Dn;
     if (batch_columns_to_grid((double)acc.r, acc.mass(), a.slots, &st->ticket, &R, &Dn) && threadIdx.x < 32) {
         const bool was_active = (s_active >> lane) & 1u;
+        const double prev = st->resid[lane];
         st->D[lane] = Dn;
         const int32_t it = st->iter + 1;
         if (was_active) {
             st->resid[lane] = R;
             st->col_iter[lane] = it;
         }
-        const bool stays = was_active && !(R < st->tol);
+        // A column converges only on FP32 iterates: in the BF16 phase the
+        // iteration contracts towards the fixed point of the rounded map, whose
+        // changes can fall below tol away from the true fixed point.
+        const bool bf = st->bf16 != 0;
+        const bool stays = was_active && (bf || !(R < st->tol));
         const uint32_t mask = __ballot_sync(0xffffffffu, stays);
+        // BF16 phase: leave it once no active column both changes by
+        // max(bf16_switch, tol) or more and still shrinks its change by 10% an
+        // iteration (past that, BF16 rounding, not the iteration, sets the change)
+        const double sw = fmax(st->bf16_switch, st->tol);
+        const uint32_t big = __ballot_sync(0xffffffffu, was_active && !(R < sw) && R < 0.9 * prev);
         if (lane == 0) {
+            if (bf && big == 0u) st->bf16 = 0;
             st->active = mask;
             st->iter = it;
             const int done = mask == 0u || it >= st->max_iter;
@@ -322,7 +369,7 @@ __global__ void __launch_bounds__(kBlock) k_b_update(BatchArgs a, const float* _
 // the loop state.  t_dense: caller order, n x k, or NULL for uniform.
 __global__ void __launch_bounds__(kBlock) k_b_init(BatchArgs a, const float* __restrict__ t_dense,
                                                    const int32_t* __restrict__ order, float* __restrict__ X,
-                                                   float* __restrict__ Y) {
+                                                   float* __restrict__ Y, __nv_bfloat16* __restrict__ Y16) {
     BatchState* st = a.state;
     const int lane = threadIdx.x & 31;
     const int k = st->k;
@@ -339,6 +386,7 @@ __global__ void __launch_bounds__(kBlock) k_b_init(BatchArgs a, const float* __r
         const float inv = a.inv_out[v];
         X[(size_t)v * kBK + lane] = tv;
         Y[(size_t)v * kBK + lane] = tv * inv;
+        if (Y16) Y16[(size_t)v * kBK + lane] = __float2bfloat16_rn(tv * inv);
         if (inv == 0.f) dsum += (double)tv;
         tsum += (double)tv;
     }
@@ -424,6 +472,8 @@ __global__ void k_b_unpermute(BatchArgs a, const float* __restrict__ X0, const f
 struct BatchCtx {
     float* X[2] = {nullptr, nullptr};
     float* Y[2] = {nullptr, nullptr};
+    __nv_bfloat16* Y16[2] = {nullptr, nullptr};   // BF16 copies of Y (first BF16 solve)
+    int graph_bf16 = -1;             // storage mode the captured loop graph was built for
     float* S = nullptr;
     float* P = nullptr;
     int32_t* tptr = nullptr;
@@ -475,19 +525,27 @@ int update_grid(const pr_graph* g, const BatchCtx* b) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)b->slot_blocks));
 }
 
+// One iteration.  With BF16 storage both gather versions are enqueued and the
+// one that does not match the current phase returns at once.
 template <typename IdxT>
 cudaError_t enqueue_batch_iteration(const pr_graph* g, const BatchCtx* b, const BatchArgs& a, int src,
-                                    cudaStream_t s) {
-    if (g->n_seg > 0)
-        k_b_segments<IdxT><<<batch_grid(g, g->n_seg, g_occ_bseg), kBlock, 0, s>>>(a, b->Y[src]);
-    k_b_light<IdxT><<<batch_grid(g, g->n_tiles, g_occ_blight), kBlock, 0, s>>>(a, b->Y[src]);
-    k_b_update<<<update_grid(g, b), kBlock, 0, s>>>(a, b->X[src], b->X[1 - src], b->Y[1 - src]);
+                                    bool bf16, cudaStream_t s) {
+    const int gs = batch_grid(g, g->n_seg, g_occ_bseg), gl = batch_grid(g, g->n_tiles, g_occ_blight);
+    if (bf16) {
+        if (g->n_seg > 0) k_b_segments<IdxT, __nv_bfloat16><<<gs, kBlock, 0, s>>>(a, b->Y16[src]);
+        k_b_light<IdxT, __nv_bfloat16><<<gl, kBlock, 0, s>>>(a, b->Y16[src]);
+    }
+    if (g->n_seg > 0) k_b_segments<IdxT, float><<<gs, kBlock, 0, s>>>(a, b->Y[src]);
+    k_b_light<IdxT, float><<<gl, kBlock, 0, s>>>(a, b->Y[src]);
+    k_b_update<<<update_grid(g, b), kBlock, 0, s>>>(a, b->X[src], b->X[1 - src], b->Y[1 - src],
+                                                   bf16 ? b->Y16[1 - src] : nullptr);
     return cudaGetLastError();
 }
 
-cudaError_t enqueue_batch(const pr_graph* g, const BatchCtx* b, const BatchArgs& a, int src, cudaStream_t s) {
-    return g->idx64 ? enqueue_batch_iteration<int64_t>(g, b, a, src, s)
-                    : enqueue_batch_iteration<int32_t>(g, b, a, src, s);
+cudaError_t enqueue_batch(const pr_graph* g, const BatchCtx* b, const BatchArgs& a, int src, bool bf16,
+                          cudaStream_t s) {
+    return g->idx64 ? enqueue_batch_iteration<int64_t>(g, b, a, src, bf16, s)
+                    : enqueue_batch_iteration<int32_t>(g, b, a, src, bf16, s);
 }
 
 pr_status ensure_batch(pr_graph* g) {
@@ -514,15 +572,15 @@ pr_status ensure_batch(pr_graph* g) {
         }
     if (g_occ_bseg == 0) {
         int o = 0;
-        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_b_segments<int32_t>, kBlock, 0));
+        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_b_segments<int32_t, float>, kBlock, 0));
         g_occ_bseg = std::max(1, o);
-        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_b_light<int32_t>, kBlock, 0));
+        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_b_light<int32_t, float>, kBlock, 0));
         g_occ_blight = std::max(1, o);
     }
     return PR_OK;
 }
 
-pr_status build_batch_graph(pr_graph* g, BatchCtx* b) {
+pr_status build_batch_graph(pr_graph* g, BatchCtx* b, bool bf16) {
     cudaGraph_t graph = nullptr;
     PRK_CHECK(cudaGraphCreate(&graph, 0));
     struct Guard {
@@ -544,15 +602,16 @@ pr_status build_batch_graph(pr_graph* g, BatchCtx* b) {
     a.use_cond = 1;
     PRK_CHECK(cudaStreamBeginCaptureToGraph(g->capture_stream, body, nullptr, nullptr, 0,
                                             cudaStreamCaptureModeThreadLocal));
-    cudaError_t e1 = enqueue_batch(g, b, a, 0, g->capture_stream);
+    cudaError_t e1 = enqueue_batch(g, b, a, 0, bf16, g->capture_stream);
     cudaError_t e2 = cudaSuccess;
-    if (e1 == cudaSuccess) e2 = enqueue_batch(g, b, a, 1, g->capture_stream);
+    if (e1 == cudaSuccess) e2 = enqueue_batch(g, b, a, 1, bf16, g->capture_stream);
     cudaGraph_t captured = nullptr;
     cudaError_t e3 = cudaStreamEndCapture(g->capture_stream, &captured);
     PRK_CHECK(e1);
     PRK_CHECK(e2);
     PRK_CHECK(e3);
     PRK_CHECK(cudaGraphInstantiate(&b->loop_exec, graph, 0));
+    b->graph_bf16 = bf16 ? 1 : 0;
     return PR_OK;
 }
 
@@ -592,8 +651,8 @@ void drop_batch_graph(pr_graph* g) {
 void destroy_batch(pr_graph* g) {
     BatchCtx* b = g->batch;
     if (!b) return;
-    void* dev[] = {b->X[0], b->X[1], b->Y[0], b->Y[1], b->S, b->P, b->tptr, b->tcol, b->tval,
-                   b->tcount, b->t_stage, b->out_stage, b->state, b->slots};
+    void* dev[] = {b->X[0], b->X[1], b->Y[0], b->Y[1], b->Y16[0], b->Y16[1], b->S, b->P, b->tptr,
+                   b->tcol, b->tval, b->tcount, b->t_stage, b->out_stage, b->state, b->slots};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (b->host_state) cudaFreeHost(b->host_state);
@@ -640,8 +699,16 @@ extern "C" pr_status pr_solve_batched(pr_graph* g, float damping, double tol, in
         out = b->out_stage;
     }
 
+    const bool bf16 = g->batch_bf16 > 0;
+    if (bf16 && !b->Y16[0]) {
+        const size_t m16 = (size_t)(g->n + kPad) * kBK * sizeof(__nv_bfloat16);
+        PRK_CHECK(dev_alloc(g, (void**)&b->Y16[0], m16));
+        PRK_CHECK(dev_alloc(g, (void**)&b->Y16[1], m16));
+    }
     BatchState* hs = b->host_state;
     memset(hs, 0, sizeof(BatchState));
+    hs->bf16 = bf16 ? 1 : 0;
+    hs->bf16_switch = bf16 ? std::pow(10.0, -(double)g->batch_bf16) : 0.0;
     hs->d = (double)damping;
     hs->inv_n = 1.0 / (double)g->n;
     hs->tol = tol;
@@ -655,12 +722,14 @@ extern "C" pr_status pr_solve_batched(pr_graph* g, float damping, double tol, in
     PRK_CHECK(cudaMemcpyAsync(b->state, hs, sizeof(BatchState), cudaMemcpyHostToDevice, s));
     BatchArgs a = batch_args(g, b);
     int launches = 0;
-    k_b_init<<<update_grid(g, b), kBlock, 0, s>>>(a, t_dev, g->order, b->X[0], b->Y[0]);
+    k_b_init<<<update_grid(g, b), kBlock, 0, s>>>(a, t_dev, g->order, b->X[0], b->Y[0],
+                                                 bf16 ? b->Y16[0] : nullptr);
     ++launches;
     PRK_CHECK(cudaGetLastError());
     PRK_CHECK(cudaEventRecord(g->ev_loop0, s));
     if (g->use_graph) {
-        if (!b->loop_exec && (rc = build_batch_graph(g, b)) != PR_OK) return rc;
+        if (b->loop_exec && b->graph_bf16 != (bf16 ? 1 : 0)) drop_batch_graph(g);
+        if (!b->loop_exec && (rc = build_batch_graph(g, b, bf16)) != PR_OK) return rc;
         PRK_CHECK(cudaGraphLaunch(b->loop_exec, s));
         ++launches;
     } else {
@@ -669,8 +738,8 @@ extern "C" pr_status pr_solve_batched(pr_graph* g, float damping, double tol, in
         for (int32_t it = 0; it < max_iter;) {
             const int c = std::min<int32_t>(8, max_iter - it);
             for (int i = 0; i < c; ++i) {
-                PRK_CHECK(enqueue_batch(g, b, a, (it + i) & 1, s));
-                launches += g->n_seg > 0 ? 3 : 2;
+                PRK_CHECK(enqueue_batch(g, b, a, (it + i) & 1, bf16, s));
+                launches += (g->n_seg > 0 ? 3 : 2) + (bf16 ? (g->n_seg > 0 ? 2 : 1) : 0);
             }
             it += c;
             PRK_CHECK(cudaMemcpyAsync(hs, b->state, sizeof(BatchState), cudaMemcpyDeviceToHost, s));

@@ -165,6 +165,11 @@ static pr_status set_option_impl(pr_graph* g, int key, int64_t value) {
                 return fail(PR_ERR_INVALID_ARG, "PR_OPT_NB_L1_HUBS must be in [0, 2^31-1]");
             g->nb_l1_hubs = value;
             return PR_OK;
+        case PR_OPT_BATCH_BF16:
+            if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_BATCH_BF16 needs a graph");
+            if (value < 0 || value > 8) return fail(PR_ERR_INVALID_ARG, "PR_OPT_BATCH_BF16 must be in [0, 8]");
+            g->batch_bf16 = (int)value;
+            return PR_OK;
         case PR_OPT_INDEX64:
             if (g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_INDEX64 is set with g = NULL (it applies to the next pr_create_graph)");
             if (value != 0 && value != 1) return fail(PR_ERR_INVALID_ARG, "PR_OPT_INDEX64 is 0 or 1");

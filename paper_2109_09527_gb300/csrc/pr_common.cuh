@@ -133,6 +133,7 @@ struct pr_graph {
     int64_t hot_cache = 0;                    // size of the shared-memory copy of y's prefix (off)
     int64_t nb_hubs = prk::kDefaultNbHubs;    // hub snapshot of the barrier-free kernel (PR_OPT_NB_HUBS)
     int64_t nb_l1_hubs = prk::kDefaultNbL1Hubs;  // weak L1-cached hub gathers (PR_OPT_NB_L1_HUBS)
+    int batch_bf16 = 0;                       // batched solver: BF16 Y until changes < 10^-value (0 = off)
     int staged_tiles = prk::kDefaultStaged;   // bit 0: Jacobi, bit 1: barrier-free (see PR_OPT_STAGED_TILES)
 
     void* rowptr = nullptr;

@@ -183,3 +183,26 @@ def test_fullsize_rmat22_k32_certified():
             xv = oracle.vertex_update(int(v), rp, ci, xj, dmass, d=D, t=tj, deg=deg)
             assert xv == pytest.approx(xn[v], rel=1e-12)
             assert abs(xv - xj[v]) <= 1e-3 * xj[v]
+
+
+@pytest.mark.parametrize("switch", [2, 3, 8])
+def test_bf16_storage_phase_reaches_the_fixed_point(switch):
+    """BF16 copy of Y gathered until the column changes fall below 10^-switch (8: below tol,
+    so until the BF16 rounding stalls them or tol is reached), then FP32: every column meets
+    tol on FP32 iterates, and its distance to the oracle's fixed point is within the
+    contraction bound of its reported residual."""
+    rp, ci = gg.rmat(13, 16, seed=31)
+    n = rp.size - 1
+    t = gg.seed_teleports(n, 32, 8, seed=31)
+    with pr.Graph(rp, ci) as g:
+        x32, info32, res32, its32 = g.solve_batched(32, t, tol=1e-6)
+        g.set_option(pr.PR_OPT_BATCH_BF16, switch)
+        x, info, res, its = g.solve_batched(32, t, tol=1e-6, max_iter=300)
+    assert info.converged == 1 and np.all(res < 1e-6)
+    assert not np.array_equal(x, x32)                    # the BF16 phase changed the iterates
+    for j in (0, 7, 31):
+        tj = t[:, j].astype(np.float64)
+        xs, _, _ = oracle.fixed_point(rp, ci, d=D, t=tj)
+        err = np.abs(x[:, j].astype(np.float64) - xs).sum()
+        assert err <= res[j] / (1 - D) + 2e-7, (j, err, res[j])
+        assert np.max(np.abs(x[:, j] - xs) / xs) <= 1e-4

@@ -345,6 +345,17 @@ def _pins_pass(lib):
         xs, _, _, _ = oracle.nosync(rp2, ci2, d=d, p=3, tol=1e-13, lib=lib)
         if not np.allclose(xs, pi, atol=1e-11):
             return False
+        # weighted forward and adjoint against the dense adjoint (numpy linear algebra)
+        rp3, ci3 = gg.random_digraph(8, 16, seed=9)   # three dangling vertices
+        w3 = 0.1 + 0.9 * gg.uniform(6, 1, ci3.size)
+        c3 = gg.uniform(6, 2, 8) - 0.5
+        xd, lamd, gtd, gwd = oracle.dense_adjoint(rp3, ci3, w3, c3, d=d)
+        xw, _, _ = oracle.w_pagerank(rp3, ci3, w3, d=d, lib=lib)
+        if not np.allclose(xw, xd, atol=1e-12):
+            return False
+        adj = oracle.w_adjoint(rp3, ci3, w3, xw, c3, d=d, lib=lib)
+        if not (np.allclose(adj["grad_t"], gtd, atol=1e-11) and np.allclose(adj["grad_w"], gwd, atol=1e-11)):
+            return False
     except oracle.OracleError:
         return False
     return True
@@ -361,6 +372,11 @@ MUTATIONS = {
                           "M[u * n + v] -= d / (double)outdeg[u];"),
     "dangling_from_wrong_set": ("if (outdeg[u] == 0) D += x[u];", "if (outdeg[u] == 1) D += x[u];"),
     "nosync_stale_nondangling_mass": ("else S += tmp - previous;", "else S += 0.0;"),
+    "weighted_forward_ignores_weight": ("s += x[u] * w[e] / W[u];", "s += x[u] / W[u];"),
+    "adjoint_drops_dangling_term": ("(W[u] == 0.0 ? L / (double)n : 0.0)", "0.0"),
+    "adjoint_edge_gradient_sign": ("(lambda[v] - mu[u])", "(mu[u] - lambda[v])"),
+    "adjoint_pushes_to_target": ("mu[u] += w[e] / W[u] * lambda[v];\n            }\n        r = 0.0;",
+                                 "mu[v] += w[e] / W[u] * lambda[u];\n            }\n        r = 0.0;"),
 }
 
 
@@ -378,3 +394,98 @@ def test_each_planted_mistake_fails_a_pin(name, tmp_path):
     out = oracle.build(force=True, src=str(mutated), out=str(tmp_path / "liboracle_mut.so"))
     lib = oracle.load(out)
     assert not _pins_pass(lib), f"planted mistake '{name}' was not caught"
+
+
+
+# ------------------------------------------------------------ weighted graphs --
+
+def weighted_case(n, m, seed, multi=False):
+    rp, ci = gg.random_digraph(n, m, seed=seed, allow_multi=multi)
+    w = 0.1 + 0.9 * gg.uniform(seed, 7, ci.size)
+    return rp, ci, w
+
+
+def test_unit_weights_reduce_to_the_unweighted_oracle():
+    rp, ci = gg.rmat(10, 16, seed=4)
+    x, it, r = oracle.w_pagerank(rp, ci, np.ones(ci.size), tol=1e-13)
+    xs, _, _ = oracle.fixed_point(rp, ci)
+    assert np.allclose(x, xs, atol=1e-14)
+
+
+def test_scaling_one_vertex_out_weights_changes_nothing():
+    """P(u, .) = w(u, .)/W(u) is invariant under scaling u's out-weights."""
+    rp, ci, w = weighted_case(40, 200, seed=3)
+    x, _, _ = oracle.w_pagerank(rp, ci, w)
+    w2 = w.copy()
+    w2[ci == 5] *= 7.0
+    x2, _, _ = oracle.w_pagerank(rp, ci, w2)
+    assert np.allclose(x, x2, atol=1e-14)
+    w3 = w.copy()
+    w3[np.flatnonzero(ci == 5)[:1]] *= 7.0      # one edge only: the ranks move
+    x3, _, _ = oracle.w_pagerank(rp, ci, w3)
+    assert np.abs(x - x3).sum() > 1e-6
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_weighted_forward_and_adjoint_match_the_dense_adjoint(seed):
+    n = 3 + seed
+    rp, ci, w = weighted_case(n, 2 * n + seed, seed=seed, multi=seed % 2 == 1)
+    t = gg.uniform(seed, 8, n) + 0.05
+    t /= t.sum()
+    c = gg.uniform(seed, 9, n) - 0.5
+    xd, lamd, gtd, gwd = oracle.dense_adjoint(rp, ci, w, c, t=t)
+    x, _, _ = oracle.w_pagerank(rp, ci, w, t=t)
+    assert np.allclose(x, xd, atol=1e-13)
+    adj = oracle.w_adjoint(rp, ci, w, x, c)
+    assert np.allclose(adj["lambda"], lamd, atol=1e-12)
+    assert np.allclose(adj["grad_t"], gtd, atol=1e-12)
+    assert np.allclose(adj["grad_w"], gwd, atol=1e-12)
+
+
+def test_adjoint_identities():
+    """L = c^T x is linear in t (so (1-d) lambda^T t = L) and unchanged by scaling one
+    vertex's out-weights (so the weight gradients of each vertex's out-edges, weighted by
+    the weights, sum to zero)."""
+    rp, ci = gg.rmat(11, 8, seed=9)
+    w = 0.1 + 0.9 * gg.uniform(9, 1, ci.size)
+    n = rp.size - 1
+    t = gg.uniform(9, 2, n)
+    t /= t.sum()
+    c = gg.uniform(9, 3, n) - 0.5
+    x, _, _ = oracle.w_pagerank(rp, ci, w, t=t)
+    adj = oracle.w_adjoint(rp, ci, w, x, c)
+    assert abs(adj["grad_t"] @ t - c @ x) < 1e-12
+    per_src = np.zeros(n)
+    np.add.at(per_src, ci, w * adj["grad_w"])
+    assert np.max(np.abs(per_src)) < 1e-12
+
+
+def test_adjoint_against_central_differences():
+    """Central differences (h = 1e-3) of L through the FP64 forward at tol 1e-14: exact for
+    the teleport (L is linear in t), second order for the weights."""
+    rp, ci = gg.rmat(9, 8, seed=5)
+    n = rp.size - 1
+    w = 0.1 + 0.9 * gg.uniform(5, 1, ci.size)
+    t = np.full(n, 1.0 / n)
+    c = gg.uniform(5, 3, n) - 0.5
+    x, _, _ = oracle.w_pagerank(rp, ci, w, t=t, tol=1e-15)
+    adj = oracle.w_adjoint(rp, ci, w, x, c)
+    h = 1e-3
+
+    def L(tt, ww):
+        xx, _, _ = oracle.w_pagerank(rp, ci, ww, t=tt, tol=1e-15, x0=x)
+        return c @ xx
+
+    rng = np.random.default_rng(0)
+    for i in rng.integers(0, n, 8):
+        tp, tm = t.copy(), t.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (L(tp, w) - L(tm, w)) / (2 * h)
+        assert fd == pytest.approx(adj["grad_t"][i], rel=1e-7, abs=1e-11)
+    for e in rng.integers(0, ci.size, 8):
+        wp, wm = w.copy(), w.copy()
+        wp[e] += h
+        wm[e] -= h
+        fd = (L(t, wp) - L(t, wm)) / (2 * h)
+        assert fd == pytest.approx(adj["grad_w"][e], rel=1e-4, abs=1e-9)
