@@ -591,6 +591,126 @@ def run_set(args):
     return 0
 
 
+ADJ_SCALE = 20
+
+
+def run_adjoint(args):
+    """Weighted R-MAT-20 (weights U(0.1, 1], row-normalised), L = c^T x with c ~ N(0, 1): one
+    step = the weighted forward solve to L1 < 1e-6 plus the adjoint solve (relative L1 change
+    < 1e-6) and both gradients; against the plain FP32 Jacobi solve of the same graph."""
+    import numpy as np
+    import torch
+
+    import graphgen as gg
+    import paper_2109_09527_gb300 as pr
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    rp, ci = gg.rmat(ADJ_SCALE, 16, seed=ADJ_SCALE)
+    n, nnz = rp.size - 1, ci.size
+    w = (0.1 + 0.9 * gg.uniform(ADJ_SCALE, 11, nnz)).astype(np.float32)
+    c = torch.from_numpy(np.random.default_rng(ADJ_SCALE).standard_normal(n).astype(np.float32)).to(dev)
+    drp, dci, dw = (torch.from_numpy(a).to(dev) for a in (rp, ci, w))
+    g = pr.WeightedGraph(drp, dci, dw)
+    x = torch.empty(n, dtype=torch.float32, device=dev)
+    gt = torch.empty(n, dtype=torch.float32, device=dev)
+    gw = torch.empty(nnz, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        _, fi = g.solve(DAMPING, TOL, MAX_ITER, out=x)
+        _, _, ai = g.adjoint(x, c, DAMPING, TOL, 1000, grad_teleport=gt, grad_weights=gw)
+        return fi, ai
+
+    for _ in range(args.warmup):
+        step()
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    runs = [step() for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    visits = sum(fi.edge_visits + ai.edge_visits for fi, ai in runs)
+    value = world * visits / (ms * 1e-3) / 1e9
+    fi, ai = runs[-1]
+    # one weighted iteration moves colidx + P + the gathered value per edge, 8 B row offsets
+    b_iter = 12 * nnz + 8 * (n + 1) + 16 * n
+    f_ms = fi.ms_device / max(1, fi.iterations)
+    peak, peak_kind = peaks()
+    # the plain FP32 Jacobi solve of the same (unweighted) graph
+    pg = pr.Graph(drp, dci)
+    out1 = torch.empty(n, dtype=torch.float32, device=dev)
+    pg.solve(tol=TOL, out=out1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    _, pinfo = pg.solve(tol=TOL, out=out1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    pg.close()
+    # end to end: c in from pinned host memory, both gradients back to pinned host memory
+    c_pin = c.cpu().pin_memory()
+    gt_pin = torch.empty(n, dtype=torch.float32).pin_memory()
+    gw_pin = torch.empty(nnz, dtype=torch.float32).pin_memory()
+    x_pin = torch.empty(n, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_visits = 0.0
+    for _ in range(max(1, args.e2e_steps)):
+        _, fi2 = g.solve(DAMPING, TOL, MAX_ITER, out=x_pin)
+        _, _, ai2 = g.adjoint(x_pin, c_pin, DAMPING, TOL, 1000, grad_teleport=gt_pin, grad_weights=gw_pin)
+        e2e_visits += fi2.edge_visits + ai2.edge_visits
+    e2e_s = time.perf_counter() - t0
+    g.close()
+    if rank == 0:
+        line = {"metric": "weighted PageRank forward + adjoint gradients: GTEPS (edges gathered "
+                          "per second, both solves)",
+                "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"weighted rmat{ADJ_SCALE} (ef 16), weights U(0.1, 1] "
+                                       "row-normalised, L = c^T x with c ~ N(0,1); d=0.85",
+                           "n": n, "nnz": nnz, "tol": TOL, "l2": "inputs larger than L2"},
+                "forward": {"iterations": fi.iterations, "ms": fi.ms_device,
+                            "residual_l1": fi.residual_l1},
+                "adjoint": {"iterations": ai.iterations, "ms": ai.ms_device,
+                            "relative_residual": ai.residual_l1},
+                "roofline": {"bound": "hbm", "achieved": b_iter / (f_ms * 1e-3) / 1e9, "peak": peak,
+                             "unit": "GB/s", "frac": b_iter / (f_ms * 1e-3) / 1e9 / peak,
+                             "traffic": None, "kernel": "k_w_forward iteration",
+                             "bytes_per_iteration": b_iter, "ms_per_iteration": f_ms,
+                             "peak_source": f"{peak_kind} hbm_gbs"},
+                "vs_plain_jacobi": {"plain_ms": plain_ms, "plain_iterations": pinfo.iterations,
+                                    "forward_plus_adjoint_ms": ms / args.steps},
+                "e2e": {"value": world * e2e_visits / e2e_s / 1e9, "unit": "GTEPS",
+                        "h2d_bytes_per_step": 2 * n * 4, "d2h_bytes_per_step": (2 * n + nnz) * 4,
+                        "ms_per_step": e2e_s * 1e3 / max(1, args.e2e_steps)},
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -604,7 +724,7 @@ def main():
     ap.add_argument("--profile", choices=["jacobi", "nonblocking", "batched"], default=None,
                     help="run a short fixed workload for a profiler instead of the benchmark")
     ap.add_argument("--graph", choices=["rmat", "er"], default="rmat")
-    ap.add_argument("--workload", choices=["pagerank", "batched", "set"], default="pagerank",
+    ap.add_argument("--workload", choices=["pagerank", "batched", "set", "adjoint"], default="pagerank",
                     help="batched: 32 personalised PageRank vectors on R-MAT-22; set: 64 R-MAT "
                          "graphs of 1e3..1e6 vertices in one solve (each its own JSON line)")
     args = ap.parse_args()
@@ -620,6 +740,8 @@ def main():
         return run_batched(args)
     if args.workload == "set":
         return run_set(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
 
     import numpy as np
     import torch

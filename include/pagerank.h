@@ -56,6 +56,7 @@ extern "C" {
 #endif
 
 typedef struct pr_graph pr_graph; /* opaque; owned by the library */
+typedef struct pr_wgraph pr_wgraph; /* opaque weighted graph of the adjoint path */
 
 typedef enum pr_status {
     PR_OK = 0,
@@ -307,6 +308,52 @@ PR_API pr_status pr_graph_set_partition(pr_graph* g, int32_t count, const int64_
 PR_API pr_status pr_solve_set(pr_graph* g, float damping, double tol, int32_t max_iter, float* x_out,
                               double* graph_residual, int32_t* graph_iterations, pr_info* info,
                               void* stream);
+
+/* Weighted graphs and the adjoint (gradients through the fixed point).
+ *
+ * Edge e = (u, v) carries a weight w(e) > 0; the transition probability is
+ * P(u, v) = w(e) / W(u) with W(u) the sum of u's out-weights (the weights are
+ * row-normalised), and a vertex without out-edges is dangling.  The forward
+ * problem is Eq. 1 on P with teleport t: M x = (1-d) t, M = I - d P^T -
+ * (d/n) 1 a^T.  For a loss L(x) with gradient c = dL/dx, implicit
+ * differentiation of the fixed point gives M^T lambda = c and
+ *   dL/dt(u)  = (1-d) lambda(u),
+ *   dL/dw(e)  = d x(u) / W(u) * (lambda(v) - sum_v' P(u, v') lambda(v')).
+ * The transposed system is solved by the synchronous iteration along the
+ * out-edges (the forward "push"); the library keeps an out-edge CSR for it.
+ * Vertices keep the caller's order (no relabelling).
+ *
+ * pr_create_wgraph: n, nnz as for pr_create_graph; rowptr int64 [n+1] and
+ *   colidx int32 [nnz] (host or device) give the in-edge CSR, weights [nnz]
+ *   (host or device) are aligned with colidx.  nnz < 2^31.  Validation is on
+ *   the host (PR_ERR_INVALID_GRAPH); a weight that is not positive and finite
+ *   returns PR_ERR_INVALID_ARG.  Synchronises `stream`. */
+PR_API pr_status pr_create_wgraph(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
+                                  const float* weights, void* stream, pr_wgraph** out);
+PR_API pr_status pr_destroy_wgraph(pr_wgraph* g);
+
+/* Replace the edge weights (host or device, nnz floats aligned with colidx);
+ * the structure is kept.  Synchronises `stream`. */
+PR_API pr_status pr_wgraph_set_weights(pr_wgraph* g, const float* weights, void* stream);
+
+/* The weighted PageRank vector: Alg. 1 on P from x0 = t until the L1 change
+ * is below tol or max_iter, then rescaled to sum(t) in FP64 (so the result
+ * is a linear function of t).  teleport: host or device, n floats, or NULL
+ * for 1/n.  x_out: host or device, n floats.  Fills info like pr_solve. */
+PR_API pr_status pr_solve_weighted(pr_wgraph* g, float damping, double tol, int32_t max_iter,
+                                   const float* teleport, float* x_out, pr_info* info, void* stream);
+
+/* Gradients of a loss L on the weighted PageRank vector x (the output of
+ * pr_solve_weighted with the same damping):
+ *   x, dL_dx         host or device, n floats;
+ *   dL_dteleport     NULL or host or device, n floats;
+ *   dL_dweights      NULL or host or device, nnz floats aligned with colidx.
+ * lambda is iterated from c until its L1 change is below tol * ||c||_1 or
+ * max_iter (PR_NOT_CONVERGED, outputs still written).  info->iterations are
+ * the adjoint iterations, info->residual_l1 the last L1 change of lambda. */
+PR_API pr_status pr_adjoint(pr_wgraph* g, float damping, double tol, int32_t max_iter, const float* x,
+                            const float* dL_dx, float* dL_dteleport, float* dL_dweights, pr_info* info,
+                            void* stream);
 
 /* One synchronous PageRank update that allocates no memory -- for callers
  * that cannot call cudaMalloc (or anything that allocates) where they need an

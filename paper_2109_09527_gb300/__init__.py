@@ -100,6 +100,11 @@ SIGNATURES = {
     "pr_solve_batched": (ctypes.c_int, [_VP, _F, _D, _I32, _I32, _VP, _VP, ctypes.POINTER(_D),
                                         ctypes.POINTER(_I32), ctypes.POINTER(pr_info), _VP]),
     "pr_graph_set_partition": (ctypes.c_int, [_VP, _I32, _VP, _VP]),
+    "pr_create_wgraph": (ctypes.c_int, [_I64, _I64, _VP, _VP, _VP, _VP, ctypes.POINTER(_VP)]),
+    "pr_destroy_wgraph": (ctypes.c_int, [_VP]),
+    "pr_wgraph_set_weights": (ctypes.c_int, [_VP, _VP, _VP]),
+    "pr_solve_weighted": (ctypes.c_int, [_VP, _F, _D, _I32, _VP, _VP, ctypes.POINTER(pr_info), _VP]),
+    "pr_adjoint": (ctypes.c_int, [_VP, _F, _D, _I32, _VP, _VP, _VP, _VP, ctypes.POINTER(pr_info), _VP]),
     "pr_solve_set": (ctypes.c_int, [_VP, _F, _D, _I32, _VP, ctypes.POINTER(_D), ctypes.POINTER(_I32),
                                     ctypes.POINTER(pr_info), _VP]),
     "pr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -351,3 +356,117 @@ class Graph:
 def set_heavy_degree(value: int):
     """Heavy in-degree threshold for graphs created next on this thread (power of two)."""
     pr_set_option(None, PR_OPT_HEAVY_DEGREE, value)
+
+
+# ------------------------------------------------------ weighted graphs, adjoint --
+
+def pr_create_wgraph(n, nnz, rowptr, colidx, weights, stream=None):
+    out = _VP()
+    _check(load().pr_create_wgraph(int(n), int(nnz), _addr(rowptr, np.int64), _addr(colidx, np.int32),
+                                   _addr(weights, np.float32), _stream(stream), ctypes.byref(out)))
+    return out.value
+
+
+def pr_destroy_wgraph(g):
+    return _check(load().pr_destroy_wgraph(g))
+
+
+def pr_wgraph_set_weights(g, weights, stream=None):
+    return _check(load().pr_wgraph_set_weights(g, _addr(weights, np.float32), _stream(stream)))
+
+
+def pr_solve_weighted(g, damping, tol, max_iter, teleport, x_out, stream=None):
+    info = pr_info()
+    st = _check(load().pr_solve_weighted(g, float(damping), float(tol), int(max_iter),
+                                         _addr(teleport, np.float32), _addr(x_out, np.float32),
+                                         ctypes.byref(info), _stream(stream)),
+                allow_not_converged=True)
+    return st, info
+
+
+def pr_adjoint(g, damping, tol, max_iter, x, dL_dx, dL_dteleport, dL_dweights, stream=None):
+    info = pr_info()
+    st = _check(load().pr_adjoint(g, float(damping), float(tol), int(max_iter), _addr(x, np.float32),
+                                  _addr(dL_dx, np.float32), _addr(dL_dteleport, np.float32),
+                                  _addr(dL_dweights, np.float32), ctypes.byref(info), _stream(stream)),
+                allow_not_converged=True)
+    return st, info
+
+
+class WeightedGraph:
+    """Owns a pr_wgraph: an in-edge CSR with positive edge weights (row-normalised by
+    source into transition probabilities), for the weighted solve and its adjoint."""
+
+    def __init__(self, rowptr, colidx, weights, stream=None):
+        self.n = (rowptr.shape[0] if hasattr(rowptr, "shape") else len(rowptr)) - 1
+        self.nnz = colidx.shape[0] if hasattr(colidx, "shape") else len(colidx)
+        self.handle = pr_create_wgraph(self.n, self.nnz, rowptr, colidx, weights, stream=stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            pr_destroy_wgraph(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+    def set_weights(self, weights, stream=None):
+        pr_wgraph_set_weights(self.handle, weights, stream=stream)
+
+    def solve(self, damping=0.85, tol=1e-6, max_iter=200, teleport=None, out=None, stream=None):
+        if out is None:
+            out = np.empty(self.n, dtype=np.float32)
+        _, info = pr_solve_weighted(self.handle, damping, tol, max_iter, teleport, out, stream=stream)
+        return out, info
+
+    def adjoint(self, x, dL_dx, damping=0.85, tol=1e-6, max_iter=500, grad_teleport=None,
+                grad_weights=None, stream=None):
+        """dL/dteleport and dL/dweights (numpy arrays unless buffers are given)."""
+        if grad_teleport is None:
+            grad_teleport = np.empty(self.n, dtype=np.float32)
+        if grad_weights is None:
+            grad_weights = np.empty(self.nnz, dtype=np.float32)
+        _, info = pr_adjoint(self.handle, damping, tol, max_iter, x, dL_dx, grad_teleport,
+                             grad_weights, stream=stream)
+        return grad_teleport, grad_weights, info
+
+
+def weighted_pagerank(graph, teleport, weights, damping=0.85, tol=1e-6, max_iter=200,
+                      adjoint_tol=1e-6, adjoint_max_iter=500):
+    """Differentiable weighted PageRank: x = PageRank(graph with edge weights, teleport), as
+    a torch.autograd.Function whose backward runs the library's adjoint solve (implicit
+    differentiation of the fixed point).  teleport (n) and weights (nnz) are CUDA float32
+    tensors; returns x (n).  The graph's weights are set from `weights` on every call."""
+    import torch
+
+    class _WeightedPageRank(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, t, w):
+            t = t.detach().contiguous()
+            w = w.detach().contiguous()
+            graph.set_weights(w)
+            x = torch.empty_like(t)
+            graph.solve(damping, tol, max_iter, teleport=t, out=x)
+            ctx.save_for_backward(x, w)
+            return x
+
+        @staticmethod
+        def backward(ctx, grad_x):
+            x, w = ctx.saved_tensors
+            graph.set_weights(w)
+            gt = torch.empty_like(x)
+            gw = torch.empty_like(w)
+            graph.adjoint(x, grad_x.contiguous(), damping, adjoint_tol, adjoint_max_iter,
+                          grad_teleport=gt, grad_weights=gw)
+            return gt, gw
+
+    return _WeightedPageRank.apply(teleport, weights)
