@@ -347,6 +347,46 @@ def run_profile_batched(args):
     return 0
 
 
+def run_profile_other(args):
+    """Short fixed workloads for ncu: the 64-graph set solved twice (separate launches), or
+    the weighted R-MAT-20 forward and adjoint solved twice."""
+    import numpy as np
+    import torch
+
+    import graphgen as gg
+    import paper_2109_09527_gb300 as pr
+    dev = torch.device("cuda", 0)
+    if args.profile == "set":
+        graphs = gg.multi_rmat(SET_COUNT, 1e3, 1e6, 8, seed=SET_SEED)
+        rp, ci, off = gg.block_diagonal(graphs)
+        g = pr.Graph(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev))
+        g.set_partition(off)
+        g.set_option(pr.PR_OPT_USE_GRAPH, 0)
+        out = torch.empty(rp.size - 1, dtype=torch.float32, device=dev)
+        for rep in range(2):
+            _, info, _, _ = g.solve_set(tol=TOL, max_iter=MAX_ITER, out=out)
+            torch.cuda.synchronize()
+            log(f"[profile] set rep {rep}: {info.ms_device:.3f} ms, iterations {info.iterations}")
+        g.close()
+        return 0
+    rp, ci = gg.rmat(ADJ_SCALE, 16, seed=ADJ_SCALE)
+    n, nnz = rp.size - 1, ci.size
+    w = (0.1 + 0.9 * gg.uniform(ADJ_SCALE, 11, nnz)).astype(np.float32)
+    c = torch.from_numpy(np.random.default_rng(ADJ_SCALE).standard_normal(n).astype(np.float32)).to(dev)
+    g = pr.WeightedGraph(*(torch.from_numpy(a).to(dev) for a in (rp, ci, w)))
+    x = torch.empty(n, dtype=torch.float32, device=dev)
+    gt = torch.empty(n, dtype=torch.float32, device=dev)
+    gw = torch.empty(nnz, dtype=torch.float32, device=dev)
+    for rep in range(2):
+        _, fi = g.solve(DAMPING, TOL, MAX_ITER, out=x)
+        _, _, ai = g.adjoint(x, c, DAMPING, TOL, 1000, grad_teleport=gt, grad_weights=gw)
+        torch.cuda.synchronize()
+        log(f"[profile] adjoint rep {rep}: forward {fi.iterations} it {fi.ms_device:.3f} ms, "
+            f"adjoint {ai.iterations} it {ai.ms_device:.3f} ms")
+    g.close()
+    return 0
+
+
 def run_batched(args):
     """Batched personalised PageRank: 32 seed-set teleport vectors (8 seeds each) on R-MAT-22,
     solved together (pr_solve_batched) against the same 32 solved one at a time with the
@@ -721,7 +761,7 @@ def main():
     ap.add_argument("--er-log2", type=int, default=24)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile", choices=["jacobi", "nonblocking", "batched"], default=None,
+    ap.add_argument("--profile", choices=["jacobi", "nonblocking", "batched", "set", "adjoint"], default=None,
                     help="run a short fixed workload for a profiler instead of the benchmark")
     ap.add_argument("--graph", choices=["rmat", "er"], default="rmat")
     ap.add_argument("--workload", choices=["pagerank", "batched", "set", "adjoint"], default="pagerank",
@@ -730,6 +770,8 @@ def main():
     args = ap.parse_args()
     if args.profile == "batched":
         return run_profile_batched(args)
+    if args.profile in ("set", "adjoint"):
+        return run_profile_other(args)
     if args.profile:
         return run_profile(args)
     if args.warmup < 3:

@@ -229,6 +229,16 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
  *                         copy to the end.  X stays FP32 throughout, so the
  *                         result meets the same tol; BF16's 2^-9 rounding
  *                         limits how far the BF16 phase can go (m ~ 2..3).
+ *   PR_OPT_PERFORATION    loop perforation (Alg. 5) in the synchronous solver
+ *                         (PR_JACOBI, pr_iterate): 0 (default) off; m in 1..30
+ *                         freezes a vertex once an update changes its rank by
+ *                         a nonzero amount below 10^-m -- it is no longer
+ *                         recomputed (its rank still feeds its out-neighbours
+ *                         and the dangling mass).  An approximation: the
+ *                         result differs from the fixed point by more than
+ *                         the contraction bound of the residual; frozen rows
+ *                         count as changes of 0 in the residual.  Row-by-row
+ *                         tiles only (PR_OPT_STAGED_TILES is ignored).
  *   PR_OPT_INDEX64        1: keep 64-bit row offsets on the device even when
  *                         the edge count fits 32 bits (thread-local default
  *                         for the next pr_create_graph, set with g = NULL;
@@ -244,6 +254,7 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
 #define PR_OPT_NB_HUBS 8
 #define PR_OPT_NB_L1_HUBS 9
 #define PR_OPT_BATCH_BF16 10
+#define PR_OPT_PERFORATION 11
 PR_API pr_status pr_set_option(pr_graph* g, int key, int64_t value);
 
 /* Batched personalised PageRank: k independent solves on one graph, one per

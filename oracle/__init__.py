@@ -62,6 +62,8 @@ def _declare(lib):
                                        vp, vp, vp]
     lib.or_dense_solve.restype = ctypes.c_int
     lib.or_dense_solve.argtypes = [i64, vp, vp, dbl, vp, ctypes.c_int, vp]
+    lib.or_pagerank_perforated.restype = ctypes.c_int
+    lib.or_pagerank_perforated.argtypes = [i64, vp, vp, dbl, vp, dbl, i32, dbl, vp, vp, vp, vp]
     lib.or_w_outweight.restype = ctypes.c_int
     lib.or_w_outweight.argtypes = [i64, vp, vp, vp, vp]
     lib.or_w_jacobi.restype = ctypes.c_int
@@ -308,3 +310,17 @@ def dense_adjoint(rowptr, colidx, w, c, d=0.85, t=None):
         dM = -d * dP.T
         grad_w[e] = -lam @ dM @ x
     return x, lam, grad_t, grad_w
+
+
+def pagerank_perforated(rowptr, colidx, d=0.85, tol=1e-10, max_iter=1000, eps=0.0, t=None, lib=None):
+    """Alg. 5 (loop perforation): a vertex whose change is nonzero and below eps stops being
+    recomputed.  Returns (x, iterations, last_l1_change, frozen_count)."""
+    lib = lib or load()
+    rowptr, colidx = _csr(rowptr, colidx)
+    n = rowptr.size - 1
+    x = np.empty(n, dtype=np.float64)
+    it, res, nf = ctypes.c_int32(), ctypes.c_double(), ctypes.c_int64()
+    _check(lib.or_pagerank_perforated(n, _p(rowptr), _p(colidx), d, _p(_vec(t, n)), tol, max_iter, eps,
+                                      _p(x), ctypes.byref(it), ctypes.byref(res), ctypes.byref(nf)),
+           "or_pagerank_perforated")
+    return x, it.value, res.value, nf.value

@@ -30,6 +30,12 @@
  *   or_dense_solve     the fixed point as the solution of the linear system
  *                      (I - d*A - (d/n)*1*a^T) x = (1-d)*t by Gaussian
  *                      elimination with partial pivoting (small n only).
+ *   or_pagerank_perforated  Alg. 5 (loop perforation) on the synchronous
+ *                      iteration: a vertex whose update changed its rank by
+ *                      a nonzero amount below eps is frozen, and from the
+ *                      next iteration on keeps its rank without being
+ *                      recomputed (its rank still feeds its out-neighbours
+ *                      and the dangling mass).  eps = 0 is Alg. 1.
  *   or_w_outweight     weighted graphs: W(u) = sum of the weights of u's
  *                      out-edges (the row normaliser of the transition
  *                      matrix P(u,v) = w(u,v)/W(u)).
@@ -164,6 +170,50 @@ OR_API int or_pagerank_jacobi(int64_t n, const int64_t* rowptr, const int32_t* c
     if (resid) *resid = l1;
     free(outdeg);
     free(xn);
+    return OR_OK;
+}
+
+/* Alg. 5: Alg. 1 with loop perforation.  frozen_out (may be NULL) receives
+ * how many vertices ended frozen. */
+OR_API int or_pagerank_perforated(int64_t n, const int64_t* rowptr, const int32_t* colidx, double d,
+                                  const double* t, double tol, int32_t max_iter, double eps, double* x,
+                                  int32_t* iters, double* resid, int64_t* frozen_out) {
+    int rc = or_check_csr(n, rowptr, colidx);
+    if (rc) return rc;
+    if (!(d >= 0.0 && d < 1.0) || max_iter < 0 || !(eps >= 0.0)) return OR_BAD_ARG;
+    int64_t* outdeg = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+    double* xn = (double*)malloc((size_t)n * sizeof(double));
+    unsigned char* frozen = (unsigned char*)calloc((size_t)n, 1);
+    if (!outdeg || !xn || !frozen) { free(outdeg); free(xn); free(frozen); return OR_NO_MEM; }
+    or_outdeg(n, rowptr, colidx, outdeg);
+    for (int64_t v = 0; v < n; ++v) x[v] = or_teleport(n, t, v);
+    int32_t k = 0;
+    double l1 = INFINITY;
+    while (k < max_iter) {
+        const double D = or_dangling_mass(n, outdeg, x);
+        l1 = 0.0;
+        for (int64_t v = 0; v < n; ++v) {
+            if (frozen[v]) {
+                xn[v] = x[v];
+                continue;
+            }
+            xn[v] = or_vertex_update(v, n, rowptr, colidx, outdeg, d, t, D, x);
+            const double change = fabs(xn[v] - x[v]);
+            l1 += change;
+            if (change != 0.0 && change < eps) frozen[v] = 1;
+        }
+        memcpy(x, xn, (size_t)n * sizeof(double));
+        ++k;
+        if (tol > 0.0 && l1 < tol) break;
+    }
+    int64_t nf = 0;
+    for (int64_t v = 0; v < n; ++v) nf += frozen[v];
+    if (iters) *iters = k;
+    if (resid) *resid = l1;
+    if (frozen_out) *frozen_out = nf;
+    free(outdeg);
+    free(xn);
+    free(frozen);
     return OR_OK;
 }
 

@@ -48,6 +48,7 @@ PR_OPT_STAGED_TILES = 7
 PR_OPT_NB_HUBS = 8
 PR_OPT_NB_L1_HUBS = 9
 PR_OPT_BATCH_BF16 = 10
+PR_OPT_PERFORATION = 11
 
 LIB_PATH = _build.LIB_PATH
 

@@ -20,8 +20,9 @@
 // forward pull) and an out-edge CSR (the adjoint pull, i.e. the forward
 // push), each with its edges' transition probabilities.
 //
-// Vertices stay in the caller's order (no degree binning): rows are gathered
-// a warp each.  The out-edge CSR is built on the host by a stable counting
+// Vertices stay in the caller's order (no relabelling): rows with 32 or more
+// edges are gathered a warp each, the others by groups of 8 lanes, from a row
+// list sorted into those two classes.  The out-edge CSR is built on the host by a stable counting
 // sort of the in-edges by source, so each out-row lists its edges in in-edge
 // order and every sum has a fixed order (bitwise reproducible results).
 #include <algorithm>
@@ -62,9 +63,43 @@ struct WArgs {
     const int32_t* out_dst;
     const float* out_p;         // P(u, v) of each out-edge
     const float* inv_w;         // 1/W(u), 0 for dangling u
+    const int32_t* in_order;    // rows by in-degree: the n_in_heavy rows with >= 32 in-edges first
+    int64_t n_in_heavy;
+    const int32_t* out_order;   // rows by out-degree: the n_out_heavy rows with >= 32 out-edges first
+    int64_t n_out_heavy;
     WState* state;
     double* slots;
 };
+
+// Rows are visited in two passes: rows with at least 32 edges a warp each,
+// then the rest by groups of 8 lanes (four rows per warp at a time).  The row
+// body f(row, lane_in_group, group_size) returns the group-reduced sum in
+// the group's first lane; `epilogue(row, sum)` runs there.
+constexpr int kWLightLanes = 8;
+
+template <typename Gather, typename Epilogue>
+__device__ __forceinline__ void w_rows(const int32_t* order, int64_t n, int64_t n_heavy, Gather gather,
+                                       Epilogue epilogue) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < n_heavy; i += nwarp) {
+        const int32_t r = order[i];
+        float s = warp_sum(gather(r, lane, 32));
+        if (lane == 0) epilogue(r, s);
+    }
+    constexpr int per = 32 / kWLightLanes;
+    const int sub = lane / kWLightLanes, sl = lane % kWLightLanes;
+    for (int64_t i0 = n_heavy + warp * per; i0 < n; i0 += nwarp * per) {
+        const int64_t i = i0 + sub;
+        const bool act = i < n;
+        const int32_t r = act ? order[i] : 0;
+        float s = act ? gather(r, sl, kWLightLanes) : 0.f;
+#pragma unroll
+        for (int o = kWLightLanes / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (act && sl == 0) epilogue(r, s);
+    }
+}
 
 // ------------------------------------------------------------------ kernels --
 
@@ -85,23 +120,21 @@ __global__ void __launch_bounds__(kBlock) k_w_forward(WArgs a, const float* __re
     const float d = (float)s_d;
     const float share = (float)(s_D * s_inv_n);
     const float tu = (float)s_inv_n;
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
     float r = 0.f;
     Acc acc;
-    for (int64_t v = warp; v < a.n; v += nwarp) {
-        float s = 0.f;
-        for (int64_t e = a.rowptr[v] + lane; e < a.rowptr[v + 1]; e += 32) s += a.in_p[e] * x[a.colidx[e]];
-        s = warp_sum(s);
-        if (lane == 0) {
-            const float tv = t ? t[v] : tu;
-            const float xn = fmaf(1.f - d, tv, d * (s + share));
-            xo[v] = xn;
-            r += fabsf(xn - x[v]);
-            if (a.inv_w[v] == 0.f) acc.kahan(xn);
-        }
-    }
+    w_rows(a.in_order, a.n, a.n_in_heavy,
+           [&](int32_t v, int l, int g) {
+               float s = 0.f;
+               for (int64_t e = a.rowptr[v] + l; e < a.rowptr[v + 1]; e += g) s += a.in_p[e] * x[a.colidx[e]];
+               return s;
+           },
+           [&](int32_t v, float s) {
+               const float tv = t ? t[v] : tu;
+               const float xn = fmaf(1.f - d, tv, d * (s + share));
+               xo[v] = xn;
+               r += fabsf(xn - x[v]);
+               if (a.inv_w[v] == 0.f) acc.kahan(xn);
+           });
     double R, Dn;
     if (block_pair_to_grid((double)r, acc.mass(), a.slots, &st->ticket, &R, &Dn) && threadIdx.x == 0) {
         st->resid = R;
@@ -130,25 +163,23 @@ __global__ void __launch_bounds__(kBlock) k_w_adjoint(WArgs a, const float* __re
     if (s_done && !final) return;
     const float d = (float)s_d;
     const float lshare = (float)(s_L * s_inv_n);
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double r = 0.0, L = 0.0;
-    for (int64_t u = warp; u < a.n; u += nwarp) {
-        float m = 0.f;
-        for (int64_t e = a.out_rowptr[u] + lane; e < a.out_rowptr[u + 1]; e += 32) m += a.out_p[e] * lam[a.out_dst[e]];
-        m = warp_sum(m);
-        if (lane == 0) {
-            if (final) {
-                mu[u] = m;
-            } else {
-                const float ln = c[u] + d * (m + (a.inv_w[u] == 0.f ? lshare : 0.f));
-                lo[u] = ln;
-                r += fabs((double)ln - (double)lam[u]);
-                L += (double)ln;
-            }
-        }
-    }
+    w_rows(a.out_order, a.n, a.n_out_heavy,
+           [&](int32_t u, int l, int g) {
+               float m = 0.f;
+               for (int64_t e = a.out_rowptr[u] + l; e < a.out_rowptr[u + 1]; e += g) m += a.out_p[e] * lam[a.out_dst[e]];
+               return m;
+           },
+           [&](int32_t u, float m) {
+               if (final) {
+                   mu[u] = m;
+               } else {
+                   const float ln = c[u] + d * (m + (a.inv_w[u] == 0.f ? lshare : 0.f));
+                   lo[u] = ln;
+                   r += fabs((double)ln - (double)lam[u]);
+                   L += (double)ln;
+               }
+           });
     if (final) return;
     double R, Ln;
     if (block_pair_to_grid(r, L, a.slots, &st->ticket, &R, &Ln) && threadIdx.x == 0) {
@@ -170,16 +201,16 @@ __global__ void __launch_bounds__(kBlock) k_w_grads(WArgs a, const float* __rest
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < a.n; u += stride)
         if (grad_t) grad_t[u] = (1.f - d) * lam[u];
     if (!grad_w) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarp = stride >> 5;
-    for (int64_t v = warp; v < a.n; v += nwarp) {
-        const float lv = lam[v];
-        for (int64_t e = a.rowptr[v] + lane; e < a.rowptr[v + 1]; e += 32) {
-            const int32_t u = a.colidx[e];
-            grad_w[e] = d * x[u] * a.inv_w[u] * (lv - mu[u]);
-        }
-    }
+    w_rows(a.in_order, a.n, a.n_in_heavy,
+           [&](int32_t v, int l, int g) {
+               const float lv = lam[v];
+               for (int64_t e = a.rowptr[v] + l; e < a.rowptr[v + 1]; e += g) {
+                   const int32_t u = a.colidx[e];
+                   grad_w[e] = d * x[u] * a.inv_w[u] * (lv - mu[u]);
+               }
+               return 0.f;
+           },
+           [&](int32_t, float) {});
 }
 
 // Sums for the forward init (D of x0, sum t) or the adjoint init (sum c, ||c||_1).
@@ -286,6 +317,10 @@ struct pr_wgraph {
     float* out_p = nullptr;
     float* inv_w = nullptr;
     double* W = nullptr;
+    int32_t* in_order = nullptr;
+    int32_t* out_order = nullptr;
+    int64_t n_in_heavy = 0;
+    int64_t n_out_heavy = 0;
     float* vec[4] = {nullptr, nullptr, nullptr, nullptr};   // iterate buffers, mu
     float* stage = nullptr;                                 // host inputs / outputs
     prk::WState* state = nullptr;
@@ -312,6 +347,10 @@ WArgs w_args(const pr_wgraph* g) {
     a.out_dst = g->out_dst;
     a.out_p = g->out_p;
     a.inv_w = g->inv_w;
+    a.in_order = g->in_order;
+    a.n_in_heavy = g->n_in_heavy;
+    a.out_order = g->out_order;
+    a.n_out_heavy = g->n_out_heavy;
     a.state = g->state;
     a.slots = g->slots;
     return a;
@@ -374,7 +413,7 @@ extern "C" pr_status pr_destroy_wgraph(pr_wgraph* g) {
     if (!g) return PR_OK;
     void* dev[] = {g->rowptr, g->colidx, g->w, g->in_p, g->out_rowptr, g->out_dst, g->out_eid, g->out_p,
                    g->inv_w, g->W, g->vec[0], g->vec[1], g->vec[2], g->vec[3], g->stage, g->state, g->slots,
-                   g->bad};
+                   g->bad, g->in_order, g->out_order};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (g->host_state) cudaFreeHost(g->host_state);
@@ -419,8 +458,24 @@ extern "C" pr_status pr_create_wgraph(int64_t n, int64_t nnz, const int64_t* row
                 oeid[slot] = k;
             }
     }
+    // rows with >= 32 edges first (a warp each), then the rest (groups of 8 lanes)
+    auto split = [&](const std::vector<int64_t>& ptr, std::vector<int32_t>& order, int64_t& n_heavy) {
+        order.clear();
+        order.reserve((size_t)n);
+        for (int64_t v = 0; v < n; ++v)
+            if (ptr[v + 1] - ptr[v] >= 32) order.push_back((int32_t)v);
+        n_heavy = (int64_t)order.size();
+        for (int64_t v = 0; v < n; ++v)
+            if (ptr[v + 1] - ptr[v] < 32) order.push_back((int32_t)v);
+    };
+    std::vector<int32_t> in_order, out_order;
+    int64_t n_in_heavy = 0, n_out_heavy = 0;
+    split(rp, in_order, n_in_heavy);
+    split(orp, out_order, n_out_heavy);
     pr_wgraph* g = new (std::nothrow) pr_wgraph();
     if (!g) return fail(PR_ERR_OOM, "pr_create_wgraph: host allocation failed");
+    g->n_in_heavy = n_in_heavy;
+    g->n_out_heavy = n_out_heavy;
     g->n = n;
     g->nnz = nnz;
     pr_status rc = PR_OK;
@@ -445,6 +500,8 @@ extern "C" pr_status pr_create_wgraph(int64_t n, int64_t nnz, const int64_t* row
                   cudaMalloc((void**)&g->state, sizeof(WState)) == cudaSuccess &&
                   cudaMalloc((void**)&g->slots, (size_t)g->sm_count * 4 * 2 * sizeof(double)) == cudaSuccess &&
                   cudaMalloc((void**)&g->bad, sizeof(unsigned int)) == cudaSuccess &&
+                  cudaMalloc((void**)&g->in_order, N * sizeof(int32_t)) == cudaSuccess &&
+                  cudaMalloc((void**)&g->out_order, N * sizeof(int32_t)) == cudaSuccess &&
                   cudaMallocHost((void**)&g->host_state, sizeof(WState)) == cudaSuccess &&
                   cudaEventCreate(&g->ev0) == cudaSuccess && cudaEventCreate(&g->ev1) == cudaSuccess;
         for (int i = 0; ok && i < 4; ++i) ok = cudaMalloc((void**)&g->vec[i], N * sizeof(float)) == cudaSuccess;
@@ -457,6 +514,8 @@ extern "C" pr_status pr_create_wgraph(int64_t n, int64_t nnz, const int64_t* row
         if (e == cudaSuccess) e = cudaMemcpyAsync(g->out_rowptr, orp.data(), orp.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(g->out_dst, odst.data(), odst.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(g->out_eid, oeid.data(), oeid.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g->in_order, in_order.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g->out_order, out_order.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) {
             rc = cuda_fail(e, "pr_create_wgraph: upload");
             break;

@@ -64,7 +64,7 @@ extern "C" pr_status pr_destroy_graph(pr_graph* g) {
     void* dev[] = {g->rowptr, g->colidx, g->inv_out, g->order, g->rank, g->x[0], g->x[1],
                    g->y[0], g->y[1], g->teleport, g->stage, g->seg_row, g->seg_ptr, g->seg_sum,
                    g->tiles, g->state, g->slots, g->nb_items, g->nb_slots,
-                   g->nb_scalars, g->nb_block_sweeps};
+                   g->nb_scalars, g->nb_block_sweeps, g->frozen};
     cudaError_t first = cudaSuccess;
     for (void* p : dev)
         if (p) {
@@ -169,6 +169,15 @@ static pr_status set_option_impl(pr_graph* g, int key, int64_t value) {
             if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_BATCH_BF16 needs a graph");
             if (value < 0 || value > 8) return fail(PR_ERR_INVALID_ARG, "PR_OPT_BATCH_BF16 must be in [0, 8]");
             g->batch_bf16 = (int)value;
+            return PR_OK;
+        case PR_OPT_PERFORATION:
+            if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_PERFORATION needs a graph");
+            if (value < 0 || value > 30) return fail(PR_ERR_INVALID_ARG, "PR_OPT_PERFORATION must be in [0, 30]");
+            if (value > 0 && !g->frozen) {
+                cudaError_t e = dev_alloc(g, (void**)&g->frozen, (size_t)(g->n + kPad));
+                if (e != cudaSuccess) return cuda_fail(e, "PR_OPT_PERFORATION: allocation");
+            }
+            g->perforation = (int)value;
             return PR_OK;
         case PR_OPT_INDEX64:
             if (g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_INDEX64 is set with g = NULL (it applies to the next pr_create_graph)");

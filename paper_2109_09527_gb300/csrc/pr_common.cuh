@@ -115,6 +115,9 @@ struct IterArgs {
     int32_t hot;                 // L1 policy of the global gathers (ld_gather)
     int32_t hot_n;               // ids [0, hot_n) of y are cached in shared memory
     int32_t staged;              // 1: light tiles gathered edge-parallel (process_staged_tile)
+    uint8_t* frozen;             // loop perforation: frozen rows (NULL = off)
+    float perf_eps;
+    int32_t pad3;
 };
 
 }  // namespace prk
@@ -134,6 +137,8 @@ struct pr_graph {
     int64_t nb_hubs = prk::kDefaultNbHubs;    // hub snapshot of the barrier-free kernel (PR_OPT_NB_HUBS)
     int64_t nb_l1_hubs = prk::kDefaultNbL1Hubs;  // weak L1-cached hub gathers (PR_OPT_NB_L1_HUBS)
     int batch_bf16 = 0;                       // batched solver: BF16 Y until changes < 10^-value (0 = off)
+    int perforation = 0;                      // loop perforation eps = 10^-value (0 = off)
+    uint8_t* frozen = nullptr;                // frozen rows of the perforated synchronous solve
     int staged_tiles = prk::kDefaultStaged;   // bit 0: Jacobi, bit 1: barrier-free (see PR_OPT_STAGED_TILES)
 
     void* rowptr = nullptr;

@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kIterBlock, kGatherMinBlocks) k_heavy_segments
 // One block of kIterBlock threads per SM; each 256-thread group walks its own
 // tiles (round-robin over all groups of the grid) and shares the block's copy
 // of the hot prefix of y.
-template <typename IdxT, bool kUniform, bool kStaged>
+template <typename IdxT, bool kUniform, bool kStaged, bool kPerf>
 __global__ void __launch_bounds__(kIterBlock, kGatherMinBlocks) k_rows(IterArgs a, const float* __restrict__ x_in,
                                                      const float* __restrict__ y_in,
                                                      float* __restrict__ x_out, float* __restrict__ y_out) {
@@ -113,6 +113,8 @@ __global__ void __launch_bounds__(kIterBlock, kGatherMinBlocks) k_rows(IterArgs 
     c.hot = a.hot;
     c.hot_n = a.hot_n;
     c.hot_sm = hot_sm;
+    c.frozen = a.frozen;
+    c.perf_eps = a.perf_eps;
     Acc acc;
     const int groups = blockDim.x / kBlock;
     const int tid = threadIdx.x & (kBlock - 1);
@@ -128,20 +130,26 @@ __global__ void __launch_bounds__(kIterBlock, kGatherMinBlocks) k_rows(IterArgs 
                     threadIdx.x == 0)
                     atomicOr(&st->error, 1u);
             } else {
-                process_light_tile<IdxT, kUniform, false>(tile, a.rowptr, a.colidx, a.inv_out, a.teleport,
-                                                           x_in, y_in, x_out, y_out, c, acc, tid);
+                process_light_tile<IdxT, kUniform, false, kPerf>(tile, a.rowptr, a.colidx, a.inv_out, a.teleport,
+                                                                  x_in, y_in, x_out, y_out, c, acc, tid);
             }
         } else if (tile.kind == kTileZero) {
-            process_zero_tile<kUniform, false>(tile, a.inv_out, a.teleport, x_in, x_out, y_out, c, acc, tid);
+            process_zero_tile<kUniform, false, kPerf>(tile, a.inv_out, a.teleport, x_in, x_out, y_out, c, acc, tid,
+                                                      y_in);
         } else {  // heavy rows: sum of the segment partials
             for (int64_t r = tile.row_begin + tid; r < tile.row_end; r += kBlock) {
                 const float xo = ld_stream(x_in + r);
                 const float inv = ld_stream(a.inv_out + r);
+                if (kPerf && c.frozen[r]) {
+                    perf_copy(r, xo, ld_stream(y_in + r), inv, x_out, y_out, acc);
+                    continue;
+                }
                 const float tv = kUniform ? 0.f : ld_stream(a.teleport + r);
                 float s = 0.f;
                 const int32_t j1 = a.seg_ptr[r + 1];
                 for (int32_t j = a.seg_ptr[r]; j < j1; ++j) s += __ldcg(a.seg_sum + j);
-                row_update<kUniform, false>(r, s, xo, inv, tv, c, x_out, y_out, acc);
+                const float xn = row_update<kUniform, false>(r, s, xo, inv, tv, c, x_out, y_out, acc);
+                if (kPerf) perf_check(r, xn, xo, c);
             }
         }
     }
@@ -251,6 +259,8 @@ IterArgs make_args(const pr_graph* g, bool uniform) {
                       std::min<int64_t>(g->hot_vertices & 0x0fffffff, g->n));
     a.hot_n = (int32_t)(std::min<int64_t>(g->hot_cache, g->n) & ~(int64_t)3);
     a.staged = g->staged_tiles & 1;
+    a.frozen = g->perforation > 0 ? g->frozen : nullptr;
+    a.perf_eps = g->perforation > 0 ? (float)std::pow(10.0, -(double)g->perforation) : 0.f;
     return a;
 }
 
@@ -269,17 +279,20 @@ cudaError_t enqueue_iteration_t(const pr_graph* g, const IterArgs& a, int src, b
         k_heavy_segments<IdxT><<<seg_grid(g), kIterBlock, hot, s>>>(a, g->y[src]);
         ++*launches;
     }
-    const int grid = row_grid(g, a.staged != 0);
+    const int grid = row_grid(g, a.staged != 0 && !a.frozen);
     const float* xi = g->x[src];
     const float* yi = g->y[src];
     float* xo = g->x[1 - src];
     float* yo = g->y[1 - src];
-    if (a.staged) {
-        if (uniform) k_rows<IdxT, true, true><<<grid, kIterBlock, rows_smem, s>>>(a, xi, yi, xo, yo);
-        else k_rows<IdxT, false, true><<<grid, kIterBlock, rows_smem, s>>>(a, xi, yi, xo, yo);
+    if (a.frozen) {   // loop perforation (row-by-row tiles only)
+        if (uniform) k_rows<IdxT, true, false, true><<<grid, kIterBlock, hot, s>>>(a, xi, yi, xo, yo);
+        else k_rows<IdxT, false, false, true><<<grid, kIterBlock, hot, s>>>(a, xi, yi, xo, yo);
+    } else if (a.staged) {
+        if (uniform) k_rows<IdxT, true, true, false><<<grid, kIterBlock, rows_smem, s>>>(a, xi, yi, xo, yo);
+        else k_rows<IdxT, false, true, false><<<grid, kIterBlock, rows_smem, s>>>(a, xi, yi, xo, yo);
     } else {
-        if (uniform) k_rows<IdxT, true, false><<<grid, kIterBlock, rows_smem, s>>>(a, xi, yi, xo, yo);
-        else k_rows<IdxT, false, false><<<grid, kIterBlock, rows_smem, s>>>(a, xi, yi, xo, yo);
+        if (uniform) k_rows<IdxT, true, false, false><<<grid, kIterBlock, rows_smem, s>>>(a, xi, yi, xo, yo);
+        else k_rows<IdxT, false, false, false><<<grid, kIterBlock, rows_smem, s>>>(a, xi, yi, xo, yo);
     }
     ++*launches;
     return cudaGetLastError();
@@ -415,30 +428,33 @@ pr_status alloc_solver(pr_graph* g) {
         const int hot = (int)(kHotCacheMax * sizeof(float));
         const int rows = (int)((kHotCacheMax + kStageFloats) * sizeof(float));
         const void* row_kernels[] = {
-            (const void*)k_rows<int32_t, true, false>, (const void*)k_rows<int32_t, false, false>,
-            (const void*)k_rows<int64_t, true, false>, (const void*)k_rows<int64_t, false, false>,
-            (const void*)k_rows<int32_t, true, true>,  (const void*)k_rows<int32_t, false, true>,
-            (const void*)k_rows<int64_t, true, true>,  (const void*)k_rows<int64_t, false, true>};
+            (const void*)k_rows<int32_t, true, false, false>, (const void*)k_rows<int32_t, false, false, false>,
+            (const void*)k_rows<int64_t, true, false, false>, (const void*)k_rows<int64_t, false, false, false>,
+            (const void*)k_rows<int32_t, true, true, false>,  (const void*)k_rows<int32_t, false, true, false>,
+            (const void*)k_rows<int64_t, true, true, false>,  (const void*)k_rows<int64_t, false, true, false>,
+            (const void*)k_rows<int32_t, true, false, true>,  (const void*)k_rows<int32_t, false, false, true>,
+            (const void*)k_rows<int64_t, true, false, true>,  (const void*)k_rows<int64_t, false, false, true>};
         const void* seg_kernels[] = {(const void*)k_heavy_segments<int32_t>,
                                      (const void*)k_heavy_segments<int64_t>};
         // These kernels need little shared memory: the preferred carveout 0
         // gives the rest of the SRAM to L1, which caches the hub ranks.
-        // The staged kernels (the last four) hold a 24.6 KB staging area per
+        // The staged kernels (entries 4..7) hold a 24.6 KB staging area per
         // block: carve out enough shared memory for four blocks per SM.
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < 12; ++i) {
+            const bool staged = i >= 4 && i < 8;
             PRK_CHECK(cudaFuncSetAttribute(row_kernels[i], cudaFuncAttributeMaxDynamicSharedMemorySize, rows));
             PRK_CHECK(cudaFuncSetAttribute(row_kernels[i], cudaFuncAttributePreferredSharedMemoryCarveout,
-                                           i < 4 ? 0 : 50));
+                                           staged ? 50 : 0));
         }
         for (const void* k : seg_kernels) {
             PRK_CHECK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, hot));
             PRK_CHECK(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
         }
         int occ = 0;
-        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rows<int32_t, false, true>, kIterBlock,
+        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rows<int32_t, false, true, false>, kIterBlock,
                                                                  kStageFloats * sizeof(float)));
         g_occ_rows_staged = std::max(1, occ);
-        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rows<int32_t, false, false>, kIterBlock, 0));
+        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rows<int32_t, false, false, false>, kIterBlock, 0));
         int occ_seg = 0;
         PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_seg, k_heavy_segments<int32_t>, kIterBlock, 0));
         g_occ_seg = std::max(1, occ_seg);
@@ -493,6 +509,7 @@ pr_status run_jacobi(pr_graph* g, float damping, double tol, int32_t max_iter, c
     launch_init(g, a, t_dev, x0_dev, s);
     ++launches;
     PRK_CHECK(cudaGetLastError());
+    if (a.frozen) PRK_CHECK(cudaMemsetAsync(g->frozen, 0, (size_t)g->n, s));   // nothing frozen yet
     PRK_CHECK(cudaEventRecord(g->ev_loop0, s));
 
     if (allow_graph && g->use_graph) {

@@ -31,6 +31,9 @@
 #ifndef PRK_L2_YSTORE
 #define PRK_L2_YSTORE 0
 #endif
+#ifndef PRK_NB_X_WEAK
+#define PRK_NB_X_WEAK 0
+#endif
 
 namespace prk {
 
@@ -245,6 +248,8 @@ struct RowCtx {
     int32_t hot;      // L1 policy of the global gathers (see ld_gather)
     int32_t hot_n;    // binned ids [0, hot_n) are read from hot_sm (shared memory)
     const float* hot_sm;
+    uint8_t* frozen;  // loop perforation (Alg. 5): 1 = row no longer recomputed
+    float perf_eps;   // a row whose change is nonzero and below this freezes
 };
 
 template <bool kInPlace>
@@ -267,8 +272,14 @@ struct Mem<true> {
         if (c < x.hot) return ld_weak_l1(y + c);
         return ld_relaxed_p<PRK_L2_GATHER>(y + c);
     }
+#if PRK_NB_X_WEAK
+    // x(v) is read and written by v's owner alone: weak L2 accesses, no race
+    static __device__ __forceinline__ float load_x(const float* p) { return __ldcg(p); }
+    static __device__ __forceinline__ void store_x(float* p, float v) { __stcg(p, v); }
+#else
     static __device__ __forceinline__ float load_x(const float* p) { return ld_relaxed_p<PRK_L2_STREAM>(p); }
     static __device__ __forceinline__ void store_x(float* p, float v) { st_relaxed_p<PRK_L2_STREAM>(p, v); }
+#endif
     static __device__ __forceinline__ void store_y(float* p, float v) { st_relaxed_p<PRK_L2_GATHER>(p, v); }
 };
 
@@ -290,8 +301,8 @@ struct Acc {
 };
 
 template <bool kUniform, bool kInPlace>
-__device__ __forceinline__ void row_update(int64_t r, float s, float xo, float inv, float tv,
-                                           const RowCtx& c, float* x_out, float* y_out, Acc& acc) {
+__device__ __forceinline__ float row_update(int64_t r, float s, float xo, float inv, float tv,
+                                            const RowCtx& c, float* x_out, float* y_out, Acc& acc) {
     const float base = kUniform ? c.base : fmaf(c.one_m_d, tv, c.d_share);
     const float xn = fmaf(c.d, s, base);
     Mem<kInPlace>::store_x(x_out + r, xn);
@@ -303,18 +314,40 @@ __device__ __forceinline__ void row_update(int64_t r, float s, float xo, float i
     } else {
         if (inv == 0.f) acc.kahan(xn);
     }
+    return xn;
+}
+
+// Loop perforation (Alg. 5), synchronous form: a frozen row is copied forward
+// (its rank still feeds the gathers and, if dangling, the dangling mass); a
+// row whose update changed it by a nonzero amount below eps freezes.
+__device__ __forceinline__ void perf_copy(int64_t r, float xo, float yo, float inv, float* x_out, float* y_out,
+                                          Acc& acc) {
+    st_stream(x_out + r, xo);
+    st_y(y_out + r, yo);
+    if (inv == 0.f) acc.kahan(xo);
+}
+
+__device__ __forceinline__ void perf_check(int64_t r, float xn, float xo, const RowCtx& c) {
+    const float ch = fabsf(xn - xo);
+    if (ch != 0.f && ch < c.perf_eps) c.frozen[r] = 1;
 }
 
 // Rows without in-edges: thread per row, s = 0.
-template <bool kUniform, bool kInPlace>
+template <bool kUniform, bool kInPlace, bool kPerf = false>
 __device__ __forceinline__ void process_zero_tile(const Tile& tile, const float* inv_out,
                                                   const float* teleport, const float* x_in,
                                                   float* x_out, float* y_out, const RowCtx& c,
-                                                  Acc& acc, int tid) {
+                                                  Acc& acc, int tid, const float* y_in = nullptr) {
     for (int64_t r = tile.row_begin + tid; r < tile.row_end; r += kBlock) {
         const float tv = kUniform ? 0.f : ld_stream(teleport + r);
-        row_update<kUniform, kInPlace>(r, 0.f, Mem<kInPlace>::load_x(x_in + r), ld_stream(inv_out + r),
-                                       tv, c, x_out, y_out, acc);
+        const float xo = Mem<kInPlace>::load_x(x_in + r);
+        const float inv = ld_stream(inv_out + r);
+        if (kPerf && c.frozen[r]) {
+            perf_copy(r, xo, ld_stream(y_in + r), inv, x_out, y_out, acc);
+            continue;
+        }
+        const float xn = row_update<kUniform, kInPlace>(r, 0.f, xo, inv, tv, c, x_out, y_out, acc);
+        if (kPerf) perf_check(r, xn, xo, c);
     }
 }
 
@@ -326,7 +359,7 @@ __device__ __forceinline__ void process_zero_tile(const Tile& tile, const float*
 // has up to four colidx loads and four gathers in flight; coalesced colidx
 // reads within the group; shuffle reduction; the group's first lane updates
 // both rows.
-template <typename IdxT, bool kUniform, bool kInPlace>
+template <typename IdxT, bool kUniform, bool kInPlace, bool kPerf = false>
 __device__ __forceinline__ void process_light_tile(const Tile& tile, const void* rowptr,
                                                    const int32_t* colidx, const float* inv_out,
                                                    const float* teleport, const float* x_in,
@@ -339,18 +372,22 @@ __device__ __forceinline__ void process_light_tile(const Tile& tile, const void*
     const int gl = tid & (g - 1);
     for (int64_t r0 = tile.row_begin; r0 < tile.row_end; r0 += 2 * rpp) {
         int64_t rr[2];
-        bool act[2];
+        bool act[2], fz[2];
         int64_t b[2], e[2];
         float xo[2], inv[2], tv[2];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             rr[q] = r0 + q * rpp + grp;
             act[q] = rr[q] < tile.row_end;
+            fz[q] = false;
             b[q] = e[q] = 0;
             xo[q] = inv[q] = tv[q] = 0.f;
             if (act[q]) {
-                b[q] = row_at<IdxT>(rowptr, rr[q]);
-                e[q] = row_at<IdxT>(rowptr, rr[q] + 1);
+                if (kPerf) fz[q] = c.frozen[rr[q]] != 0;   // frozen rows gather nothing
+                if (!fz[q]) {
+                    b[q] = row_at<IdxT>(rowptr, rr[q]);
+                    e[q] = row_at<IdxT>(rowptr, rr[q] + 1);
+                }
                 if (gl == 0) {
                     xo[q] = Mem<kInPlace>::load_x(x_in + rr[q]);
                     inv[q] = ld_stream(inv_out + rr[q]);
@@ -384,8 +421,16 @@ __device__ __forceinline__ void process_light_tile(const Tile& tile, const void*
             }
         if (gl == 0) {
 #pragma unroll
-            for (int q = 0; q < 2; ++q)
-                if (act[q]) row_update<kUniform, kInPlace>(rr[q], s[q], xo[q], inv[q], tv[q], c, x_out, y_out, acc);
+            for (int q = 0; q < 2; ++q) {
+                if (!act[q]) continue;
+                if (kPerf && fz[q]) {
+                    perf_copy(rr[q], xo[q], ld_stream(y_in + rr[q]), inv[q], x_out, y_out, acc);
+                    continue;
+                }
+                const float xn = row_update<kUniform, kInPlace>(rr[q], s[q], xo[q], inv[q], tv[q], c, x_out,
+                                                                y_out, acc);
+                if (kPerf) perf_check(rr[q], xn, xo[q], c);
+            }
         }
     }
 }

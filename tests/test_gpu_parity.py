@@ -330,3 +330,36 @@ def test_nonblocking_l1_hub_gathers(l1_hubs):
     assert info.converged == 1 and info.residual_l1 < 1e-6
     assert l1(x, xstar) <= info.residual_l1 / (1 - D) + 2e-7
     assert max_rel(x, xstar) <= 1e-4
+
+
+# ------------------------------------------------------- loop perforation --
+
+@pytest.mark.parametrize("heavy", [1024, 64])
+def test_loop_perforation(heavy):
+    """Alg. 5 in the synchronous solver.  A bound no FP32 change goes below freezes nothing,
+    so the solve is the plain one, bit for bit; with eps = 1e-11 rows freeze, the solve
+    needs no more iterations, and its distance to the fixed point is of the size the FP64
+    oracle's own perforated run reaches (within 5x, plus the FP32 rounding)."""
+    rp, ci = gg.rmat(14, seed=21)
+    pr.set_heavy_degree(heavy)
+    try:
+        g = pr.Graph(rp, ci)
+    finally:
+        pr.set_heavy_degree(1024)
+    xstar, _, _ = oracle.fixed_point(rp, ci, d=D)
+    with g:
+        x0, info0 = g.solve(tol=1e-7, max_iter=300)
+        g.set_option(pr.PR_OPT_PERFORATION, 30)
+        x1, info1 = g.solve(tol=1e-7, max_iter=300)
+        assert np.array_equal(x0, x1) and info1.iterations == info0.iterations
+        g.set_option(pr.PR_OPT_PERFORATION, 11)
+        x2, info2 = g.solve(tol=1e-7, max_iter=300)
+        g.set_option(pr.PR_OPT_PERFORATION, 0)
+        x3, info3 = g.solve(tol=1e-7, max_iter=300)
+    assert np.array_equal(x0, x3)                      # off again: the plain solve
+    assert info2.converged == 1 and info2.iterations <= info0.iterations
+    xo, _, _, nf = oracle.pagerank_perforated(rp, ci, d=D, tol=1e-7, max_iter=300, eps=1e-11)
+    assert nf > 0
+    err_gpu = l1(x2, xstar)
+    err_oracle = l1(xo, xstar)
+    assert err_gpu <= 5 * err_oracle + info2.residual_l1 / (1 - D) + 2e-7, (err_gpu, err_oracle)

@@ -489,3 +489,32 @@ def test_adjoint_against_central_differences():
         wm[e] -= h
         fd = (L(t, wp) - L(t, wm)) / (2 * h)
         assert fd == pytest.approx(adj["grad_w"][e], rel=1e-4, abs=1e-9)
+
+
+
+# ------------------------------------------------------------ loop perforation --
+
+def test_perforation_with_eps_zero_is_alg1():
+    rp, ci = gg.rmat(11, 16, seed=8)
+    x0, it0, r0 = oracle.pagerank_jacobi(rp, ci, tol=1e-12, max_iter=500)
+    x1, it1, r1, nf = oracle.pagerank_perforated(rp, ci, tol=1e-12, max_iter=500, eps=0.0)
+    assert nf == 0 and it0 == it1 and np.array_equal(x0, x1)
+
+
+def test_perforation_freezes_and_stays_close():
+    """Vertices freeze as their changes shrink (on R-MAT-11 all of them by the end); the
+    perforated result stays close to the fixed point, and a larger eps stops sooner and
+    errs more."""
+    rp, ci = gg.rmat(11, 16, seed=8)
+    xs, _, _ = oracle.fixed_point(rp, ci)
+    _, it_plain, _ = oracle.pagerank_jacobi(rp, ci, tol=1e-10, max_iter=500)
+    errs, iters = [], []
+    for eps in (1e-12, 1e-9):
+        x, it, r, nf = oracle.pagerank_perforated(rp, ci, tol=1e-10, max_iter=500, eps=eps)
+        errs.append(float(np.abs(x - xs).sum()))
+        iters.append(it)
+        assert r < 1e-10 and nf > 0
+        assert abs(x.sum() - 1.0) < 1e-5        # frozen ranks no longer conserve mass exactly
+    assert iters[1] < iters[0] <= it_plain
+    assert errs[0] < errs[1]
+    assert errs[0] < 1e-8 and errs[1] < 1e-5
