@@ -42,6 +42,13 @@ constexpr int kIterBlock = 256;          // threads per block of the Jacobi iter
 #define PRK_GATHER_MIN_BLOCKS 4
 #endif
 constexpr int kGatherMinBlocks = PRK_GATHER_MIN_BLOCKS;
+// The barrier-free kernel is latency-bound: six blocks per SM (40 registers a
+// thread, a few spilled) measured faster than four (ER-24: 2.15 -> 1.77 ms
+// per sweep-equivalent), while the synchronous kernels are best at four.
+#ifndef PRK_NB_MIN_BLOCKS
+#define PRK_NB_MIN_BLOCKS 6
+#endif
+constexpr int kNbMinBlocks = PRK_NB_MIN_BLOCKS;
 constexpr int kHotCacheMax = 40960;      // largest shared-memory copy of y's hot prefix (160 KB)
 constexpr int kTileEdgesMax = 6144;      // edges of a light tile
 constexpr int kTileRowsMax = 2048;       // rows of a light tile

@@ -151,7 +151,7 @@ __device__ __forceinline__ void warp_segment(int64_t sid, const NbArgs& a, const
 }
 
 template <typename IdxT, bool kUniform, bool kStaged>
-__global__ void __launch_bounds__(kNbBlock, kGatherMinBlocks) k_nonblocking(NbArgs a) {
+__global__ void __launch_bounds__(kNbBlock, kNbMinBlocks) k_nonblocking(NbArgs a) {
     // dynamic shared memory: the hub snapshot (hub_n floats), then the staging
     // area of kStaged tiles (kStageFloats floats)
     extern __shared__ __align__(16) float nb_smem[];
