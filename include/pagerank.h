@@ -239,6 +239,15 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
  *                         the contraction bound of the residual; frozen rows
  *                         count as changes of 0 in the residual.  Row-by-row
  *                         tiles only (PR_OPT_STAGED_TILES is ignored).
+ *   PR_OPT_DYNAMIC_TILES  synchronous solver: 0 (default) each block owns a
+ *                         fixed round-robin share of the row tiles; 1 blocks
+ *                         take tiles from a shared counter, so a slow block's
+ *                         work is taken over by the others (the GPU form of
+ *                         Barrier-Helper, Alg. 6).
+ *   PR_OPT_DELAY_NS       synchronous solver, for experiments: block 0 sleeps
+ *                         this many nanoseconds (0..1e6, __nanosleep, bounded)
+ *                         before taking each tile -- a slowed processor, as
+ *                         in the paper's delayed-thread experiments.  0 = off.
  *   PR_OPT_INDEX64        1: keep 64-bit row offsets on the device even when
  *                         the edge count fits 32 bits (thread-local default
  *                         for the next pr_create_graph, set with g = NULL;
@@ -255,6 +264,8 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
 #define PR_OPT_NB_L1_HUBS 9
 #define PR_OPT_BATCH_BF16 10
 #define PR_OPT_PERFORATION 11
+#define PR_OPT_DYNAMIC_TILES 12
+#define PR_OPT_DELAY_NS 13
 PR_API pr_status pr_set_option(pr_graph* g, int key, int64_t value);
 
 /* Batched personalised PageRank: k independent solves on one graph, one per

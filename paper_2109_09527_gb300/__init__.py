@@ -49,6 +49,8 @@ PR_OPT_NB_HUBS = 8
 PR_OPT_NB_L1_HUBS = 9
 PR_OPT_BATCH_BF16 = 10
 PR_OPT_PERFORATION = 11
+PR_OPT_DYNAMIC_TILES = 12
+PR_OPT_DELAY_NS = 13
 
 LIB_PATH = _build.LIB_PATH
 

@@ -179,6 +179,16 @@ static pr_status set_option_impl(pr_graph* g, int key, int64_t value) {
             }
             g->perforation = (int)value;
             return PR_OK;
+        case PR_OPT_DYNAMIC_TILES:
+            if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_DYNAMIC_TILES needs a graph");
+            if (value != 0 && value != 1) return fail(PR_ERR_INVALID_ARG, "PR_OPT_DYNAMIC_TILES is 0 or 1");
+            g->dynamic_tiles = (int)value;
+            return PR_OK;
+        case PR_OPT_DELAY_NS:
+            if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_DELAY_NS needs a graph");
+            if (value < 0 || value > 1000000) return fail(PR_ERR_INVALID_ARG, "PR_OPT_DELAY_NS must be in [0, 1e6]");
+            g->delay_ns = (int)value;
+            return PR_OK;
         case PR_OPT_INDEX64:
             if (g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_INDEX64 is set with g = NULL (it applies to the next pr_create_graph)");
             if (value != 0 && value != 1) return fail(PR_ERR_INVALID_ARG, "PR_OPT_INDEX64 is 0 or 1");

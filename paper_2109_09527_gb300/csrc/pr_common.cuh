@@ -99,7 +99,7 @@ struct SolveState {
     uint32_t ticket;   // arrival counter of the last-block reductions
     uint32_t error;    // device-side error bits
     int32_t sweeps_max;
-    int32_t pad;
+    uint32_t tile_next;  // next tile to hand out (dynamic tile assignment)
 };
 
 // Arguments of the per-iteration kernels (passed by value).
@@ -124,6 +124,8 @@ struct IterArgs {
     int32_t staged;              // 1: light tiles gathered edge-parallel (process_staged_tile)
     uint8_t* frozen;             // loop perforation: frozen rows (NULL = off)
     float perf_eps;
+    int32_t dynamic;             // 1: blocks take tiles from a shared counter (helping)
+    int32_t delay_ns;            // > 0: block 0 sleeps this long per tile (slow-processor model)
     int32_t pad3;
 };
 
@@ -145,6 +147,8 @@ struct pr_graph {
     int64_t nb_l1_hubs = prk::kDefaultNbL1Hubs;  // weak L1-cached hub gathers (PR_OPT_NB_L1_HUBS)
     int batch_bf16 = 0;                       // batched solver: BF16 Y until changes < 10^-value (0 = off)
     int perforation = 0;                      // loop perforation eps = 10^-value (0 = off)
+    int dynamic_tiles = 0;                    // PR_OPT_DYNAMIC_TILES
+    int delay_ns = 0;                         // PR_OPT_DELAY_NS
     uint8_t* frozen = nullptr;                // frozen rows of the perforated synchronous solve
     int staged_tiles = prk::kDefaultStaged;   // bit 0: Jacobi, bit 1: barrier-free (see PR_OPT_STAGED_TILES)
 

@@ -113,14 +113,30 @@ __global__ void __launch_bounds__(kIterBlock, kGatherMinBlocks) k_rows(IterArgs 
     c.hot = a.hot;
     c.hot_n = a.hot_n;
     c.hot_sm = hot_sm;
-    c.frozen = a.frozen;
-    c.perf_eps = a.perf_eps;
+    const Perf pf{a.frozen, a.perf_eps};
     Acc acc;
     const int groups = blockDim.x / kBlock;
     const int tid = threadIdx.x & (kBlock - 1);
     const int group = blockIdx.x * groups + threadIdx.x / kBlock;
 
-    for (int t = group; t < a.n_tiles; t += gridDim.x * groups) {
+    // Static assignment: tiles group, group + #groups, ...  Dynamic (the GPU
+    // form of Barrier-Helper, Alg. 6): a block takes the next unclaimed tile
+    // from a shared counter, so blocks that finish early take over the work of
+    // slow ones and no block waits on another's share.
+    // A slowed block 0 (PR_OPT_DELAY_NS) sleeps before taking each tile.
+    __shared__ int s_tile;
+    auto next_tile = [&](int prev) -> int {
+        if (a.delay_ns > 0 && blockIdx.x == 0) {
+            if (threadIdx.x == 0) __nanosleep((unsigned)a.delay_ns);
+            __syncthreads();
+        }
+        if (!a.dynamic) return prev < 0 ? group : prev + (int)gridDim.x * groups;
+        __syncthreads();
+        if (threadIdx.x == 0) s_tile = (int)atomicAdd(&st->tile_next, 1u);
+        __syncthreads();
+        return s_tile;
+    };
+    for (int t = next_tile(-1); t < a.n_tiles; t = next_tile(t)) {
         const Tile tile = a.tiles[t];
         if (tile.kind >= 0) {
             if (kStaged) {
@@ -129,18 +145,23 @@ __global__ void __launch_bounds__(kIterBlock, kGatherMinBlocks) k_rows(IterArgs 
                                                                 acc, tid, hot_sm + a.hot_n) &&
                     threadIdx.x == 0)
                     atomicOr(&st->error, 1u);
+            } else if (kPerf) {
+                perf_light_tile<IdxT, kUniform>(tile, a.rowptr, a.colidx, a.inv_out, a.teleport, x_in, y_in,
+                                                x_out, y_out, c, pf, acc, tid);
             } else {
-                process_light_tile<IdxT, kUniform, false, kPerf>(tile, a.rowptr, a.colidx, a.inv_out, a.teleport,
-                                                                  x_in, y_in, x_out, y_out, c, acc, tid);
+                process_light_tile<IdxT, kUniform, false>(tile, a.rowptr, a.colidx, a.inv_out, a.teleport,
+                                                           x_in, y_in, x_out, y_out, c, acc, tid);
             }
         } else if (tile.kind == kTileZero) {
-            process_zero_tile<kUniform, false, kPerf>(tile, a.inv_out, a.teleport, x_in, x_out, y_out, c, acc, tid,
-                                                      y_in);
+            if (kPerf)
+                perf_zero_tile<kUniform>(tile, a.inv_out, a.teleport, x_in, y_in, x_out, y_out, c, pf, acc, tid);
+            else
+                process_zero_tile<kUniform, false>(tile, a.inv_out, a.teleport, x_in, x_out, y_out, c, acc, tid);
         } else {  // heavy rows: sum of the segment partials
             for (int64_t r = tile.row_begin + tid; r < tile.row_end; r += kBlock) {
                 const float xo = ld_stream(x_in + r);
                 const float inv = ld_stream(a.inv_out + r);
-                if (kPerf && c.frozen[r]) {
+                if (kPerf && pf.frozen[r]) {
                     perf_copy(r, xo, ld_stream(y_in + r), inv, x_out, y_out, acc);
                     continue;
                 }
@@ -148,8 +169,8 @@ __global__ void __launch_bounds__(kIterBlock, kGatherMinBlocks) k_rows(IterArgs 
                 float s = 0.f;
                 const int32_t j1 = a.seg_ptr[r + 1];
                 for (int32_t j = a.seg_ptr[r]; j < j1; ++j) s += __ldcg(a.seg_sum + j);
-                const float xn = row_update<kUniform, false>(r, s, xo, inv, tv, c, x_out, y_out, acc);
-                if (kPerf) perf_check(r, xn, xo, c);
+                if (kPerf) perf_update<kUniform>(r, s, xo, inv, tv, c, pf, x_out, y_out, acc);
+                else row_update<kUniform, false>(r, s, xo, inv, tv, c, x_out, y_out, acc);
             }
         }
     }
@@ -163,6 +184,7 @@ __global__ void __launch_bounds__(kIterBlock, kGatherMinBlocks) k_rows(IterArgs 
         const int done = (R < st->tol) || (st->iter >= st->max_iter);
         st->done = done;
         st->ticket = 0;
+        st->tile_next = 0;
         if (done && a.use_cond) cudaGraphSetConditional(a.cond, 0);
     }
 }
@@ -198,6 +220,7 @@ __global__ void __launch_bounds__(kBlock) k_init(IterArgs a, const float* __rest
         st->resid = INFINITY;
         st->error = 0;
         st->ticket = 0;
+        st->tile_next = 0;
     }
 }
 
@@ -261,6 +284,8 @@ IterArgs make_args(const pr_graph* g, bool uniform) {
     a.staged = g->staged_tiles & 1;
     a.frozen = g->perforation > 0 ? g->frozen : nullptr;
     a.perf_eps = g->perforation > 0 ? (float)std::pow(10.0, -(double)g->perforation) : 0.f;
+    a.dynamic = g->dynamic_tiles;
+    a.delay_ns = g->delay_ns;
     return a;
 }
 

@@ -31,9 +31,6 @@
 #ifndef PRK_L2_YSTORE
 #define PRK_L2_YSTORE 0
 #endif
-#ifndef PRK_NB_X_WEAK
-#define PRK_NB_X_WEAK 0
-#endif
 
 namespace prk {
 
@@ -248,8 +245,6 @@ struct RowCtx {
     int32_t hot;      // L1 policy of the global gathers (see ld_gather)
     int32_t hot_n;    // binned ids [0, hot_n) are read from hot_sm (shared memory)
     const float* hot_sm;
-    uint8_t* frozen;  // loop perforation (Alg. 5): 1 = row no longer recomputed
-    float perf_eps;   // a row whose change is nonzero and below this freezes
 };
 
 template <bool kInPlace>
@@ -272,14 +267,8 @@ struct Mem<true> {
         if (c < x.hot) return ld_weak_l1(y + c);
         return ld_relaxed_p<PRK_L2_GATHER>(y + c);
     }
-#if PRK_NB_X_WEAK
-    // x(v) is read and written by v's owner alone: weak L2 accesses, no race
-    static __device__ __forceinline__ float load_x(const float* p) { return __ldcg(p); }
-    static __device__ __forceinline__ void store_x(float* p, float v) { __stcg(p, v); }
-#else
     static __device__ __forceinline__ float load_x(const float* p) { return ld_relaxed_p<PRK_L2_STREAM>(p); }
     static __device__ __forceinline__ void store_x(float* p, float v) { st_relaxed_p<PRK_L2_STREAM>(p, v); }
-#endif
     static __device__ __forceinline__ void store_y(float* p, float v) { st_relaxed_p<PRK_L2_GATHER>(p, v); }
 };
 
@@ -301,8 +290,8 @@ struct Acc {
 };
 
 template <bool kUniform, bool kInPlace>
-__device__ __forceinline__ float row_update(int64_t r, float s, float xo, float inv, float tv,
-                                            const RowCtx& c, float* x_out, float* y_out, Acc& acc) {
+__device__ __forceinline__ void row_update(int64_t r, float s, float xo, float inv, float tv,
+                                           const RowCtx& c, float* x_out, float* y_out, Acc& acc) {
     const float base = kUniform ? c.base : fmaf(c.one_m_d, tv, c.d_share);
     const float xn = fmaf(c.d, s, base);
     Mem<kInPlace>::store_x(x_out + r, xn);
@@ -314,40 +303,18 @@ __device__ __forceinline__ float row_update(int64_t r, float s, float xo, float 
     } else {
         if (inv == 0.f) acc.kahan(xn);
     }
-    return xn;
-}
-
-// Loop perforation (Alg. 5), synchronous form: a frozen row is copied forward
-// (its rank still feeds the gathers and, if dangling, the dangling mass); a
-// row whose update changed it by a nonzero amount below eps freezes.
-__device__ __forceinline__ void perf_copy(int64_t r, float xo, float yo, float inv, float* x_out, float* y_out,
-                                          Acc& acc) {
-    st_stream(x_out + r, xo);
-    st_y(y_out + r, yo);
-    if (inv == 0.f) acc.kahan(xo);
-}
-
-__device__ __forceinline__ void perf_check(int64_t r, float xn, float xo, const RowCtx& c) {
-    const float ch = fabsf(xn - xo);
-    if (ch != 0.f && ch < c.perf_eps) c.frozen[r] = 1;
 }
 
 // Rows without in-edges: thread per row, s = 0.
-template <bool kUniform, bool kInPlace, bool kPerf = false>
+template <bool kUniform, bool kInPlace>
 __device__ __forceinline__ void process_zero_tile(const Tile& tile, const float* inv_out,
                                                   const float* teleport, const float* x_in,
                                                   float* x_out, float* y_out, const RowCtx& c,
-                                                  Acc& acc, int tid, const float* y_in = nullptr) {
+                                                  Acc& acc, int tid) {
     for (int64_t r = tile.row_begin + tid; r < tile.row_end; r += kBlock) {
         const float tv = kUniform ? 0.f : ld_stream(teleport + r);
-        const float xo = Mem<kInPlace>::load_x(x_in + r);
-        const float inv = ld_stream(inv_out + r);
-        if (kPerf && c.frozen[r]) {
-            perf_copy(r, xo, ld_stream(y_in + r), inv, x_out, y_out, acc);
-            continue;
-        }
-        const float xn = row_update<kUniform, kInPlace>(r, 0.f, xo, inv, tv, c, x_out, y_out, acc);
-        if (kPerf) perf_check(r, xn, xo, c);
+        row_update<kUniform, kInPlace>(r, 0.f, Mem<kInPlace>::load_x(x_in + r), ld_stream(inv_out + r),
+                                       tv, c, x_out, y_out, acc);
     }
 }
 
@@ -359,7 +326,7 @@ __device__ __forceinline__ void process_zero_tile(const Tile& tile, const float*
 // has up to four colidx loads and four gathers in flight; coalesced colidx
 // reads within the group; shuffle reduction; the group's first lane updates
 // both rows.
-template <typename IdxT, bool kUniform, bool kInPlace, bool kPerf = false>
+template <typename IdxT, bool kUniform, bool kInPlace>
 __device__ __forceinline__ void process_light_tile(const Tile& tile, const void* rowptr,
                                                    const int32_t* colidx, const float* inv_out,
                                                    const float* teleport, const float* x_in,
@@ -372,22 +339,18 @@ __device__ __forceinline__ void process_light_tile(const Tile& tile, const void*
     const int gl = tid & (g - 1);
     for (int64_t r0 = tile.row_begin; r0 < tile.row_end; r0 += 2 * rpp) {
         int64_t rr[2];
-        bool act[2], fz[2];
+        bool act[2];
         int64_t b[2], e[2];
         float xo[2], inv[2], tv[2];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             rr[q] = r0 + q * rpp + grp;
             act[q] = rr[q] < tile.row_end;
-            fz[q] = false;
             b[q] = e[q] = 0;
             xo[q] = inv[q] = tv[q] = 0.f;
             if (act[q]) {
-                if (kPerf) fz[q] = c.frozen[rr[q]] != 0;   // frozen rows gather nothing
-                if (!fz[q]) {
-                    b[q] = row_at<IdxT>(rowptr, rr[q]);
-                    e[q] = row_at<IdxT>(rowptr, rr[q] + 1);
-                }
+                b[q] = row_at<IdxT>(rowptr, rr[q]);
+                e[q] = row_at<IdxT>(rowptr, rr[q] + 1);
                 if (gl == 0) {
                     xo[q] = Mem<kInPlace>::load_x(x_in + rr[q]);
                     inv[q] = ld_stream(inv_out + rr[q]);
@@ -421,15 +384,116 @@ __device__ __forceinline__ void process_light_tile(const Tile& tile, const void*
             }
         if (gl == 0) {
 #pragma unroll
+            for (int q = 0; q < 2; ++q)
+                if (act[q]) row_update<kUniform, kInPlace>(rr[q], s[q], xo[q], inv[q], tv[q], c, x_out, y_out, acc);
+        }
+    }
+}
+
+// ---- loop perforation (Alg. 5), synchronous form --------------------------
+// Copies of the row-update paths above for the perforated solve, kept apart so
+// the plain paths compile exactly as before.  A frozen row is copied forward
+// (its rank still feeds the gathers and, if dangling, the dangling mass); a
+// row whose update changed it by a nonzero amount below eps freezes.
+struct Perf {
+    uint8_t* frozen;   // 1 = row no longer recomputed
+    float eps;
+};
+
+__device__ __forceinline__ void perf_copy(int64_t r, float xo, float yo, float inv, float* x_out, float* y_out,
+                                          Acc& acc) {
+    st_stream(x_out + r, xo);
+    st_y(y_out + r, yo);
+    if (inv == 0.f) acc.kahan(xo);
+}
+
+template <bool kUniform>
+__device__ __forceinline__ void perf_update(int64_t r, float s, float xo, float inv, float tv, const RowCtx& c,
+                                            const Perf& p, float* x_out, float* y_out, Acc& acc) {
+    const float base = kUniform ? c.base : fmaf(c.one_m_d, tv, c.d_share);
+    const float xn = fmaf(c.d, s, base);
+    st_stream(x_out + r, xn);
+    st_y(y_out + r, xn * inv);
+    acc.r += fabsf(xn - xo);
+    if (inv == 0.f) acc.kahan(xn);
+    const float ch = fabsf(xn - xo);
+    if (ch != 0.f && ch < p.eps) p.frozen[r] = 1;
+}
+
+template <bool kUniform>
+__device__ __forceinline__ void perf_zero_tile(const Tile& tile, const float* inv_out, const float* teleport,
+                                               const float* x_in, const float* y_in, float* x_out, float* y_out,
+                                               const RowCtx& c, const Perf& p, Acc& acc, int tid) {
+    for (int64_t r = tile.row_begin + tid; r < tile.row_end; r += kBlock) {
+        const float xo = ld_stream(x_in + r);
+        const float inv = ld_stream(inv_out + r);
+        if (p.frozen[r]) {
+            perf_copy(r, xo, ld_stream(y_in + r), inv, x_out, y_out, acc);
+            continue;
+        }
+        const float tv = kUniform ? 0.f : ld_stream(teleport + r);
+        perf_update<kUniform>(r, 0.f, xo, inv, tv, c, p, x_out, y_out, acc);
+    }
+}
+
+// process_light_tile with frozen rows skipped (Jacobi buffers only).
+template <typename IdxT, bool kUniform>
+__device__ __forceinline__ void perf_light_tile(const Tile& tile, const void* rowptr, const int32_t* colidx,
+                                                const float* inv_out, const float* teleport, const float* x_in,
+                                                const float* y_in, float* x_out, float* y_out, const RowCtx& c,
+                                                const Perf& p, Acc& acc, int tid) {
+    const int lg = tile.kind;
+    const int g = 1 << lg;
+    const int rpp = kBlock >> lg;
+    const int grp = tid >> lg;
+    const int gl = tid & (g - 1);
+    for (int64_t r0 = tile.row_begin; r0 < tile.row_end; r0 += 2 * rpp) {
+        int64_t rr[2];
+        bool act[2], fz[2];
+        int64_t b[2], e[2];
+        float xo[2], inv[2], tv[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            rr[q] = r0 + q * rpp + grp;
+            act[q] = rr[q] < tile.row_end;
+            fz[q] = act[q] && p.frozen[rr[q]] != 0;   // frozen rows gather nothing
+            b[q] = e[q] = 0;
+            xo[q] = inv[q] = tv[q] = 0.f;
+            if (act[q]) {
+                if (!fz[q]) {
+                    b[q] = row_at<IdxT>(rowptr, rr[q]);
+                    e[q] = row_at<IdxT>(rowptr, rr[q] + 1);
+                }
+                if (gl == 0) {
+                    xo[q] = ld_stream(x_in + rr[q]);
+                    inv[q] = ld_stream(inv_out + rr[q]);
+                    if (!kUniform) tv[q] = ld_stream(teleport + rr[q]);
+                }
+            }
+        }
+        float s[2] = {0.f, 0.f};
+        const int64_t len = max(e[0] - b[0], e[1] - b[1]);
+        for (int64_t k = gl; k < len; k += 2 * g) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int32_t c0 = b[q] + k < e[q] ? ld_stream(colidx + b[q] + k) : -1;
+                const int32_t c1 = b[q] + k + g < e[q] ? ld_stream(colidx + b[q] + k + g) : -1;
+                s[q] += (c0 >= 0 ? Mem<false>::gather(y_in, c0, c) : 0.f) +
+                        (c1 >= 0 ? Mem<false>::gather(y_in, c1, c) : 0.f);
+            }
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1)
+            if (o < g) {
+                s[0] += __shfl_xor_sync(0xffffffffu, s[0], o);
+                s[1] += __shfl_xor_sync(0xffffffffu, s[1], o);
+            }
+        if (gl == 0) {
+#pragma unroll
             for (int q = 0; q < 2; ++q) {
                 if (!act[q]) continue;
-                if (kPerf && fz[q]) {
-                    perf_copy(rr[q], xo[q], ld_stream(y_in + rr[q]), inv[q], x_out, y_out, acc);
-                    continue;
-                }
-                const float xn = row_update<kUniform, kInPlace>(rr[q], s[q], xo[q], inv[q], tv[q], c, x_out,
-                                                                y_out, acc);
-                if (kPerf) perf_check(rr[q], xn, xo[q], c);
+                if (fz[q]) perf_copy(rr[q], xo[q], ld_stream(y_in + rr[q]), inv[q], x_out, y_out, acc);
+                else perf_update<kUniform>(rr[q], s[q], xo[q], inv[q], tv[q], c, p, x_out, y_out, acc);
             }
         }
     }

@@ -363,3 +363,30 @@ def test_loop_perforation(heavy):
     err_gpu = l1(x2, xstar)
     err_oracle = l1(xo, xstar)
     assert err_gpu <= 5 * err_oracle + info2.residual_l1 / (1 - D) + 2e-7, (err_gpu, err_oracle)
+
+
+# ------------------------------------------------ helping and slow blocks --
+
+def test_dynamic_tiles_take_over_a_slow_block():
+    """Barrier-Helper's GPU form: with block 0 slowed (a bounded sleep before it takes each
+    tile), dynamic tile assignment lets the other blocks take its share, so the solve is
+    faster than with the static assignment.  A delay changes no arithmetic: the static run
+    is bit for bit the undelayed one; the dynamic run differs only in the order of the
+    per-block partial sums (last-bit changes of D and r)."""
+    rp, ci = gg.rmat(20, seed=23)     # several tiles per block
+    with pr.Graph(rp, ci) as g:
+        assert g.stats()["n_tiles"] > 3 * 608
+        x_ref, info_ref = g.solve(tol=1e-6, max_iter=200)
+        g.set_option(pr.PR_OPT_DELAY_NS, 100000)
+        times, xs = {}, {}
+        for dyn in (0, 1):
+            g.set_option(pr.PR_OPT_DYNAMIC_TILES, dyn)
+            best = None
+            for _ in range(2):
+                x, info = g.solve(tol=1e-6, max_iter=200)
+                best = info.ms_loop if best is None else min(best, info.ms_loop)
+            assert info.converged == 1
+            times[dyn], xs[dyn] = best, x
+    assert np.array_equal(xs[0], x_ref)
+    assert max_rel(xs[1], x_ref) <= 1e-5
+    assert times[1] < 0.7 * times[0], times
