@@ -56,6 +56,20 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", "1")))
 
 
+def combine_ranks(dist, device, elapsed, work):
+    """The whole job's figures from every rank's: the slowest rank's elapsed time (max) and
+    the work of all ranks (sum).  `dist` is torch.distributed or None (one process);
+    `device` is where the reduction tensors live (the rank's GPU for NCCL, cpu for gloo)."""
+    if dist is None:
+        return float(elapsed), float(work)
+    import torch
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    w = torch.tensor([float(work)], dtype=torch.float64, device=device)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(w.item())
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -434,15 +448,11 @@ def run_batched(args):
     if dist:
         dist.barrier()
     clocks = sampler.stop() if sampler else None
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
     iters = sum(i.iterations for i, _ in infos)
     col_iters = sum(int(its.sum()) for _, its in infos)
-    # edge-column updates that did work: each active column of each iteration
-    value = world * nnz * col_iters / (ms * 1e-3) / 1e9
+    # edge-column updates that did work: each active column of each iteration, all ranks
+    ms, work = combine_ranks(dist, dev, ev0.elapsed_time(ev1), float(nnz) * col_iters)
+    value = work / (ms * 1e-3) / 1e9
     loop_ms = sum(i.ms_loop for i, _ in infos)
     b_iter = batched_bytes(n, nnz, 32, st["rowptr_bytes"])
     achieved = b_iter * iters / (loop_ms * 1e-3) / 1e9
@@ -483,7 +493,7 @@ def run_batched(args):
                                               out=out_pin)
         e2e_iters += int(its_e.sum())
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_s, e2e_work = combine_ranks(dist, dev, time.perf_counter() - t0, float(nnz) * e2e_iters)
     g.close()
     if rank == 0:
         steps = args.steps
@@ -511,7 +521,7 @@ def run_batched(args):
                                             "speedup": single_ms / (ms / steps),
                                             "single_iterations_total": single_iters,
                                             "batched_iterations": infos[-1][0].iterations},
-                "e2e": {"value": world * nnz * e2e_iters / e2e_s / 1e9, "unit": "G edge-columns/s",
+                "e2e": {"value": e2e_work / e2e_s / 1e9, "unit": "G edge-columns/s",
                         "h2d_bytes_per_step": n * BATCH_K * 4, "d2h_bytes_per_step": n * BATCH_K * 4,
                         "ms_per_step": e2e_s * 1e3 / max(1, args.e2e_steps)},
                 "clocks": clocks}
@@ -566,15 +576,11 @@ def run_set(args):
     if dist:
         dist.barrier()
     clocks = sampler.stop() if sampler else None
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
     nnz_g = np.array([c.size for _, c in graphs], dtype=np.float64)
-    # edges of the graphs still iterating, summed over the iterations
-    visits = sum(float((nnz_g * its).sum()) for _, _, _, its in runs)
-    value = world * visits / (ms * 1e-3) / 1e9
+    # edges of the graphs still iterating, summed over the iterations, all ranks
+    ms, visits = combine_ranks(dist, dev, ev0.elapsed_time(ev1),
+                               sum(float((nnz_g * its).sum()) for _, _, _, its in runs))
+    value = visits / (ms * 1e-3) / 1e9
     iters = sum(info.iterations for _, info, _, _ in runs)
     loop_ms = sum(info.ms_loop for _, info, _, _ in runs)
     b_iter = algorithmic_bytes(n, nnz, st["rowptr_bytes"])
@@ -603,7 +609,7 @@ def run_set(args):
     for _ in range(max(1, args.e2e_steps)):
         _, _, _, its_e = g.solve_set(tol=TOL, max_iter=MAX_ITER, out=out_pin)
         e2e_visits += float((nnz_g * its_e).sum())
-    e2e_s = time.perf_counter() - t0
+    e2e_s, e2e_visits = combine_ranks(dist, dev, time.perf_counter() - t0, e2e_visits)
     g.close()
     if rank == 0:
         line = {"metric": "PageRank of 64 graphs in one solve: GTEPS (edges of iterating graphs "
@@ -621,7 +627,7 @@ def run_set(args):
                              "peak_source": f"{peak_kind} hbm_gbs"},
                 "vs_one_graph_at_a_time": {"set_ms": ms / args.steps, "single_ms_total": single_ms,
                                            "speedup": single_ms / (ms / args.steps)},
-                "e2e": {"value": world * e2e_visits / e2e_s / 1e9, "unit": "GTEPS",
+                "e2e": {"value": e2e_visits / e2e_s / 1e9, "unit": "GTEPS",
                         "h2d_bytes_per_step": 0, "d2h_bytes_per_step": n * 4,
                         "ms_per_step": e2e_s * 1e3 / max(1, args.e2e_steps)},
                 "clocks": clocks}
@@ -683,13 +689,9 @@ def run_adjoint(args):
     if dist:
         dist.barrier()
     clocks = sampler.stop() if sampler else None
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    visits = sum(fi.edge_visits + ai.edge_visits for fi, ai in runs)
-    value = world * visits / (ms * 1e-3) / 1e9
+    ms, visits = combine_ranks(dist, dev, ev0.elapsed_time(ev1),
+                               sum(fi.edge_visits + ai.edge_visits for fi, ai in runs))
+    value = visits / (ms * 1e-3) / 1e9
     fi, ai = runs[-1]
     # one weighted iteration moves colidx + P + the gathered value per edge, 8 B row offsets
     b_iter = 12 * nnz + 8 * (n + 1) + 16 * n
@@ -719,7 +721,7 @@ def run_adjoint(args):
         _, fi2 = g.solve(DAMPING, TOL, MAX_ITER, out=x_pin)
         _, _, ai2 = g.adjoint(x_pin, c_pin, DAMPING, TOL, 1000, grad_teleport=gt_pin, grad_weights=gw_pin)
         e2e_visits += fi2.edge_visits + ai2.edge_visits
-    e2e_s = time.perf_counter() - t0
+    e2e_s, e2e_visits = combine_ranks(dist, dev, time.perf_counter() - t0, e2e_visits)
     g.close()
     if rank == 0:
         line = {"metric": "weighted PageRank forward + adjoint gradients: GTEPS (edges gathered "
@@ -741,7 +743,7 @@ def run_adjoint(args):
                              "peak_source": f"{peak_kind} hbm_gbs"},
                 "vs_plain_jacobi": {"plain_ms": plain_ms, "plain_iterations": pinfo.iterations,
                                     "forward_plus_adjoint_ms": ms / args.steps},
-                "e2e": {"value": world * e2e_visits / e2e_s / 1e9, "unit": "GTEPS",
+                "e2e": {"value": e2e_visits / e2e_s / 1e9, "unit": "GTEPS",
                         "h2d_bytes_per_step": 2 * n * 4, "d2h_bytes_per_step": (2 * n + nnz) * 4,
                         "ms_per_step": e2e_s * 1e3 / max(1, args.e2e_steps)},
                 "clocks": clocks}
@@ -854,14 +856,7 @@ def main():
     if dist:
         dist.barrier()
     clocks = sampler.stop() if sampler else None
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        vt = torch.tensor([visits], dtype=torch.float64, device=dev)
-        dist.all_reduce(vt, op=dist.ReduceOp.SUM)
-        visits = float(vt.item())
+    ms, visits = combine_ranks(dist, dev, ev0.elapsed_time(ev1), visits)
     value = visits / (ms * 1e-3) / 1e9
 
     roofline, roofline_all = rooflines(records, resident)
@@ -909,14 +904,7 @@ def main():
     for _ in range(args.e2e_steps):
         ev += e2e_step()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-        vt = torch.tensor([ev], dtype=torch.float64, device=dev)
-        dist.all_reduce(vt, op=dist.ReduceOp.SUM)
-        ev = float(vt.item())
+    e2e_s, ev = combine_ranks(dist, dev, time.perf_counter() - t0, ev)
     e2e = {"value": ev / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
            "ms_per_step": e2e_s * 1e3 / args.e2e_steps,

@@ -1,0 +1,67 @@
+"""The benchmark's multi-process path on CPU: two gloo ranks on 127.0.0.1.
+
+Every rank times its own replica; the job's figures are the slowest rank's time and the
+work of all ranks (bench.combine_ranks), which both ranks must receive.  Under torchrun the
+reference arm runs on rank 0 alone: the other ranks return at once, printing nothing."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank_main(rank, world, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ms, work = bench.combine_ranks(dist, "cpu", 10.0 + rank, 100.0 * (rank + 1))
+        with open(os.path.join(out_dir, f"r{rank}.json"), "w") as f:
+            json.dump({"ms": ms, "work": work}, f)
+        assert bench.dist_env() == (rank, 0, world)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_combine_ranks_over_two_gloo_ranks(tmp_path):
+    port = free_port()
+    mp.start_processes(_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True,
+                       start_method="spawn")
+    for r in range(2):
+        got = json.load(open(tmp_path / f"r{r}.json"))
+        assert got == {"ms": 11.0, "work": 300.0}
+
+
+def test_combine_ranks_single_process():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.combine_ranks(None, "cpu", 3.5, 7.0) == (3.5, 7.0)
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    """rank 1 of a two-process job exits 0 at once and prints nothing (no oracle work)."""
+    env = dict(os.environ, RANK="1", LOCAL_RANK="1", WORLD_SIZE="2", MASTER_ADDR="127.0.0.1",
+               MASTER_PORT=str(free_port()))
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--gpus", "2", "--steps", "1", "--warmup", "3"],
+                       capture_output=True, text=True, env=env, timeout=120)
+    assert r.returncode == 0
+    assert r.stdout.strip() == ""
