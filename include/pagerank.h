@@ -113,6 +113,8 @@ typedef struct pr_graph_stats {
     int32_t sm_count;
     int64_t device_bytes;  /* device memory owned by the graph                 */
     float setup_ms;        /* device time of pr_create_graph's kernels         */
+    int64_t n_tma_tiles;   /* tiles of the pipelined synchronous row kernel (0:
+                              the layout cannot use it; see PR_OPT_TMA_TILES)   */
 } pr_graph_stats;
 
 /* Build a graph on the current device.
@@ -173,9 +175,12 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
 /* Tuning knobs, mostly for tests that force one code path at a time.
  *   PR_OPT_HEAVY_DEGREE   rows with in-degree >= value are gathered in
  *                         segments (a power of two in [64, 4096]; default
- *                         1024).  Takes effect at the next pr_create_graph
+ *                         256).  Takes effect at the next pr_create_graph
  *                         of the same thread (it changes the layout), so it
- *                         is a thread-local default, set with g = NULL.
+ *                         is a thread-local default, set with g = NULL.  The
+ *                         barrier-free kernel gathers in segments only the
+ *                         rows of in-degree >= max(value, 1024) and works
+ *                         the others as light rows.
  *   PR_OPT_USE_GRAPH      1 (default): the Jacobi loop runs as one CUDA
  *                         graph with a conditional while node; 0: the host
  *                         enqueues iterations in chunks.
@@ -248,6 +253,15 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
  *                         this many nanoseconds (0..1e6, __nanosleep, bounded)
  *                         before taking each tile -- a slowed processor, as
  *                         in the paper's delayed-thread experiments.  0 = off.
+ *   PR_OPT_TMA_TILES      synchronous solver: 1 (default) runs the pipelined
+ *                         row kernel where it applies (32-bit row offsets,
+ *                         heavy threshold <= 2048, static tile order, no
+ *                         perforation, staging or shared-memory copy of y):
+ *                         a producer warp copies each tile's offsets, column
+ *                         indices and per-row vectors into shared memory with
+ *                         bulk asynchronous copies ahead of the gathering
+ *                         warps.  0 = the row-by-row kernel that loads them
+ *                         itself.  Same arithmetic either way.
  *   PR_OPT_INDEX64        1: keep 64-bit row offsets on the device even when
  *                         the edge count fits 32 bits (thread-local default
  *                         for the next pr_create_graph, set with g = NULL;
@@ -266,6 +280,7 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
 #define PR_OPT_PERFORATION 11
 #define PR_OPT_DYNAMIC_TILES 12
 #define PR_OPT_DELAY_NS 13
+#define PR_OPT_TMA_TILES 14
 PR_API pr_status pr_set_option(pr_graph* g, int key, int64_t value);
 
 /* Batched personalised PageRank: k independent solves on one graph, one per

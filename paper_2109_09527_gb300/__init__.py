@@ -51,6 +51,7 @@ PR_OPT_BATCH_BF16 = 10
 PR_OPT_PERFORATION = 11
 PR_OPT_DYNAMIC_TILES = 12
 PR_OPT_DELAY_NS = 13
+PR_OPT_TMA_TILES = 14
 
 LIB_PATH = _build.LIB_PATH
 
@@ -79,7 +80,7 @@ class pr_graph_stats(ctypes.Structure):
                 ("n_segments", ctypes.c_int64), ("n_tiles", ctypes.c_int64),
                 ("max_indeg", ctypes.c_int64), ("rowptr_bytes", ctypes.c_int32),
                 ("sm_count", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
-                ("setup_ms", ctypes.c_float)]
+                ("setup_ms", ctypes.c_float), ("n_tma_tiles", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -356,8 +357,12 @@ class Graph:
         pr_set_option(self.handle, key, value)
 
 
+DEFAULT_HEAVY_DEGREE = 256   # the library's default heavy in-degree threshold
+
+
 def set_heavy_degree(value: int):
-    """Heavy in-degree threshold for graphs created next on this thread (power of two)."""
+    """Heavy in-degree threshold for graphs created next on this thread (power of two;
+    DEFAULT_HEAVY_DEGREE restores the default)."""
     pr_set_option(None, PR_OPT_HEAVY_DEGREE, value)
 
 

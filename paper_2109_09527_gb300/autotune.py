@@ -1,6 +1,6 @@
 """Autotuner for the layout and launch options of a graph.
 
-The library's defaults (heavy-row threshold 1024, 48K L1-cached hub ranks, occupancy-sized
+The library's defaults (heavy-row threshold 256, 48K L1-cached hub ranks, occupancy-sized
 grids) were measured on R-MAT and Erdos-Renyi graphs of 2^24 vertices.  A caller with
 another graph can let `tune` time the synchronous update on that graph under each candidate
 and keep the fastest:
@@ -20,9 +20,10 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import (PR_OPT_CTAS_PER_SM, PR_OPT_HOT_VERTICES, Graph, pr_iterate, set_heavy_degree)
+from . import (DEFAULT_HEAVY_DEGREE, PR_OPT_CTAS_PER_SM, PR_OPT_HOT_VERTICES, Graph, pr_iterate,
+               set_heavy_degree)
 
-HEAVY_CANDIDATES = (256, 512, 1024, 2048, 4096)
+HEAVY_CANDIDATES = (128, 256, 512, 1024, 2048, 4096)
 HOT_CANDIDATES = (16384, 49152, 131072)
 CTAS_CANDIDATES = (0, 2, 3)
 POLICY_L1_HUBS = 4   # see PR_OPT_HOT_VERTICES: hubs through L1, the rest L2-only
@@ -53,7 +54,7 @@ def tune(rowptr, colidx, iterations: int = 6, damping: float = 0.85,
         x = np.full(n, 1.0 / n, dtype=np.float32)
         out = np.empty(n, dtype=np.float32)
     trials = []
-    best = {"heavy_degree": 1024, "hot_vertices": 49152, "ctas_per_sm": 0, "ms_per_iteration": float("inf")}
+    best = {"heavy_degree": DEFAULT_HEAVY_DEGREE, "hot_vertices": 49152, "ctas_per_sm": 0, "ms_per_iteration": float("inf")}
     graphs = {}
     try:
         for h in heavy:
@@ -61,7 +62,7 @@ def tune(rowptr, colidx, iterations: int = 6, damping: float = 0.85,
             try:
                 graphs[h] = Graph(rowptr, colidx)
             finally:
-                set_heavy_degree(1024)
+                set_heavy_degree(DEFAULT_HEAVY_DEGREE)
             ms = _time(graphs[h], x, out, iterations, damping)
             trials.append({"heavy_degree": h, "hot_vertices": 49152, "ctas_per_sm": 0, "ms": ms})
             if ms < best["ms_per_iteration"]:
@@ -101,5 +102,5 @@ def build_tuned(rowptr, colidx, result: dict) -> Graph:
     try:
         g = Graph(rowptr, colidx)
     finally:
-        set_heavy_degree(1024)
+        set_heavy_degree(DEFAULT_HEAVY_DEGREE)
     return apply(g, result)

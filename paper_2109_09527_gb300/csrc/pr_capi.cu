@@ -63,7 +63,7 @@ extern "C" pr_status pr_destroy_graph(pr_graph* g) {
     destroy_set(g);
     void* dev[] = {g->rowptr, g->colidx, g->inv_out, g->order, g->rank, g->x[0], g->x[1],
                    g->y[0], g->y[1], g->teleport, g->stage, g->seg_row, g->seg_ptr, g->seg_sum,
-                   g->tiles, g->state, g->slots, g->nb_items, g->nb_slots,
+                   g->tiles, g->tma_tiles, g->state, g->slots, g->nb_items, g->nb_slots,
                    g->nb_scalars, g->nb_block_sweeps, g->frozen};
     cudaError_t first = cudaSuccess;
     for (void* p : dev)
@@ -100,6 +100,7 @@ extern "C" pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* s) {
     s->sm_count = g->sm_count;
     s->device_bytes = g->device_bytes;
     s->setup_ms = g->setup_ms;
+    s->n_tma_tiles = g->n_tma_tiles;
     return PR_OK;
 }
 
@@ -188,6 +189,11 @@ static pr_status set_option_impl(pr_graph* g, int key, int64_t value) {
             if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_DELAY_NS needs a graph");
             if (value < 0 || value > 1000000) return fail(PR_ERR_INVALID_ARG, "PR_OPT_DELAY_NS must be in [0, 1e6]");
             g->delay_ns = (int)value;
+            return PR_OK;
+        case PR_OPT_TMA_TILES:
+            if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_TMA_TILES needs a graph");
+            if (value != 0 && value != 1) return fail(PR_ERR_INVALID_ARG, "PR_OPT_TMA_TILES is 0 or 1");
+            g->use_tma = (int)value;
             return PR_OK;
         case PR_OPT_INDEX64:
             if (g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_INDEX64 is set with g = NULL (it applies to the next pr_create_graph)");

@@ -53,11 +53,38 @@ constexpr int kHotCacheMax = 40960;      // largest shared-memory copy of y's ho
 constexpr int kTileEdgesMax = 6144;      // edges of a light tile
 constexpr int kTileRowsMax = 2048;       // rows of a light tile
 constexpr int kSegEdges = 2048;          // edges per segment of a heavy row
-constexpr int kDefaultHeavy = 1024;      // default heavy in-degree threshold
+constexpr int kDefaultHeavy = 256;       // default heavy in-degree threshold
+constexpr int kNbSegDegree = 1024;       // rows the barrier-free kernel gathers in segments (see build_items)
 constexpr int kPad = 64;                 // spare elements after every device array
 constexpr int kTileHeavy = -1;           // tile kind: epilogue of heavy rows
 constexpr int kTileZero = -2;            // tile kind: rows without in-edges
 constexpr int kMaxBins = 42;
+
+// Pipelined synchronous row kernel (k_rows_tma): a producer warp copies each
+// tile's offsets, column indices and per-row vectors into shared memory with
+// bulk asynchronous copies, kTmaStages tiles deep, for 8 consumer warps.  Its
+// tiles are the same bins cut to at most kTmaEdges edges and kTmaRows rows.
+#ifndef PRK_TMA_STAGES
+#define PRK_TMA_STAGES 2
+#endif
+#ifndef PRK_TMA_EDGES
+#define PRK_TMA_EDGES 2048
+#endif
+#ifndef PRK_TMA_ROWS
+#define PRK_TMA_ROWS 512
+#endif
+#ifndef PRK_TMA_MIN_BLOCKS
+#define PRK_TMA_MIN_BLOCKS 4
+#endif
+constexpr int kTmaStages = PRK_TMA_STAGES;
+constexpr int kTmaEdges = PRK_TMA_EDGES;
+constexpr int kTmaRows = PRK_TMA_ROWS;
+constexpr int kTmaMinBlocks = PRK_TMA_MIN_BLOCKS;
+constexpr int kTmaColWords = kTmaEdges + 8;    // a copy starts up to 3 words early and ends up to 3 late
+constexpr int kTmaRowWords = kTmaRows + 8;     // rows + 1 offsets, same slack
+constexpr int kTmaStageWords = kTmaColWords + 4 * kTmaRowWords;   // colidx, rowptr, x, 1/outdeg, teleport
+constexpr int kTmaThreads = kBlock + 32;       // 8 consumer warps + 1 producer warp
+constexpr size_t kTmaSmemBytes = 2 * kTmaStages * sizeof(uint64_t) + (size_t)kTmaStages * kTmaStageWords * 4;
 #ifndef PRK_DEFAULT_STAGED
 #define PRK_DEFAULT_STAGED 0
 #endif
@@ -127,6 +154,7 @@ struct IterArgs {
     int32_t dynamic;             // 1: blocks take tiles from a shared counter (helping)
     int32_t delay_ns;            // > 0: block 0 sleeps this long per tile (slow-processor model)
     int32_t pad3;
+    int64_t nnz;
 };
 
 }  // namespace prk
@@ -151,6 +179,7 @@ struct pr_graph {
     int delay_ns = 0;                         // PR_OPT_DELAY_NS
     uint8_t* frozen = nullptr;                // frozen rows of the perforated synchronous solve
     int staged_tiles = prk::kDefaultStaged;   // bit 0: Jacobi, bit 1: barrier-free (see PR_OPT_STAGED_TILES)
+    int use_tma = 1;                          // PR_OPT_TMA_TILES: pipelined synchronous row kernel
 
     void* rowptr = nullptr;
     int32_t* colidx = nullptr;
@@ -165,6 +194,8 @@ struct pr_graph {
     int32_t* seg_ptr = nullptr;
     float* seg_sum = nullptr;
     prk::Tile* tiles = nullptr;
+    prk::Tile* tma_tiles = nullptr;  // tiles of k_rows_tma (pad = first edge), + a sentinel at n
+    int64_t n_tma_tiles = 0;         // 0: the layout cannot use k_rows_tma
     prk::SolveState* state = nullptr;
     double* slots = nullptr;
     int slot_capacity = 0;       // blocks the slot array can serve
@@ -178,6 +209,7 @@ struct pr_graph {
     int32_t* nb_block_sweeps = nullptr;  // sweeps per block of the last launch (+ diagnostics)
     int nb_grid = 0;
     int64_t nb_items_count = 0;
+    int64_t nb_n_seg = 0;                // segments the barrier-free kernel gathers (the first ones)
     std::vector<int64_t> nb_cta_edges;  // edges owned by each block (items dealt round-robin)
     std::vector<int64_t> nb_item_edges; // edges of each work item
     std::vector<int64_t> nb_seg_edges;  // edges of each heavy-row segment
@@ -235,6 +267,12 @@ int small_grid(const pr_graph* g);
 cudaError_t enqueue_iteration(const pr_graph* g, const IterArgs& a, int src, bool uniform,
                               cudaStream_t s, int* launches);
 cudaError_t launch_segments(const pr_graph* g, const IterArgs& a, int src, cudaStream_t s, int* launches);
+// Tile list of the layout for another heavy threshold (>= the layout's own),
+// and the number of rows at or above it.
+std::vector<Tile> tiles_with_threshold(const pr_graph* g, int heavy_degree, int64_t* heavy_rows);
+// Set pad = offset of the first edge for tiles[0..count] (the last one a
+// sentinel at row n), 32-bit offsets.
+cudaError_t fill_tile_edges(Tile* tiles, int64_t count, const int32_t* rowptr, cudaStream_t s);
 pr_status stage_input(pr_graph* g, const float* src, int slot, cudaStream_t s, const float** out);
 pr_status ensure_stage(pr_graph* g);
 pr_status ensure_teleport(pr_graph* g);

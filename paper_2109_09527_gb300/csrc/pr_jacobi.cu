@@ -189,6 +189,300 @@ __global__ void __launch_bounds__(kIterBlock, kGatherMinBlocks) k_rows(IterArgs 
     }
 }
 
+// ------------------------------------------------ pipelined row kernel --
+//
+// k_rows_tma computes exactly what k_rows computes, for the configuration
+// the solver runs by default (32-bit offsets, tiles in a fixed round-robin
+// order, no perforation, no shared-memory copy of y).  In k_rows a row group
+// waits on three memory latencies per pair of rows: the row offsets, then the
+// column indices, then the gathers.  Here a producer warp moves every tile's
+// offsets, column indices and per-row vectors (x, 1/outdeg, teleport) into
+// shared memory with bulk asynchronous copies (cp.async.bulk, completion
+// counted in bytes on an mbarrier), kTmaStages tiles ahead of the 8 consumer
+// warps, so that the only latency a row group still waits on is its gathers.
+// Each stage has a "full" barrier (the producer's expect-tx arrival + the
+// copies' bytes) and an "empty" barrier (one arrival per consumer warp when it
+// is done with the stage).  Every wait is bounded: a wait that runs out sets
+// error bit 2 and the solve reports PR_ERR_DEVICE_TIMEOUT.
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait until the phase of `bar` with this parity has completed; false after
+// about one second (the bound every device-side wait of the library has).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > 1000000000ull) return false;
+    return true;
+}
+
+// Bulk copy of `bytes` (a multiple of 16) from global to this block's shared
+// memory, both addresses 16-byte aligned, completing on `bar`.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// Shared-memory stage of one tile: colidx, then rowptr, x, 1/outdeg and
+// teleport, each copied from its 16-byte aligned start at or before the
+// tile's first element.
+struct TmaStage {
+    int32_t* col;
+    int32_t* rp;
+    float* x;
+    float* inv;
+    float* tel;
+    __device__ __forceinline__ TmaStage(uint32_t* base, int s) {
+        uint32_t* p = base + (size_t)s * kTmaStageWords;
+        col = (int32_t*)p;
+        rp = (int32_t*)(p + kTmaColWords);
+        x = (float*)(p + kTmaColWords + kTmaRowWords);
+        inv = (float*)(p + kTmaColWords + 2 * kTmaRowWords);
+        tel = (float*)(p + kTmaColWords + 3 * kTmaRowWords);
+    }
+};
+
+// Producer side: copies of tile `t` into stage st, arrival with the bytes.
+template <bool kUniform>
+__device__ __forceinline__ void tma_issue(const IterArgs& a, const Tile& tile, int64_t e0, int64_t e1,
+                                          const float* x_in, TmaStage st, uint64_t* full) {
+    const int64_t r0 = tile.row_begin & ~3, r1 = (tile.row_end + 3) & ~3;
+    const uint32_t vec_bytes = (uint32_t)(r1 - r0) * 4u;
+    uint32_t bytes = (kUniform ? 2u : 3u) * vec_bytes;
+    int64_t c0 = 0, p1 = 0;
+    uint32_t col_bytes = 0, rp_bytes = 0;
+    if (tile.kind >= 0) {
+        c0 = e0 & ~(int64_t)3;
+        col_bytes = (uint32_t)((((e1 + 3) & ~(int64_t)3) - c0) * 4);
+        p1 = (tile.row_end + 1 + 3) & ~3;
+        rp_bytes = (uint32_t)(p1 - r0) * 4u;
+        bytes += col_bytes + rp_bytes;
+    }
+    if (vec_bytes > kTmaRowWords * 4u || col_bytes > kTmaColWords * 4u || rp_bytes > kTmaRowWords * 4u) {
+        // a tile larger than a stage (the tiling at set-up rules this out):
+        // copy nothing, complete the phase, flag the solve
+        atomicOr(&a.state->error, 4u);
+        mbar_arrive_expect_tx(full, 0);
+        return;
+    }
+    mbar_arrive_expect_tx(full, bytes);
+    bulk_copy_g2s(st.x, x_in + r0, vec_bytes, full);
+    bulk_copy_g2s(st.inv, a.inv_out + r0, vec_bytes, full);
+    if (!kUniform) bulk_copy_g2s(st.tel, a.teleport + r0, vec_bytes, full);
+    if (tile.kind >= 0) {
+        if (col_bytes) bulk_copy_g2s(st.col, a.colidx + c0, col_bytes, full);
+        bulk_copy_g2s(st.rp, (const int32_t*)a.rowptr + r0, rp_bytes, full);
+    }
+}
+
+// Consumer side: one light tile from its stage (same groups, passes and
+// update as process_light_tile).
+template <bool kUniform>
+__device__ __forceinline__ void tma_light_tile(const Tile& tile, const TmaStage& st, const float* y_in,
+                                               float* x_out, float* y_out, const RowCtx& c, Acc& acc, int tid) {
+    const int lg = tile.kind;
+    const int g = 1 << lg;
+    const int rpp = kBlock >> lg;
+    const int grp = tid >> lg;
+    const int gl = tid & (g - 1);
+    const int o = tile.row_begin & 3;                  // row i of the tile is element o + i
+    const int32_t* rp = st.rp + o;
+    const int32_t base = rp[0] & ~3;                  // st.col[e - base] = colidx[e]
+    const int nrows = tile.row_end - tile.row_begin;
+    for (int i0 = 0; i0 < nrows; i0 += 2 * rpp) {
+        int ii[2];
+        bool act[2];
+        int32_t b[2], e[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            ii[q] = i0 + q * rpp + grp;
+            act[q] = ii[q] < nrows;
+            b[q] = act[q] ? rp[ii[q]] - base : 0;
+            e[q] = act[q] ? rp[ii[q] + 1] - base : 0;
+        }
+        float s[2] = {0.f, 0.f};
+        const int32_t len = max(e[0] - b[0], e[1] - b[1]);
+        for (int32_t k = gl; k < len; k += 2 * g) {
+            int32_t cc[2][2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                cc[q][0] = b[q] + k < e[q] ? st.col[b[q] + k] : -1;
+                cc[q][1] = b[q] + k + g < e[q] ? st.col[b[q] + k + g] : -1;
+            }
+            float v[2][2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                v[q][0] = cc[q][0] >= 0 ? Mem<false>::gather(y_in, cc[q][0], c) : 0.f;
+                v[q][1] = cc[q][1] >= 0 ? Mem<false>::gather(y_in, cc[q][1], c) : 0.f;
+            }
+            s[0] += v[0][0] + v[0][1];
+            s[1] += v[1][0] + v[1][1];
+        }
+#pragma unroll
+        for (int m = 1; m < 32; m <<= 1)
+            if (m < g) {
+                s[0] += __shfl_xor_sync(0xffffffffu, s[0], m);
+                s[1] += __shfl_xor_sync(0xffffffffu, s[1], m);
+            }
+        if (gl == 0) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+                if (act[q]) {
+                    const int i = o + ii[q];
+                    row_update<kUniform, false>(tile.row_begin + ii[q], s[q], st.x[i], st.inv[i],
+                                                kUniform ? 0.f : st.tel[i], c, x_out, y_out, acc);
+                }
+        }
+    }
+}
+
+template <bool kUniform>
+__global__ void __launch_bounds__(kTmaThreads, kTmaMinBlocks) k_rows_tma(IterArgs a, const float* __restrict__ x_in,
+                                                                      const float* __restrict__ y_in,
+                                                                      float* __restrict__ x_out,
+                                                                      float* __restrict__ y_out) {
+    extern __shared__ __align__(128) uint64_t tma_smem[];
+    uint64_t* full = tma_smem;
+    uint64_t* empty = tma_smem + kTmaStages;
+    uint32_t* stages = (uint32_t*)(tma_smem + 2 * kTmaStages);
+    SolveState* st = a.state;
+    const StateView sv = block_state(st);
+    if (sv.done) {
+        if (a.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTmaStages; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, kWarps);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const double d = sv.d;
+    const double share = sv.D * sv.inv_n;
+    RowCtx c;
+    c.d = (float)d;
+    c.one_m_d = (float)(1.0 - d);
+    c.d_share = (float)(d * share);
+    c.base = (float)((1.0 - d) * sv.inv_n + d * share);
+    c.hot = a.hot;
+    c.hot_n = 0;
+    c.hot_sm = nullptr;
+    Acc acc;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    bool timed_out = false;
+    if (warp == kWarps) {
+        // producer: lane 0 issues the copies of the block's tiles in order
+        if (lane == 0) {
+            int k = 0;
+            for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x, ++k) {
+                const int s = k % kTmaStages;
+                const int use = k / kTmaStages;
+                if (use > 0 && !mbar_wait(empty + s, (uint32_t)(use - 1) & 1u)) {
+                    timed_out = true;
+                    break;
+                }
+                const Tile tile = a.tiles[t];
+                tma_issue<kUniform>(a, tile, a.tiles[t].pad, a.tiles[t + 1].pad, x_in,
+                                    TmaStage(stages, s), full + s);
+            }
+            // let every copy land before the block can exit
+            const int issued = k;
+            for (int s = 0; s < kTmaStages && s < issued; ++s) {
+                const int last = (issued - 1 - s) / kTmaStages;   // last use of stage s
+                if (!mbar_wait(full + s, (uint32_t)last & 1u)) timed_out = true;
+            }
+        }
+    } else {
+        const int tid = threadIdx.x;
+        int k = 0;
+        for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x, ++k) {
+            const int s = k % kTmaStages;
+            if (!mbar_wait(full + s, (uint32_t)(k / kTmaStages) & 1u)) {
+                timed_out = true;
+                break;
+            }
+            const Tile tile = a.tiles[t];
+            const TmaStage stg(stages, s);
+            if (tile.kind >= 0) {
+                tma_light_tile<kUniform>(tile, stg, y_in, x_out, y_out, c, acc, tid);
+            } else {
+                const int o = tile.row_begin & 3;
+                for (int i = tid; i < tile.row_end - tile.row_begin; i += kBlock) {
+                    const int64_t r = tile.row_begin + i;
+                    float sum = 0.f;
+                    if (tile.kind == kTileHeavy) {
+                        const int32_t j1 = a.seg_ptr[r + 1];
+                        for (int32_t j = a.seg_ptr[r]; j < j1; ++j) sum += __ldcg(a.seg_sum + j);
+                    }
+                    row_update<kUniform, false>(r, sum, stg.x[o + i], stg.inv[o + i],
+                                                kUniform ? 0.f : stg.tel[o + i], c, x_out, y_out, acc);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty + s);
+        }
+    }
+    if (timed_out) atomicOr(&st->error, 2u);
+
+    double R, Dn;
+    if (block_pair_to_grid((double)acc.r, acc.mass(), a.slots, &st->ticket, &R, &Dn) && threadIdx.x == 0) {
+        st->resid = R;
+        st->D = Dn;
+        st->iter += 1;
+        const int done = (R < st->tol) || (st->iter >= st->max_iter) || st->error != 0;
+        st->done = done;
+        st->ticket = 0;
+        st->tile_next = 0;
+        if (done && a.use_cond) cudaGraphSetConditional(a.cond, 0);
+    }
+}
+
+// pad of every tile of the pipelined kernel (and of the sentinel after the
+// last) = offset of the tile's first edge.
+__global__ void k_tile_edges(Tile* tiles, int64_t count, const int32_t* __restrict__ rowptr) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= count; i += stride)
+        tiles[i].pad = rowptr[tiles[i].row_begin];
+}
+
 // x = t or x0 (both in the caller's order), y = x/outdeg, D = dangling mass of
 // x, sum(t); resets the running state.
 __global__ void __launch_bounds__(kBlock) k_init(IterArgs a, const float* __restrict__ t_src,
@@ -259,7 +553,27 @@ namespace {
 int g_occ_rows = 0;
 int g_occ_rows_staged = 0;
 int g_occ_seg = 0;
+int g_occ_tma = 0;
 }  // namespace
+
+cudaError_t fill_tile_edges(Tile* tiles, int64_t count, const int32_t* rowptr, cudaStream_t s) {
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((count + kBlock) / kBlock, 1024));
+    k_tile_edges<<<grid, kBlock, 0, s>>>(tiles, count, rowptr);
+    return cudaGetLastError();
+}
+
+// The pipelined row kernel applies to this graph and these options.
+static bool tma_applies(const pr_graph* g, const IterArgs& a) {
+    return g->use_tma && g->n_tma_tiles > 0 && !g->idx64 && !a.frozen && !a.staged && a.hot_n == 0 &&
+           !a.dynamic && a.delay_ns == 0;
+}
+
+static int tma_grid(const pr_graph* g) {
+    int per_sm = g->ctas_per_sm > 0 ? std::min(g->ctas_per_sm, g_occ_tma) : g_occ_tma;
+    int64_t blocks = (int64_t)g->sm_count * std::max(1, per_sm);
+    blocks = std::min<int64_t>(blocks, std::max<int64_t>(1, g->n_tma_tiles));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)g->slot_capacity));
+}
 
 IterArgs make_args(const pr_graph* g, bool uniform) {
     IterArgs a{};
@@ -309,7 +623,14 @@ cudaError_t enqueue_iteration_t(const pr_graph* g, const IterArgs& a, int src, b
     const float* yi = g->y[src];
     float* xo = g->x[1 - src];
     float* yo = g->y[1 - src];
-    if (a.frozen) {   // loop perforation (row-by-row tiles only)
+    if (sizeof(IdxT) == 4 && tma_applies(g, a)) {
+        IterArgs at = a;
+        at.tiles = g->tma_tiles;
+        at.n_tiles = (int32_t)g->n_tma_tiles;
+        const int tg = tma_grid(g);
+        if (uniform) k_rows_tma<true><<<tg, kTmaThreads, kTmaSmemBytes, s>>>(at, xi, yi, xo, yo);
+        else k_rows_tma<false><<<tg, kTmaThreads, kTmaSmemBytes, s>>>(at, xi, yi, xo, yo);
+    } else if (a.frozen) {   // loop perforation (row-by-row tiles only)
         if (uniform) k_rows<IdxT, true, false, true><<<grid, kIterBlock, hot, s>>>(a, xi, yi, xo, yo);
         else k_rows<IdxT, false, false, true><<<grid, kIterBlock, hot, s>>>(a, xi, yi, xo, yo);
     } else if (a.staged) {
@@ -480,6 +801,19 @@ pr_status alloc_solver(pr_graph* g) {
                                                                  kStageFloats * sizeof(float)));
         g_occ_rows_staged = std::max(1, occ);
         PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rows<int32_t, false, false, false>, kIterBlock, 0));
+        // the pipelined kernel: shared memory for kTmaMinBlocks blocks of
+        // kTmaSmemBytes each (plus the 1 KB the driver reserves per block),
+        // the rest of the SRAM to L1
+        const void* tma_kernels[] = {(const void*)k_rows_tma<true>, (const void*)k_rows_tma<false>};
+        const int carve = (int)std::min<int64_t>(
+            100, (int64_t)(kTmaMinBlocks * (kTmaSmemBytes + 1024) * 100 + 228 * 1024 - 1) / (228 * 1024));
+        for (const void* k : tma_kernels) {
+            PRK_CHECK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmemBytes));
+            PRK_CHECK(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, carve));
+        }
+        int occ_tma = 0;
+        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_tma, k_rows_tma<false>, kTmaThreads, kTmaSmemBytes));
+        g_occ_tma = std::max(1, occ_tma);
         int occ_seg = 0;
         PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_seg, k_heavy_segments<int32_t>, kIterBlock, 0));
         g_occ_seg = std::max(1, occ_seg);
@@ -587,6 +921,8 @@ pr_status run_jacobi(pr_graph* g, float damping, double tol, int32_t max_iter, c
         PRK_CHECK(cudaMemcpyAsync(x_out, out, (size_t)g->n * sizeof(float), cudaMemcpyDeviceToHost, s));
     PRK_CHECK(cudaMemcpyAsync(hs, g->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
     PRK_CHECK(cudaStreamSynchronize(s));
+    if (hs->error & 2u)
+        return fail(PR_ERR_DEVICE_TIMEOUT, "a bounded device-side wait for a tile copy gave up");
     if (hs->error)
         return fail(PR_ERR_CUDA, "internal error: a row tile exceeded its shared-memory staging area");
     float ms = 0.f, ms_loop = 0.f;

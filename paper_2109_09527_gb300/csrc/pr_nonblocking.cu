@@ -57,6 +57,13 @@ namespace prk {
 #ifndef PRK_NB_HUB_REFRESH
 #define PRK_NB_HUB_REFRESH 4
 #endif
+// 1: a heavy row is updated from its segments' partial sums by the block that
+// owns its row tile (thread per row, like the synchronous kernels); 0: by the
+// warp that gathers the row's last segment, right after it.
+#ifndef PRK_NB_HEAVY_TILES
+#define PRK_NB_HEAVY_TILES 0
+#endif
+constexpr bool kNbHeavyTiles = PRK_NB_HEAVY_TILES != 0;
 constexpr int kPublishEvery = PRK_NB_PUBLISH_EVERY;
 constexpr int kSegPublish = PRK_NB_SEG_PUBLISH;
 constexpr int kHubRefresh = PRK_NB_HUB_REFRESH;
@@ -142,7 +149,7 @@ __device__ __forceinline__ void warp_segment(int64_t sid, const NbArgs& a, const
     }
     v = warp_sum(v);
     if (lane == 0) st_relaxed(a.seg_sum + sid, v);
-    if (sid + 1 == s1) {
+    if (!kNbHeavyTiles && sid + 1 == s1) {
         float p = 0.f;
         for (int32_t j = s0 + lane; j < s1; j += 32) p += (j == sid) ? v : ld_relaxed(a.seg_sum + j);
         p = warp_sum(p);
@@ -154,7 +161,10 @@ __device__ __forceinline__ void warp_segment(int64_t sid, const NbArgs& a, const
     }
 }
 
-template <typename IdxT, bool kUniform, bool kStaged>
+// kTrace: the diagnostics form, which records the per-block timeline and
+// block 0's sweep history (NbArgs::trace, NbArgs::history); the production
+// form carries none of that state.
+template <typename IdxT, bool kUniform, bool kStaged, bool kTrace>
 __global__ void __launch_bounds__(kNbBlock, kNbMinBlocks) k_nonblocking(NbArgs a) {
     // dynamic shared memory: the hub snapshot (hub_n floats), then the staging
     // area of kStaged tiles (kStageFloats floats)
@@ -173,7 +183,7 @@ __global__ void __launch_bounds__(kNbBlock, kNbMinBlocks) k_nonblocking(NbArgs a
     const int64_t wstep = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int32_t sweeps = 0;
     long long t_start = 0;
-    if (a.trace && threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
+    if (kTrace && threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
     double last_R = 0.0, last_est = 0.0;
     long long seg_ns = 0;
     Acc acc;
@@ -221,7 +231,7 @@ __global__ void __launch_bounds__(kNbBlock, kNbMinBlocks) k_nonblocking(NbArgs a
         };
         warp_publish(false);
         long long t_seg0 = 0;
-        if (a.trace && threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_seg0));
+        if (kTrace && threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_seg0));
         // heavy-row segments, a warp each, in rounds of one segment per warp of
         // the grid (the same round count in every block, so the hub snapshot
         // can be refreshed between rounds)
@@ -234,7 +244,7 @@ __global__ void __launch_bounds__(kNbBlock, kNbMinBlocks) k_nonblocking(NbArgs a
             if (a.hub_n && (rd % kHubRefresh) == kHubRefresh - 1) refresh_hubs(a.y, hub_sm, a.hub_n);
         }
         warp_publish(true);
-        if (a.trace) {
+        if (kTrace) {
             __syncthreads();   // diagnostics only: time the segment phase of the whole block
             if (threadIdx.x == 0) {
                 long long t_seg1;
@@ -253,10 +263,21 @@ __global__ void __launch_bounds__(kNbBlock, kNbMinBlocks) k_nonblocking(NbArgs a
                                                                nb_stage) &&
                     threadIdx.x == 0)
                     atomicOr(&a.state->error, 1u);
-            } else if (item.kind >= 0)
+            } else if (item.kind >= 0) {
                 process_light_tile<IdxT, kUniform, true>(item, a.rowptr, a.colidx, a.inv_out, a.teleport,
                                                           xr, a.y, xw, a.y, c, acc, tid);
-            else
+            } else if (item.kind == kTileHeavy) {
+                // heavy rows: the latest partial sums of their segments (this
+                // sweep's, or the previous one's where a segment is not done yet)
+                for (int64_t r = item.row_begin + tid; r < item.row_end; r += kBlock) {
+                    const int32_t j1 = a.seg_ptr[r + 1];
+                    float p = 0.f;
+                    for (int32_t j = a.seg_ptr[r]; j < j1; ++j) p += ld_relaxed(a.seg_sum + j);
+                    const float tv = kUniform ? 0.f : ld_stream(a.teleport + r);
+                    row_update<kUniform, true>(r, p, Mem<true>::load_x(xr + r), ld_stream(a.inv_out + r), tv, c,
+                                               xw, a.y, acc);
+                }
+            } else
                 process_zero_tile<kUniform, true>(item, a.inv_out, a.teleport, xr, xw, a.y, c, acc, tid);
             if (++since == kPublishEvery) {
                 warp_publish(true);
@@ -270,13 +291,15 @@ __global__ void __launch_bounds__(kNbBlock, kNbMinBlocks) k_nonblocking(NbArgs a
         block_sum2(R, unused1);
         if (threadIdx.x == 0) {
             st_relaxed(a.slots + blockIdx.x, R);
-            if (a.history && blockIdx.x == 0 && sweeps <= 256) a.history[sweeps - 1] = (float)R;
+            if (kTrace && blockIdx.x == 0 && sweeps <= 256) a.history[sweeps - 1] = (float)R;
         }
         double est = 0.0, unused = 0.0;
         for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) est += ld_relaxed(a.slots + i);
         block_sum2(est, unused);
-        last_R = R;
-        last_est = est;
+        if (kTrace) {
+            last_R = R;
+            last_est = est;
+        }
         if (est < a.tol_int) break;
     }
     // After an odd number of sweeps the block's latest ranks are in x_alt:
@@ -289,13 +312,13 @@ __global__ void __launch_bounds__(kNbBlock, kNbMinBlocks) k_nonblocking(NbArgs a
             for (int64_t r = item.row_begin + tid; r < item.row_end; r += kBlock)
                 st_relaxed(a.x + r, ld_relaxed(a.x_alt + r));
         }
-        if ((threadIdx.x & 31) == 0)
+        if (!kNbHeavyTiles && (threadIdx.x & 31) == 0)
             for (int64_t sid = wid; sid < a.n_seg; sid += wstep) {
                 const int32_t h = a.seg_row[sid];
                 if (sid + 1 == a.seg_ptr[h + 1]) st_relaxed(a.x + h, ld_relaxed(a.x_alt + h));
             }
     }
-    if (a.trace && threadIdx.x == 0) {
+    if (kTrace && threadIdx.x == 0) {
         // per block: sweeps, start/end (ns, %globaltimer), last sweep change, last estimate,
         // first item, tile count, ns spent in the segment phase
         long long t_end;
@@ -350,19 +373,22 @@ __global__ void k_item_edges(const void* rowptr, const Tile* items, int64_t coun
 
 namespace {
 
-template <typename IdxT, bool kUniform, bool kStaged>
+template <typename IdxT, bool kUniform, bool kStaged, bool kTrace>
 void* nb_kernel() {
-    return (void*)k_nonblocking<IdxT, kUniform, kStaged>;
+    return (void*)k_nonblocking<IdxT, kUniform, kStaged, kTrace>;
 }
 
+// The traced (diagnostics) form exists without staged tiles only.
 template <typename IdxT>
-void* pick_kernel_t(bool uniform, bool staged) {
-    if (staged) return uniform ? nb_kernel<IdxT, true, true>() : nb_kernel<IdxT, false, true>();
-    return uniform ? nb_kernel<IdxT, true, false>() : nb_kernel<IdxT, false, false>();
+void* pick_kernel_t(bool uniform, bool staged, bool trace) {
+    if (trace) return uniform ? nb_kernel<IdxT, true, false, true>() : nb_kernel<IdxT, false, false, true>();
+    if (staged) return uniform ? nb_kernel<IdxT, true, true, false>() : nb_kernel<IdxT, false, true, false>();
+    return uniform ? nb_kernel<IdxT, true, false, false>() : nb_kernel<IdxT, false, false, false>();
 }
 
-void* pick_kernel(const pr_graph* g, bool uniform, bool staged) {
-    return g->idx64 ? pick_kernel_t<int64_t>(uniform, staged) : pick_kernel_t<int32_t>(uniform, staged);
+void* pick_kernel(const pr_graph* g, bool uniform, bool staged, bool trace) {
+    return g->idx64 ? pick_kernel_t<int64_t>(uniform, staged, trace)
+                    : pick_kernel_t<int32_t>(uniform, staged, trace);
 }
 
 // Blocks of `kernel` that fit on one SM with `smem` bytes of dynamic shared
@@ -394,9 +420,16 @@ pr_status nb_occupancy(const void* kernel, size_t smem, int* occ) {
 }
 
 // Work items (light and empty row tiles; heavy rows are worked as segments)
-// and the edges of each item and segment, built on first use.
+// and the edges of each item and segment, built on first use.  The kernel
+// gathers in segments only the rows of in-degree >= kNbSegDegree (or the
+// layout's heavy threshold, if higher): a row just above a lower threshold is
+// a single short segment, whose gather and update by one warp cost more per
+// sweep than the same row in a light tile.  Those rows are the first rows of
+// the layout, so their segments are the first nb_n_seg segments.
 pr_status build_items(pr_graph* g, cudaStream_t s) {
     if (g->nb_items) return PR_OK;
+    int64_t nb_heavy_rows = 0;
+    const std::vector<Tile> tiles = tiles_with_threshold(g, std::max(g->heavy_degree, kNbSegDegree), &nb_heavy_rows);
     std::vector<int32_t> seg_ptr((size_t)g->n_heavy + 1, 0);
     std::vector<int64_t> heavy_rp((size_t)g->n_heavy + 1, 0);
     if (g->n_heavy > 0) {
@@ -409,9 +442,10 @@ pr_status build_items(pr_graph* g, cudaStream_t s) {
             for (size_t i = 0; i < tmp.size(); ++i) heavy_rp[i] = tmp[i];
         }
     }
+    g->nb_n_seg = nb_heavy_rows > 0 ? seg_ptr[(size_t)nb_heavy_rows] : 0;
     std::vector<Tile> items;
-    for (const Tile& t : g->host_tiles)
-        if (t.kind != kTileHeavy) items.push_back(t);
+    for (const Tile& t : tiles)
+        if (kNbHeavyTiles || t.kind != kTileHeavy) items.push_back(t);
     const int64_t count = (int64_t)items.size();
 
     Tile* d_items = nullptr;
@@ -430,8 +464,12 @@ pr_status build_items(pr_graph* g, cudaStream_t s) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(d_edges);
     PRK_CHECK(e);
-    g->nb_seg_edges.assign((size_t)g->n_seg, 0);
-    for (int64_t h = 0; h < g->n_heavy; ++h)
+    // a heavy-row tile gathers nothing itself (its rows' edges are counted
+    // with their segments)
+    for (int64_t i = 0; i < count; ++i)
+        if (items[(size_t)i].kind == kTileHeavy) g->nb_item_edges[(size_t)i] = 0;
+    g->nb_seg_edges.assign((size_t)g->nb_n_seg, 0);
+    for (int64_t h = 0; h < nb_heavy_rows; ++h)
         for (int32_t sg = seg_ptr[h]; sg < seg_ptr[h + 1]; ++sg) {
             const int64_t e0 = heavy_rp[h] + (int64_t)(sg - seg_ptr[h]) * kSegEdges;
             g->nb_seg_edges[sg] = std::min<int64_t>(kSegEdges, heavy_rp[h + 1] - e0);
@@ -453,12 +491,12 @@ void nb_partition(pr_graph* g, int per_sm) {
     per_sm = std::min(per_sm, 8);
     const int groups = kNbBlock / kBlock, warps = kNbBlock / 32;
     const int64_t count = g->nb_items_count;
-    const int64_t work = std::max<int64_t>((count + groups - 1) / groups, (g->n_seg + warps - 1) / warps);
+    const int64_t work = std::max<int64_t>((count + groups - 1) / groups, (g->nb_n_seg + warps - 1) / warps);
     const int G = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * per_sm, work));
     if (G == g->nb_grid) return;
     g->nb_cta_edges.assign((size_t)G, 0);
     for (int64_t i = 0; i < count; ++i) g->nb_cta_edges[(i % ((int64_t)G * groups)) / groups] += g->nb_item_edges[i];
-    for (int64_t sg = 0; sg < g->n_seg; ++sg) g->nb_cta_edges[(sg % ((int64_t)G * warps)) / warps] += g->nb_seg_edges[sg];
+    for (int64_t sg = 0; sg < g->nb_n_seg; ++sg) g->nb_cta_edges[(sg % ((int64_t)G * warps)) / warps] += g->nb_seg_edges[sg];
     g->nb_grid = G;
 }
 
@@ -478,10 +516,14 @@ pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_
     if (!uniform && (rc = ensure_teleport(g)) != PR_OK) return rc;
     const bool out_dev = is_device_pointer(x_out);
     float* out = out_dev ? x_out : g->stage + (size_t)2 * (size_t)(g->n + kPad);
-    const bool staged = (g->staged_tiles >> 1) & 1;
+    // Opt-in diagnostics: PR_TRACE_NB=<file> runs the traced form of the kernel
+    // and appends one CSV line per block and launch.
+    const char* trace_path = getenv("PR_TRACE_NB");
+    const bool trace = trace_path && *trace_path;
+    const bool staged = !trace && ((g->staged_tiles >> 1) & 1);
     const int32_t hub_n = (int32_t)(std::min<int64_t>(g->nb_hubs, g->n) & ~(int64_t)3);
     const size_t nb_smem = ((size_t)hub_n + (staged ? (size_t)kStageFloats : 0)) * sizeof(float);
-    void* kernel = pick_kernel(g, uniform, staged);
+    void* kernel = pick_kernel(g, uniform, staged, trace);
     int per_sm = 1;
     if ((rc = nb_occupancy(kernel, nb_smem, &per_sm)) != PR_OK) return rc;
     nb_partition(g, per_sm);
@@ -524,7 +566,7 @@ pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_
     na.n_items = (int32_t)g->nb_items_count;
     na.seg_ptr = g->seg_ptr;
     na.seg_row = g->seg_row;
-    na.n_seg = g->n_seg;
+    na.n_seg = g->nb_n_seg;
     na.seg_sum = g->seg_sum;
     na.slots = g->nb_slots;
     na.scalars = g->nb_scalars;
@@ -538,10 +580,8 @@ pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_
     na.x = g->x[0];
     na.y = g->y[0];
     na.x_alt = g->x[1];
-    // Opt-in diagnostics: PR_TRACE_NB=<file> appends one CSV line per block and launch.
-    const char* trace_path = getenv("PR_TRACE_NB");
     long long* d_trace = nullptr;
-    if (trace_path && *trace_path) {
+    if (trace) {
         PRK_CHECK(cudaMalloc((void**)&d_trace, (size_t)G * 8 * sizeof(long long)));
         PRK_CHECK(cudaMemsetAsync(d_trace, 0, (size_t)G * 8 * sizeof(long long), s));
     }
@@ -619,6 +659,8 @@ pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_
                 fclose(f);
             }
         }
+        if (hs->error & 2u) return fail(PR_ERR_DEVICE_TIMEOUT, "a bounded device-side wait for a tile copy gave up");
+        if (hs->error) return fail(PR_ERR_CUDA, "internal error in the verifying synchronous update");
         if (hs->resid < tol) { converged = true; break; }
         if (used >= max_iter) break;
         tol_int *= 0.25;

@@ -297,25 +297,28 @@ cudaError_t exclusive_scan(Scratch& s, const int64_t* in, int64_t count, OutT* o
 }
 
 // Host-side tile list from the bin boundaries (bin b holds binned rows
-// [bin_start[b], bin_start[b+1])); lh = log2 of the heavy threshold.
-std::vector<Tile> make_tiles(const std::vector<int64_t>& bin_start, int lh) {
+// [bin_start[b], bin_start[b+1])); lh = log2 of the heavy threshold.  A light
+// tile holds at most max_rows rows and (by its degree class) max_edges edges;
+// heavy-row and empty-row tiles hold heavy_rows and zero_rows rows.
+std::vector<Tile> make_tiles(const std::vector<int64_t>& bin_start, int lh, int64_t max_edges = kTileEdgesMax,
+                             int64_t max_rows = kTileRowsMax, int64_t heavy_rows = 4 * kBlock,
+                             int64_t zero_rows = 16 * kBlock) {
     std::vector<Tile> tiles;
     auto add = [&](int64_t lo, int64_t hi, int64_t rows, int kind) {
         for (int64_t r = lo; r < hi; r += rows)
             tiles.push_back(Tile{(int32_t)r, (int32_t)std::min(hi, r + rows), kind, 0});
     };
     const int first_light = kTopClass + 1 - lh;   // bin of degree class lh-1
-    add(0, bin_start[first_light], 4 * kBlock, kTileHeavy);
+    add(0, bin_start[first_light], heavy_rows, kTileHeavy);
     for (int b = first_light; b <= kTopClass; ++b) {
         const int k = kTopClass - b;             // degree class [2^k, 2^(k+1))
         const int lg = std::min(k, 5);           // lanes per row = 2^lg
         // every row of the class has at most 2^(k+1)-1 edges, so this many rows
         // always fit the shared-memory staging area of a tile
-        const int64_t rows = std::max<int64_t>(
-            1, std::min<int64_t>(kTileRowsMax, kTileEdgesMax / ((1LL << (k + 1)) - 1)));
+        const int64_t rows = std::max<int64_t>(1, std::min<int64_t>(max_rows, max_edges / ((1LL << (k + 1)) - 1)));
         add(bin_start[b], bin_start[b + 1], rows, lg);
     }
-    add(bin_start[kZeroBin], bin_start[kNumBins], 16 * kBlock, kTileZero);
+    add(bin_start[kZeroBin], bin_start[kNumBins], zero_rows, kTileZero);
     return tiles;
 }
 
@@ -422,6 +425,18 @@ pr_status build_layout(pr_graph* g, const RP* rp, const int32_t* ci, cudaStream_
     PRK_CHECK(cudaMemcpyAsync(g->tiles, tiles.data(), tiles.size() * sizeof(Tile),
                               cudaMemcpyHostToDevice, st));
 
+    // tiles of the pipelined row kernel: 32-bit offsets, and every light row
+    // short enough for a shared-memory stage (heavy threshold <= kTmaEdges + 1)
+    g->n_tma_tiles = 0;
+    if (sizeof(IdxT) == 4 && (1LL << lh) <= (int64_t)kTmaEdges + 1) {
+        std::vector<Tile> tt = make_tiles(bin_start, lh, kTmaEdges, kTmaRows, kTmaRows, kTmaRows);
+        tt.push_back(Tile{(int32_t)n, (int32_t)n, kTileZero, 0});   // sentinel: its pad is nnz
+        PRK_CHECK(dev_alloc(g, (void**)&g->tma_tiles, tt.size() * sizeof(Tile)));
+        PRK_CHECK(cudaMemcpyAsync(g->tma_tiles, tt.data(), tt.size() * sizeof(Tile), cudaMemcpyHostToDevice, st));
+        PRK_CHECK(fill_tile_edges(g->tma_tiles, (int64_t)tt.size() - 1, (const int32_t*)g->rowptr, st));
+        g->n_tma_tiles = (int64_t)tt.size() - 1;
+    }
+
     unsigned long long ndang = 0;
     PRK_CHECK(cudaMemcpyAsync(&ndang, dmax + 1, sizeof(ndang), cudaMemcpyDeviceToHost, st));
     PRK_CHECK(cudaStreamSynchronize(st));
@@ -461,6 +476,13 @@ pr_status create_typed(pr_graph* g, const void* rowptr, const int32_t* colidx, c
 }
 
 }  // namespace
+
+std::vector<Tile> tiles_with_threshold(const pr_graph* g, int heavy_degree, int64_t* heavy_rows) {
+    int lh = 0;
+    while ((1LL << lh) < (int64_t)heavy_degree) ++lh;
+    *heavy_rows = g->bin_start[(size_t)(kTopClass + 1 - lh)];
+    return make_tiles(g->bin_start, lh);
+}
 
 cudaError_t scan_counts_i32(const int64_t* counts, int64_t count, int32_t* offsets, cudaStream_t st) {
     Scratch s;

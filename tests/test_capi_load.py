@@ -81,7 +81,7 @@ def test_options_validate_host_side():
         pr.set_heavy_degree(32)           # too small
     with pytest.raises(pr.PageRankError):
         pr.set_heavy_degree(8192)         # light tiles must fit their staging area
-    pr.set_heavy_degree(1024)
+    pr.set_heavy_degree(pr.DEFAULT_HEAVY_DEGREE)
     with pytest.raises(pr.PageRankError):
         pr.pr_set_option(None, 99, 1)
     for key in (pr.PR_OPT_USE_GRAPH, pr.PR_OPT_STAGED_TILES, pr.PR_OPT_NB_HUBS,

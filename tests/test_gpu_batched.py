@@ -56,7 +56,7 @@ def test_seed_teleports_match_oracle(scale, heavy, index64):
     try:
         g = pr.Graph(rp, ci)
     finally:
-        pr.set_heavy_degree(1024)
+        pr.set_heavy_degree(pr.DEFAULT_HEAVY_DEGREE)
         pr.pr_set_option(None, pr.PR_OPT_INDEX64, 0)
     with g:
         x, info, res, its = g.solve_batched(32, t, tol=1e-6, max_iter=300)

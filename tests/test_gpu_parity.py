@@ -85,7 +85,7 @@ def test_rmat_jacobi_matches_oracle(scale, heavy, index64):
     try:
         x, info, st = solve(rp, ci, tol=1e-6, max_iter=200)
     finally:
-        pr.set_heavy_degree(1024)
+        pr.set_heavy_degree(pr.DEFAULT_HEAVY_DEGREE)
         pr.pr_set_option(None, pr.PR_OPT_INDEX64, 0)
     assert st["rowptr_bytes"] == (8 if index64 else 4)
     if heavy == 64:
@@ -151,7 +151,7 @@ def test_one_synchronous_update(scale, heavy):
             xo3, _, _ = oracle.pagerank_jacobi(rp, ci, d=D, tol=0, max_iter=3, x0=x_in)
             assert l1(x3, xo3) <= 1e-6
     finally:
-        pr.set_heavy_degree(1024)
+        pr.set_heavy_degree(pr.DEFAULT_HEAVY_DEGREE)
 
 
 def test_personalised_teleport_and_warm_start():
@@ -212,7 +212,7 @@ def test_nonblocking_reaches_the_fixed_point(build):
             xj, infoj, _ = solve(rp, ci, tol=tol, max_iter=500, variant="jacobi")
             assert l1(x, xj) <= (info.residual_l1 + infoj.residual_l1) / (1 - D) + 4e-7
     finally:
-        pr.set_heavy_degree(1024)
+        pr.set_heavy_degree(pr.DEFAULT_HEAVY_DEGREE)
         pr.pr_set_option(None, pr.PR_OPT_INDEX64, 0)
 
 
@@ -286,7 +286,7 @@ def test_staged_tiles_match_oracle(build):
         g = pr.Graph(rp, ci)
     finally:
         pr.pr_set_option(None, pr.PR_OPT_INDEX64, 0)
-        pr.set_heavy_degree(1024)
+        pr.set_heavy_degree(pr.DEFAULT_HEAVY_DEGREE)
     xstar, _, _ = oracle.fixed_point(rp, ci, d=D)
     with g:
         g.set_option(pr.PR_OPT_STAGED_TILES, 0)
@@ -302,6 +302,74 @@ def test_staged_tiles_match_oracle(build):
         assert infon.converged == 1 and infon.residual_l1 < 1e-6
         assert l1(xn, xstar) <= infon.residual_l1 / (1 - D) + 2e-7
         assert max_rel(xn, xstar) <= 1e-4
+
+
+@pytest.mark.parametrize("build", ["rmat14", "rmat12_heavy64", "rmat13_heavy2048", "er", "small"])
+def test_pipelined_row_kernel_matches_row_kernel_and_oracle(build):
+    """The pipelined synchronous row kernel (bulk asynchronous copies of each tile into
+    shared memory, PR_OPT_TMA_TILES = 1, the default) against the row-by-row kernel (0)
+    and the oracle: the solve in matching mode, one update with a personalised teleport,
+    and the layouts at the edges of its stage sizes (heavy threshold 2048: single light
+    rows of up to 2047 edges; graphs whose sizes are not multiples of 4)."""
+    heavy = 1024
+    if build == "rmat14":
+        rp, ci = gg.rmat(14, seed=6)
+    elif build == "rmat12_heavy64":
+        rp, ci = gg.rmat(12, seed=7)
+        heavy = 64
+    elif build == "rmat13_heavy2048":
+        rp, ci = gg.rmat(13, seed=9)
+        heavy = 2048
+    elif build == "er":
+        rp, ci = gg.er_dangling(40001, seed=11)
+    else:
+        rp, ci = gg.rmat_n(4099, 8, seed=5)
+    n = rp.size - 1
+    pr.set_heavy_degree(heavy)
+    try:
+        g = pr.Graph(rp, ci)
+    finally:
+        pr.set_heavy_degree(pr.DEFAULT_HEAVY_DEGREE)
+    t = (gg.uniform(3, 7, n) + 0.05).astype(np.float32)
+    t /= t.sum()
+    x_in = (gg.uniform(4, 7, n) + 0.1).astype(np.float32)
+    x_in /= x_in.sum()
+    with g:
+        assert g.stats()["n_tma_tiles"] > 0
+        res = {}
+        for tma in (1, 0):
+            g.set_option(pr.PR_OPT_TMA_TILES, tma)
+            x, info = g.solve(tol=1e-6, max_iter=200, variant="jacobi")
+            x1, info1 = g.iterate(x_in, n_iter=1, teleport=t)
+            res[tma] = (x, info, x1, info1)
+    x, info, x1, info1 = res[1]
+    xr, infor, x1r, info1r = res[0]
+    assert info.converged == 1 and info.iterations == infor.iterations
+    assert max_rel(x, xr) <= 1e-5 and max_rel(x1, x1r) <= 1e-5
+    xo = matching(rp, ci, x, info)
+    assert l1(x, xo) <= 1e-6 and max_rel(x, xo) <= 1e-4
+    xo1, _, l1o, _ = oracle.jacobi_step(rp, ci, x_in.astype(np.float64), d=D, t=t.astype(np.float64))
+    assert l1(x1, xo1) <= 1e-6 and max_rel(x1, xo1) <= 1e-4
+    assert info1.residual_l1 == pytest.approx(l1o, rel=1e-3, abs=1e-9)
+
+
+def test_pipelined_row_kernel_not_used_where_it_cannot_apply():
+    """Heavy threshold 4096 (light rows longer than a stage) and 64-bit offsets: no
+    pipelined tiles; the solve still matches the oracle."""
+    rp, ci = gg.rmat(12, seed=3)
+    for heavy, idx64 in ((4096, 0), (1024, 1)):
+        pr.set_heavy_degree(heavy)
+        pr.pr_set_option(None, pr.PR_OPT_INDEX64, idx64)
+        try:
+            g = pr.Graph(rp, ci)
+        finally:
+            pr.set_heavy_degree(pr.DEFAULT_HEAVY_DEGREE)
+            pr.pr_set_option(None, pr.PR_OPT_INDEX64, 0)
+        with g:
+            assert g.stats()["n_tma_tiles"] == 0
+            x, info = g.solve(tol=1e-6, max_iter=200)
+        xo = matching(rp, ci, x, info)
+        assert l1(x, xo) <= 1e-6 and max_rel(x, xo) <= 1e-4
 
 
 @pytest.mark.parametrize("hubs", [0, 4, 1000, 8192])
@@ -345,7 +413,7 @@ def test_loop_perforation(heavy):
     try:
         g = pr.Graph(rp, ci)
     finally:
-        pr.set_heavy_degree(1024)
+        pr.set_heavy_degree(pr.DEFAULT_HEAVY_DEGREE)
     xstar, _, _ = oracle.fixed_point(rp, ci, d=D)
     with g:
         x0, info0 = g.solve(tol=1e-7, max_iter=300)

@@ -63,7 +63,7 @@ def test_set_matches_each_graph_alone(heavy):
     try:
         g = pr.Graph(rp, ci)
     finally:
-        pr.set_heavy_degree(1024)
+        pr.set_heavy_degree(pr.DEFAULT_HEAVY_DEGREE)
     with g:
         g.set_partition(off)
         x, info, res, its = g.solve_set(tol=1e-6, max_iter=300)
