@@ -735,7 +735,8 @@ def run_adjoint(args):
                 "forward": {"iterations": fi.iterations, "ms": fi.ms_device,
                             "residual_l1": fi.residual_l1},
                 "adjoint": {"iterations": ai.iterations, "ms": ai.ms_device,
-                            "relative_residual": ai.residual_l1},
+                            "residual_l1": ai.residual_l1,
+                            "relative_residual": ai.residual_l1 / float(c.abs().sum())},
                 "roofline": {"bound": "hbm", "achieved": b_iter / (f_ms * 1e-3) / 1e9, "peak": peak,
                              "unit": "GB/s", "frac": b_iter / (f_ms * 1e-3) / 1e9 / peak,
                              "traffic": None, "kernel": "k_w_forward iteration",

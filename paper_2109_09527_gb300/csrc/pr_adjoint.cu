@@ -101,6 +101,29 @@ __device__ __forceinline__ void w_rows(const int32_t* order, int64_t n, int64_t 
     }
 }
 
+// sum over the edges k of row r of p[k] * vec[idx[k]], this lane's share
+// (edges l, l+g, ...), accumulated in edge order with one FMA per edge; the
+// loads of four edges are issued before their products are added.
+__device__ __forceinline__ float w_gather(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ idx,
+                                          const float* __restrict__ p, const float* __restrict__ vec, int32_t r,
+                                          int l, int g) {
+    const int64_t e = __ldg(rowptr + r + 1);
+    int64_t k = __ldg(rowptr + r) + l;
+    float s = 0.f;
+    for (; k + 3 * g < e; k += 4 * g) {
+        const int32_t c0 = __ldg(idx + k), c1 = __ldg(idx + k + g), c2 = __ldg(idx + k + 2 * g),
+                      c3 = __ldg(idx + k + 3 * g);
+        const float p0 = __ldg(p + k), p1 = __ldg(p + k + g), p2 = __ldg(p + k + 2 * g), p3 = __ldg(p + k + 3 * g);
+        const float v0 = __ldg(vec + c0), v1 = __ldg(vec + c1), v2 = __ldg(vec + c2), v3 = __ldg(vec + c3);
+        s = fmaf(p0, v0, s);
+        s = fmaf(p1, v1, s);
+        s = fmaf(p2, v2, s);
+        s = fmaf(p3, v3, s);
+    }
+    for (; k < e; k += g) s = fmaf(__ldg(p + k), __ldg(vec + __ldg(idx + k)), s);
+    return s;
+}
+
 // ------------------------------------------------------------------ kernels --
 
 // x' = (1-d) t + d (sum_e P(e) x(u_e) + D/n), with D' and the L1 change.
@@ -123,11 +146,7 @@ __global__ void __launch_bounds__(kBlock) k_w_forward(WArgs a, const float* __re
     float r = 0.f;
     Acc acc;
     w_rows(a.in_order, a.n, a.n_in_heavy,
-           [&](int32_t v, int l, int g) {
-               float s = 0.f;
-               for (int64_t e = a.rowptr[v] + l; e < a.rowptr[v + 1]; e += g) s += a.in_p[e] * x[a.colidx[e]];
-               return s;
-           },
+           [&](int32_t v, int l, int g) { return w_gather(a.rowptr, a.colidx, a.in_p, x, v, l, g); },
            [&](int32_t v, float s) {
                const float tv = t ? t[v] : tu;
                const float xn = fmaf(1.f - d, tv, d * (s + share));
@@ -165,11 +184,7 @@ __global__ void __launch_bounds__(kBlock) k_w_adjoint(WArgs a, const float* __re
     const float lshare = (float)(s_L * s_inv_n);
     double r = 0.0, L = 0.0;
     w_rows(a.out_order, a.n, a.n_out_heavy,
-           [&](int32_t u, int l, int g) {
-               float m = 0.f;
-               for (int64_t e = a.out_rowptr[u] + l; e < a.out_rowptr[u + 1]; e += g) m += a.out_p[e] * lam[a.out_dst[e]];
-               return m;
-           },
+           [&](int32_t u, int l, int g) { return w_gather(a.out_rowptr, a.out_dst, a.out_p, lam, u, l, g); },
            [&](int32_t u, float m) {
                if (final) {
                    mu[u] = m;
@@ -334,7 +349,11 @@ using namespace prk;
 
 namespace {
 
-int w_grid(const pr_wgraph* g) { return g->sm_count * 4; }
+// Blocks per SM of every weighted kernel (256 threads, 40 registers: six fit);
+// the reduction slots are allocated for exactly this grid.
+constexpr int kWBlocksPerSm = 6;
+
+int w_grid(const pr_wgraph* g) { return g->sm_count * kWBlocksPerSm; }
 
 WArgs w_args(const pr_wgraph* g) {
     WArgs a{};
@@ -498,7 +517,7 @@ extern "C" pr_status pr_create_wgraph(int64_t n, int64_t nnz, const int64_t* row
                   cudaMalloc((void**)&g->W, N * sizeof(double)) == cudaSuccess &&
                   cudaMalloc((void**)&g->stage, 3 * N * sizeof(float)) == cudaSuccess &&
                   cudaMalloc((void**)&g->state, sizeof(WState)) == cudaSuccess &&
-                  cudaMalloc((void**)&g->slots, (size_t)g->sm_count * 4 * 2 * sizeof(double)) == cudaSuccess &&
+                  cudaMalloc((void**)&g->slots, (size_t)w_grid(g) * 2 * sizeof(double)) == cudaSuccess &&
                   cudaMalloc((void**)&g->bad, sizeof(unsigned int)) == cudaSuccess &&
                   cudaMalloc((void**)&g->in_order, N * sizeof(int32_t)) == cudaSuccess &&
                   cudaMalloc((void**)&g->out_order, N * sizeof(int32_t)) == cudaSuccess &&
