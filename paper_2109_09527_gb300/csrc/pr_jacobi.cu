@@ -492,7 +492,7 @@ __global__ void __launch_bounds__(kBlock) k_init(IterArgs a, const float* __rest
                                                  float* __restrict__ y) {
     SolveState* st = a.state;
     const float tu = (float)block_state(st).inv_n;
-    double dsum = 0.0, tsum = 0.0;
+    KahanF dsum, tsum;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
     for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < a.n; i += stride) {
         const int32_t o = order[i];
@@ -502,11 +502,11 @@ __global__ void __launch_bounds__(kBlock) k_init(IterArgs a, const float* __rest
         const float inv = a.inv_out[i];
         x[i] = xv;
         y[i] = xv * inv;
-        if (inv == 0.f) dsum += (double)xv;
-        tsum += (double)tv;
+        if (inv == 0.f) dsum.add(xv);
+        tsum.add(tv);
     }
     double D, T;
-    if (block_pair_to_grid(dsum, tsum, a.slots, &st->ticket, &D, &T) && threadIdx.x == 0) {
+    if (block_pair_to_grid(dsum.value(), tsum.value(), a.slots, &st->ticket, &D, &T) && threadIdx.x == 0) {
         st->D = D;
         st->t_sum = t_src ? T : 1.0;
         st->iter = 0;
@@ -523,11 +523,11 @@ __global__ void __launch_bounds__(kBlock) k_sum_x(IterArgs a, const float* __res
                                                   const float* __restrict__ x1) {
     SolveState* st = a.state;
     const float* x = (block_state(st).iter & 1) ? x1 : x0;
-    double s = 0.0;
+    KahanF s;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
-    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < a.n; i += stride) s += (double)x[i];
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < a.n; i += stride) s.add(x[i]);
     double S, unused;
-    if (block_pair_to_grid(s, 0.0, a.slots, &st->ticket, &S, &unused) && threadIdx.x == 0) {
+    if (block_pair_to_grid(s.value(), 0.0, a.slots, &st->ticket, &S, &unused) && threadIdx.x == 0) {
         st->sum_x = S;
         st->scale = S > 0.0 ? st->t_sum / S : 1.0;
         st->ticket = 0;
@@ -644,8 +644,9 @@ cudaError_t enqueue_iteration_t(const pr_graph* g, const IterArgs& a, int src, b
     return cudaGetLastError();
 }
 
+// k_heavy_segments over segments [0, a.n_seg) alone.
 cudaError_t launch_segments(const pr_graph* g, const IterArgs& a, int src, cudaStream_t s, int* launches) {
-    if (g->n_seg == 0) return cudaSuccess;
+    if (a.n_seg == 0) return cudaSuccess;
     const size_t smem = (size_t)a.hot_n * sizeof(float);
     if (g->idx64) k_heavy_segments<int64_t><<<seg_grid(g), kIterBlock, smem, s>>>(a, g->y[src]);
     else k_heavy_segments<int32_t><<<seg_grid(g), kIterBlock, smem, s>>>(a, g->y[src]);

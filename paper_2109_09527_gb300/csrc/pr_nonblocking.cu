@@ -345,15 +345,15 @@ __global__ void __launch_bounds__(kNbBlock, kNbMinBlocks) k_nonblocking(NbArgs a
 __global__ void __launch_bounds__(kBlock) k_mass_split(IterArgs a, const float* __restrict__ x,
                                                        double* scalars) {
     SolveState* st = a.state;
-    double s_nd = 0.0, s_d = 0.0;
+    KahanF s_nd, s_d;
     const int64_t stride = (int64_t)gridDim.x * kBlock;
     for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < a.n; i += stride) {
         const float v = x[i];
-        if (a.inv_out[i] == 0.f) s_d += (double)v;
-        else s_nd += (double)v;
+        if (a.inv_out[i] == 0.f) s_d.add(v);
+        else s_nd.add(v);
     }
     double S, D;
-    if (block_pair_to_grid(s_nd, s_d, a.slots, &st->ticket, &S, &D) && threadIdx.x == 0) {
+    if (block_pair_to_grid(s_nd.value(), s_d.value(), a.slots, &st->ticket, &S, &D) && threadIdx.x == 0) {
         scalars[0] = S;
         scalars[1] = D;
         st->D = D;
@@ -604,8 +604,14 @@ pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_
         PRK_CHECK(cudaMemsetAsync(g->nb_scalars + 2, 0, 2 * sizeof(double), s));
         k_mass_split<<<small_grid(g), kBlock, 0, s>>>(a, g->x[0], g->nb_scalars);
         ++launches;
-        // segment partials of the current vector, read by the first sweep
-        PRK_CHECK(launch_segments(g, a, 0, s, &launches));
+        // partials of the kernel's segments for the current vector, read by
+        // the first sweep (the layout's other segments are rows it works as
+        // light tiles)
+        {
+            IterArgs as = a;
+            as.n_seg = (int32_t)g->nb_n_seg;
+            PRK_CHECK(launch_segments(g, as, 0, s, &launches));
+        }
         na.tol_int = tol_int;
         na.max_sweeps = std::max(1, max_iter - used);
         void* args[] = {&na};

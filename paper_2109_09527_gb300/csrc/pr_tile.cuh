@@ -289,6 +289,21 @@ struct Acc {
     __device__ __forceinline__ double mass() const { return (double)m - (double)c; }
 };
 
+// Compensated FP32 sum of one thread's elements (FP32 adds only: FP64
+// arithmetic is a slow pipe on this GPU); value() hands it to the FP64
+// cross-thread reduction.
+struct KahanF {
+    float s = 0.f;
+    float c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 template <bool kUniform, bool kInPlace>
 __device__ __forceinline__ void row_update(int64_t r, float s, float xo, float inv, float tv,
                                            const RowCtx& c, float* x_out, float* y_out, Acc& acc) {
