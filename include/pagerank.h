@@ -262,6 +262,13 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
  *                         bulk asynchronous copies ahead of the gathering
  *                         warps.  0 = the row-by-row kernel that loads them
  *                         itself.  Same arithmetic either way.
+ *   PR_OPT_TEST_WITHHOLD_COPY  test hook of the pipelined row kernel's
+ *                         bounded waits: k > 0 makes block 0's producer announce
+ *                         its k-th tile of each launch without copying it, so
+ *                         the gathering warps' wait for that tile gives up after
+ *                         about one second and the solve returns
+ *                         PR_ERR_DEVICE_TIMEOUT (nothing faults; the graph and
+ *                         the context stay usable).  0 (default) = off.
  *   PR_OPT_INDEX64        1: keep 64-bit row offsets on the device even when
  *                         the edge count fits 32 bits (thread-local default
  *                         for the next pr_create_graph, set with g = NULL;
@@ -281,6 +288,7 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
 #define PR_OPT_DYNAMIC_TILES 12
 #define PR_OPT_DELAY_NS 13
 #define PR_OPT_TMA_TILES 14
+#define PR_OPT_TEST_WITHHOLD_COPY 15
 PR_API pr_status pr_set_option(pr_graph* g, int key, int64_t value);
 
 /* Batched personalised PageRank: k independent solves on one graph, one per

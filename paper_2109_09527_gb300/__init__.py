@@ -52,6 +52,7 @@ PR_OPT_PERFORATION = 11
 PR_OPT_DYNAMIC_TILES = 12
 PR_OPT_DELAY_NS = 13
 PR_OPT_TMA_TILES = 14
+PR_OPT_TEST_WITHHOLD_COPY = 15
 
 LIB_PATH = _build.LIB_PATH
 

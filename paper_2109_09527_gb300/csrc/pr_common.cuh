@@ -153,7 +153,7 @@ struct IterArgs {
     float perf_eps;
     int32_t dynamic;             // 1: blocks take tiles from a shared counter (helping)
     int32_t delay_ns;            // > 0: block 0 sleeps this long per tile (slow-processor model)
-    int32_t pad3;
+    int32_t withhold;            // > 0: test hook of the pipelined kernel (PR_OPT_TEST_WITHHOLD_COPY)
     int64_t nnz;
 };
 
@@ -180,6 +180,7 @@ struct pr_graph {
     uint8_t* frozen = nullptr;                // frozen rows of the perforated synchronous solve
     int staged_tiles = prk::kDefaultStaged;   // bit 0: Jacobi, bit 1: barrier-free (see PR_OPT_STAGED_TILES)
     int use_tma = 1;                          // PR_OPT_TMA_TILES: pipelined synchronous row kernel
+    int test_withhold = 0;                    // PR_OPT_TEST_WITHHOLD_COPY (test hook, 0 = off)
 
     void* rowptr = nullptr;
     int32_t* colidx = nullptr;

@@ -420,6 +420,12 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaMinBlocks) k_rows_tma(IterArg
                     break;
                 }
                 const Tile tile = a.tiles[t];
+                if (a.withhold > 0 && blockIdx.x == 0 && k + 1 == a.withhold) {
+                    // test hook: announce a copy that never comes, so that the
+                    // consumers' bounded wait for this stage runs out
+                    mbar_arrive_expect_tx(full + s, 16);
+                    continue;
+                }
                 tma_issue<kUniform>(a, tile, a.tiles[t].pad, a.tiles[t + 1].pad, x_in,
                                     TmaStage(stages, s), full + s);
             }
@@ -600,6 +606,8 @@ IterArgs make_args(const pr_graph* g, bool uniform) {
     a.perf_eps = g->perforation > 0 ? (float)std::pow(10.0, -(double)g->perforation) : 0.f;
     a.dynamic = g->dynamic_tiles;
     a.delay_ns = g->delay_ns;
+    a.withhold = g->test_withhold;
+    a.nnz = g->nnz;
     return a;
 }
 

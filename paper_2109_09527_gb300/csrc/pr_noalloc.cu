@@ -41,6 +41,7 @@ struct NaScratch {
     double slots[2 * kNaMaxBlocks];      // per-block (a, b) partial sums
 };
 constexpr size_t kNaScratchBytes = sizeof(NaScratch);
+static_assert(kNaScratchBytes <= 160 * 1024, "the fixed scratch stays about 128 KiB");
 
 static __device__ __align__(256) NaScratch g_noalloc_scratch;
 

@@ -426,7 +426,6 @@ extern "C" pr_status pr_graph_set_partition(pr_graph* g, int32_t count, const in
     sc->count = count;
     sc->offsets.assign(offsets, offsets + count + 1);
     const int64_t n = g->n;
-    pr_status rc = PR_OK;
     auto bail = [&](pr_status r) {
         destroy_set(g);
         return r;
@@ -501,7 +500,6 @@ extern "C" pr_status pr_graph_set_partition(pr_graph* g, int32_t count, const in
     if (e == cudaSuccess) e = cudaMemcpyAsync(sc->gr.inv_n, inv_n.data(), C * sizeof(double), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return bail(cuda_fail(e, "pr_graph_set_partition: upload"));
-    (void)rc;
     return PR_OK;
 }
 

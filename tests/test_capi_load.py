@@ -85,7 +85,8 @@ def test_options_validate_host_side():
     with pytest.raises(pr.PageRankError):
         pr.pr_set_option(None, 99, 1)
     for key in (pr.PR_OPT_USE_GRAPH, pr.PR_OPT_STAGED_TILES, pr.PR_OPT_NB_HUBS,
-                pr.PR_OPT_HOT_VERTICES, pr.PR_OPT_HOT_CACHE, pr.PR_OPT_CTAS_PER_SM):
+                pr.PR_OPT_HOT_VERTICES, pr.PR_OPT_HOT_CACHE, pr.PR_OPT_CTAS_PER_SM,
+                pr.PR_OPT_TMA_TILES, pr.PR_OPT_TEST_WITHHOLD_COPY):
         with pytest.raises(pr.PageRankError):
             pr.pr_set_option(None, key, 1)               # needs a graph
     pr.pr_set_option(None, pr.PR_OPT_INDEX64, 0)
@@ -119,3 +120,18 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(sname, "sizeof")] == ctypes.sizeof(cls), sname
         for fname, _ in cls._fields_:
             assert got[(sname, fname)] == getattr(cls, fname).offset, (sname, fname)
+
+
+def test_binding_constants_match_the_header():
+    """Every PR_OPT_* option key and pr_status value the header defines has the same value
+    in the Python binding."""
+    import re
+    text = open(HEADER).read()
+    defines = dict(re.findall(r"#define (PR_OPT_[A-Z0-9_]+) (\d+)", text))
+    assert defines, "no option keys found in the header"
+    for name, value in defines.items():
+        assert getattr(pr, name) == int(value), name
+    statuses = dict(re.findall(r"\b(PR_(?:OK|ERR_[A-Z_]+|NOT_CONVERGED)) = (\d+)", text))
+    assert "PR_ERR_DEVICE_TIMEOUT" in statuses
+    for name, value in statuses.items():
+        assert getattr(pr, name) == int(value), name

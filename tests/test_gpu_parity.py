@@ -353,6 +353,33 @@ def test_pipelined_row_kernel_matches_row_kernel_and_oracle(build):
     assert info1.residual_l1 == pytest.approx(l1o, rel=1e-3, abs=1e-9)
 
 
+def test_pipelined_row_kernel_bounded_wait_reports_a_timeout():
+    """Failure detection without a fault: the test hook makes block 0's producer announce a
+    tile copy that never comes, so the gathering warps' mbarrier wait runs out after about
+    a second; the solve returns PR_ERR_DEVICE_TIMEOUT, and the same graph (same context)
+    then solves normally."""
+    import time
+    rp, ci = gg.rmat(16, seed=6)
+    with pr.Graph(rp, ci) as g:
+        st = g.stats()
+        # one block per SM, so that block 0 owns at least three tiles (the hook counts them)
+        assert st["n_tma_tiles"] > 2 * st["sm_count"]
+        g.set_option(pr.PR_OPT_CTAS_PER_SM, 1)
+        for k in (1, 2, 3):
+            g.set_option(pr.PR_OPT_TEST_WITHHOLD_COPY, k)
+            t0 = time.perf_counter()
+            with pytest.raises(pr.PageRankError) as e:
+                g.solve(tol=1e-6, max_iter=50)
+            assert e.value.status == pr.PR_ERR_DEVICE_TIMEOUT
+            assert time.perf_counter() - t0 < 30
+        g.set_option(pr.PR_OPT_TEST_WITHHOLD_COPY, 0)
+        g.set_option(pr.PR_OPT_CTAS_PER_SM, 0)
+        x, info = g.solve(tol=1e-6, max_iter=200)
+    assert info.converged == 1
+    xo = matching(rp, ci, x, info)
+    assert l1(x, xo) <= 1e-6 and max_rel(x, xo) <= 1e-4
+
+
 def test_pipelined_row_kernel_not_used_where_it_cannot_apply():
     """Heavy threshold 4096 (light rows longer than a stage) and 64-bit offsets: no
     pipelined tiles; the solve still matches the oracle."""
