@@ -189,7 +189,8 @@ def recorded_traffic(family):
 def rooflines(records, resident):
     """Roofline of the dominant kernel of the step, and of every (graph, variant) pair.
 
-    A launch of the synchronous variant is one iteration (k_heavy_segments + k_rows);
+    A launch of the synchronous variant is one iteration (k_heavy_segments + k_rows_tma, or
+    k_rows where the pipelined kernel does not apply);
     a launch of the barrier-free variant is one persistent k_nonblocking launch.
     Algorithmic bytes per launch = B(graph) x (edges gathered in the launch / nnz), with
     B = 4 nnz + rowptr bytes (n+1) + 20 n the bytes one full sweep must move; the
@@ -213,7 +214,9 @@ def rooflines(records, resident):
         per_visit = recorded_traffic(vname) if gname.startswith("rmat") else None
         traffic = per_visit * visits / launches if per_visit else None
         rows.append({"graph": gname, "variant": vname,
-                     "kernel": ("jacobi iteration (k_heavy_segments + k_rows)" if vname == "jacobi"
+                     "kernel": ((f"jacobi iteration (k_heavy_segments + "
+                                 f"{'k_rows_tma' if st.get('n_tma_tiles', 0) > 0 else 'k_rows'})")
+                                if vname == "jacobi"
                                 else "k_nonblocking (persistent barrier-free sweeps)"),
                      "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,

@@ -13,14 +13,19 @@
 //   k_heavy_segments  a warp per 2048-edge segment of every heavy row: streams
 //                     colidx with 16-byte loads, gathers y, writes the
 //                     segment's partial sum;
-//   k_rows            persistent blocks walk the row tiles round-robin:
+//   k_rows_tma        (default) persistent blocks walk the row tiles
+//                     round-robin, a producer warp staging each tile's
+//                     offsets, column indices and per-row vectors in shared
+//                     memory ahead of 8 gathering warps (see below):
 //                     heavy-row epilogues (sum of the segment partials),
 //                     light rows gathered by groups of 1..32 lanes sized to
 //                     the bin's degree class, rows without in-edges; the
 //                     epilogue writes x' and y' and accumulates r and D'.
 //                     The last block to finish (arrival ticket) reduces the
 //                     per-block partials in a fixed order, so D' and r are
-//                     bitwise reproducible, and applies the stopping test.
+//                     bitwise reproducible, and applies the stopping test;
+//   k_rows            the same without staging (64-bit offsets, long light
+//                     rows, and the staged, perforated and dynamic modes).
 //
 // The solve loop is a CUDA graph with a conditional while node whose body
 // holds two iterations (x0 -> x1, x1 -> x0); the last block clears the

@@ -353,6 +353,36 @@ def test_pipelined_row_kernel_matches_row_kernel_and_oracle(build):
     assert info1.residual_l1 == pytest.approx(l1o, rel=1e-3, abs=1e-9)
 
 
+@pytest.mark.parametrize("batch", range(4))
+def test_random_small_graphs_both_variants(batch):
+    """Forty seeded random digraphs (1 to 600 vertices, 0 to 8 edges per vertex on average,
+    duplicates and self-loops in half of them, so multiplicities and dangling vertices of
+    every kind occur): the synchronous solve in matching mode and the barrier-free solve
+    against the fixed point, on the default layout and with heavy threshold 64 (short
+    rows gathered in segments)."""
+    rng = np.random.default_rng(1000 + batch)
+    for case in range(10):
+        n = int(rng.integers(1, 601))
+        m = int(rng.integers(0, 8 * n + 1))
+        seed = 10000 * batch + case
+        rp, ci = gg.random_digraph(n, m, seed=seed, allow_multi=case % 2 == 0, self_loops=case % 2 == 0)
+        xstar, _, _ = oracle.fixed_point(rp, ci, d=D)
+        heavy = 64 if case % 3 == 0 else pr.DEFAULT_HEAVY_DEGREE
+        pr.set_heavy_degree(heavy)
+        try:
+            g = pr.Graph(rp, ci)
+        finally:
+            pr.set_heavy_degree(pr.DEFAULT_HEAVY_DEGREE)
+        with g:
+            x, info = g.solve(tol=1e-6, max_iter=300)
+            xn, infon = g.solve(tol=1e-6, max_iter=500, variant="nonblocking")
+        assert info.converged == 1 and infon.converged == 1, (n, m, seed)
+        xo = matching(rp, ci, x, info)
+        assert l1(x, xo) <= 1e-6 and max_rel(x, xo) <= 1e-4, (n, m, seed)
+        assert l1(xn, xstar) <= infon.residual_l1 / (1 - D) + 2e-7, (n, m, seed)
+        assert abs(float(np.sum(xn, dtype=np.float64)) - 1.0) < 1e-5
+
+
 def test_pipelined_row_kernel_bounded_wait_reports_a_timeout():
     """Failure detection without a fault: the test hook makes block 0's producer announce a
     tile copy that never comes, so the gathering warps' mbarrier wait runs out after about
