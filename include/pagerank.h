@@ -21,9 +21,11 @@
  *                   launch in which warps update ranks in place, with no grid
  *                   synchronisation and no previous-iteration array; each
  *                   block stops on its own view of the global change
- *                   (thread-level convergence, Section 4.3).  The result is
- *                   then verified with one synchronous update, whose L1
- *                   change is the reported residual.
+ *                   (thread-level convergence, Section 4.3) once it is below
+ *                   4 tol.  The result is then verified with one synchronous
+ *                   update, whose L1 change is the reported residual; if it
+ *                   is not below tol, the persistent launch resumes with a
+ *                   4x tighter internal tolerance, within the budget.
  *
  * Conventions
  *   - All functions return a pr_status.  No function aborts or exits; on an
