@@ -42,6 +42,13 @@
 namespace prk {
 
 constexpr int kBK = 32;              // row width of the batched matrices (floats)
+// Edges of a light-row task of k_b_light: a warp walks its task's rows one
+// after the other, so the row kernel's 6144-edge tiles would leave the
+// launch waiting on the warps that drew the largest ones.
+#ifndef PRK_BATCH_TASK_EDGES
+#define PRK_BATCH_TASK_EDGES 512
+#endif
+constexpr int kBTaskEdges = PRK_BATCH_TASK_EDGES;
 constexpr int kBUpdateBlocksPerSM = 4;
 
 // Device state of a batched solve.
@@ -488,6 +495,8 @@ struct BatchCtx {
     double* slots = nullptr;
     int slot_blocks = 0;
     int64_t zero_start = 0;
+    Tile* tasks = nullptr;           // light-row tasks of k_b_light (rows of one degree class)
+    int64_t n_tasks = 0;
     cudaGraphExec_t loop_exec = nullptr;
 };
 
@@ -507,12 +516,12 @@ BatchArgs batch_args(const pr_graph* g, const BatchCtx* b) {
     a.inv_out = g->inv_out;
     a.seg_row = g->seg_row;
     a.seg_ptr = g->seg_ptr;
-    a.tiles = g->tiles;
+    a.tiles = b->tasks;
     a.n = g->n;
     a.n_heavy = g->n_heavy;
     a.zero_start = b->zero_start;
     a.n_seg = (int32_t)g->n_seg;
-    a.n_tiles = (int32_t)g->n_tiles;
+    a.n_tiles = (int32_t)b->n_tasks;
     a.state = b->state;
     a.slots = b->slots;
     a.P = b->P;
@@ -530,7 +539,7 @@ int update_grid(const pr_graph* g, const BatchCtx* b) {
 template <typename IdxT>
 cudaError_t enqueue_batch_iteration(const pr_graph* g, const BatchCtx* b, const BatchArgs& a, int src,
                                     bool bf16, cudaStream_t s) {
-    const int gs = batch_grid(g, g->n_seg, g_occ_bseg), gl = batch_grid(g, g->n_tiles, g_occ_blight);
+    const int gs = batch_grid(g, g->n_seg, g_occ_bseg), gl = batch_grid(g, b->n_tasks, g_occ_blight);
     if (bf16) {
         if (g->n_seg > 0) k_b_segments<IdxT, __nv_bfloat16><<<gs, kBlock, 0, s>>>(a, b->Y16[src]);
         k_b_light<IdxT, __nv_bfloat16><<<gl, kBlock, 0, s>>>(a, b->Y16[src]);
@@ -570,6 +579,16 @@ pr_status ensure_batch(pr_graph* g) {
         if (t.kind == kTileZero) {
             b->zero_start = std::min<int64_t>(b->zero_start, t.row_begin);
         }
+    {
+        int64_t heavy_rows = 0;
+        std::vector<Tile> tasks;
+        for (const Tile& t : tiles_with_threshold(g, g->heavy_degree, &heavy_rows, kBTaskEdges, kTileRowsMax))
+            if (t.kind >= 0) tasks.push_back(t);
+        b->n_tasks = (int64_t)tasks.size();
+        PRK_CHECK(dev_alloc(g, (void**)&b->tasks, (tasks.size() + 1) * sizeof(Tile)));
+        if (!tasks.empty())
+            PRK_CHECK(cudaMemcpy(b->tasks, tasks.data(), tasks.size() * sizeof(Tile), cudaMemcpyHostToDevice));
+    }
     if (g_occ_bseg == 0) {
         int o = 0;
         PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_b_segments<int32_t, float>, kBlock, 0));
@@ -652,7 +671,7 @@ void destroy_batch(pr_graph* g) {
     BatchCtx* b = g->batch;
     if (!b) return;
     void* dev[] = {b->X[0], b->X[1], b->Y[0], b->Y[1], b->Y16[0], b->Y16[1], b->S, b->P, b->tptr,
-                   b->tcol, b->tval, b->tcount, b->t_stage, b->out_stage, b->state, b->slots};
+                   b->tcol, b->tval, b->tcount, b->t_stage, b->out_stage, b->state, b->slots, b->tasks};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (b->host_state) cudaFreeHost(b->host_state);

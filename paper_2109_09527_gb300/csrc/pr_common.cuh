@@ -270,7 +270,8 @@ cudaError_t enqueue_iteration(const pr_graph* g, const IterArgs& a, int src, boo
 cudaError_t launch_segments(const pr_graph* g, const IterArgs& a, int src, cudaStream_t s, int* launches);
 // Tile list of the layout for another heavy threshold (>= the layout's own),
 // and the number of rows at or above it.
-std::vector<Tile> tiles_with_threshold(const pr_graph* g, int heavy_degree, int64_t* heavy_rows);
+std::vector<Tile> tiles_with_threshold(const pr_graph* g, int heavy_degree, int64_t* heavy_rows,
+                                       int64_t max_edges = kTileEdgesMax, int64_t max_rows = kTileRowsMax);
 // Set pad = offset of the first edge for tiles[0..count] (the last one a
 // sentinel at row n), 32-bit offsets.
 cudaError_t fill_tile_edges(Tile* tiles, int64_t count, const int32_t* rowptr, cudaStream_t s);

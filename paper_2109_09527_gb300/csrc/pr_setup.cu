@@ -477,11 +477,12 @@ pr_status create_typed(pr_graph* g, const void* rowptr, const int32_t* colidx, c
 
 }  // namespace
 
-std::vector<Tile> tiles_with_threshold(const pr_graph* g, int heavy_degree, int64_t* heavy_rows) {
+std::vector<Tile> tiles_with_threshold(const pr_graph* g, int heavy_degree, int64_t* heavy_rows,
+                                       int64_t max_edges, int64_t max_rows) {
     int lh = 0;
     while ((1LL << lh) < (int64_t)heavy_degree) ++lh;
     *heavy_rows = g->bin_start[(size_t)(kTopClass + 1 - lh)];
-    return make_tiles(g->bin_start, lh);
+    return make_tiles(g->bin_start, lh, max_edges, max_rows);
 }
 
 cudaError_t scan_counts_i32(const int64_t* counts, int64_t count, int32_t* offsets, cudaStream_t st) {
