@@ -63,27 +63,41 @@ struct WArgs {
     const int32_t* out_dst;
     const float* out_p;         // P(u, v) of each out-edge
     const float* inv_w;         // 1/W(u), 0 for dangling u
-    const int32_t* in_order;    // rows by in-degree: the n_in_heavy rows with >= 32 in-edges first
+    const int32_t* in_order;    // rows by in-degree: the n_in_giant rows with >= kWGiantEdges in-edges,
+    int64_t n_in_giant;         // then up to n_in_heavy those with >= 32, then the rest
     int64_t n_in_heavy;
-    const int32_t* out_order;   // rows by out-degree: the n_out_heavy rows with >= 32 out-edges first
+    const int32_t* out_order;   // the same classes by out-degree
+    int64_t n_out_giant;
     int64_t n_out_heavy;
     WState* state;
     double* slots;
 };
 
-// Rows are visited in two passes: rows with at least 32 edges a warp each,
-// then the rest by groups of 8 lanes (four rows per warp at a time).  The row
-// body f(row, lane_in_group, group_size) returns the group-reduced sum in
-// the group's first lane; `epilogue(row, sum)` runs there.
+// Rows are visited in three passes: rows with at least kWGiantEdges edges a
+// block each (a power-law hub has tens of thousands: one warp walking it
+// would set the length of the whole launch), rows with at least 32 edges a
+// warp each, then the rest by groups of 8 lanes (four rows per warp at a
+// time).  The row body gather(row, lane_in_group, group_size) returns this
+// lane's share of the row's sum; the group's total reaches the group's first
+// thread, where `epilogue(row, sum)` runs.
 constexpr int kWLightLanes = 8;
+#ifndef PRK_W_GIANT_EDGES
+#define PRK_W_GIANT_EDGES 2048
+#endif
+constexpr int64_t kWGiantEdges = PRK_W_GIANT_EDGES;
 
 template <typename Gather, typename Epilogue>
-__device__ __forceinline__ void w_rows(const int32_t* order, int64_t n, int64_t n_heavy, Gather gather,
-                                       Epilogue epilogue) {
+__device__ __forceinline__ void w_rows(const int32_t* order, int64_t n, int64_t n_giant, int64_t n_heavy,
+                                       Gather gather, Epilogue epilogue) {
     const int lane = threadIdx.x & 31;
+    for (int64_t i = blockIdx.x; i < n_giant; i += gridDim.x) {   // uniform per block
+        const int32_t r = order[i];
+        const float s = block_sum(gather(r, (int)threadIdx.x, (int)blockDim.x));
+        if (threadIdx.x == 0) epilogue(r, s);
+    }
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = warp; i < n_heavy; i += nwarp) {
+    for (int64_t i = n_giant + warp; i < n_heavy; i += nwarp) {
         const int32_t r = order[i];
         float s = warp_sum(gather(r, lane, 32));
         if (lane == 0) epilogue(r, s);
@@ -145,7 +159,7 @@ __global__ void __launch_bounds__(kBlock) k_w_forward(WArgs a, const float* __re
     const float tu = (float)s_inv_n;
     float r = 0.f;
     Acc acc;
-    w_rows(a.in_order, a.n, a.n_in_heavy,
+    w_rows(a.in_order, a.n, a.n_in_giant, a.n_in_heavy,
            [&](int32_t v, int l, int g) { return w_gather(a.rowptr, a.colidx, a.in_p, x, v, l, g); },
            [&](int32_t v, float s) {
                const float tv = t ? t[v] : tu;
@@ -183,7 +197,7 @@ __global__ void __launch_bounds__(kBlock) k_w_adjoint(WArgs a, const float* __re
     const float d = (float)s_d;
     const float lshare = (float)(s_L * s_inv_n);
     double r = 0.0, L = 0.0;
-    w_rows(a.out_order, a.n, a.n_out_heavy,
+    w_rows(a.out_order, a.n, a.n_out_giant, a.n_out_heavy,
            [&](int32_t u, int l, int g) { return w_gather(a.out_rowptr, a.out_dst, a.out_p, lam, u, l, g); },
            [&](int32_t u, float m) {
                if (final) {
@@ -216,7 +230,7 @@ __global__ void __launch_bounds__(kBlock) k_w_grads(WArgs a, const float* __rest
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < a.n; u += stride)
         if (grad_t) grad_t[u] = (1.f - d) * lam[u];
     if (!grad_w) return;
-    w_rows(a.in_order, a.n, a.n_in_heavy,
+    w_rows(a.in_order, a.n, a.n_in_giant, a.n_in_heavy,
            [&](int32_t v, int l, int g) {
                const float lv = lam[v];
                for (int64_t e = a.rowptr[v] + l; e < a.rowptr[v + 1]; e += g) {
@@ -334,7 +348,9 @@ struct pr_wgraph {
     double* W = nullptr;
     int32_t* in_order = nullptr;
     int32_t* out_order = nullptr;
+    int64_t n_in_giant = 0;
     int64_t n_in_heavy = 0;
+    int64_t n_out_giant = 0;
     int64_t n_out_heavy = 0;
     float* vec[4] = {nullptr, nullptr, nullptr, nullptr};   // iterate buffers, mu
     float* stage = nullptr;                                 // host inputs / outputs
@@ -367,8 +383,10 @@ WArgs w_args(const pr_wgraph* g) {
     a.out_p = g->out_p;
     a.inv_w = g->inv_w;
     a.in_order = g->in_order;
+    a.n_in_giant = g->n_in_giant;
     a.n_in_heavy = g->n_in_heavy;
     a.out_order = g->out_order;
+    a.n_out_giant = g->n_out_giant;
     a.n_out_heavy = g->n_out_heavy;
     a.state = g->state;
     a.slots = g->slots;
@@ -477,23 +495,33 @@ extern "C" pr_status pr_create_wgraph(int64_t n, int64_t nnz, const int64_t* row
                 oeid[slot] = k;
             }
     }
-    // rows with >= 32 edges first (a warp each), then the rest (groups of 8 lanes)
-    auto split = [&](const std::vector<int64_t>& ptr, std::vector<int32_t>& order, int64_t& n_heavy) {
+    // rows with >= kWGiantEdges edges first (a block each), then those with
+    // >= 32 (a warp each), then the rest (groups of 8 lanes); caller order
+    // within each class
+    auto split = [&](const std::vector<int64_t>& ptr, std::vector<int32_t>& order, int64_t& n_giant,
+                     int64_t& n_heavy) {
         order.clear();
         order.reserve((size_t)n);
         for (int64_t v = 0; v < n; ++v)
-            if (ptr[v + 1] - ptr[v] >= 32) order.push_back((int32_t)v);
+            if (ptr[v + 1] - ptr[v] >= kWGiantEdges) order.push_back((int32_t)v);
+        n_giant = (int64_t)order.size();
+        for (int64_t v = 0; v < n; ++v) {
+            const int64_t dv = ptr[v + 1] - ptr[v];
+            if (dv >= 32 && dv < kWGiantEdges) order.push_back((int32_t)v);
+        }
         n_heavy = (int64_t)order.size();
         for (int64_t v = 0; v < n; ++v)
             if (ptr[v + 1] - ptr[v] < 32) order.push_back((int32_t)v);
     };
     std::vector<int32_t> in_order, out_order;
-    int64_t n_in_heavy = 0, n_out_heavy = 0;
-    split(rp, in_order, n_in_heavy);
-    split(orp, out_order, n_out_heavy);
+    int64_t n_in_giant = 0, n_in_heavy = 0, n_out_giant = 0, n_out_heavy = 0;
+    split(rp, in_order, n_in_giant, n_in_heavy);
+    split(orp, out_order, n_out_giant, n_out_heavy);
     pr_wgraph* g = new (std::nothrow) pr_wgraph();
     if (!g) return fail(PR_ERR_OOM, "pr_create_wgraph: host allocation failed");
+    g->n_in_giant = n_in_giant;
     g->n_in_heavy = n_in_heavy;
+    g->n_out_giant = n_out_giant;
     g->n_out_heavy = n_out_heavy;
     g->n = n;
     g->nnz = nnz;
