@@ -3,9 +3,9 @@ the torch.autograd.Function on top) against the FP64 oracle.
 
   * tiny graphs (n <= 12): forward, dL/dt and dL/dw against the dense adjoint (explicit
     matrices, numpy's solver);
-  * R-MAT scale 12: every gradient entry against the oracle's iterative adjoint, and 16
-    teleport and 16 weight entries against central differences (h = 1e-3) of the FP64
-    forward at tol 1e-14;
+  * R-MAT scale 12: every gradient entry against the oracle's iterative adjoint, and 32
+    teleport and 32 weight entries (64 sampled entries) against central differences
+    (h = 1e-3) of the FP64 forward at tol 1e-14;
   * the adjoint workload at full size (weighted R-MAT scale 20, weights U(0.1, 1],
     L = sum_i c_i x_i with c ~ N(0, 1)): the identities (1-d) lambda^T t = c^T x and
     sum over u's out-edges of w(e) dL/dw(e) = 0, and the adjoint equation at sampled
@@ -93,13 +93,13 @@ def test_rmat12_against_the_oracle_adjoint_and_central_differences():
 
     rng = np.random.default_rng(1)
     t64 = t.astype(np.float64)
-    for i in rng.integers(0, n, 16):
+    for i in rng.integers(0, n, 32):
         tp, tm = t64.copy(), t64.copy()
         tp[i] += h
         tm[i] -= h
         fd = (L(tp, w64) - L(tm, w64)) / (2 * h)
         assert abs(gt[i] - fd) <= 1e-4 * np.max(np.abs(adj["grad_t"])), i
-    for e in rng.integers(0, ci.size, 16):
+    for e in rng.integers(0, ci.size, 32):
         wp, wm = w64.copy(), w64.copy()
         wp[e] += h
         wm[e] -= h
