@@ -271,6 +271,14 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
  *                         about one second and the solve returns
  *                         PR_ERR_DEVICE_TIMEOUT (nothing faults; the graph and
  *                         the context stay usable).  0 (default) = off.
+ *   PR_OPT_NB_FAIL_AFTER  barrier-free solver, for experiments: s > 0 makes
+ *                         block 0 of the first persistent launch of each solve
+ *                         stop after s sweeps -- the paper's failing thread
+ *                         (Fig. 9) -- and take itself out of the other blocks'
+ *                         stopping test.  The verifying synchronous update
+ *                         then sees its stale rows and the solve resumes with
+ *                         every block, so the result still meets tol (more
+ *                         sweeps, two launches).  0 (default) = off.
  *   PR_OPT_INDEX64        1: keep 64-bit row offsets on the device even when
  *                         the edge count fits 32 bits (thread-local default
  *                         for the next pr_create_graph, set with g = NULL;
@@ -291,6 +299,7 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
 #define PR_OPT_DELAY_NS 13
 #define PR_OPT_TMA_TILES 14
 #define PR_OPT_TEST_WITHHOLD_COPY 15
+#define PR_OPT_NB_FAIL_AFTER 16
 PR_API pr_status pr_set_option(pr_graph* g, int key, int64_t value);
 
 /* Batched personalised PageRank: k independent solves on one graph, one per

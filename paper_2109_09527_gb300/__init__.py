@@ -53,6 +53,7 @@ PR_OPT_DYNAMIC_TILES = 12
 PR_OPT_DELAY_NS = 13
 PR_OPT_TMA_TILES = 14
 PR_OPT_TEST_WITHHOLD_COPY = 15
+PR_OPT_NB_FAIL_AFTER = 16
 
 LIB_PATH = _build.LIB_PATH
 

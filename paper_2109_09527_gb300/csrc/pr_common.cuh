@@ -181,6 +181,7 @@ struct pr_graph {
     int staged_tiles = prk::kDefaultStaged;   // bit 0: Jacobi, bit 1: barrier-free (see PR_OPT_STAGED_TILES)
     int use_tma = 1;                          // PR_OPT_TMA_TILES: pipelined synchronous row kernel
     int test_withhold = 0;                    // PR_OPT_TEST_WITHHOLD_COPY (test hook, 0 = off)
+    int nb_fail_after = 0;                    // PR_OPT_NB_FAIL_AFTER (0 = off)
 
     void* rowptr = nullptr;
     int32_t* colidx = nullptr;

@@ -102,7 +102,7 @@ struct NbArgs {
     int32_t dangling_form;       // 1: share = (T - S)/n (default); 0: running dangling mass
     int32_t hub_n;               // ids [0, hub_n) are gathered from the block's snapshot
     int32_t l1_hubs;             // ids [hub_n, l1_hubs) are gathered with weak L1-cached loads
-    int32_t pad3;
+    int32_t fail_after;          // > 0: block 0 leaves after this many sweeps (a failing thread, Fig. 9)
 };
 
 // The block's snapshot of y[0, hub_n): the hub ranks, which the degree
@@ -168,8 +168,9 @@ __device__ __forceinline__ void warp_segment(int64_t sid, const NbArgs& a, const
 }
 
 // kTrace: the diagnostics form, which records the per-block timeline and
-// block 0's sweep history (NbArgs::trace, NbArgs::history); the production
-// form carries none of that state.
+// block 0's sweep history (NbArgs::trace, NbArgs::history, when not NULL) and
+// can make block 0 fail (NbArgs::fail_after); the production form carries
+// none of that state.
 template <typename IdxT, bool kUniform, bool kStaged, bool kTrace>
 __global__ void __launch_bounds__(kNbBlock, kNbMinBlocks) k_nonblocking(NbArgs a) {
     // dynamic shared memory: the hub snapshot (hub_n floats), then the staging
@@ -189,11 +190,19 @@ __global__ void __launch_bounds__(kNbBlock, kNbMinBlocks) k_nonblocking(NbArgs a
     const int64_t wstep = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int32_t sweeps = 0;
     long long t_start = 0;
-    if (kTrace && threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
+    if (kTrace && a.trace && threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
     double last_R = 0.0, last_est = 0.0;
     long long seg_ns = 0;
     Acc acc;
     while (sweeps < a.max_sweeps) {
+        if (kTrace && a.fail_after > 0 && blockIdx.x == 0 && sweeps >= a.fail_after) {
+            // a failing block (the paper's failing threads, Fig. 9): it stops
+            // updating its rows and takes itself out of the others' stopping
+            // test; the verifying synchronous update then finds its stale
+            // rows, and the solve resumes with every block
+            if (threadIdx.x == 0) st_relaxed(a.slots + blockIdx.x, 0.0);
+            break;
+        }
         // A row's rank x is read and written only by the block that owns the
         // row, so the block keeps it in two copies and alternates by sweep
         // parity: sweep k reads the copy sweep k-1 wrote and writes the other
@@ -237,7 +246,7 @@ __global__ void __launch_bounds__(kNbBlock, kNbMinBlocks) k_nonblocking(NbArgs a
         };
         warp_publish(false);
         long long t_seg0 = 0;
-        if (kTrace && threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_seg0));
+        if (kTrace && a.trace && threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_seg0));
         // heavy-row segments, a warp each, in rounds of one segment per warp of
         // the grid (the same round count in every block, so the hub snapshot
         // can be refreshed between rounds)
@@ -250,7 +259,7 @@ __global__ void __launch_bounds__(kNbBlock, kNbMinBlocks) k_nonblocking(NbArgs a
             if (a.hub_n && (rd % kHubRefresh) == kHubRefresh - 1) refresh_hubs(a.y, hub_sm, a.hub_n);
         }
         warp_publish(true);
-        if (kTrace) {
+        if (kTrace && a.trace) {
             __syncthreads();   // diagnostics only: time the segment phase of the whole block
             if (threadIdx.x == 0) {
                 long long t_seg1;
@@ -297,7 +306,7 @@ __global__ void __launch_bounds__(kNbBlock, kNbMinBlocks) k_nonblocking(NbArgs a
         block_sum2(R, unused1);
         if (threadIdx.x == 0) {
             st_relaxed(a.slots + blockIdx.x, R);
-            if (kTrace && blockIdx.x == 0 && sweeps <= 256) a.history[sweeps - 1] = (float)R;
+            if (kTrace && a.history && blockIdx.x == 0 && sweeps <= 256) a.history[sweeps - 1] = (float)R;
         }
         double est = 0.0, unused = 0.0;
         for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) est += ld_relaxed(a.slots + i);
@@ -324,7 +333,7 @@ __global__ void __launch_bounds__(kNbBlock, kNbMinBlocks) k_nonblocking(NbArgs a
                 if (sid + 1 == a.seg_ptr[h + 1]) st_relaxed(a.x + h, ld_relaxed(a.x_alt + h));
             }
     }
-    if (kTrace && threadIdx.x == 0) {
+    if (kTrace && a.trace && threadIdx.x == 0) {
         // per block: sweeps, start/end (ns, %globaltimer), last sweep change, last estimate,
         // first item, tile count, ns spent in the segment phase
         long long t_end;
@@ -526,10 +535,11 @@ pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_
     // and appends one CSV line per block and launch.
     const char* trace_path = getenv("PR_TRACE_NB");
     const bool trace = trace_path && *trace_path;
-    const bool staged = !trace && ((g->staged_tiles >> 1) & 1);
+    const bool diag = trace || g->nb_fail_after > 0;   // the diagnostics form of the kernel
+    const bool staged = !diag && ((g->staged_tiles >> 1) & 1);
     const int32_t hub_n = (int32_t)(std::min<int64_t>(g->nb_hubs, g->n) & ~(int64_t)3);
     const size_t nb_smem = ((size_t)hub_n + (staged ? (size_t)kStageFloats : 0)) * sizeof(float);
-    void* kernel = pick_kernel(g, uniform, staged, trace);
+    void* kernel = pick_kernel(g, uniform, staged, diag);
     int per_sm = 1;
     if ((rc = nb_occupancy(kernel, nb_smem, &per_sm)) != PR_OK) return rc;
     nb_partition(g, per_sm);
@@ -627,6 +637,7 @@ pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_
         }
         na.tol_int = tol_int;
         na.max_sweeps = std::max(1, max_iter - used);
+        na.fail_after = launch_no == 0 ? g->nb_fail_after : 0;
         void* args[] = {&na};
         PRK_CHECK(cudaEventRecord(g->ev_loop0, s));
         PRK_CHECK(cudaLaunchCooperativeKernel(kernel, dim3(G), dim3(kNbBlock), args, nb_smem, s));

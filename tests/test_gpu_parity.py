@@ -216,6 +216,28 @@ def test_nonblocking_reaches_the_fixed_point(build):
         pr.pr_set_option(None, pr.PR_OPT_INDEX64, 0)
 
 
+@pytest.mark.parametrize("fail_after", [1, 3])
+def test_nonblocking_recovers_from_a_failing_block(fail_after):
+    """The paper's failing thread (Fig. 9) on the GPU: block 0 of the first persistent launch
+    stops after `fail_after` sweeps and leaves the other blocks' stopping test.  The verifying
+    synchronous update sees its stale rows, the solve resumes with every block, and the
+    result still meets tol and the fixed-point bound -- in more sweeps than without the
+    failure."""
+    rp, ci = gg.rmat(14, seed=3)
+    xstar, _, _ = oracle.fixed_point(rp, ci, d=D)
+    with pr.Graph(rp, ci) as g:
+        x0, info0 = g.solve(tol=1e-6, max_iter=500, variant="nonblocking")
+        g.set_option(pr.PR_OPT_NB_FAIL_AFTER, fail_after)
+        x, info = g.solve(tol=1e-6, max_iter=500, variant="nonblocking")
+        g.set_option(pr.PR_OPT_NB_FAIL_AFTER, 0)
+    assert info0.converged == 1 and info.converged == 1
+    assert info.residual_l1 < 1e-6
+    assert info.launches > info0.launches          # a second persistent launch
+    assert info.iterations > info0.iterations
+    assert l1(x, xstar) <= info.residual_l1 / (1 - D) + 2e-7
+    assert max_rel(x, xstar) <= 1e-4
+
+
 def test_nonblocking_budget_of_one_sweep_returns():
     rp, ci = gg.rmat(12, seed=5)
     with pr.Graph(rp, ci) as g:
