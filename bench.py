@@ -640,6 +640,109 @@ def run_set(args):
     return 0
 
 
+def run_edge(args):
+    """The edge-centric synchronous iteration of Alg. 2 (Barriers-Edge, PR_EDGE) against the
+    vertex-centric pull (PR_JACOBI) on the two graphs of the default step, each solved to
+    L1 < 1e-6; value = edges processed per second by the edge-centric solves."""
+    import torch
+
+    import paper_2109_09527_gb300 as pr
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    graphs = make_graphs(args.scale, 1 << args.er_log2)
+    resident = []
+    for name, (rp, ci) in graphs:
+        g = pr.Graph(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev))
+        resident.append((name, g, g.stats(), torch.empty(rp.size - 1, dtype=torch.float32, device=dev)))
+    stream = torch.cuda.current_stream()
+
+    def solve_all(variant):
+        return [(name, g.solve(tol=TOL, max_iter=MAX_ITER, variant=variant, out=out)[1])
+                for name, g, _, out in resident]
+
+    for _ in range(args.warmup):
+        solve_all(pr.PR_EDGE)
+        solve_all(pr.PR_JACOBI)
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    runs = [solve_all(pr.PR_EDGE) for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    ms, visits = combine_ranks(dist, dev, ev0.elapsed_time(ev1),
+                               sum(info.edge_visits for run in runs for _, info in run))
+    value = visits / (ms * 1e-3) / 1e9
+    jac = [solve_all(pr.PR_JACOBI) for _ in range(args.steps)]
+    peak, peak_kind = peaks()
+    per_graph = {}
+    for name, g, st, _ in resident:
+        e_inf = [info for run in runs for nm, info in run if nm == name]
+        j_inf = [info for run in jac for nm, info in run if nm == name]
+        e_it = sum(i.iterations for i in e_inf)
+        j_it = sum(i.iterations for i in j_inf)
+        e_loop = sum(i.ms_loop for i in e_inf)
+        j_loop = sum(i.ms_loop for i in j_inf)
+        # Alg. 2 per iteration: out-edge source and slot, the slot written and read back, the
+        # row offsets, and the five rank vectors of the vertex form
+        b_edge = 16 * st["nnz"] + 4 * (st["n"] + 1) + 20 * st["n"]
+        per_graph[name] = {"edge_ms": sum(i.ms_device for i in e_inf) / len(e_inf),
+                           "jacobi_ms": sum(i.ms_device for i in j_inf) / len(j_inf),
+                           "edge_ms_per_iteration": e_loop / e_it, "jacobi_ms_per_iteration": j_loop / j_it,
+                           "edge_iterations": e_inf[-1].iterations, "jacobi_iterations": j_inf[-1].iterations,
+                           "edge_residual_l1": e_inf[-1].residual_l1,
+                           "edge_bytes_per_iteration": b_edge,
+                           "edge_achieved_gbs": b_edge * e_it / (e_loop * 1e-3) / 1e9}
+    head = per_graph[resident[0][0]]
+    out_pin = torch.empty(resident[0][2]["n"], dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_visits = 0.0
+    for _ in range(max(1, args.e2e_steps)):
+        _, info = resident[0][1].solve(tol=TOL, max_iter=MAX_ITER, variant=pr.PR_EDGE, out=out_pin)
+        e2e_visits += info.edge_visits
+    e2e_s, e2e_visits = combine_ranks(dist, dev, time.perf_counter() - t0, e2e_visits)
+    for _, g, _, _ in resident:
+        g.close()
+    if rank == 0:
+        line = {"metric": "PageRank GTEPS of the edge-centric synchronous iteration (Barriers-Edge, "
+                          "Alg. 2) to L1<1e-6, against the vertex-centric pull",
+                "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "rmat24 + er24 as in the default step, PR_EDGE solves; d=0.85",
+                           "tol": TOL, "l2": "inputs larger than L2"},
+                "roofline": {"bound": "hbm", "achieved": head["edge_achieved_gbs"], "peak": peak,
+                             "unit": "GB/s", "frac": head["edge_achieved_gbs"] / peak, "traffic": None,
+                             "kernel": f"edge-centric iteration (k_edge_scatter + k_edge_rows) on "
+                                       f"{resident[0][0]}",
+                             "bytes_per_iteration": head["edge_bytes_per_iteration"],
+                             "ms_per_iteration": head["edge_ms_per_iteration"],
+                             "peak_source": f"{peak_kind} hbm_gbs"},
+                "vs_vertex_jacobi": per_graph,
+                "e2e": {"value": e2e_visits / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": resident[0][2]["n"] * 4,
+                        "ms_per_step": e2e_s * 1e3 / max(1, args.e2e_steps)},
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 ADJ_SCALE = 20
 
 
@@ -770,7 +873,7 @@ def main():
     ap.add_argument("--profile", choices=["jacobi", "nonblocking", "batched", "set", "adjoint"], default=None,
                     help="run a short fixed workload for a profiler instead of the benchmark")
     ap.add_argument("--graph", choices=["rmat", "er"], default="rmat")
-    ap.add_argument("--workload", choices=["pagerank", "batched", "set", "adjoint"], default="pagerank",
+    ap.add_argument("--workload", choices=["pagerank", "batched", "set", "adjoint", "edge"], default="pagerank",
                     help="batched: 32 personalised PageRank vectors on R-MAT-22; set: 64 R-MAT "
                          "graphs of 1e3..1e6 vertices in one solve (each its own JSON line)")
     args = ap.parse_args()
@@ -790,6 +893,8 @@ def main():
         return run_set(args)
     if args.workload == "adjoint":
         return run_adjoint(args)
+    if args.workload == "edge":
+        return run_edge(args)
 
     import numpy as np
     import torch

@@ -26,6 +26,14 @@
  *                   update, whose L1 change is the reported residual; if it
  *                   is not below tol, the persistent launch resumes with a
  *                   4x tighter internal tolerance, within the budget.
+ *   PR_EDGE         the edge-centric synchronous iteration of Alg. 2
+ *                   (Barriers-Edge), for comparison: each iteration first
+ *                   pushes every source's rank/outdeg into a per-edge array
+ *                   along its out-edges, then sums each vertex's in-edge slots;
+ *                   same iterates as PR_JACOBI up to rounding, more bytes per
+ *                   edge.  32-bit row offsets only (else PR_ERR_UNSUPPORTED);
+ *                   its out-edge list (8 bytes per edge) and per-edge array
+ *                   (4 bytes per edge) are allocated on first use.
  *
  * Conventions
  *   - All functions return a pr_status.  No function aborts or exits; on an
@@ -78,6 +86,7 @@ typedef enum pr_status {
 /* variant argument of pr_solve */
 #define PR_JACOBI 0
 #define PR_NONBLOCKING 1
+#define PR_EDGE 2
 
 typedef struct pr_info {
     int32_t iterations;    /* Jacobi: iterations run.  Non-blocking: the largest
@@ -149,7 +158,7 @@ PR_API pr_status pr_destroy_graph(pr_graph* g);
  *   tol           > 0: stop when ||x_k - x_{k-1}||_1 < tol (the paper's
  *                 threshold, Alg. 1, compared in L1 rather than max-abs).
  *   max_iter      >= 1: iteration budget (sweep budget for PR_NONBLOCKING).
- *   variant       PR_JACOBI or PR_NONBLOCKING.
+ *   variant       PR_JACOBI, PR_NONBLOCKING or PR_EDGE.
  *   teleport      host or device, n floats >= 0, or NULL for uniform 1/n.
  *   x0            host or device, n floats (warm start), or NULL for x0 = t.
  *   x_out         host or device, n floats: the result, rescaled in FP64 so

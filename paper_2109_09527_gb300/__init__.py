@@ -37,6 +37,7 @@ PR_IN_CSR = 0
 PR_OUT_CSR = 1
 PR_JACOBI = 0
 PR_NONBLOCKING = 1
+PR_EDGE = 2
 
 PR_OPT_HEAVY_DEGREE = 1
 PR_OPT_USE_GRAPH = 2
@@ -319,7 +320,7 @@ class Graph:
         if out is None:
             out = np.empty(self.n, dtype=np.float32)
         if isinstance(variant, str):
-            variant = {"jacobi": PR_JACOBI, "nonblocking": PR_NONBLOCKING}[variant]
+            variant = {"jacobi": PR_JACOBI, "nonblocking": PR_NONBLOCKING, "edge": PR_EDGE}[variant]
         status, info = pr_solve(self.handle, damping, tol, max_iter, variant, teleport, x0, out,
                                 stream=stream)
         return out, info

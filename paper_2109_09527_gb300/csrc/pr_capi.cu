@@ -63,7 +63,8 @@ extern "C" pr_status pr_destroy_graph(pr_graph* g) {
     destroy_set(g);
     void* dev[] = {g->rowptr, g->colidx, g->inv_out, g->order, g->rank, g->x[0], g->x[1],
                    g->y[0], g->y[1], g->teleport, g->stage, g->seg_row, g->seg_ptr, g->seg_sum,
-                   g->tiles, g->tma_tiles, g->state, g->slots, g->nb_items, g->nb_slots,
+                   g->tiles, g->tma_tiles, g->out_src, g->out_pos, g->contrib, g->state, g->slots,
+                   g->nb_items, g->nb_slots,
                    g->nb_scalars, g->nb_block_sweeps, g->frozen};
     cudaError_t first = cudaSuccess;
     for (void* p : dev)

@@ -155,6 +155,10 @@ struct IterArgs {
     int32_t delay_ns;            // > 0: block 0 sleeps this long per tile (slow-processor model)
     int32_t withhold;            // > 0: test hook of the pipelined kernel (PR_OPT_TEST_WITHHOLD_COPY)
     int64_t nnz;
+    int32_t edge;                // 1: the edge-centric iteration (Alg. 2, pr_edge.cu)
+    int32_t pad4;
+    const int32_t* out_src;      // edge-centric form: source of each out-edge, in out-edge order
+    const int32_t* out_pos;      // edge-centric form: in-edge slot of each out-edge
 };
 
 }  // namespace prk
@@ -197,6 +201,9 @@ struct pr_graph {
     float* seg_sum = nullptr;
     prk::Tile* tiles = nullptr;
     prk::Tile* tma_tiles = nullptr;  // tiles of k_rows_tma (pad = first edge), + a sentinel at n
+    int32_t* out_src = nullptr;      // edge-centric form (first use): out-edge sources and in-edge slots,
+    int32_t* out_pos = nullptr;      // and the per-edge contribution array
+    float* contrib = nullptr;
     int64_t n_tma_tiles = 0;         // 0: the layout cannot use k_rows_tma
     prk::SolveState* state = nullptr;
     double* slots = nullptr;
@@ -269,6 +276,11 @@ int small_grid(const pr_graph* g);
 cudaError_t enqueue_iteration(const pr_graph* g, const IterArgs& a, int src, bool uniform,
                               cudaStream_t s, int* launches);
 cudaError_t launch_segments(const pr_graph* g, const IterArgs& a, int src, cudaStream_t s, int* launches);
+// Edge-centric iteration (Alg. 2): its out-edge list, built on first use, and
+// one iteration reading buffer src.
+pr_status ensure_edge(pr_graph* g, cudaStream_t s);
+cudaError_t enqueue_edge_iteration(const pr_graph* g, const IterArgs& a, int src, bool uniform, cudaStream_t s,
+                                   int* launches);
 // Tile list of the layout for another heavy threshold (>= the layout's own),
 // and the number of rows at or above it.
 std::vector<Tile> tiles_with_threshold(const pr_graph* g, int heavy_degree, int64_t* heavy_rows,

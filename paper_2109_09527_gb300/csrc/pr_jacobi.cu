@@ -625,6 +625,7 @@ int small_grid(const pr_graph* g) {
 template <typename IdxT>
 cudaError_t enqueue_iteration_t(const pr_graph* g, const IterArgs& a, int src, bool uniform,
                                 cudaStream_t s, int* launches) {
+    if (a.edge) return enqueue_edge_iteration(g, a, src, uniform, s, launches);
     const size_t hot = (size_t)a.hot_n * sizeof(float);
     const size_t rows_smem = hot + (a.staged ? (size_t)kStageFloats * sizeof(float) : 0);
     if (g->n_seg > 0) {
@@ -852,11 +853,15 @@ pr_status check_solve_args(pr_graph* g, float damping, double tol, int32_t max_i
 }
 
 // Shared body of pr_solve (Jacobi) and pr_iterate.
+// edge: the edge-centric form of the iteration (Alg. 2, pr_edge.cu), run by
+// the host-driven loop.
 pr_status run_jacobi(pr_graph* g, float damping, double tol, int32_t max_iter, const float* teleport,
                      const float* x0, float* x_out, bool renormalise, bool allow_graph, pr_info* info,
-                     cudaStream_t s) {
+                     cudaStream_t s, bool edge = false) {
     pr_status rc = ensure_stage(g);
     if (rc != PR_OK) return rc;
+    if (edge && (rc = ensure_edge(g, s)) != PR_OK) return rc;
+    if (edge) allow_graph = false;
     const float* t_dev = nullptr;
     const float* x0_dev = nullptr;
     if ((rc = stage_input(g, teleport, 0, s, &t_dev)) != PR_OK) return rc;
@@ -878,6 +883,11 @@ pr_status run_jacobi(pr_graph* g, float damping, double tol, int32_t max_iter, c
     PRK_CHECK(cudaMemcpyAsync(g->state, hs, sizeof(SolveState), cudaMemcpyHostToDevice, s));
 
     IterArgs a = make_args(g, uniform);
+    if (edge) {
+        a.edge = 1;
+        a.out_src = g->out_src;
+        a.out_pos = g->out_pos;
+    }
     int launches = 0;
     launch_init(g, a, t_dev, x0_dev, s);
     ++launches;
@@ -972,7 +982,10 @@ extern "C" pr_status pr_solve(pr_graph* g, float damping, double tol, int32_t ma
     if (variant == PR_NONBLOCKING)
         return solve_nonblocking(g, damping, tol, max_iter, teleport, x0, x_out, info,
                                  (cudaStream_t)stream);
-    return fail(PR_ERR_INVALID_ARG, "variant must be PR_JACOBI or PR_NONBLOCKING");
+    if (variant == PR_EDGE)
+        return run_jacobi(g, damping, tol, max_iter, teleport, x0, x_out, true, false, info,
+                          (cudaStream_t)stream, true);
+    return fail(PR_ERR_INVALID_ARG, "variant must be PR_JACOBI, PR_NONBLOCKING or PR_EDGE");
 }
 
 extern "C" pr_status pr_iterate(pr_graph* g, float damping, const float* teleport, const float* x_in,

@@ -238,6 +238,57 @@ def test_nonblocking_recovers_from_a_failing_block(fail_after):
     assert max_rel(x, xstar) <= 1e-4
 
 
+@pytest.mark.parametrize("build", ["rmat12", "rmat12_heavy64", "er", "cycle", "in_star"])
+def test_edge_centric_variant_matches_jacobi_and_oracle(build):
+    """Barriers-Edge (Alg. 2, PR_EDGE): the same synchronous iterates as the vertex form up to
+    FP32 rounding -- against the oracle in matching mode, against PR_JACOBI, with a uniform
+    and a personalised teleport, on the default layout and with heavy threshold 64."""
+    heavy = pr.DEFAULT_HEAVY_DEGREE
+    if build == "rmat12":
+        rp, ci = gg.rmat(12, seed=4)
+    elif build == "rmat12_heavy64":
+        rp, ci = gg.rmat(12, seed=5)
+        heavy = 64
+    elif build == "er":
+        rp, ci = gg.er_dangling(20001, seed=7)
+    elif build == "cycle":
+        rp, ci = gg.cycle(37)
+    else:
+        rp, ci = gg.in_star(3001)
+    n = rp.size - 1
+    t = (gg.uniform(8, 3, n) + 0.05).astype(np.float32)
+    t /= t.sum()
+    pr.set_heavy_degree(heavy)
+    try:
+        g = pr.Graph(rp, ci)
+    finally:
+        pr.set_heavy_degree(pr.DEFAULT_HEAVY_DEGREE)
+    with g:
+        for tt in (None, t):
+            xj, ij = g.solve(tol=1e-6, max_iter=300, variant="jacobi", teleport=tt)
+            xe, ie = g.solve(tol=1e-6, max_iter=300, variant="edge", teleport=tt)
+            assert ie.converged == 1 and abs(ie.iterations - ij.iterations) <= 1, (ie.iterations, ij.iterations)
+            assert max_rel(xe, xj) <= 1e-5
+            xo = matching(rp, ci, xe, ie, t=None if tt is None else tt.astype(np.float64))
+            assert l1(xe, xo) <= 1e-6 and max_rel(xe, xo) <= 1e-4
+            assert ie.edge_visits == ie.iterations * ci.size
+
+
+def test_edge_centric_variant_needs_32_bit_offsets():
+    rp, ci = gg.rmat(10, seed=2)
+    pr.pr_set_option(None, pr.PR_OPT_INDEX64, 1)
+    try:
+        g = pr.Graph(rp, ci)
+    finally:
+        pr.pr_set_option(None, pr.PR_OPT_INDEX64, 0)
+    with g:
+        with pytest.raises(pr.PageRankError) as e:
+            g.solve(variant="edge")
+        assert e.value.status == pr.PR_ERR_UNSUPPORTED
+        x, info = g.solve(variant="jacobi")
+        assert info.converged == 1
+
+
 def test_nonblocking_budget_of_one_sweep_returns():
     rp, ci = gg.rmat(12, seed=5)
     with pr.Graph(rp, ci) as g:
