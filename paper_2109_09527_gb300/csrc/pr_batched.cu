@@ -23,9 +23,10 @@
 //   k_b_segments  heavy rows: a warp per 2048-edge segment sums 32 rows of Y
 //                 per step (32 independent 128-byte loads in flight per
 //                 warp) into a partial row P(segment, :);
-//   k_b_light     light rows: a warp per row tile walks the tile's edges in
-//                 windows of 16 (one colidx load, then 16 independent row
-//                 loads), closing a row of S at each row end;
+//   k_b_light     light rows: a warp per task (rows of one degree class, at
+//                 most kBTaskEdges edges) walks the task's edges in windows
+//                 of 16 (one colidx load, then 16 independent row loads),
+//                 closing a row of S at each row end;
 //   k_b_update    four rows per warp over the n x 32 matrix: the update, the
 //                 quotient, and per-column Kahan dangling mass and L1 change,
 //                 reduced in a fixed block order by the last block, which
