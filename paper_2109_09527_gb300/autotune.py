@@ -15,6 +15,8 @@ Every candidate is timed by the library itself (CUDA events around `iterations`
 synchronous updates, `pr_info.ms_loop`), after one untimed warm-up run; the result is a
 dict of the winning options and the measured times of every candidate.  `build_tuned`
 builds a graph with a result, `apply` sets its launch options on a built graph.
+`tune_batched` does the same for the batched solver's row binning (its k-tile is fixed at
+32 columns, one 128-byte row per gathered edge).
 """
 from __future__ import annotations
 
@@ -85,6 +87,36 @@ def tune(rowptr, colidx, iterations: int = 6, damping: float = 0.85,
     finally:
         for gg in graphs.values():
             gg.close()
+    best["trials"] = trials
+    return best
+
+
+def tune_batched(rowptr, colidx, teleport, k: int, damping: float = 0.85, tol: float = 1e-6,
+                 heavy=HEAVY_CANDIDATES) -> dict:
+    """Time the batched solver (pr_solve_batched with these k teleport columns, n x k row-major,
+    host or device) on this graph under each heavy threshold -- the row binning of its
+    gathers: rows at or above it are walked in 2048-edge segments, the rest as light-row
+    tasks -- one untimed warm-up solve each, and keep the fastest.  The k-tile is fixed: one
+    gathered row of the batched matrices is always 32 columns (128 bytes), so fewer
+    columns per solve would move the same bytes.  Returns {"heavy_degree",
+    "ms_per_solve", "trials"}."""
+    import numpy as np
+    n = (rowptr.shape[0] if hasattr(rowptr, "shape") else len(rowptr)) - 1
+    trials = []
+    best = {"heavy_degree": DEFAULT_HEAVY_DEGREE, "ms_per_solve": float("inf")}
+    out = np.empty((n, k), dtype=np.float32)
+    for h in heavy:
+        set_heavy_degree(h)
+        try:
+            g = Graph(rowptr, colidx)
+        finally:
+            set_heavy_degree(DEFAULT_HEAVY_DEGREE)
+        with g:
+            g.solve_batched(k, teleport, damping=damping, tol=tol, out=out)     # warm-up
+            _, info, _, _ = g.solve_batched(k, teleport, damping=damping, tol=tol, out=out)
+        trials.append({"heavy_degree": h, "ms": info.ms_device, "iterations": info.iterations})
+        if info.ms_device < best["ms_per_solve"]:
+            best.update(heavy_degree=h, ms_per_solve=info.ms_device)
     best["trials"] = trials
     return best
 

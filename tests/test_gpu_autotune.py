@@ -35,3 +35,25 @@ def test_tune_picks_a_timed_candidate_and_the_tuned_graph_is_correct():
         assert g.stats()["n_heavy"] >= 0
     assert info.converged == 1
     assert float(np.abs(x.astype(np.float64) - xstar).sum()) <= info.residual_l1 / 0.15 + 2e-7
+
+
+def test_tune_batched_picks_a_timed_threshold_and_solves_correctly():
+    from paper_2109_09527_gb300 import autotune
+    rp, ci = gg.rmat(13, 16, seed=13)
+    n = rp.size - 1
+    t = gg.seed_teleports(n, 8, 8, seed=13)
+    res = autotune.tune_batched(rp, ci, t, 8, heavy=(64, 256, 1024))
+    assert [tr["heavy_degree"] for tr in res["trials"]] == [64, 256, 1024]
+    assert all(tr["ms"] > 0 for tr in res["trials"])
+    assert res["ms_per_solve"] == min(tr["ms"] for tr in res["trials"])
+    pr.set_heavy_degree(res["heavy_degree"])
+    try:
+        g = pr.Graph(rp, ci)
+    finally:
+        pr.set_heavy_degree(pr.DEFAULT_HEAVY_DEGREE)
+    with g:
+        xb, info, res_cols, its = g.solve_batched(8, t, tol=1e-6)
+    assert info.converged == 1
+    for j in range(8):
+        xj, _, _ = oracle.fixed_point(rp, ci, d=0.85, t=t[:, j].astype(np.float64))
+        assert float(np.abs(xb[:, j] - xj).sum()) <= res_cols[j] / 0.15 + 2e-7, j
