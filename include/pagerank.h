@@ -11,7 +11,7 @@
  * t = 1/n and no dangling term; the dangling share is this library's reading
  * (mass is conserved: sum(x) = sum(t)).
  *
- * Two solvers run the same update:
+ * Three solvers run the same update:
  *   PR_JACOBI       the synchronous iteration of Alg. 1 (Barrier baseline):
  *                   every vertex is recomputed from the previous vector, the
  *                   dangling mass and the L1 change ||x_k - x_{k-1}||_1 are
@@ -165,7 +165,8 @@ PR_API pr_status pr_destroy_graph(pr_graph* g);
  *                 that sum(x_out) = sum(teleport) (1 when uniform).
  *   info          may be NULL; filled after the stream is synchronised.
  * Returns PR_OK, or PR_NOT_CONVERGED when the budget ran out (x_out and info
- * are written in both cases). */
+ * are written in both cases); PR_ERR_DEVICE_TIMEOUT if a bounded wait of the
+ * pipelined row kernel gave up (see PR_OPT_TEST_WITHHOLD_COPY). */
 PR_API pr_status pr_solve(pr_graph* g, float damping, double tol, int32_t max_iter, int variant,
                           const float* teleport, const float* x0, float* x_out, pr_info* info,
                           void* stream);
