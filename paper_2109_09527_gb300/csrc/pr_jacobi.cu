@@ -817,7 +817,7 @@ pr_status alloc_solver(pr_graph* g) {
         g_occ_rows_staged = std::max(1, occ);
         PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rows<int32_t, false, false, false>, kIterBlock, 0));
         // the pipelined kernel: shared memory for kTmaMinBlocks blocks of
-        // kTmaSmemBytes each (plus the 1 KB the driver reserves per block),
+        // kTmaSmemBytes each (plus the 1 KB the CUDA driver reserves per block),
         // the rest of the SRAM to L1
         const void* tma_kernels[] = {(const void*)k_rows_tma<true>, (const void*)k_rows_tma<false>};
         const int carve = (int)std::min<int64_t>(

@@ -407,7 +407,7 @@ void* pick_kernel(const pr_graph* g, bool uniform, bool staged, bool trace) {
 }
 
 // Blocks of `kernel` that fit on one SM with `smem` bytes of dynamic shared
-// memory (cached per kernel and size).  The carveout is left to the driver:
+// memory (cached per kernel and size).  The carveout is left to the CUDA driver:
 // asking for a small shared-memory carveout measured slower (the offsets and
 // tile metadata the kernel reads live in L1).
 pr_status nb_occupancy(const void* kernel, size_t smem, int* occ) {

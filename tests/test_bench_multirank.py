@@ -86,3 +86,15 @@ def test_reference_arm_json_line_on_a_small_graph():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
+
+
+def test_recorded_traffic_follows_the_kernel_code_not_its_comments():
+    """The committed DRAM-traffic figures apply while the kernel sources' code is the
+    code that was captured: the sha ignores comments and layout, not code or literals."""
+    sys.path.insert(0, ROOT)
+    import bench
+    a = "int f(int x) { return x + 1; }  // one\n/* block */ const char* s = \"// kept\";\n"
+    b = "/* other */ int f(int x) {\n  return x + 1;  // two\n}\nconst char* s = \"// kept\";"
+    assert bench._code_only(a) == bench._code_only(b)
+    assert bench._code_only(a) != bench._code_only(a.replace("x + 1", "x + 2"))
+    assert bench._code_only(a) != bench._code_only(a.replace("// kept", "// gone"))
