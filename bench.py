@@ -885,6 +885,61 @@ def run_adjoint(args):
     return 0
 
 
+def run_ceiling(args):
+    """The gather ceiling of this GPU: random 4-byte loads from a 2^24-float (64 MB,
+    L2-resident) vector, 16 independent loads in flight per lane, indices streamed in
+    16-byte vectors (pr_measure_gather_rate).  Four configurations: loads bypassing L1
+    (ld.global.cg) or through it (ld.global.nc), at 4 and 8 resident blocks per SM; each
+    timed --steps times, the median kept.  value = the best L1-bypassing rate in loads per
+    SM-cycle at the median SM clock sampled meanwhile: every gather that misses L1 costs one
+    such load, which bounds any pull-gather iteration whose quotient vector fits in L2."""
+    import torch
+
+    import paper_2109_09527_gb300 as pr
+    rank, local_rank, world = dist_env()
+    if rank != 0:
+        return 0   # a property of one GPU: rank 0 alone measures it
+    torch.cuda.set_device(local_rank)
+    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    n_values, n_indices, chunks = 1 << 24, 1 << 27, 4096
+    configs = [(cached, bps) for cached in (0, 1) for bps in (4, 8)]
+    stream = torch.cuda.current_stream()
+    for cached, bps in configs:
+        for _ in range(args.warmup):
+            pr.pr_measure_gather_rate(n_values, n_indices, cached, bps, 256, seed=1, stream=stream)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    t0 = time.perf_counter()
+    samples = {c: [] for c in configs}
+    for _ in range(args.steps):
+        for cached, bps in configs:
+            r = pr.pr_measure_gather_rate(n_values, n_indices, cached, bps, chunks, seed=1, stream=stream)
+            samples[(cached, bps)].append(r)
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    mhz = clocks.get("sm_mhz") or 2070.0
+    rows = []
+    for (cached, bps), rs in samples.items():
+        rate = statistics.median(r["gathers_per_s"] for r in rs)
+        rows.append({"loads": "ld.global.nc (L1)" if cached else "ld.global.cg (L2 only)",
+                     "blocks_per_sm": bps, "loads_per_s": rate,
+                     "ms_per_launch": statistics.median(r["ms"] for r in rs),
+                     "loads_per_launch": rs[0]["gathers"],
+                     "loads_per_sm_cycle": rate / (sms * mhz * 1e6)})
+    best = max(r["loads_per_sm_cycle"] for r in rows if r["loads"].startswith("ld.global.cg"))
+    line = {"metric": "random 4-byte loads per SM-cycle from an L2-resident 64 MB vector",
+            "value": best, "unit": "loads/SM-cycle", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "wall_s": wall, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "gather ceiling: 2^24-float vector, 2^27 SplitMix64 indices "
+                                   "(512 MB, streamed), 16 loads in flight per lane",
+                       "sms": sms, "clock_mhz_used": mhz},
+            "rows": rows, "clocks": clocks,
+            "gpu_launches": len(configs) * args.steps * 3}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -898,9 +953,11 @@ def main():
     ap.add_argument("--profile", choices=["jacobi", "nonblocking", "batched", "set", "adjoint"], default=None,
                     help="run a short fixed workload for a profiler instead of the benchmark")
     ap.add_argument("--graph", choices=["rmat", "er"], default="rmat")
-    ap.add_argument("--workload", choices=["pagerank", "batched", "set", "adjoint", "edge"], default="pagerank",
+    ap.add_argument("--workload", choices=["pagerank", "batched", "set", "adjoint", "edge", "ceiling"],
+                    default="pagerank",
                     help="batched: 32 personalised PageRank vectors on R-MAT-22; set: 64 R-MAT "
-                         "graphs of 1e3..1e6 vertices in one solve (each its own JSON line)")
+                         "graphs of 1e3..1e6 vertices in one solve; ceiling: the random-gather "
+                         "rate that bounds a pull gather (each its own JSON line)")
     args = ap.parse_args()
     if args.profile == "batched":
         return run_profile_batched(args)
@@ -920,6 +977,8 @@ def main():
         return run_adjoint(args)
     if args.workload == "edge":
         return run_edge(args)
+    if args.workload == "ceiling":
+        return run_ceiling(args)
 
     import numpy as np
     import torch

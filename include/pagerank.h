@@ -448,6 +448,36 @@ PR_API pr_status pr_step_noalloc(int64_t n, const int32_t* rowptr, const int32_t
                                  const float* inv_outdeg, float damping, const float* x_in,
                                  float* x_out, double* sums_out, void* stream);
 
+/* ---- Diagnostics: the gather ceiling ---------------------------------------
+ *
+ * pr_measure_gather_rate times random 4-byte loads from a float vector, the
+ * operation that dominates every pull gather of Eq. 1 (one load of
+ * y(colidx[e]) per in-edge e), without a graph.  Warps stream random indices
+ * in 16-byte vectors and keep 16 independent loads in flight per lane.  With
+ * a vector that stays in L2 (n_values = 2^24, 64 MB) the result is the rate
+ * at which the SMs can send L1 misses to L2, which bounds the iteration of
+ * any pull-gather kernel on a graph whose quotient vector fits in L2.
+ *   n_values       length of the gathered vector, in [1, 2^31 - 1].
+ *   n_indices      random indices drawn on the device (SplitMix64 of
+ *                  seed + i, modulo n_values); a multiple of 512 in
+ *                  [1024, 2^31 - 1].  Warps wrap around them.
+ *   cached         0: loads bypass L1 (ld.global.cg); 1: loads through L1
+ *                  (ld.global.nc).
+ *   blocks_per_sm  resident 256-thread blocks per SM, in [1, 8]; more than
+ *                  fit on an SM returns PR_ERR_INVALID_ARG.
+ *   chunks         512-index chunks each warp gathers in the timed launch, in
+ *                  [1, 65536]; the launch makes
+ *                  SMs x blocks_per_sm x 256 x 16 x chunks loads.
+ *   out            host, 3 doubles: [0] loads per second, [1] milliseconds
+ *                  of the timed launch (CUDA events on `stream`), [2] loads.
+ * The call allocates its own device buffers (4 n_values + 4 n_indices bytes
+ * and a small sink), runs one untimed warm-up launch, times one launch,
+ * synchronises `stream` and frees the buffers.  Arguments are checked before
+ * any CUDA call. */
+PR_API pr_status pr_measure_gather_rate(int64_t n_values, int64_t n_indices, int cached,
+                                        int blocks_per_sm, int32_t chunks, uint64_t seed,
+                                        double* out, void* stream);
+
 /* Static text for a status code. */
 PR_API const char* pr_status_string(pr_status s);
 

@@ -114,6 +114,8 @@ SIGNATURES = {
     "pr_adjoint": (ctypes.c_int, [_VP, _F, _D, _I32, _VP, _VP, _VP, _VP, ctypes.POINTER(pr_info), _VP]),
     "pr_solve_set": (ctypes.c_int, [_VP, _F, _D, _I32, _VP, ctypes.POINTER(_D), ctypes.POINTER(_I32),
                                     ctypes.POINTER(pr_info), _VP]),
+    "pr_measure_gather_rate": (ctypes.c_int, [_I64, _I64, ctypes.c_int, ctypes.c_int, _I32,
+                                              ctypes.c_uint64, ctypes.POINTER(_D), _VP]),
     "pr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pr_last_error": (ctypes.c_char_p, []),
 }
@@ -270,6 +272,15 @@ def pr_step_noalloc(n, rowptr, colidx, inv_outdeg, damping, x_in, x_out, sums_ou
                                          _addr(inv_outdeg, np.float32), float(damping),
                                          _addr(x_in, np.float32), _addr(x_out, np.float32),
                                          _addr(sums_out), _stream(stream)))
+
+
+def pr_measure_gather_rate(n_values, n_indices, cached, blocks_per_sm, chunks, seed=1, stream=None):
+    """Random 4-byte loads per second from an n_values-float vector (see the header):
+    returns {"gathers_per_s", "ms", "gathers"} of one timed launch."""
+    out = (_D * 3)()
+    _check(load().pr_measure_gather_rate(int(n_values), int(n_indices), int(cached), int(blocks_per_sm),
+                                         int(chunks), int(seed), out, _stream(stream)))
+    return {"gathers_per_s": out[0], "ms": out[1], "gathers": out[2]}
 
 
 def pr_status_string(status):

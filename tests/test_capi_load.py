@@ -72,6 +72,20 @@ def test_argument_errors_return_status_without_a_gpu():
     assert lib.pr_iterate(None, 0.85, None, x, 1, x, ctypes.byref(info), None) == pr.PR_ERR_INVALID_ARG
     assert lib.pr_destroy_graph(None) == pr.PR_OK
     assert lib.pr_graph_get_stats(None, None) == pr.PR_ERR_INVALID_ARG
+    # the gather-rate diagnostic checks every argument before touching CUDA
+    res = (ctypes.c_double * 3)()
+    bad = [(1 << 24, 1 << 20, 0, 4, 4, None),      # no output array
+           (0, 1 << 20, 0, 4, 4, res),             # empty vector
+           (1 << 24, 1000, 0, 4, 4, res),          # indices not a multiple of 512
+           (1 << 24, 512, 0, 4, 4, res),           # fewer than two chunks
+           (1 << 24, 1 << 20, 2, 4, 4, res),       # cached not 0/1
+           (1 << 24, 1 << 20, 0, 0, 4, res),       # no blocks
+           (1 << 24, 1 << 20, 0, 9, 4, res),       # more than 8 blocks per SM
+           (1 << 24, 1 << 20, 0, 4, 0, res),       # no chunks
+           (1 << 24, 1 << 20, 0, 4, 65537, res)]   # too many chunks
+    for nv, ni, cached, bps, chunks, o in bad:
+        assert lib.pr_measure_gather_rate(nv, ni, cached, bps, chunks, 1, o, None) == pr.PR_ERR_INVALID_ARG
+        assert "pr_measure_gather_rate" in pr.pr_last_error()
 
 
 def test_options_validate_host_side():
