@@ -98,3 +98,48 @@ def test_recorded_traffic_follows_the_kernel_code_not_its_comments():
     assert bench._code_only(a) == bench._code_only(b)
     assert bench._code_only(a) != bench._code_only(a.replace("x + 1", "x + 2"))
     assert bench._code_only(a) != bench._code_only(a.replace("// kept", "// gone"))
+
+
+def test_roofline_arithmetic_on_synthetic_records():
+    """The roofline object from per-solve records: algorithmic bytes per launch (B of a full
+    sweep, scaled by the edges a launch gathered), achieved = bytes / loop time, traffic =
+    recorded bytes per gathered edge x edges per launch, and the dominant kernel = the
+    variant with the larger share of solve time, reported on the R-MAT graph."""
+    sys.path.insert(0, ROOT)
+    import bench
+    n, nnz = 1 << 24, 263_429_870
+    st = {"n": n, "nnz": nnz, "rowptr_bytes": 4, "n_tma_tiles": 10}
+    resident = [("rmat24", None, st), ("er24", None, dict(st, n_tma_tiles=0))]
+    recs = []
+    for g in ("rmat24", "er24"):
+        # Jacobi: 19 iterations of nnz edges each, 0.9 ms apiece; barrier-free: one launch
+        # that gathered 15.5 sweeps' worth of edges in 14 ms
+        recs.append({"graph": g, "variant": "jacobi", "iterations": 19, "loop_ms": 19 * 0.9,
+                     "loop_edge_visits": 19.0 * nnz, "time_to_tol_ms": 17.0})
+        recs.append({"graph": g, "variant": "nonblocking", "iterations": 17, "loop_ms": 14.0,
+                     "loop_edge_visits": 15.5 * nnz, "time_to_tol_ms": 16.0})
+    roof, rows = bench.rooflines(recs, resident)
+    B = bench.algorithmic_bytes(n, nnz, 4)
+    assert B == 4 * nnz + 4 * (n + 1) + 20 * n
+    by = {(r["graph"], r["variant"]): r for r in rows}
+    j = by[("rmat24", "jacobi")]
+    assert j["launches"] == 19
+    assert j["bytes_per_launch"] == pytest.approx(B)
+    assert j["achieved"] == pytest.approx(B / 0.9e-3 / 1e9)
+    assert j["frac"] == pytest.approx(j["achieved"] / j["peak"])
+    assert "k_rows_tma" in j["kernel"] and "k_rows_tma" not in by[("er24", "jacobi")]["kernel"]
+    nb = by[("rmat24", "nonblocking")]
+    assert nb["launches"] == 1
+    assert nb["bytes_per_launch"] == pytest.approx(15.5 * B)
+    assert nb["achieved"] == pytest.approx(15.5 * B / 14e-3 / 1e9)
+    for (g, v), r in by.items():
+        per_edge = bench.recorded_traffic(v) if g.startswith("rmat") else None
+        if per_edge is None:
+            assert r["traffic"] is None
+        else:
+            assert r["traffic"] == pytest.approx(per_edge * r["bytes_per_launch"] / B * nnz)
+    # Jacobi holds 34 of the 66 ms of solve time: it is the dominant kernel
+    assert roof["kernel"].startswith("jacobi iteration") and roof["kernel"].endswith("on rmat24")
+    assert roof["share_of_step"] == pytest.approx(34.0 / 66.0)
+    assert roof["achieved"] == pytest.approx(j["achieved"]) and roof["traffic"] == j["traffic"]
+    assert set(roof) >= {"bound", "achieved", "peak", "unit", "frac", "traffic"}
