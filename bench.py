@@ -130,9 +130,15 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.t.join(timeout=2)
+        return self.summarise(self.lines)
+
+    @staticmethod
+    def summarise(lines):
+        """Median and maximum SM clock and the throttle reasons seen in nvidia-smi CSV lines
+        (the FIELDS above, no header, no units)."""
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 8:
                 continue
@@ -151,7 +157,7 @@ class ClockSampler:
 
 
 # Sources each timed kernel family is compiled from: a recorded ncu traffic figure is
-# used only while these files are unchanged.
+# used only while the code in these files (comments aside) is unchanged.
 KERNEL_SOURCES = {
     "jacobi": ["pr_common.cuh", "pr_tile.cuh", "pr_jacobi.cu"],
     "nonblocking": ["pr_common.cuh", "pr_tile.cuh", "pr_nonblocking.cu"],

@@ -143,3 +143,22 @@ def test_roofline_arithmetic_on_synthetic_records():
     assert roof["share_of_step"] == pytest.approx(34.0 / 66.0)
     assert roof["achieved"] == pytest.approx(j["achieved"]) and roof["traffic"] == j["traffic"]
     assert set(roof) >= {"bound", "achieved", "peak", "unit", "frac", "traffic"}
+
+
+def test_clock_samples_summary():
+    """nvidia-smi lines (csv, noheader, nounits) -> median SM clock, the maximum clock and
+    every throttle reason seen Active; malformed lines are skipped."""
+    sys.path.insert(0, ROOT)
+    import bench
+    lines = ["2070, 2070, 812.33, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+             "1980, 2070, 1390.02, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+             "2070, 2070, 901.50, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+             "garbage",
+             "[N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    c = bench.ClockSampler.summarise(lines)
+    assert c["sm_mhz"] == 2070.0 and c["sm_max_mhz"] == 2070.0 and c["samples"] == 3
+    assert c["reasons"] == ["sw_power_cap"]
+    hot = lines[:1] + ["1500, 2070, 1200.0, 0x0000000000000048, Active, Active, Not Active, Not Active"]
+    c = bench.ClockSampler.summarise(hot)
+    assert c["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"] and c["sm_mhz"] == 1785.0
+    assert bench.ClockSampler.summarise([])["reasons"] == ["no samples"]
