@@ -18,6 +18,7 @@ header; in short:
 * :func:`vertex_update`     -- one vertex's update from a given vector.
 * :func:`dense_solve`       -- the fixed point by Gaussian elimination.
 * :func:`nosync`            -- Alg. 3 (No-Sync) with simulated threads.
+* :func:`nosync_perforated` -- the same with the loop perforation of Alg. 5.
 * :func:`fixed_point`       -- Alg. 1 run until the change stops shrinking.
 """
 from __future__ import annotations
@@ -72,7 +73,7 @@ def _declare(lib):
     lib.or_w_adjoint.argtypes = [i64, vp, vp, vp, dbl, vp, vp, dbl, i32, vp, vp, vp, vp, vp, vp]
     lib.or_nosync.restype = ctypes.c_int
     lib.or_nosync.argtypes = [i64, vp, vp, dbl, vp, ctypes.c_int, ctypes.c_int, i32, vp,
-                              ctypes.c_int, dbl, i32, vp, vp, vp, vp, vp]
+                              ctypes.c_int, dbl, i32, vp, vp, vp, vp, vp, dbl, vp]
     return lib
 
 
@@ -208,6 +209,19 @@ def nosync(rowptr, colidx, d=0.85, p=4, tol=1e-10, max_sweeps=1000, t=None, x0=N
     """Alg. 3 with p simulated threads.  ``dangling`` picks the form of the dangling share:
     "mass" (running dangling mass D) or "complement" (sum(t) minus the running mass of the
     vertices with out-edges).  Returns (x, sweeps_per_thread, updates, estimate)."""
+    x, sweeps, upd, est, _ = nosync_perforated(rowptr, colidx, d=d, p=p, tol=tol,
+                                               max_sweeps=max_sweeps, t=t, x0=x0, speed=speed,
+                                               norm=norm, redistribute=redistribute,
+                                               dangling=dangling, eps=0.0, lib=lib)
+    return x, sweeps, upd, est
+
+
+def nosync_perforated(rowptr, colidx, d=0.85, p=4, tol=1e-10, max_sweeps=1000, t=None, x0=None,
+                      speed=None, norm="l1", redistribute=True, dangling="complement", eps=0.0,
+                      lib=None):
+    """Alg. 3 with the loop perforation of Alg. 5: a vertex whose change is nonzero and below
+    eps is no longer recomputed (eps = 0: plain Alg. 3).  Returns (x, sweeps_per_thread,
+    updates_computed, estimate, frozen_count)."""
     if dangling not in ("mass", "complement"):
         raise ValueError("dangling must be 'mass' or 'complement'")
     lib = lib or load()
@@ -220,12 +234,13 @@ def nosync(rowptr, colidx, d=0.85, p=4, tol=1e-10, max_sweeps=1000, t=None, x0=N
         raise ValueError("speed needs one entry per thread")
     x = np.empty(n, dtype=np.float64)
     sweeps = np.zeros(p, dtype=np.int32)
-    upd, est = ctypes.c_int64(), ctypes.c_double()
+    upd, est, nf = ctypes.c_int64(), ctypes.c_double(), ctypes.c_int64()
     _check(lib.or_nosync(n, _p(rowptr), _p(colidx), d, _p(t), int(redistribute),
                          1 if dangling == "complement" else 0, p, _p(sp),
                          0 if norm == "l1" else 1, tol, max_sweeps, _p(x0), _p(x), _p(sweeps),
-                         ctypes.byref(upd), ctypes.byref(est)), "or_nosync")
-    return x, sweeps, upd.value, est.value
+                         ctypes.byref(upd), ctypes.byref(est), float(eps), ctypes.byref(nf)),
+           "or_nosync")
+    return x, sweeps, upd.value, est.value, nf.value
 
 
 # ------------------------------------------------------------ weighted graphs --

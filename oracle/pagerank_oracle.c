@@ -51,13 +51,20 @@
  *                      threads, static equal partitions, in-place updates,
  *                      thread-level convergence; two forms of the dangling
  *                      share (running dangling mass, or total minus the
- *                      running non-dangling mass).
+ *                      running non-dangling mass); with eps > 0 the loop
+ *                      perforation of Alg. 5, which the paper applies to
+ *                      its No-Sync variants as well (Section 4, the
+ *                      optimisation of the Barrier and No-Sync variants).
  *
  * Parity status: or_outdeg, or_jacobi_step, or_pagerank_jacobi,
  * or_vertex_update and or_dense_solve are pinned by closed forms, by the
  * random-surfer stationary distribution and by a library PageRank in the
  * CPU test suite; or_nosync is pinned by Lemma 2 (same fixed point) and by
- * its single-thread case, Gauss-Seidel.  or_w_jacobi is pinned by unit
+ * its single-thread case, Gauss-Seidel.  Perforation (or_pagerank_perforated,
+ * or_nosync with eps > 0) is pinned by eps = 0 (plain Alg. 1 / Alg. 3), by
+ * eps = inf (every vertex frozen at its first update: exactly one Jacobi step,
+ * or one Gauss-Seidel sweep), and by a graph whose ranks never change (the
+ * directed cycle: nothing freezes).  or_w_jacobi is pinned by unit
  * weights (the unweighted oracle), by invariance under scaling one vertex's
  * out-weights, and by a dense solve; or_w_adjoint by the dense adjoint
  * (numpy linear algebra on explicit dM/dw matrices, n <= 12), by central
@@ -300,24 +307,32 @@ OR_API int or_dense_solve(int64_t n, const int64_t* rowptr, const int32_t* colid
  * has stopped does nothing.  The run ends when all threads have stopped or a
  * thread has done max_sweeps sweeps.
  *
+ * Loop perforation (eps > 0): a vertex whose update changed its rank by a
+ * nonzero amount below eps is frozen; its turn in later sweeps passes without
+ * recomputing it (it keeps its rank, which still feeds its out-neighbours and
+ * the shares, and adds nothing to its thread's error).  eps = 0 is plain
+ * Alg. 3.
+ *
  * Outputs: x (in place, initialised to t or x0), sweeps[p] (iterations per
- * thread), *updates (total vertex updates), *est (the final combined error). */
+ * thread), *updates (vertex updates actually computed), *est (the final
+ * combined error), *frozen_out (vertices frozen at the end; may be NULL). */
 OR_API int or_nosync(int64_t n, const int64_t* rowptr, const int32_t* colidx, double d,
                      const double* t, int redistribute, int dangling_form, int32_t p,
                      const int32_t* speed, int norm, double tol, int32_t max_sweeps,
                      const double* x0, double* x, int32_t* sweeps, int64_t* updates,
-                     double* est) {
+                     double* est, double eps, int64_t* frozen_out) {
     int rc = or_check_csr(n, rowptr, colidx);
     if (rc) return rc;
-    if (p < 1 || p > n || !(d >= 0.0 && d < 1.0) || max_sweeps < 1) return OR_BAD_ARG;
+    if (p < 1 || p > n || !(d >= 0.0 && d < 1.0) || max_sweeps < 1 || !(eps >= 0.0)) return OR_BAD_ARG;
     if (dangling_form != 0 && dangling_form != 1) return OR_BAD_ARG;
     int64_t* outdeg = (int64_t*)malloc((size_t)n * sizeof(int64_t));
     double* thread_err = (double*)malloc((size_t)p * sizeof(double));
     double* local_err = (double*)malloc((size_t)p * sizeof(double));
     int64_t* pos = (int64_t*)malloc((size_t)p * sizeof(int64_t));
     int* stopped = (int*)calloc((size_t)p, sizeof(int));
-    if (!outdeg || !thread_err || !local_err || !pos || !stopped) {
-        free(outdeg); free(thread_err); free(local_err); free(pos); free(stopped);
+    unsigned char* frozen = (unsigned char*)calloc((size_t)n, 1);
+    if (!outdeg || !thread_err || !local_err || !pos || !stopped || !frozen) {
+        free(outdeg); free(thread_err); free(local_err); free(pos); free(stopped); free(frozen);
         return OR_NO_MEM;
     }
     or_outdeg(n, rowptr, colidx, outdeg);
@@ -346,16 +361,20 @@ OR_API int or_nosync(int64_t n, const int64_t* rowptr, const int32_t* colidx, do
             int32_t steps = speed ? speed[i] : 1;
             for (int32_t s = 0; s < steps; ++s) {
                 int64_t u = pos[i];
-                double previous = x[u];
-                double share = !redistribute ? 0.0 : (dangling_form == 1 ? T - S : D);
-                double tmp = or_vertex_update(u, n, rowptr, colidx, outdeg, d, t, share, x);
-                x[u] = tmp;
-                if (outdeg[u] == 0) D += tmp - previous;
-                else S += tmp - previous;
-                double diff = fabs(tmp - previous);
+                double diff = 0.0;
+                if (!frozen[u]) {
+                    double previous = x[u];
+                    double share = !redistribute ? 0.0 : (dangling_form == 1 ? T - S : D);
+                    double tmp = or_vertex_update(u, n, rowptr, colidx, outdeg, d, t, share, x);
+                    x[u] = tmp;
+                    if (outdeg[u] == 0) D += tmp - previous;
+                    else S += tmp - previous;
+                    diff = fabs(tmp - previous);
+                    if (diff != 0.0 && diff < eps) frozen[u] = 1;
+                    ++total_updates;
+                }
                 if (norm == 0) local_err[i] += diff;
                 else if (diff > local_err[i]) local_err[i] = diff;
-                ++total_updates;
                 if (++pos[i] == hi) {                 /* end of a sweep */
                     pos[i] = lo;
                     sweeps[i] += 1;
@@ -374,7 +393,12 @@ OR_API int or_nosync(int64_t n, const int64_t* rowptr, const int32_t* colidx, do
     }
     if (updates) *updates = total_updates;
     if (est) *est = combined;
-    free(outdeg); free(thread_err); free(local_err); free(pos); free(stopped);
+    if (frozen_out) {
+        int64_t nf = 0;
+        for (int64_t v = 0; v < n; ++v) nf += frozen[v];
+        *frozen_out = nf;
+    }
+    free(outdeg); free(thread_err); free(local_err); free(pos); free(stopped); free(frozen);
     return OR_OK;
 }
 

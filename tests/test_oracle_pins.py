@@ -345,6 +345,23 @@ def _pins_pass(lib):
         xs, _, _, _ = oracle.nosync(rp2, ci2, d=d, p=3, tol=1e-13, lib=lib)
         if not np.allclose(xs, pi, atol=1e-11):
             return False
+        # loop perforation (Alg. 5): with eps = inf every vertex freezes after its first
+        # update, so the synchronous form is one Jacobi step and the No-Sync form one sweep;
+        # on the cycle nothing changes, so nothing may freeze
+        x1, _, _, _ = oracle.jacobi_step(rp2, ci2, np.full(9, 1 / 9), d=d, lib=lib)
+        xp, itp, rpf, nfp = oracle.pagerank_perforated(rp2, ci2, d=d, tol=1e-12, eps=np.inf, lib=lib)
+        if not (np.array_equal(xp, x1) and itp == 2 and rpf == 0.0 and nfp == 9):
+            return False
+        xg, _, _, _ = oracle.nosync(rp2, ci2, d=d, p=1, tol=1e-300, max_sweeps=1, lib=lib)
+        xq, swq, updq, estq, nfq = oracle.nosync_perforated(rp2, ci2, d=d, p=1, tol=1e-12,
+                                                            eps=np.inf, lib=lib)
+        if not (np.array_equal(xq, xg) and list(swq) == [2] and updq == 9 and nfq == 9):
+            return False
+        rpc, cic = gg.cycle(5)
+        if oracle.pagerank_perforated(rpc, cic, d=d, tol=1e-12, eps=np.inf, lib=lib)[3] != 0:
+            return False
+        if oracle.nosync_perforated(rpc, cic, d=d, p=2, tol=1e-12, eps=np.inf, lib=lib)[4] != 0:
+            return False
         # weighted forward and adjoint against the dense adjoint (numpy linear algebra)
         rp3, ci3 = gg.random_digraph(8, 16, seed=9)   # three dangling vertices
         w3 = 0.1 + 0.9 * gg.uniform(6, 1, ci3.size)
@@ -375,6 +392,12 @@ MUTATIONS = {
     "weighted_forward_ignores_weight": ("s += x[u] * w[e] / W[u];", "s += x[u] / W[u];"),
     "adjoint_drops_dangling_term": ("(W[u] == 0.0 ? L / (double)n : 0.0)", "0.0"),
     "adjoint_edge_gradient_sign": ("(lambda[v] - mu[u])", "(mu[u] - lambda[v])"),
+    "perforation_recomputes_frozen": ("if (frozen[v]) {", "if (0 && frozen[v]) {"),
+    "perforation_freezes_unchanged": ("if (change != 0.0 && change < eps) frozen[v] = 1;",
+                                      "if (change < eps) frozen[v] = 1;"),
+    "nosync_perforation_recomputes_frozen": ("if (!frozen[u]) {", "if (1) {"),
+    "nosync_perforation_freezes_unchanged": ("if (diff != 0.0 && diff < eps) frozen[u] = 1;",
+                                             "if (diff < eps) frozen[u] = 1;"),
     "adjoint_pushes_to_target": ("mu[u] += w[e] / W[u] * lambda[v];\n            }\n        r = 0.0;",
                                  "mu[v] += w[e] / W[u] * lambda[u];\n            }\n        r = 0.0;"),
 }
@@ -518,3 +541,39 @@ def test_perforation_freezes_and_stays_close():
     assert iters[1] < iters[0] <= it_plain
     assert errs[0] < errs[1]
     assert errs[0] < 1e-8 and errs[1] < 1e-5
+
+
+def test_perforation_with_infinite_eps_is_one_step():
+    """Alg. 5 with eps = inf freezes every vertex at its first update: the synchronous form
+    returns exactly one Jacobi step from t (its second iteration changes nothing), the No-Sync
+    form exactly one Gauss-Seidel sweep, and every vertex is computed once."""
+    rp, ci = gg.rmat(10, 16, seed=3)
+    n = rp.size - 1
+    x1, _, _ = oracle.pagerank_jacobi(rp, ci, tol=0, max_iter=1)
+    assert np.all(x1 != 1.0 / n)                 # every vertex changes in the first step
+    x, it, r, nf = oracle.pagerank_perforated(rp, ci, tol=1e-12, max_iter=50, eps=np.inf)
+    assert np.array_equal(x, x1) and it == 2 and r == 0.0 and nf == n
+    xg, _, upd_g, _ = oracle.nosync(rp, ci, p=1, tol=1e-300, max_sweeps=1)
+    xq, sw, upd, est, nfq = oracle.nosync_perforated(rp, ci, p=1, tol=1e-12, max_sweeps=50, eps=np.inf)
+    assert np.array_equal(xq, xg) and list(sw) == [2] and upd == upd_g == n and est == 0.0 and nfq == n
+    # several threads: each vertex is still computed exactly once, then all are frozen.  The
+    # threads finish their sweeps in the same rounds, in thread order, so at the end of its
+    # second (empty) sweep each thread but the last still sees a later thread's first-sweep
+    # error, and makes a third
+    xm, sw4, upd4, est4, nf4 = oracle.nosync_perforated(rp, ci, p=4, tol=1e-12, max_sweeps=50, eps=np.inf)
+    assert upd4 == n and nf4 == n and est4 == 0.0 and list(sw4) == [3, 3, 3, 2]
+
+
+def test_nosync_perforation_freezes_and_stays_close():
+    """No-Sync with perforation (the paper's No-Sync-Opt): vertices freeze as their changes
+    shrink, fewer updates are computed than by plain Alg. 3 to the same tolerance, and the
+    result stays close to the fixed point; eps = 0 is plain Alg. 3."""
+    rp, ci = gg.rmat(11, 16, seed=8)
+    xs, _, _ = oracle.fixed_point(rp, ci)
+    x0, sw0, upd0, _ = oracle.nosync(rp, ci, p=4, tol=1e-10)
+    xz, swz, updz, _, nfz = oracle.nosync_perforated(rp, ci, p=4, tol=1e-10, eps=0.0)
+    assert nfz == 0 and updz == upd0 and np.array_equal(xz, x0)
+    x, sw, upd, est, nf = oracle.nosync_perforated(rp, ci, p=4, tol=1e-10, eps=1e-12)
+    assert nf > 0 and upd < upd0 and est <= 1e-10
+    assert float(np.abs(x - xs).sum()) < 1e-8
+    assert float(np.abs(x0 - xs).sum()) < float(np.abs(x - xs).sum()) + 1e-9
