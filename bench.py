@@ -305,7 +305,6 @@ def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
         return 0
-    import graphgen  # noqa: F401
     import oracle
     graphs = make_graphs(args.scale, 1 << args.er_log2)
     name, (rp, ci) = graphs[0]

@@ -9,8 +9,6 @@ The last test compiles deliberately broken copies of the oracle and checks that 
 plausible mistake (dropped term, wrong sign, transposed operand) fails a pin.
 """
 import os
-import re
-import subprocess
 from fractions import Fraction
 
 import numpy as np
