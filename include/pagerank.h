@@ -435,15 +435,18 @@ PR_API pr_status pr_adjoint(pr_wgraph* g, float damping, double tol, int32_t max
  *                2048 rows); larger n returns PR_ERR_INVALID_ARG.
  *   rowptr       device, n+1 int32 offsets; colidx device, int32 sources.
  *   inv_outdeg   device, n floats: 1/outdeg(u), or 0 for dangling u.
- *   x_in, x_out  device, n floats each; must be different buffers.
+ *   x_in, x_out  device, n floats each; the two ranges must not overlap
+ *                (any shared element returns PR_ERR_INVALID_ARG).
  *   sums_out     device, 3 doubles: [0] dangling mass of x_in, [1] dangling
  *                mass of x_out, [2] ||x_out - x_in||_1.
  * The call is asynchronous on `stream` and does not validate the CSR.
  * Scratch lives in one fixed device array (about 128 KiB) that the library
  * keeps on every GPU that loads it, until the process exits; all calls share
- * it, so calls that overlap on the GPU race -- serialise them.  The first call
- * on a device looks up that array's address (cudaGetSymbolAddress); make it
- * before any stream capture. */
+ * it, so calls that overlap on the GPU race -- serialise them.  Every call
+ * looks up that array's address on the current device (cudaGetSymbolAddress,
+ * which allocates nothing), so a cudaDeviceReset between calls is safe; the
+ * first call on a device, and the first after a reset, loads the module:
+ * make it before any stream capture. */
 PR_API pr_status pr_step_noalloc(int64_t n, const int32_t* rowptr, const int32_t* colidx,
                                  const float* inv_outdeg, float damping, const float* x_in,
                                  float* x_out, double* sums_out, void* stream);

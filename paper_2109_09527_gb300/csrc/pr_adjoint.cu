@@ -157,7 +157,6 @@ __global__ void __launch_bounds__(kBlock) k_w_forward(WArgs a, const float* __re
     const float d = (float)s_d;
     const float share = (float)(s_D * s_inv_n);
     const float tu = (float)s_inv_n;
-    float r = 0.f;
     Acc acc;
     w_rows(a.in_order, a.n, a.n_in_giant, a.n_in_heavy,
            [&](int32_t v, int l, int g) { return w_gather(a.rowptr, a.colidx, a.in_p, x, v, l, g); },
@@ -165,11 +164,11 @@ __global__ void __launch_bounds__(kBlock) k_w_forward(WArgs a, const float* __re
                const float tv = t ? t[v] : tu;
                const float xn = fmaf(1.f - d, tv, d * (s + share));
                xo[v] = xn;
-               r += fabsf(xn - x[v]);
+               acc.add_r(fabsf(xn - x[v]));
                if (a.inv_w[v] == 0.f) acc.kahan(xn);
            });
     double R, Dn;
-    if (block_pair_to_grid((double)r, acc.mass(), a.slots, &st->ticket, &R, &Dn) && threadIdx.x == 0) {
+    if (block_pair_to_grid(acc.resid(), acc.mass(), a.slots, &st->ticket, &R, &Dn) && threadIdx.x == 0) {
         st->resid = R;
         st->D = Dn;
         st->iter += 1;

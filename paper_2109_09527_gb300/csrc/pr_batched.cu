@@ -336,12 +336,12 @@ __global__ void __launch_bounds__(kBlock) k_b_update(BatchArgs a, const float* _
             __stcs(Xout + (size_t)v * kBK + lane, xn);
             __stcs(Yout + (size_t)v * kBK + lane, xn * inv[q]);
             if (s_bf16) Yout16[(size_t)v * kBK + lane] = __float2bfloat16_rn(xn * inv[q]);
-            acc.r += fabsf(xn - xo[q]);
+            acc.add_r(fabsf(xn - xo[q]));
             if (inv[q] == 0.f) acc.kahan(xn);
         }
     }
     double R, Dn;
-    if (batch_columns_to_grid((double)acc.r, acc.mass(), a.slots, &st->ticket, &R, &Dn) && threadIdx.x < 32) {
+    if (batch_columns_to_grid(acc.resid(), acc.mass(), a.slots, &st->ticket, &R, &Dn) && threadIdx.x < 32) {
         const bool was_active = (s_active >> lane) & 1u;
         const double prev = st->resid[lane];
         st->D[lane] = Dn;

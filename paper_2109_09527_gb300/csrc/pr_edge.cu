@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_edge_rows(IterArgs a, const float
         }
     }
     double R, Dn;
-    if (block_pair_to_grid((double)acc.r, acc.mass(), a.slots, &st->ticket, &R, &Dn) && threadIdx.x == 0) {
+    if (block_pair_to_grid(acc.resid(), acc.mass(), a.slots, &st->ticket, &R, &Dn) && threadIdx.x == 0) {
         st->resid = R;
         st->D = Dn;
         st->iter += 1;

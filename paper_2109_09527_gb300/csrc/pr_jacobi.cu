@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kIterBlock, kGatherMinBlocks) k_rows(IterArgs 
     }
 
     double R, Dn;
-    if (block_pair_to_grid((double)acc.r, acc.mass(), a.slots, &st->ticket, &R, &Dn) &&
+    if (block_pair_to_grid(acc.resid(), acc.mass(), a.slots, &st->ticket, &R, &Dn) &&
         threadIdx.x == 0) {
         st->resid = R;
         st->D = Dn;
@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaMinBlocks) k_rows_tma(IterArg
     if (timed_out) atomicOr(&st->error, 2u);
 
     double R, Dn;
-    if (block_pair_to_grid((double)acc.r, acc.mass(), a.slots, &st->ticket, &R, &Dn) && threadIdx.x == 0) {
+    if (block_pair_to_grid(acc.resid(), acc.mass(), a.slots, &st->ticket, &R, &Dn) && threadIdx.x == 0) {
         st->resid = R;
         st->D = Dn;
         st->iter += 1;

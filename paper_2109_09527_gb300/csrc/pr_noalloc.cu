@@ -18,10 +18,13 @@
 // threads) race on it and give wrong sums, so serialise them.  Each call
 // clears the ticket before its kernels run.
 //
-// The device address of the array is looked up with cudaGetSymbolAddress the
-// first time the entry point runs on a device (with that device current) and
-// remembered; make that first call before any stream capture.
-#include <mutex>
+// The device address of the array is looked up with cudaGetSymbolAddress on
+// every call, with the caller's device current, and is not remembered: after
+// a cudaDeviceReset (or any other teardown of the primary context) the module
+// is loaded again, possibly at another address, and a remembered pointer
+// would go stale.  The lookup allocates nothing.  The first call on a device
+// (or after a reset) is the one that loads the module; make it before any
+// stream capture.
 
 #include "pr_tile.cuh"
 
@@ -31,7 +34,6 @@ namespace {
 constexpr int kNaRowsPerBlock = 2048;   // rows handled by one block
 constexpr int kNaMaxBlocks = 8192;      // partial-sum slots in the scratch array
 constexpr int64_t kNaMaxRows = (int64_t)kNaRowsPerBlock * kNaMaxBlocks;  // 16,777,216
-constexpr int kNaMaxDevices = 64;
 
 struct NaScratch {
     unsigned int ticket;                 // blocks that have finished (last-block pattern)
@@ -44,9 +46,6 @@ constexpr size_t kNaScratchBytes = sizeof(NaScratch);
 static_assert(kNaScratchBytes <= 160 * 1024, "the fixed scratch stays about 128 KiB");
 
 static __device__ __align__(256) NaScratch g_noalloc_scratch;
-
-std::mutex g_na_mutex;
-NaScratch* g_na_ptr[kNaMaxDevices] = {};
 
 // Block sum of (a, b) into slots[2*blockIdx.x]; the last block to arrive gets
 // the grid totals, summed over the slots in slot order.
@@ -98,12 +97,12 @@ __global__ void __launch_bounds__(kBlock) k_na_update(int64_t n, const int32_t* 
         if (lane == 0) {
             const float xn = fmaf(fd, s, base);
             x_out[r] = xn;
-            acc.r += fabsf(xn - x_in[r]);
+            acc.add_r(fabsf(xn - x_in[r]));
             if (inv[r] == 0.f) acc.kahan(xn);
         }
     }
     double D1, L1;
-    if (na_pair_to_grid(acc.mass(), (double)acc.r, sc, &D1, &L1) && threadIdx.x == 0) {
+    if (na_pair_to_grid(acc.mass(), acc.resid(), sc, &D1, &L1) && threadIdx.x == 0) {
         sums_out[1] = D1;
         sums_out[2] = L1;
         sc->ticket = 0;
@@ -125,8 +124,14 @@ extern "C" pr_status pr_step_noalloc(int64_t n, const int32_t* rowptr, const int
                     "(8192 blocks of 2048 rows); use pr_create_graph/pr_iterate for larger graphs");
     if (!rowptr || !colidx || !inv_outdeg || !x_in || !x_out || !sums_out)
         return fail(PR_ERR_INVALID_ARG, "pr_step_noalloc: NULL pointer argument");
-    if ((const void*)x_in == (const void*)x_out)
-        return fail(PR_ERR_INVALID_ARG, "pr_step_noalloc: x_in and x_out must be different buffers");
+    {
+        // the update reads every x_in(u) while it writes x_out: the two ranges
+        // [x_in, x_in + n) and [x_out, x_out + n) must not share an element
+        const uintptr_t a0 = (uintptr_t)x_in, b0 = (uintptr_t)x_out;
+        const uintptr_t bytes = (uintptr_t)n * sizeof(float);
+        if (a0 < b0 + bytes && b0 < a0 + bytes)
+            return fail(PR_ERR_INVALID_ARG, "pr_step_noalloc: x_in and x_out overlap; they must be disjoint buffers");
+    }
     if (!(damping >= 0.0f && damping < 1.0f))
         return fail(PR_ERR_INVALID_ARG, "pr_step_noalloc: damping must be in [0, 1)");
     const void* ptrs[] = {rowptr, colidx, inv_outdeg, x_in, x_out, sums_out};
@@ -134,21 +139,12 @@ extern "C" pr_status pr_step_noalloc(int64_t n, const int32_t* rowptr, const int
         if (!is_device_pointer(p))
             return fail(PR_ERR_INVALID_ARG, "pr_step_noalloc: every array must be device memory");
 
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "pr_step_noalloc: cudaGetDevice");
-    if (dev < 0 || dev >= kNaMaxDevices) return fail(PR_ERR_UNSUPPORTED, "pr_step_noalloc: device index too large");
-    NaScratch* sc = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_na_mutex);
-        if (!g_na_ptr[dev]) {
-            void* p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-            if (e != cudaSuccess) return cuda_fail(e, "pr_step_noalloc: cudaGetSymbolAddress");
-            g_na_ptr[dev] = (NaScratch*)p;
-        }
-        sc = g_na_ptr[dev];
-    }
+    // The host-side name g_noalloc_scratch is not a device address: ask the
+    // runtime where the current device's copy lives.
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "pr_step_noalloc: cudaGetSymbolAddress");
+    NaScratch* sc = (NaScratch*)p;
     cudaStream_t s = (cudaStream_t)stream;
     PRK_CHECK(cudaMemsetAsync(&sc->ticket, 0, sizeof(unsigned int), s));
     const int blocks = (int)((n + kNaRowsPerBlock - 1) / kNaRowsPerBlock);

@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(kNbBlock, kNbMinBlocks) k_nonblocking(NbArgs a
                 m = a.dangling_form ? ld_relaxed(a.scalars) : ld_relaxed(a.scalars + 1);
             }
             m = __shfl_sync(0xffffffffu, m, 0);
-            r_sweep += acc.r;
+            r_sweep += (float)acc.resid();
             acc = Acc();
             const double share = a.dangling_form ? (T - m) * inv_n : m * inv_n;
             c.d_share = (float)(d * share);

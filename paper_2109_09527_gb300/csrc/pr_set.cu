@@ -80,7 +80,7 @@ __device__ __forceinline__ int32_t set_done(const SetState* st) {
 
 // Block reduction of the thread's (r, D) into the tile's partial slot.
 __device__ __forceinline__ void tile_flush(Acc& acc, double* part) {
-    double r = (double)acc.r, m = acc.mass();
+    double r = acc.resid(), m = acc.mass();
     block_sum2(r, m);
     if (threadIdx.x == 0) {
         part[0] = r;

@@ -272,11 +272,14 @@ struct Mem<true> {
     static __device__ __forceinline__ void store_y(float* p, float v) { st_relaxed_p<PRK_L2_GATHER>(p, v); }
 };
 
-// Per-thread accumulators.  r: L1 change.  (m, c): Kahan sum of the mass the
-// kernel tracks -- the new dangling mass (synchronous form) or the change of
-// the non-dangling mass (in-place form).
+// Per-thread accumulators, both Kahan-compensated in FP32 (FP64 arithmetic
+// is a slow pipe on this GPU) and handed to the FP64 cross-thread reduction:
+// (r, rc) the L1 change; (m, c) the mass the kernel tracks -- the new
+// dangling mass (synchronous form) or the change of the non-dangling mass
+// (in-place form).
 struct Acc {
     float r = 0.f;
+    float rc = 0.f;
     float m = 0.f;
     float c = 0.f;
     float dd = 0.f;   // in-place form: change of the dangling mass (diagnostic form only)
@@ -286,7 +289,14 @@ struct Acc {
         c = (tk - m) - yk;
         m = tk;
     }
+    __device__ __forceinline__ void add_r(float v) {
+        const float yk = v - rc;
+        const float tk = r + yk;
+        rc = (tk - r) - yk;
+        r = tk;
+    }
     __device__ __forceinline__ double mass() const { return (double)m - (double)c; }
+    __device__ __forceinline__ double resid() const { return (double)r - (double)rc; }
 };
 
 // Compensated FP32 sum of one thread's elements (FP32 adds only: FP64
@@ -311,7 +321,7 @@ __device__ __forceinline__ void row_update(int64_t r, float s, float xo, float i
     const float xn = fmaf(c.d, s, base);
     Mem<kInPlace>::store_x(x_out + r, xn);
     Mem<kInPlace>::store_y(y_out + r, xn * inv);
-    acc.r += fabsf(xn - xo);
+    acc.add_r(fabsf(xn - xo));
     if (kInPlace) {
         if (inv != 0.f) acc.kahan(xn - xo);
         else acc.dd += xn - xo;
@@ -429,7 +439,7 @@ __device__ __forceinline__ void perf_update(int64_t r, float s, float xo, float 
     const float xn = fmaf(c.d, s, base);
     st_stream(x_out + r, xn);
     st_y(y_out + r, xn * inv);
-    acc.r += fabsf(xn - xo);
+    acc.add_r(fabsf(xn - xo));
     if (inv == 0.f) acc.kahan(xn);
     const float ch = fabsf(xn - xo);
     if (ch != 0.f && ch < p.eps) p.frozen[r] = 1;

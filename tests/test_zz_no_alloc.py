@@ -3,14 +3,16 @@
 Some callers cannot allocate device memory where they need an update (a fixed memory
 pool, another framework's allocator, a latency-bound loop); this entry point works on
 their own buffers plus one fixed scratch array inside the library.  The test checks it
-against the existing entry point (pr_iterate on a pr_graph) on two calls in a row, with
-the tolerances of the other parity tests (L1 <= 1e-6, per-vertex relative <= 1e-4).
+against the existing entry point (pr_iterate on a pr_graph) and against the FP64
+oracle's update (Eq. 1 with the dangling share D/n) on two calls in a row, with the
+tolerances of the other parity tests (L1 <= 1e-6, per-vertex relative <= 1e-4).
 It is collected last so that a failure here leaves every other test already run.
 """
 import numpy as np
 import pytest
 
 import graphgen as gg
+import oracle
 
 pr = pytest.importorskip("paper_2109_09527_gb300")
 torch = pytest.importorskip("torch")
@@ -58,6 +60,14 @@ def test_no_alloc_step_matches_pr_iterate_twice(graph):
         assert _l1(got, ref) <= 1e-6 and _max_rel(got, ref) <= 1e-4
         assert sums[1] == pytest.approx(info.dangling_mass, rel=1e-5, abs=1e-12)
         assert sums[2] == pytest.approx(info.residual_l1, rel=1e-4, abs=1e-9)
+    # the same two updates by the FP64 oracle, each from the vector the call was given
+    for x_prev, got, sums in ((x0.cpu().numpy(), x1h, s1), (x1h, x2h, s2)):
+        xo, d_in, l1o, _ = oracle.jacobi_step(rp, ci, x_prev.astype(np.float64), d=0.85)
+        assert _l1(got, xo) <= 1e-6 and _max_rel(got, xo) <= 1e-4
+        assert sums[0] == pytest.approx(d_in, rel=1e-6, abs=1e-12)
+        d_out = oracle.dangling_mass(rp, ci, xo)
+        assert sums[1] == pytest.approx(d_out, rel=1e-5, abs=1e-12)
+        assert sums[2] == pytest.approx(l1o, rel=1e-3, abs=1e-8)
     assert s1[0] == pytest.approx(float(np.sum(np.float64(1.0 / n) * (outdeg == 0))), rel=1e-6)
     # the dangling mass of x1: summed in FP64 by the second call, Kahan-compensated FP32 per
     # thread by the first
@@ -70,3 +80,21 @@ def test_no_alloc_rejects_sizes_beyond_its_scratch():
         pr.pr_step_noalloc(big, 1, 1, 1, 0.85, 1, 2, 1)
     assert e.value.status == pr.PR_ERR_INVALID_ARG
     assert "16,777,216" in str(e.value)
+
+
+def test_no_alloc_rejects_overlapping_vectors():
+    """x_out starting one element after x_in shares n - 1 elements with it: rejected
+    before any GPU work."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    n = 64
+    dev = torch.device("cuda:0")
+    rp = torch.arange(n + 1, dtype=torch.int32, device=dev)
+    ci = torch.roll(torch.arange(n, dtype=torch.int32, device=dev), 1)
+    inv = torch.ones(n, dtype=torch.float32, device=dev)
+    buf = torch.full((n + 1,), 1.0 / n, dtype=torch.float32, device=dev)
+    sums = torch.zeros(3, dtype=torch.float64, device=dev)
+    with pytest.raises(pr.PageRankError) as e:
+        pr.pr_step_noalloc(n, rp, ci, inv, 0.85, buf.data_ptr(), buf.data_ptr() + 4, sums)
+    assert e.value.status == pr.PR_ERR_INVALID_ARG
+    assert "overlap" in str(e.value)
