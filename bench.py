@@ -45,6 +45,8 @@ TOL = 1e-6
 MAX_ITER = 200
 SEED_RMAT = 24
 SEED_ER = 1024
+FORM_STEPS = 3                # timed solves of each form under `forms` and `massive`
+NB_L1_HUBS_DEFAULT = 49152    # the library's default PR_OPT_NB_L1_HUBS
 
 
 def log(*a):
@@ -359,6 +361,75 @@ def run_profile(args):
     return 0
 
 
+# ------------------------------------------------- error against the FP64 oracle --
+#
+# Every result a bench line reports carries a certificate from the oracle: one FP64
+# synchronous update F of the returned vector x (Eq. 1 with the dangling share D/n, or
+# its weighted / transposed form).  r = ||F(x) - x||_1, and since F is an L1
+# contraction with factor d, ||x - x*||_1 <= r / (1 - d) for the exact solution x*.
+# The jobs run on host threads after the timed regions (the oracle is plain C called
+# through ctypes, which releases the GIL, so the threads run in parallel).
+
+def certificate_job(rp, ci, x, t=None):
+    def job():
+        import numpy as np
+
+        import oracle
+        tt = None if t is None else np.asarray(t, np.float64)
+        _, _, r, _ = oracle.jacobi_step(rp, ci, np.asarray(x, np.float64), d=DAMPING, t=tt)
+        return {"oracle_r_l1": r, "err_l1_bound": r / (1.0 - DAMPING)}
+    return job
+
+
+def weighted_certificate_job(rp, ci, w64, x64):
+    def job():
+        import oracle
+        _, _, r = oracle.w_pagerank(rp, ci, w64, d=DAMPING, tol=0.0, max_iter=1, x0=x64)
+        return {"oracle_r_l1": r, "err_l1_bound": r / (1.0 - DAMPING)}
+    return job
+
+
+def adjoint_certificate_job(rp, ci, w64, c64, lam):
+    def job():
+        import numpy as np
+
+        import oracle
+        _, r = oracle.w_adjoint_step(rp, ci, w64, c64, lam, d=DAMPING)
+        cn = float(np.abs(c64).sum())
+        return {"oracle_r_l1": r, "err_l1_bound": r / (1.0 - DAMPING),
+                "relative_err_l1_bound": r / (1.0 - DAMPING) / cn}
+    return job
+
+
+def run_certificates(jobs, threads=None):
+    """Run (name, job) pairs on host threads; returns {name: result}."""
+    import concurrent.futures
+
+    import oracle
+    oracle.load()   # build and load once, before the threads share it
+    threads = threads or max(1, min(16, os.cpu_count() or 1))
+    t0 = time.perf_counter()
+    with concurrent.futures.ThreadPoolExecutor(max_workers=threads) as ex:
+        futs = {name: ex.submit(job) for name, job in jobs}
+        out = {name: f.result() for name, f in futs.items()}
+    log(f"[bench] {len(jobs)} oracle certificates in {time.perf_counter() - t0:.1f} s")
+    return out
+
+
+def summarise_certificates(results):
+    """The worst certificate of a group of results (and how many there were)."""
+    if not results:
+        return None
+    worst = max(results, key=lambda k: results[k]["err_l1_bound"])
+    out = {"results": len(results), "max_err_l1_bound": results[worst]["err_l1_bound"],
+           "max_oracle_r_l1": max(r["oracle_r_l1"] for r in results.values()), "worst": worst,
+           "how": "one FP64 oracle update F of each returned vector x: r = ||F(x) - x||_1, "
+                  "bound ||x - x*||_1 <= r/(1-d)"}
+    if "relative_err_l1_bound" in results[worst]:
+        out["relative_err_l1_bound"] = results[worst]["relative_err_l1_bound"]
+    return out
+
+
 BATCH_SCALE = 22
 BATCH_K = 32
 BATCH_SEEDS = 8
@@ -434,14 +505,9 @@ def run_profile_other(args):
     return 0
 
 
-def run_batched(args):
-    """Batched personalised PageRank: 32 seed-set teleport vectors (8 seeds each) on R-MAT-22,
-    solved together (pr_solve_batched) against the same 32 solved one at a time with the
-    plain FP32 Jacobi solver (pr_solve with a teleport), both to L1 < 1e-6 per column."""
+def setup_dist():
+    """(rank, local_rank, world, device, torch.distributed or None), device made current."""
     import torch
-
-    import graphgen as gg
-    import paper_2109_09527_gb300 as pr
     rank, local_rank, world = dist_env()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -449,6 +515,30 @@ def run_batched(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
+    return rank, local_rank, world, dev, dist
+
+
+def run_batched(args):
+    """Batched personalised PageRank as its own JSON line (see measure_batched)."""
+    rank, local_rank, world, dev, dist = setup_dist()
+    line, jobs = measure_batched(args, dev, dist, rank, local_rank, world)
+    if rank == 0:
+        line["oracle_certificate"] = summarise_certificates(run_certificates(jobs))
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def measure_batched(args, dev, dist, rank, local_rank, world):
+    """Batched personalised PageRank: 32 seed-set teleport vectors (8 seeds each) on R-MAT-22,
+    solved together (pr_solve_batched) against the same 32 solved one at a time with the
+    plain FP32 Jacobi solver (pr_solve with a teleport), both to L1 < 1e-6 per column.
+    Returns (line, certificate jobs: one oracle update of every returned column)."""
+    import torch
+
+    import graphgen as gg
+    import paper_2109_09527_gb300 as pr
     rp, ci = gg.rmat(BATCH_SCALE, 16, seed=BATCH_SCALE)
     n, nnz = rp.size - 1, ci.size
     t_host = gg.seed_teleports(n, BATCH_K, BATCH_SEEDS, seed=BATCH_SCALE)
@@ -508,12 +598,16 @@ def run_batched(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     single_iters = 0
+    single_loop_ms = 0.0
     for j in range(BATCH_K):
         _, info1 = pr.pr_solve(g.handle, DAMPING, TOL, MAX_ITER, pr.PR_JACOBI, t_cols[j], None, out1)
         single_iters += info1.iterations
+        single_loop_ms += info1.ms_loop
     e1.record(stream)
     torch.cuda.synchronize()
     single_ms = e0.elapsed_time(e1)
+    single_b = algorithmic_bytes(n, nnz, st["rowptr_bytes"])
+    single_gbs = single_b * single_iters / (single_loop_ms * 1e-3) / 1e9
 
     # end to end: teleports from pinned host memory, results back to pinned host memory
     t_pin = torch.from_numpy(t_host).pin_memory()
@@ -528,6 +622,9 @@ def run_batched(args):
     torch.cuda.synchronize()
     e2e_s, e2e_work = combine_ranks(dist, dev, time.perf_counter() - t0, float(nnz) * e2e_iters)
     g.close()
+    xb = out_pin.numpy().copy()
+    jobs = [(f"column {j}", certificate_job(rp, ci, xb[:, j], t=t_host[:, j])) for j in range(BATCH_K)]
+    line = None
     if rank == 0:
         steps = args.steps
         line = {"metric": "batched personalised PageRank: edge-column updates per second "
@@ -553,15 +650,18 @@ def run_batched(args):
                 "vs_single_vector_jacobi": {"batched_ms": ms / steps, "single_ms_total": single_ms,
                                             "speedup": single_ms / (ms / steps),
                                             "single_iterations_total": single_iters,
-                                            "batched_iterations": infos[-1][0].iterations},
+                                            "batched_iterations": infos[-1][0].iterations,
+                                            "single_roofline": {
+                                                "bound": "hbm", "achieved": single_gbs, "peak": peak,
+                                                "unit": "GB/s", "frac": single_gbs / peak,
+                                                "kernel": "jacobi iteration, one teleport column",
+                                                "bytes_per_iteration": single_b,
+                                                "ms_per_iteration": single_loop_ms / single_iters}},
                 "e2e": {"value": e2e_work / e2e_s / 1e9, "unit": "G edge-columns/s",
                         "h2d_bytes_per_step": n * BATCH_K * 4, "d2h_bytes_per_step": n * BATCH_K * 4,
                         "ms_per_step": e2e_s * 1e3 / max(1, args.e2e_steps)},
                 "clocks": clocks}
-        print(json.dumps(line), flush=True)
-    if dist:
-        dist.destroy_process_group()
-    return 0
+    return line, jobs
 
 
 SET_COUNT = 64
@@ -569,21 +669,27 @@ SET_SEED = 64
 
 
 def run_set(args):
+    """The 64-graph set as its own JSON line (see measure_set)."""
+    rank, local_rank, world, dev, dist = setup_dist()
+    line, jobs = measure_set(args, dev, dist, rank, local_rank, world)
+    if rank == 0:
+        line["oracle_certificate"] = summarise_certificates(run_certificates(jobs))
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def measure_set(args, dev, dist, rank, local_rank, world):
     """64 independent R-MAT graphs (vertex counts log-uniform in [1e3, 1e6], edge factor 8)
     as one block-diagonal graph, solved together (pr_solve_set) against the same graphs
-    solved one at a time (pr_solve, plain FP32 Jacobi), each to L1 < 1e-6."""
+    solved one at a time (pr_solve, plain FP32 Jacobi), each to L1 < 1e-6.  Returns (line,
+    certificate jobs: one oracle update of every graph's returned vector)."""
     import numpy as np
     import torch
 
     import graphgen as gg
     import paper_2109_09527_gb300 as pr
-    rank, local_rank, world = dist_env()
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
     graphs = gg.multi_rmat(SET_COUNT, 1e3, 1e6, 8, seed=SET_SEED)
     rp, ci, off = gg.block_diagonal(graphs)
     n, nnz = rp.size - 1, ci.size
@@ -627,11 +733,15 @@ def run_set(args):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
+    single_infos = []
     for sg, o in zip(singles, outs):
-        sg.solve(tol=TOL, max_iter=MAX_ITER, out=o)
+        single_infos.append(sg.solve(tol=TOL, max_iter=MAX_ITER, out=o)[1])
     e1.record(stream)
     torch.cuda.synchronize()
     single_ms = e0.elapsed_time(e1)
+    single_bytes = sum(algorithmic_bytes(r.size - 1, c.size) * i.iterations
+                       for (r, c), i in zip(graphs, single_infos))
+    single_gbs = single_bytes / (sum(i.ms_loop for i in single_infos) * 1e-3) / 1e9
     for sg in singles:
         sg.close()
     # end to end: the result read back to pinned host memory every step
@@ -644,6 +754,10 @@ def run_set(args):
         e2e_visits += float((nnz_g * its_e).sum())
     e2e_s, e2e_visits = combine_ranks(dist, dev, time.perf_counter() - t0, e2e_visits)
     g.close()
+    xs = out_pin.numpy().copy()
+    jobs = [(f"graph {i}", certificate_job(r, c, xs[off[i]:off[i + 1]]))
+            for i, (r, c) in enumerate(graphs)]
+    line = None
     if rank == 0:
         line = {"metric": "PageRank of 64 graphs in one solve: GTEPS (edges of iterating graphs "
                           "per second), each graph to L1<1e-6",
@@ -659,15 +773,17 @@ def run_set(args):
                              "bytes_per_iteration": b_iter, "ms_per_iteration": loop_ms / iters,
                              "peak_source": f"{peak_kind} hbm_gbs"},
                 "vs_one_graph_at_a_time": {"set_ms": ms / args.steps, "single_ms_total": single_ms,
-                                           "speedup": single_ms / (ms / args.steps)},
+                                           "speedup": single_ms / (ms / args.steps),
+                                           "single_roofline": {
+                                               "bound": "hbm", "achieved": single_gbs, "peak": peak,
+                                               "unit": "GB/s", "frac": single_gbs / peak,
+                                               "kernel": "jacobi iterations of the 64 graphs, "
+                                                         "one graph at a time"}},
                 "e2e": {"value": e2e_visits / e2e_s / 1e9, "unit": "GTEPS",
                         "h2d_bytes_per_step": 0, "d2h_bytes_per_step": n * 4,
                         "ms_per_step": e2e_s * 1e3 / max(1, args.e2e_steps)},
                 "clocks": clocks}
-        print(json.dumps(line), flush=True)
-    if dist:
-        dist.destroy_process_group()
-    return 0
+    return line, jobs
 
 
 def run_edge(args):
@@ -773,25 +889,128 @@ def run_edge(args):
     return 0
 
 
+MASSIVE_SCALE = 26
+
+
+def run_massive(args):
+    """The massive-graph configuration as its own JSON line (see measure_massive)."""
+    rank, local_rank, world, dev, dist = setup_dist()
+    line, jobs = measure_massive(args, dev, dist, rank, local_rank, world)
+    if rank == 0:
+        line["oracle_certificate"] = run_certificates(jobs)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def measure_massive(args, dev, dist, rank, local_rank, world):
+    """R-MAT scale 26 (67,108,864 vertices, about 1.07e9 edges, Graph500 parameters) with
+    64-bit row offsets kept on the device: the barrier-free solve to L1 < 1e-6, beside the
+    plain FP32 Jacobi solve of the same graph.  GTEPS = edges gathered / solve time;
+    roofline against B = 4 nnz + 8 (n+1) + 20 n bytes per sweep.  Returns (line,
+    certificate jobs: one oracle update of each variant's returned vector)."""
+    import torch
+
+    import graphgen as gg
+    import paper_2109_09527_gb300 as pr
+    t0 = time.time()
+    rp, ci = gg.rmat(MASSIVE_SCALE, 16, seed=MASSIVE_SCALE)
+    n, nnz = rp.size - 1, ci.size
+    log(f"[bench] generated rmat-{MASSIVE_SCALE} nnz={nnz} in {time.time() - t0:.1f}s")
+    pr.pr_set_option(None, pr.PR_OPT_INDEX64, 1)
+    try:
+        drp, dci = torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)
+        g = pr.Graph(drp, dci)
+        del drp, dci
+    finally:
+        pr.pr_set_option(None, pr.PR_OPT_INDEX64, 0)
+    st = g.stats()
+    assert st["rowptr_bytes"] == 8
+    out = torch.empty(n, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    peak, peak_kind = peaks()
+    b_sweep = algorithmic_bytes(n, nnz, 8)
+    cases, jobs = {}, []
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    for vid, vname in ((pr.PR_NONBLOCKING, "nonblocking"), (pr.PR_JACOBI, "jacobi")):
+        for _ in range(args.warmup):
+            pr.pr_solve(g.handle, DAMPING, TOL, MAX_ITER, vid, None, None, out)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if sampler and vname == "nonblocking":
+            sampler.start()
+            time.sleep(0.3)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        infos = [pr.pr_solve(g.handle, DAMPING, TOL, MAX_ITER, vid, None, None, out)[1]
+                 for _ in range(args.steps)]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ms, visits = combine_ranks(dist, dev, ev0.elapsed_time(ev1), sum(i.edge_visits for i in infos))
+        loop_ms = sum(i.ms_loop for i in infos)
+        loop_visits = sum(i.loop_edge_visits for i in infos)
+        launches = sum(i.iterations if vname == "jacobi" else 1 for i in infos)
+        alg = b_sweep * loop_visits / nnz
+        achieved = alg / (loop_ms * 1e-3) / 1e9
+        last = infos[-1]
+        cases[vname] = {
+            "gteps": visits / (ms * 1e-3) / 1e9, "time_to_tol_ms": ms / args.steps,
+            "iterations": last.iterations, "residual_l1": last.residual_l1,
+            "converged": all(bool(i.converged) for i in infos),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": ("k_nonblocking (persistent barrier-free sweeps)" if vname == "nonblocking"
+                                    else "jacobi iteration (k_heavy_segments + k_rows, 64-bit offsets)"),
+                         "bytes_per_launch": alg / launches, "ms_per_launch": loop_ms / launches,
+                         "bytes_per_sweep": b_sweep,
+                         "peak_source": f"{peak_kind} hbm_gbs (of {peak_kind})"}}
+        x = out.cpu().numpy()
+        jobs.append((vname, certificate_job(rp, ci, x)))
+    clocks = sampler.stop() if sampler else None
+    g.close()
+    line = None
+    if rank == 0:
+        nb = cases["nonblocking"]
+        line = {"metric": "PageRank GTEPS and time-to-L1<1e-6, barrier-free, 64-bit offsets",
+                "value": nb["gteps"], "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": nb["time_to_tol_ms"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"rmat{MASSIVE_SCALE} (Graph500 a/b/c .57/.19/.19, ef 16), "
+                                       "64-bit row offsets, barrier-free solve to L1<1e-6, d=0.85",
+                           "n": n, "nnz": nnz, "tol": TOL, "l2": "inputs larger than L2"},
+                "roofline": nb["roofline"], "cases": cases, "clocks": clocks}
+    return line, jobs
+
+
 ADJ_SCALE = 20
 
 
 def run_adjoint(args):
+    """The weighted forward + adjoint workload as its own JSON line (see measure_adjoint)."""
+    rank, local_rank, world, dev, dist = setup_dist()
+    line, jobs = measure_adjoint(args, dev, dist, rank, local_rank, world)
+    if rank == 0:
+        line["oracle_certificate"] = summarise_certificates(run_certificates(jobs))
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def measure_adjoint(args, dev, dist, rank, local_rank, world):
     """Weighted R-MAT-20 (weights U(0.1, 1], row-normalised), L = c^T x with c ~ N(0, 1): one
     step = the weighted forward solve to L1 < 1e-6 plus the adjoint solve (relative L1 change
-    < 1e-6) and both gradients; against the plain FP32 Jacobi solve of the same graph."""
+    < 1e-6) and both gradients; against the plain FP32 Jacobi solve of the same graph.
+    Returns (line, certificate jobs: one oracle update of x and one of lambda)."""
     import numpy as np
     import torch
 
     import graphgen as gg
     import paper_2109_09527_gb300 as pr
-    rank, local_rank, world = dist_env()
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
     rp, ci = gg.rmat(ADJ_SCALE, 16, seed=ADJ_SCALE)
     n, nnz = rp.size - 1, ci.size
     w = (0.1 + 0.9 * gg.uniform(ADJ_SCALE, 11, nnz)).astype(np.float32)
@@ -844,6 +1063,8 @@ def run_adjoint(args):
     e1.record(stream)
     torch.cuda.synchronize()
     plain_ms = e0.elapsed_time(e1)
+    plain_b = algorithmic_bytes(n, nnz, pg.stats()["rowptr_bytes"])
+    plain_gbs = plain_b * pinfo.iterations / (pinfo.ms_loop * 1e-3) / 1e9
     pg.close()
     # end to end: c in from pinned host memory, both gradients back to pinned host memory
     c_pin = c.cpu().pin_memory()
@@ -859,6 +1080,12 @@ def run_adjoint(args):
         e2e_visits += fi2.edge_visits + ai2.edge_visits
     e2e_s, e2e_visits = combine_ranks(dist, dev, time.perf_counter() - t0, e2e_visits)
     g.close()
+    xh = x_pin.numpy().astype(np.float64)
+    lam = gt_pin.numpy().astype(np.float64) / (1.0 - DAMPING)
+    w64, c64 = w.astype(np.float64), c_pin.numpy().astype(np.float64)
+    jobs = [("forward x", weighted_certificate_job(rp, ci, w64, xh)),
+            ("adjoint lambda", adjoint_certificate_job(rp, ci, w64, c64, lam))]
+    line = None
     if rank == 0:
         line = {"metric": "weighted PageRank forward + adjoint gradients: GTEPS (edges gathered "
                           "per second, both solves)",
@@ -879,15 +1106,18 @@ def run_adjoint(args):
                              "bytes_per_iteration": b_iter, "ms_per_iteration": f_ms,
                              "peak_source": f"{peak_kind} hbm_gbs"},
                 "vs_plain_jacobi": {"plain_ms": plain_ms, "plain_iterations": pinfo.iterations,
-                                    "forward_plus_adjoint_ms": ms / args.steps},
+                                    "forward_plus_adjoint_ms": ms / args.steps,
+                                    "plain_roofline": {
+                                        "bound": "hbm", "achieved": plain_gbs, "peak": peak,
+                                        "unit": "GB/s", "frac": plain_gbs / peak,
+                                        "kernel": "jacobi iteration of the unweighted graph",
+                                        "bytes_per_iteration": plain_b,
+                                        "ms_per_iteration": pinfo.ms_loop / pinfo.iterations}},
                 "e2e": {"value": e2e_visits / e2e_s / 1e9, "unit": "GTEPS",
                         "h2d_bytes_per_step": 2 * n * 4, "d2h_bytes_per_step": (2 * n + nnz) * 4,
                         "ms_per_step": e2e_s * 1e3 / max(1, args.e2e_steps)},
                 "clocks": clocks}
-        print(json.dumps(line), flush=True)
-    if dist:
-        dist.destroy_process_group()
-    return 0
+    return line, jobs
 
 
 def run_ceiling(args):
@@ -955,10 +1185,14 @@ def main():
     ap.add_argument("--er-log2", type=int, default=24)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the batched, graph-set, adjoint and massive-graph cases that the "
+                         "default line carries under `forms` and `massive`")
     ap.add_argument("--profile", choices=["jacobi", "nonblocking", "batched", "set", "adjoint"], default=None,
                     help="run a short fixed workload for a profiler instead of the benchmark")
     ap.add_argument("--graph", choices=["rmat", "er"], default="rmat")
-    ap.add_argument("--workload", choices=["pagerank", "batched", "set", "adjoint", "edge", "ceiling"],
+    ap.add_argument("--workload", choices=["pagerank", "batched", "set", "adjoint", "edge", "ceiling",
+                                           "massive"],
                     default="pagerank",
                     help="batched: 32 personalised PageRank vectors on R-MAT-22; set: 64 R-MAT "
                          "graphs of 1e3..1e6 vertices in one solve; ceiling: the random-gather "
@@ -984,6 +1218,8 @@ def main():
         return run_edge(args)
     if args.workload == "ceiling":
         return run_ceiling(args)
+    if args.workload == "massive":
+        return run_massive(args)
 
     import numpy as np
     import torch
@@ -1113,8 +1349,65 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(graphs[0])
 
+    # every returned vector of the step, for its oracle certificate
+    jobs = []
+    host_graphs = dict(graphs)
+    for name, g, st in resident:
+        for vid, vname in variants:
+            pr.pr_solve(g.handle, DAMPING, TOL, MAX_ITER, vid, None, None, outs[name])
+            rp_h, ci_h = host_graphs[name]
+            jobs.append((f"{name} {vname}", certificate_job(rp_h, ci_h, outs[name].cpu().numpy())))
+
+    # the barrier-free kernel with every gather a relaxed gpu-scope load (no weak L1 hub
+    # loads: free of data races under the PTX memory model) against the default
+    race_free = {}
+    for name, g, st in resident:
+        row = {}
+        for label, hubs in (("race_free", 0), ("default_weak_l1_hubs", NB_L1_HUBS_DEFAULT)):
+            g.set_option(pr.PR_OPT_NB_L1_HUBS, hubs)
+            for _ in range(2):
+                pr.pr_solve(g.handle, DAMPING, TOL, MAX_ITER, pr.PR_NONBLOCKING, None, None, outs[name])
+            torch.cuda.synchronize()
+            r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            r0.record(stream)
+            infos = [pr.pr_solve(g.handle, DAMPING, TOL, MAX_ITER, pr.PR_NONBLOCKING, None, None,
+                                 outs[name])[1] for _ in range(3)]
+            r1.record(stream)
+            torch.cuda.synchronize()
+            row[label] = {"time_to_tol_ms": r0.elapsed_time(r1) / 3, "sweeps": infos[-1].iterations,
+                          "residual_l1": infos[-1].residual_l1,
+                          "converged": all(bool(i.converged) for i in infos)}
+        g.set_option(pr.PR_OPT_NB_L1_HUBS, NB_L1_HUBS_DEFAULT)
+        row["weak_hub_gain"] = row["race_free"]["time_to_tol_ms"] / row["default_weak_l1_hubs"]["time_to_tol_ms"]
+        race_free[name] = row
+
     for _, g, _ in resident:
         g.close()
+    del resident, outs
+
+    # the other forms of the method, each beside the plain FP32 Jacobi solve, and the
+    # massive-graph configuration: extra keys, outside `value`
+    forms, massive = None, None
+    if not args.no_forms:
+        fargs = argparse.Namespace(**vars(args))
+        fargs.steps, fargs.warmup, fargs.e2e_steps = FORM_STEPS, 3, 1
+        forms = {}
+        for key, fn in (("batched", measure_batched), ("set", measure_set), ("adjoint", measure_adjoint)):
+            line_f, jobs_f = fn(fargs, dev, dist, rank, local_rank, world)
+            forms[key] = line_f
+            jobs += [(f"{key}: {k}", j) for k, j in jobs_f]
+        massive, jobs_m = measure_massive(fargs, dev, dist, rank, local_rank, world)
+        jobs += [(f"massive: {k}", j) for k, j in jobs_m]
+
+    certs = run_certificates(jobs) if rank == 0 else {}
+    for cl in case_lines:
+        cl["oracle_certificate"] = certs.get(f"{cl['graph']} {cl['variant']}")
+    if forms and rank == 0:
+        for key in forms:
+            sub = {k[len(key) + 2:]: v for k, v in certs.items() if k.startswith(key + ": ")}
+            forms[key]["oracle_certificate"] = (sub if key == "adjoint" else summarise_certificates(sub))
+        for vname, c in massive["cases"].items():
+            c["oracle_certificate"] = certs.get(f"massive: {vname}")
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -1130,7 +1423,8 @@ def main():
                            "l2": "inputs larger than L2 (colidx alone 1.07 GB per graph)"},
                 "roofline": roofline, "roofline_all": roofline_all, "cpu_baseline": cpu,
                 "e2e": e2e,
-                "gpu_launches": launches, "clocks": clocks, "cases": case_lines}
+                "gpu_launches": launches, "clocks": clocks, "cases": case_lines,
+                "barrier_free_race_free": race_free, "forms": forms, "massive": massive}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

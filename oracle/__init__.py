@@ -71,6 +71,8 @@ def _declare(lib):
     lib.or_w_jacobi.argtypes = [i64, vp, vp, vp, dbl, vp, dbl, i32, vp, vp, vp, vp]
     lib.or_w_adjoint.restype = ctypes.c_int
     lib.or_w_adjoint.argtypes = [i64, vp, vp, vp, dbl, vp, vp, dbl, i32, vp, vp, vp, vp, vp, vp]
+    lib.or_w_adjoint_step.restype = ctypes.c_int
+    lib.or_w_adjoint_step.argtypes = [i64, vp, vp, vp, dbl, vp, vp, vp, vp]
     lib.or_nosync.restype = ctypes.c_int
     lib.or_nosync.argtypes = [i64, vp, vp, dbl, vp, ctypes.c_int, ctypes.c_int, i32, vp,
                               ctypes.c_int, dbl, i32, vp, vp, vp, vp, vp, dbl, vp]
@@ -293,6 +295,19 @@ def w_adjoint(rowptr, colidx, w, x, c, d=0.85, tol=1e-14, max_iter=5000, lib=Non
                             ctypes.byref(it), ctypes.byref(res)), "or_w_adjoint")
     return {"lambda": lam, "mu": mu, "grad_t": gt, "grad_w": gw[:nnz], "iterations": it.value,
             "residual": res.value}
+
+
+def w_adjoint_step(rowptr, colidx, w, c, lam, d=0.85, lib=None):
+    """One update of the adjoint system from lam: returns (lambda_out, l1_change)."""
+    lib = lib or load()
+    rowptr, colidx = _csr(rowptr, colidx)
+    n = rowptr.size - 1
+    out = np.empty(n, dtype=np.float64)
+    l1 = ctypes.c_double()
+    _check(lib.or_w_adjoint_step(n, _p(rowptr), _p(colidx), _p(_weights(w, int(rowptr[-1]))), d,
+                                 _p(_vec(c, n)), _p(_vec(lam, n)), _p(out), ctypes.byref(l1)),
+           "or_w_adjoint_step")
+    return out, l1.value
 
 
 def dense_adjoint(rowptr, colidx, w, c, d=0.85, t=None):

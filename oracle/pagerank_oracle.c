@@ -47,6 +47,9 @@
  *                      transposed system), then dL/dt = (1-d) lambda and, for
  *                      an edge e = (u, v), dL/dw(e) = d x(u)/W(u) *
  *                      (lambda(v) - sum_{v'} P(u,v') lambda(v')).
+ *   or_w_adjoint_step  one update of that transposed system from a given
+ *                      lambda, with its L1 change (a certificate for a
+ *                      lambda computed elsewhere).
  *   or_nosync          the lock-free No-Sync scheme, Alg. 3: p simulated
  *                      threads, static equal partitions, in-place updates,
  *                      thread-level convergence; two forms of the dangling
@@ -69,7 +72,10 @@
  * out-weights, and by a dense solve; or_w_adjoint by the dense adjoint
  * (numpy linear algebra on explicit dM/dw matrices, n <= 12), by central
  * finite differences of or_w_jacobi, and by the identities
- * (1-d) lambda^T t = c^T x and sum_{e out of u} w(e) dL/dw(e) = 0.
+ * (1-d) lambda^T t = c^T x and sum_{e out of u} w(e) dL/dw(e) = 0;
+ * or_w_adjoint_step by the directed cycle (lambda_out(u) = c(u) + d
+ * lambda(u+1) in closed form), by the dense adjoint's lambda (a fixed point:
+ * change ~ 0) and by the first iterate of or_w_adjoint.
  */
 #include <math.h>
 #include <stdint.h>
@@ -457,6 +463,44 @@ OR_API int or_w_jacobi(int64_t n, const int64_t* rowptr, const int32_t* colidx, 
     if (residual) *residual = r;
     free(W);
     free(xn);
+    return OR_OK;
+}
+
+/* One synchronous update of the adjoint (transposed) system from a given
+ * lambda:
+ *   lambda_out(u) = c(u) + d * ( sum_{(u,v)} P(u,v) lambda(v) + a(u) * sum(lambda)/n ),
+ * the loop body of or_w_adjoint.  *l1 = ||lambda_out - lambda||_1, which bounds
+ * the distance of lambda to the solution of M^T lambda = c by l1 / (1 - d)
+ * (the transposed map is an L1 contraction with factor d as well). */
+OR_API int or_w_adjoint_step(int64_t n, const int64_t* rowptr, const int32_t* colidx, const double* w,
+                             double d, const double* c, const double* lambda, double* lambda_out,
+                             double* l1) {
+    int rc = or_check_csr(n, rowptr, colidx);
+    if (rc) return rc;
+    if (!(d >= 0.0 && d < 1.0) || !c || !lambda || !lambda_out) return OR_BAD_ARG;
+    double* W = (double*)malloc((size_t)n * sizeof(double));
+    double* mu = (double*)malloc((size_t)n * sizeof(double));
+    if (!W || !mu) { free(W); free(mu); return OR_NO_MEM; }
+    rc = or_w_outweight(n, rowptr, colidx, w, W);
+    if (rc) { free(W); free(mu); return rc; }
+    double L = 0.0;
+    for (int64_t u = 0; u < n; ++u) {
+        L += lambda[u];
+        mu[u] = 0.0;
+    }
+    for (int64_t v = 0; v < n; ++v)
+        for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+            int64_t u = colidx[e];
+            mu[u] += w[e] / W[u] * lambda[v];
+        }
+    double r = 0.0;
+    for (int64_t u = 0; u < n; ++u) {
+        lambda_out[u] = c[u] + d * (mu[u] + (W[u] == 0.0 ? L / (double)n : 0.0));
+        r += fabs(lambda_out[u] - lambda[u]);
+    }
+    if (l1) *l1 = r;
+    free(W);
+    free(mu);
     return OR_OK;
 }
 

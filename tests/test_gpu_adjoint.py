@@ -131,7 +131,8 @@ def test_block_per_row_class_against_the_oracle(graph):
     c = loss_weights(n, 7)
     w64, c64 = w.astype(np.float64), c.astype(np.float64)
     with pr.WeightedGraph(rp, ci, w) as g:
-        x, info = g.solve(D, 1e-7, 500)
+        # tol 1e-6: the stars' hub rank (~0.8) alone changes by ~1e-7 per FP32 rounding
+        x, info = g.solve(D, 1e-6, 500)
         assert info.converged == 1
         # forward: the oracle's Alg. 1 after the same iterations (matching mode)
         xo, _, _ = oracle.w_pagerank(rp, ci, w64, d=D, tol=0.0, max_iter=info.iterations)

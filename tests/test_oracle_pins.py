@@ -463,6 +463,36 @@ def test_weighted_forward_and_adjoint_match_the_dense_adjoint(seed):
     assert np.allclose(adj["grad_w"], gwd, atol=1e-12)
 
 
+def test_adjoint_step_cycle_closed_form():
+    """Directed cycle u -> u+1 (mod n), unit weights, no dangling vertex: P(u, u+1) = 1, so
+    one update of the adjoint system is lambda_out(u) = c(u) + d lambda(u+1)."""
+    n = 7
+    rp, ci = gg.cycle(n)
+    w = np.ones(ci.size)
+    c = gg.uniform(3, 4, n) - 0.5
+    lam = gg.uniform(3, 5, n) * 3.0 - 1.0
+    out, l1 = oracle.w_adjoint_step(rp, ci, w, c, lam, d=0.8)
+    expect = c + 0.8 * np.roll(lam, -1)
+    assert np.allclose(out, expect, atol=1e-15)
+    assert l1 == pytest.approx(np.abs(expect - lam).sum(), rel=1e-14)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_adjoint_step_fixed_point_and_first_iterate(seed):
+    """The dense adjoint's lambda (numpy's solver on M^T) is a fixed point of the step, with
+    dangling vertices present; from lambda = c the step gives or_w_adjoint's first iterate."""
+    n = 5 + seed
+    rp, ci, w = weighted_case(n, 2 * n, seed=10 + seed, multi=False)
+    c = gg.uniform(seed, 13, n) - 0.5
+    _, lamd, _, _ = oracle.dense_adjoint(rp, ci, w, c)
+    out, l1 = oracle.w_adjoint_step(rp, ci, w, c, lamd)
+    assert l1 < 1e-12 and np.allclose(out, lamd, atol=1e-13)
+    first, _ = oracle.w_adjoint_step(rp, ci, w, c, c)
+    x, _, _ = oracle.w_pagerank(rp, ci, w)
+    adj1 = oracle.w_adjoint(rp, ci, w, x, c, tol=0.0, max_iter=1)
+    assert np.allclose(first, adj1["lambda"], atol=1e-15)
+
+
 def test_adjoint_identities():
     """L = c^T x is linear in t (so (1-d) lambda^T t = L) and unchanged by scaling one
     vertex's out-weights (so the weight gradients of each vertex's out-edges, weighted by
