@@ -1381,6 +1381,7 @@ def main():
         row["weak_hub_gain"] = row["race_free"]["time_to_tol_ms"] / row["default_weak_l1_hubs"]["time_to_tol_ms"]
         race_free[name] = row
 
+    graph_info = [{"name": n, "n": st["n"], "nnz": st["nnz"]} for n, _, st in resident]
     for _, g, _ in resident:
         g.close()
     del resident, outs
@@ -1416,8 +1417,7 @@ def main():
                 "config": {"workload": f"rmat{args.scale} (Graph500 a/b/c .57/.19/.19, ef 16) + "
                                        f"er{args.er_log2} (mean out-degree 16, 20% dangling); "
                                        "Jacobi and barrier-free solves to L1<1e-6, d=0.85",
-                           "graphs": [{"name": n, "n": st["n"], "nnz": st["nnz"]}
-                                      for n, _, st in resident],
+                           "graphs": graph_info,
                            "tol": TOL, "damping": DAMPING, "max_iter": MAX_ITER,
                            "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (colidx alone 1.07 GB per graph)"},

@@ -108,7 +108,8 @@ typedef struct pr_info {
                               the call's stream around the while-graph or the
                               host-driven iterations, or around each
                               persistent launch, summed)                      */
-    int32_t reserved;      /* 0                                               */
+    int32_t frozen_rows;   /* rows frozen by loop perforation at the end of
+                              the solve (PR_OPT_PERFORATION); 0 otherwise     */
 } pr_info;
 
 typedef struct pr_graph_stats {
@@ -247,15 +248,22 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
  *                         result meets the same tol; BF16's 2^-9 rounding
  *                         limits how far the BF16 phase can go (m ~ 2..3).
  *   PR_OPT_PERFORATION    loop perforation (Alg. 5) in the synchronous solver
- *                         (PR_JACOBI, pr_iterate): 0 (default) off; m in 1..30
- *                         freezes a vertex once an update changes its rank by
- *                         a nonzero amount below 10^-m -- it is no longer
- *                         recomputed (its rank still feeds its out-neighbours
- *                         and the dangling mass).  An approximation: the
- *                         result differs from the fixed point by more than
- *                         the contraction bound of the residual; frozen rows
- *                         count as changes of 0 in the residual.  Row-by-row
- *                         tiles only (PR_OPT_STAGED_TILES is ignored).
+ *                         (PR_JACOBI, pr_iterate) and in the barrier-free one
+ *                         (PR_NONBLOCKING: the paper's No-Sync-Opt, Section
+ *                         4): 0 (default) off; m in 1..30 freezes a vertex
+ *                         once an update changes its rank by a nonzero amount
+ *                         below 10^-m -- it is no longer recomputed (its rank
+ *                         still feeds its out-neighbours and the dangling
+ *                         mass).  An approximation: the result differs from
+ *                         the fixed point by more than the contraction bound
+ *                         of the residual; frozen rows count as changes of 0
+ *                         in the residual, also in the barrier-free solver's
+ *                         verifying synchronous update.  pr_info.frozen_rows
+ *                         reports how many rows froze.  Row-by-row tiles only
+ *                         (PR_OPT_STAGED_TILES is ignored); in the
+ *                         barrier-free solver not together with
+ *                         PR_OPT_NB_FAIL_AFTER or PR_TRACE_NB
+ *                         (PR_ERR_UNSUPPORTED).
  *   PR_OPT_DYNAMIC_TILES  synchronous solver: 0 (default) each block owns a
  *                         fixed round-robin share of the row tiles; 1 blocks
  *                         take tiles from a shared counter, so a slow block's

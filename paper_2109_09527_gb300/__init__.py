@@ -71,7 +71,7 @@ class pr_info(ctypes.Structure):
                 ("dangling_mass", ctypes.c_double), ("edge_visits", ctypes.c_double),
                 ("ms_device", ctypes.c_float), ("launches", ctypes.c_int32),
                 ("loop_edge_visits", ctypes.c_double), ("ms_loop", ctypes.c_float),
-                ("reserved", ctypes.c_int32)]
+                ("frozen_rows", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -804,7 +804,7 @@ extern "C" pr_status pr_solve_batched(pr_graph* g, float damping, double tol, in
         info->launches = launches;
         info->loop_edge_visits = info->edge_visits;
         info->ms_loop = ms_loop;
-        info->reserved = 0;
+        info->frozen_rows = 0;
     }
     return conv ? PR_OK : PR_NOT_CONVERGED;
 }

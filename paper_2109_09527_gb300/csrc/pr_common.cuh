@@ -127,6 +127,8 @@ struct SolveState {
     uint32_t error;    // device-side error bits
     int32_t sweeps_max;
     uint32_t tile_next;  // next tile to hand out (dynamic tile assignment)
+    uint32_t frozen;     // rows frozen by loop perforation (counted after the solve)
+    uint32_t pad_;
 };
 
 // Arguments of the per-iteration kernels (passed by value).
@@ -293,6 +295,8 @@ pr_status ensure_stage(pr_graph* g);
 pr_status ensure_teleport(pr_graph* g);
 void launch_init(const pr_graph* g, const IterArgs& a, const float* t_dev, const float* x0_dev,
                  cudaStream_t s);
+// Count the frozen rows of a perforated solve into SolveState::frozen.
+cudaError_t launch_count_frozen(const pr_graph* g, cudaStream_t s);
 void launch_finalize(const pr_graph* g, const IterArgs& a, float* out, bool renormalise,
                      cudaStream_t s, int* launches);
 

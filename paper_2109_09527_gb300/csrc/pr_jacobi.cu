@@ -486,6 +486,17 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaMinBlocks) k_rows_tma(IterArg
     }
 }
 
+// Rows frozen by loop perforation, added into the solve state.
+__global__ void __launch_bounds__(kBlock) k_count_frozen(const uint8_t* __restrict__ frozen, int64_t n,
+                                                         SolveState* st) {
+    uint32_t c = 0;
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < n; i += stride) c += frozen[i] != 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&st->frozen, c);
+}
+
 // pad of every tile of the pipelined kernel (and of the sentinel after the
 // last) = offset of the tile's first edge.
 __global__ void k_tile_edges(Tile* tiles, int64_t count, const int32_t* __restrict__ rowptr) {
@@ -619,6 +630,13 @@ IterArgs make_args(const pr_graph* g, bool uniform) {
 int small_grid(const pr_graph* g) {
     int64_t blocks = (g->n + kBlock - 1) / kBlock;
     return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)g->slot_capacity));
+}
+
+cudaError_t launch_count_frozen(const pr_graph* g, cudaStream_t s) {
+    if (g->perforation <= 0 || !g->frozen) return cudaSuccess;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((g->n + kBlock - 1) / kBlock, 4096));
+    k_count_frozen<<<grid, kBlock, 0, s>>>(g->frozen, g->n, g->state);
+    return cudaGetLastError();
 }
 
 // Enqueue one iteration reading buffer `src` and writing buffer 1-src.
@@ -940,6 +958,10 @@ pr_status run_jacobi(pr_graph* g, float damping, double tol, int32_t max_iter, c
 
     launch_finalize(g, a, out, renormalise, s, &launches);
     PRK_CHECK(cudaGetLastError());
+    if (a.frozen) {
+        PRK_CHECK(launch_count_frozen(g, s));
+        ++launches;
+    }
     PRK_CHECK(cudaEventRecord(g->ev_stop, s));
     if (!out_dev)
         PRK_CHECK(cudaMemcpyAsync(x_out, out, (size_t)g->n * sizeof(float), cudaMemcpyDeviceToHost, s));
@@ -964,7 +986,7 @@ pr_status run_jacobi(pr_graph* g, float damping, double tol, int32_t max_iter, c
         info->launches = launches;
         info->loop_edge_visits = info->edge_visits;
         info->ms_loop = ms_loop;
-        info->reserved = 0;
+        info->frozen_rows = a.frozen ? (int32_t)hs->frozen : 0;
     }
     return converged ? PR_OK : PR_NOT_CONVERGED;
 }

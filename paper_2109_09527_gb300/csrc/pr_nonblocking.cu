@@ -103,7 +103,119 @@ struct NbArgs {
     int32_t hub_n;               // ids [0, hub_n) are gathered from the block's snapshot
     int32_t l1_hubs;             // ids [hub_n, l1_hubs) are gathered with weak L1-cached loads
     int32_t fail_after;          // > 0: block 0 leaves after this many sweeps (a failing thread, Fig. 9)
+    uint8_t* frozen;             // loop perforation (Alg. 5): 1 = row frozen (perforated form only)
+    float perf_eps;              // freeze bound: a nonzero change below it freezes the row
 };
+
+// ---- loop perforation (Alg. 5) in the barrier-free kernel ------------------
+// The paper applies Alg. 5 to its No-Sync variants as well (No-Sync-Opt): a
+// vertex whose update changed its rank by a nonzero amount below the bound
+// is not recomputed again.  Here a frozen row gathers nothing and updates
+// nothing: y, which the other blocks read, keeps its value in place, and the
+// row's rank is carried into the other parity copy of x (the next sweep reads
+// that copy).  A frozen row counts as zero change and moves no mass.  The
+// freeze flag of a row is written only by the thread that updates the row;
+// the warps that gather a heavy row's other segments read it (relaxed) to skip
+// their gathers, and a stale read only costs a gather.
+__device__ __forceinline__ bool nb_is_frozen(const uint8_t* f, int64_t r) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u8 %0, [%1];" : "=r"(v) : "l"(f + r));
+    return v != 0;
+}
+
+__device__ __forceinline__ void nb_freeze(uint8_t* f, int64_t r) {
+    asm volatile("st.relaxed.gpu.global.u8 [%0], %1;" ::"l"(f + r), "r"(1u));
+}
+
+template <bool kUniform>
+__device__ __forceinline__ void nb_perf_update(int64_t r, float s, float xo, float inv, float tv, const RowCtx& c,
+                                               const NbArgs& a, float* xw, Acc& acc) {
+    const float base = kUniform ? c.base : fmaf(c.one_m_d, tv, c.d_share);
+    const float xn = fmaf(c.d, s, base);
+    Mem<true>::store_x(xw + r, xn);
+    Mem<true>::store_y(a.y + r, xn * inv);
+    const float ch = fabsf(xn - xo);
+    acc.add_r(ch);
+    if (inv != 0.f) acc.kahan(xn - xo);
+    if (ch != 0.f && ch < a.perf_eps) nb_freeze(a.frozen, r);
+}
+
+// Rows without in-edges, perforated.
+template <bool kUniform>
+__device__ __forceinline__ void nb_perf_zero_tile(const Tile& tile, const NbArgs& a, const float* xr, float* xw,
+                                                  const RowCtx& c, Acc& acc, int tid) {
+    for (int64_t r = tile.row_begin + tid; r < tile.row_end; r += kBlock) {
+        const float xo = Mem<true>::load_x(xr + r);
+        if (nb_is_frozen(a.frozen, r)) {
+            Mem<true>::store_x(xw + r, xo);
+            continue;
+        }
+        const float tv = kUniform ? 0.f : ld_stream(a.teleport + r);
+        nb_perf_update<kUniform>(r, 0.f, xo, ld_stream(a.inv_out + r), tv, c, a, xw, acc);
+    }
+}
+
+// Light rows of one degree class, perforated: process_light_tile's groups and
+// passes, with frozen rows gathering nothing.
+template <typename IdxT, bool kUniform>
+__device__ __forceinline__ void nb_perf_light_tile(const Tile& tile, const NbArgs& a, const float* xr, float* xw,
+                                                   const RowCtx& c, Acc& acc, int tid) {
+    const int lg = tile.kind;
+    const int g = 1 << lg;
+    const int rpp = kBlock >> lg;
+    const int grp = tid >> lg;
+    const int gl = tid & (g - 1);
+    for (int64_t r0 = tile.row_begin; r0 < tile.row_end; r0 += 2 * rpp) {
+        int64_t rr[2];
+        bool act[2], fz[2];
+        int64_t b[2], e[2];
+        float xo[2], inv[2], tv[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            rr[q] = r0 + q * rpp + grp;
+            act[q] = rr[q] < tile.row_end;
+            fz[q] = act[q] && nb_is_frozen(a.frozen, rr[q]);
+            b[q] = e[q] = 0;
+            xo[q] = inv[q] = tv[q] = 0.f;
+            if (act[q]) {
+                if (!fz[q]) {
+                    b[q] = row_at<IdxT>(a.rowptr, rr[q]);
+                    e[q] = row_at<IdxT>(a.rowptr, rr[q] + 1);
+                }
+                if (gl == 0) {
+                    xo[q] = Mem<true>::load_x(xr + rr[q]);
+                    inv[q] = ld_stream(a.inv_out + rr[q]);
+                    if (!kUniform) tv[q] = ld_stream(a.teleport + rr[q]);
+                }
+            }
+        }
+        float s[2] = {0.f, 0.f};
+        const int64_t len = max(e[0] - b[0], e[1] - b[1]);
+        for (int64_t k = gl; k < len; k += 2 * g) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int32_t c0 = b[q] + k < e[q] ? ld_stream(a.colidx + b[q] + k) : -1;
+                const int32_t c1 = b[q] + k + g < e[q] ? ld_stream(a.colidx + b[q] + k + g) : -1;
+                s[q] += (c0 >= 0 ? Mem<true>::gather(a.y, c0, c) : 0.f) +
+                        (c1 >= 0 ? Mem<true>::gather(a.y, c1, c) : 0.f);
+            }
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1)
+            if (o < g) {
+                s[0] += __shfl_xor_sync(0xffffffffu, s[0], o);
+                s[1] += __shfl_xor_sync(0xffffffffu, s[1], o);
+            }
+        if (gl == 0) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                if (!act[q]) continue;
+                if (fz[q]) Mem<true>::store_x(xw + rr[q], xo[q]);
+                else nb_perf_update<kUniform>(rr[q], s[q], xo[q], inv[q], tv[q], c, a, xw, acc);
+            }
+        }
+    }
+}
 
 // The block's snapshot of y[0, hub_n): the hub ranks, which the degree
 // binning puts first.  In power-law graphs a few 32-byte sectors of y take a
@@ -125,12 +237,17 @@ __device__ __forceinline__ void refresh_hubs(const float* y, float* sm, int32_t 
 // sum is published with a relaxed store; the warp that gathers a row's last
 // segment then sums the latest partials of all the row's segments -- some may
 // be a sweep old, which an asynchronous iteration allows -- and updates the row.
-template <typename IdxT, bool kUniform>
+template <typename IdxT, bool kUniform, bool kPerf = false>
 __device__ __forceinline__ void warp_segment(int64_t sid, const NbArgs& a, const float* xr, float* xw, const RowCtx& c,
                                              Acc& acc) {
     const int lane = threadIdx.x & 31;
     const int32_t h = a.seg_row[sid];
     const int32_t s0 = a.seg_ptr[h], s1 = a.seg_ptr[h + 1];
+    if (kPerf && nb_is_frozen(a.frozen, h)) {
+        // a frozen heavy row: no gathers; the warp of its last segment carries x
+        if (!kNbHeavyTiles && sid + 1 == s1 && lane == 0) Mem<true>::store_x(xw + h, Mem<true>::load_x(xr + h));
+        return;
+    }
     const int64_t re = row_at<IdxT>(a.rowptr, h + 1);
     const int64_t e0 = row_at<IdxT>(a.rowptr, h) + (sid - s0) * (int64_t)kSegEdges;
     const int64_t e1 = min(e0 + (int64_t)kSegEdges, re);
@@ -161,8 +278,11 @@ __device__ __forceinline__ void warp_segment(int64_t sid, const NbArgs& a, const
         p = warp_sum(p);
         if (lane == 0) {
             const float tv = kUniform ? 0.f : ld_stream(a.teleport + h);
-            row_update<kUniform, true>(h, p, Mem<true>::load_x(xr + h), ld_stream(a.inv_out + h), tv, c, xw, a.y,
-                                       acc);
+            if (kPerf)
+                nb_perf_update<kUniform>(h, p, Mem<true>::load_x(xr + h), ld_stream(a.inv_out + h), tv, c, a, xw, acc);
+            else
+                row_update<kUniform, true>(h, p, Mem<true>::load_x(xr + h), ld_stream(a.inv_out + h), tv, c, xw,
+                                           a.y, acc);
         }
     }
 }
@@ -171,7 +291,8 @@ __device__ __forceinline__ void warp_segment(int64_t sid, const NbArgs& a, const
 // block 0's sweep history (NbArgs::trace, NbArgs::history, when not NULL) and
 // can make block 0 fail (NbArgs::fail_after); the production form carries
 // none of that state.
-template <typename IdxT, bool kUniform, bool kStaged, bool kTrace>
+// kPerf: the perforated form (Alg. 5, see nb_perf_update), production form only.
+template <typename IdxT, bool kUniform, bool kStaged, bool kTrace, bool kPerf = false>
 __global__ void __launch_bounds__(kNbBlock, kNbMinBlocks) k_nonblocking(NbArgs a) {
     // dynamic shared memory: the hub snapshot (hub_n floats), then the staging
     // area of kStaged tiles (kStageFloats floats)
@@ -254,7 +375,7 @@ __global__ void __launch_bounds__(kNbBlock, kNbMinBlocks) k_nonblocking(NbArgs a
         const int64_t rounds = (a.n_seg + wstep - 1) / wstep;
         for (int64_t rd = 0; rd < rounds; ++rd) {
             const int64_t sid = wid + rd * wstep;
-            if (sid < a.n_seg) warp_segment<IdxT, kUniform>(sid, a, xr, xw, c, acc);
+            if (sid < a.n_seg) warp_segment<IdxT, kUniform, kPerf>(sid, a, xr, xw, c, acc);
             if ((rd % kSegPublish) == kSegPublish - 1) warp_publish(true);
             if (a.hub_n && (rd % kHubRefresh) == kHubRefresh - 1) refresh_hubs(a.y, hub_sm, a.hub_n);
         }
@@ -272,7 +393,11 @@ __global__ void __launch_bounds__(kNbBlock, kNbMinBlocks) k_nonblocking(NbArgs a
         int since = 0;
         for (int32_t it = i0; it < i1; it += istep) {
             const Tile item = a.items[it];
-            if (kStaged && item.kind >= 0) {
+            if (kPerf && item.kind >= 0) {
+                nb_perf_light_tile<IdxT, kUniform>(item, a, xr, xw, c, acc, tid);
+            } else if (kPerf && item.kind == kTileZero) {
+                nb_perf_zero_tile<kUniform>(item, a, xr, xw, c, acc, tid);
+            } else if (kStaged && item.kind >= 0) {
                 if (!process_staged_tile<IdxT, kUniform, true>(item, a.rowptr, a.colidx, a.inv_out,
                                                                a.teleport, xr, a.y, xw, a.y, c, acc, tid,
                                                                nb_stage) &&
@@ -388,22 +513,24 @@ __global__ void k_item_edges(const void* rowptr, const Tile* items, int64_t coun
 
 namespace {
 
-template <typename IdxT, bool kUniform, bool kStaged, bool kTrace>
+template <typename IdxT, bool kUniform, bool kStaged, bool kTrace, bool kPerf = false>
 void* nb_kernel() {
-    return (void*)k_nonblocking<IdxT, kUniform, kStaged, kTrace>;
+    return (void*)k_nonblocking<IdxT, kUniform, kStaged, kTrace, kPerf>;
 }
 
-// The traced (diagnostics) form exists without staged tiles only.
+// The traced (diagnostics) form exists without staged tiles only; the
+// perforated form without staged tiles and without tracing.
 template <typename IdxT>
-void* pick_kernel_t(bool uniform, bool staged, bool trace) {
+void* pick_kernel_t(bool uniform, bool staged, bool trace, bool perf) {
+    if (perf) return uniform ? nb_kernel<IdxT, true, false, false, true>() : nb_kernel<IdxT, false, false, false, true>();
     if (trace) return uniform ? nb_kernel<IdxT, true, false, true>() : nb_kernel<IdxT, false, false, true>();
     if (staged) return uniform ? nb_kernel<IdxT, true, true, false>() : nb_kernel<IdxT, false, true, false>();
     return uniform ? nb_kernel<IdxT, true, false, false>() : nb_kernel<IdxT, false, false, false>();
 }
 
-void* pick_kernel(const pr_graph* g, bool uniform, bool staged, bool trace) {
-    return g->idx64 ? pick_kernel_t<int64_t>(uniform, staged, trace)
-                    : pick_kernel_t<int32_t>(uniform, staged, trace);
+void* pick_kernel(const pr_graph* g, bool uniform, bool staged, bool trace, bool perf) {
+    return g->idx64 ? pick_kernel_t<int64_t>(uniform, staged, trace, perf)
+                    : pick_kernel_t<int32_t>(uniform, staged, trace, perf);
 }
 
 // Blocks of `kernel` that fit on one SM with `smem` bytes of dynamic shared
@@ -536,10 +663,15 @@ pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_
     const char* trace_path = getenv("PR_TRACE_NB");
     const bool trace = trace_path && *trace_path;
     const bool diag = trace || g->nb_fail_after > 0;   // the diagnostics form of the kernel
-    const bool staged = !diag && ((g->staged_tiles >> 1) & 1);
+    const bool perf = g->perforation > 0 && g->frozen;  // No-Sync-Opt (Alg. 5 on Alg. 3)
+    if (perf && diag)
+        return fail(PR_ERR_UNSUPPORTED,
+                    "loop perforation in the barrier-free solver cannot be combined with its diagnostics form "
+                    "(PR_TRACE_NB or PR_OPT_NB_FAIL_AFTER)");
+    const bool staged = !diag && !perf && ((g->staged_tiles >> 1) & 1);
     const int32_t hub_n = (int32_t)(std::min<int64_t>(g->nb_hubs, g->n) & ~(int64_t)3);
     const size_t nb_smem = ((size_t)hub_n + (staged ? (size_t)kStageFloats : 0)) * sizeof(float);
-    void* kernel = pick_kernel(g, uniform, staged, diag);
+    void* kernel = pick_kernel(g, uniform, staged, diag, perf);
     int per_sm = 1;
     if ((rc = nb_occupancy(kernel, nb_smem, &per_sm)) != PR_OK) return rc;
     nb_partition(g, per_sm);
@@ -596,6 +728,9 @@ pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_
     na.x = g->x[0];
     na.y = g->y[0];
     na.x_alt = g->x[1];
+    na.frozen = perf ? g->frozen : nullptr;
+    na.perf_eps = perf ? (float)std::pow(10.0, -(double)g->perforation) : 0.f;
+    if (perf) PRK_CHECK(cudaMemsetAsync(g->frozen, 0, (size_t)g->n, s));   // nothing frozen yet
     long long* d_trace = nullptr;
     if (trace) {
         PRK_CHECK(cudaMalloc((void**)&d_trace, (size_t)G * 8 * sizeof(long long)));
@@ -697,6 +832,10 @@ pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_
     }
     launch_finalize(g, a, out, true, s, &launches);
     PRK_CHECK(cudaGetLastError());
+    if (perf) {
+        PRK_CHECK(launch_count_frozen(g, s));
+        ++launches;
+    }
     PRK_CHECK(cudaEventRecord(g->ev_stop, s));
     if (!out_dev)
         PRK_CHECK(cudaMemcpyAsync(x_out, out, (size_t)g->n * sizeof(float), cudaMemcpyDeviceToHost, s));
@@ -717,7 +856,7 @@ pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_
         info->launches = launches;
         info->loop_edge_visits = loop_visits;
         info->ms_loop = ms_loop;
-        info->reserved = 0;
+        info->frozen_rows = perf ? (int32_t)hs->frozen : 0;
     }
     return converged ? PR_OK : PR_NOT_CONVERGED;
 }

@@ -131,8 +131,11 @@ def test_block_per_row_class_against_the_oracle(graph):
     c = loss_weights(n, 7)
     w64, c64 = w.astype(np.float64), c.astype(np.float64)
     with pr.WeightedGraph(rp, ci, w) as g:
-        # tol 1e-6: the stars' hub rank (~0.8) alone changes by ~1e-7 per FP32 rounding
-        x, info = g.solve(D, 1e-6, 500)
+        # The stars' FP32 iterates end in a rounding 2-cycle: the hub (~46% of the mass)
+        # and its 4096 identical leaves flip by a few ulps each iteration, an L1 change of
+        # ~6e-7 in an FP32 emulation of the kernel's arithmetic; their tolerance sits above
+        # that floor.
+        x, info = g.solve(D, 2e-6 if graph.endswith("star") else 1e-6, 500)
         assert info.converged == 1
         # forward: the oracle's Alg. 1 after the same iterations (matching mode)
         xo, _, _ = oracle.w_pagerank(rp, ci, w64, d=D, tol=0.0, max_iter=info.iterations)

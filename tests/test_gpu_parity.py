@@ -555,12 +555,57 @@ def test_loop_perforation(heavy):
         g.set_option(pr.PR_OPT_PERFORATION, 0)
         x3, info3 = g.solve(tol=1e-7, max_iter=300)
     assert np.array_equal(x0, x3)                      # off again: the plain solve
+    assert info1.frozen_rows == 0 and info0.frozen_rows == 0
     assert info2.converged == 1 and info2.iterations <= info0.iterations
+    assert info2.frozen_rows > 0
     xo, _, _, nf = oracle.pagerank_perforated(rp, ci, d=D, tol=1e-7, max_iter=300, eps=1e-11)
     assert nf > 0
     err_gpu = l1(x2, xstar)
     err_oracle = l1(xo, xstar)
     assert err_gpu <= 5 * err_oracle + info2.residual_l1 / (1 - D) + 2e-7, (err_gpu, err_oracle)
+
+
+@pytest.mark.parametrize("graph", ["rmat14", "er14"])
+def test_nosync_opt_perforated_barrier_free(graph):
+    """Alg. 5 applied to the barrier-free solver (the paper's No-Sync-Opt).  A bound no FP32
+    change goes below freezes nothing: the solve is the plain barrier-free one, certified
+    like it.  With eps = 1e-9 rows freeze (reported in frozen_rows), the verifying
+    synchronous update certifies the perforated vector, and its distance to the fixed
+    point is of the size the FP64 oracle's perforated No-Sync runs reach: within 5x the
+    largest of three simulated thread counts (the freeze pattern depends on the update
+    order), plus the bound of the certificate and the FP32 rounding."""
+    rp, ci = gg.rmat(14, seed=21) if graph == "rmat14" else gg.er_dangling(1 << 14, seed=5)
+    xstar, _, _ = oracle.fixed_point(rp, ci, d=D)
+    with pr.Graph(rp, ci) as g:
+        x0, info0 = g.solve(tol=1e-7, max_iter=300, variant="nonblocking")
+        g.set_option(pr.PR_OPT_PERFORATION, 30)
+        x1, info1 = g.solve(tol=1e-7, max_iter=300, variant="nonblocking")
+        g.set_option(pr.PR_OPT_PERFORATION, 9)
+        x2, info2 = g.solve(tol=1e-7, max_iter=300, variant="nonblocking")
+        g.set_option(pr.PR_OPT_PERFORATION, 0)
+        x3, info3 = g.solve(tol=1e-7, max_iter=300, variant="nonblocking")
+    for x, info in ((x0, info0), (x1, info1), (x3, info3)):
+        assert info.converged == 1 and info.frozen_rows == 0
+        assert l1(x, xstar) <= info.residual_l1 / (1 - D) + 2e-7
+    assert info2.converged == 1 and info2.frozen_rows > 0
+    errs = []
+    for p in (4, 64, 1024):
+        xo, _, _, _, nf = oracle.nosync_perforated(rp, ci, d=D, p=p, tol=1e-7, eps=1e-9)
+        assert nf > 0
+        errs.append(l1(xo, xstar))
+    err_gpu = l1(x2, xstar)
+    assert err_gpu <= 5 * max(errs) + info2.residual_l1 / (1 - D) + 2e-7, (err_gpu, errs)
+    assert abs(float(np.sum(x2, dtype=np.float64)) - 1.0) < 1e-5
+
+
+def test_nosync_opt_rejects_the_diagnostics_form():
+    rp, ci = gg.rmat(10, seed=3)
+    with pr.Graph(rp, ci) as g:
+        g.set_option(pr.PR_OPT_PERFORATION, 9)
+        g.set_option(pr.PR_OPT_NB_FAIL_AFTER, 2)
+        with pytest.raises(pr.PageRankError) as e:
+            g.solve(tol=1e-6, variant="nonblocking")
+        assert e.value.status == pr.PR_ERR_UNSUPPORTED
 
 
 # ------------------------------------------------ helping and slow blocks --
