@@ -297,6 +297,13 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
  *                         then sees its stale rows and the solve resumes with
  *                         every block, so the result still meets tol (more
  *                         sweeps, two launches).  0 (default) = off.
+ *   PR_OPT_LIGHT_LANES    lanes per row of the light-row tiles of every
+ *                         solver: 1 (default) by the tile's row count, so that
+ *                         a block covers a tile in one pass of two rows per
+ *                         lane group where it can and each lane walks its
+ *                         rows' edges four at a time; 0 by degree class
+ *                         (2^min(k,5) lanes for degrees in [2^k, 2^(k+1))).
+ *                         Changes the summation order only.
  *   PR_OPT_INDEX64        1: keep 64-bit row offsets on the device even when
  *                         the edge count fits 32 bits (thread-local default
  *                         for the next pr_create_graph, set with g = NULL;
@@ -318,6 +325,7 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
 #define PR_OPT_TMA_TILES 14
 #define PR_OPT_TEST_WITHHOLD_COPY 15
 #define PR_OPT_NB_FAIL_AFTER 16
+#define PR_OPT_LIGHT_LANES 17
 PR_API pr_status pr_set_option(pr_graph* g, int key, int64_t value);
 
 /* Batched personalised PageRank: k independent solves on one graph, one per

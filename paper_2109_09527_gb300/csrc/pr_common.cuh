@@ -59,6 +59,12 @@ constexpr int kPad = 64;                 // spare elements after every device ar
 constexpr int kTileHeavy = -1;           // tile kind: epilogue of heavy rows
 constexpr int kTileZero = -2;            // tile kind: rows without in-edges
 constexpr int kMaxBins = 42;
+// Lanes per row of light tiles (PR_OPT_LIGHT_LANES): 0 by degree class, 1 by
+// the tile's row count (see light_lanes_log2).
+#ifndef PRK_DEFAULT_LANE_MODE
+#define PRK_DEFAULT_LANE_MODE 1
+#endif
+constexpr int kDefaultLaneMode = PRK_DEFAULT_LANE_MODE;
 
 // Pipelined synchronous row kernel (k_rows_tma): a producer warp copies each
 // tile's offsets, column indices and per-row vectors into shared memory with
@@ -158,7 +164,7 @@ struct IterArgs {
     int32_t withhold;            // > 0: test hook of the pipelined kernel (PR_OPT_TEST_WITHHOLD_COPY)
     int64_t nnz;
     int32_t edge;                // 1: the edge-centric iteration (Alg. 2, pr_edge.cu)
-    int32_t pad4;
+    int32_t lane_mode;           // lanes per light row (PR_OPT_LIGHT_LANES)
     const int32_t* out_src;      // edge-centric form: source of each out-edge, in out-edge order
     const int32_t* out_pos;      // edge-centric form: in-edge slot of each out-edge
 };
@@ -186,6 +192,7 @@ struct pr_graph {
     uint8_t* frozen = nullptr;                // frozen rows of the perforated synchronous solve
     int staged_tiles = prk::kDefaultStaged;   // bit 0: Jacobi, bit 1: barrier-free (see PR_OPT_STAGED_TILES)
     int use_tma = 1;                          // PR_OPT_TMA_TILES: pipelined synchronous row kernel
+    int lane_mode = prk::kDefaultLaneMode;    // PR_OPT_LIGHT_LANES: lanes per light row
     int test_withhold = 0;                    // PR_OPT_TEST_WITHHOLD_COPY (test hook, 0 = off)
     int nb_fail_after = 0;                    // PR_OPT_NB_FAIL_AFTER (0 = off)
 

@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(kIterBlock, kGatherMinBlocks) k_rows(IterArgs 
     c.hot = a.hot;
     c.hot_n = a.hot_n;
     c.hot_sm = hot_sm;
+    c.lane_mode = a.lane_mode;
     const Perf pf{a.frozen, a.perf_eps};
     Acc acc;
     const int groups = blockDim.x / kBlock;
@@ -321,7 +322,7 @@ __device__ __forceinline__ void tma_issue(const IterArgs& a, const Tile& tile, i
 template <bool kUniform>
 __device__ __forceinline__ void tma_light_tile(const Tile& tile, const TmaStage& st, const float* y_in,
                                                float* x_out, float* y_out, const RowCtx& c, Acc& acc, int tid) {
-    const int lg = tile.kind;
+    const int lg = light_lanes_log2(tile, c.lane_mode);
     const int g = 1 << lg;
     const int rpp = kBlock >> lg;
     const int grp = tid >> lg;
@@ -342,23 +343,9 @@ __device__ __forceinline__ void tma_light_tile(const Tile& tile, const TmaStage&
             e[q] = act[q] ? rp[ii[q] + 1] - base : 0;
         }
         float s[2] = {0.f, 0.f};
-        const int32_t len = max(e[0] - b[0], e[1] - b[1]);
-        for (int32_t k = gl; k < len; k += 2 * g) {
-            int32_t cc[2][2];
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                cc[q][0] = b[q] + k < e[q] ? st.col[b[q] + k] : -1;
-                cc[q][1] = b[q] + k + g < e[q] ? st.col[b[q] + k + g] : -1;
-            }
-            float v[2][2];
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                v[q][0] = cc[q][0] >= 0 ? Mem<false>::gather(y_in, cc[q][0], c) : 0.f;
-                v[q][1] = cc[q][1] >= 0 ? Mem<false>::gather(y_in, cc[q][1], c) : 0.f;
-            }
-            s[0] += v[0][0] + v[0][1];
-            s[1] += v[1][0] + v[1][1];
-        }
+        const int32_t* col = st.col;
+        gather_row_pair<false>([col](int32_t p) { return col[p]; }, b[0] + gl, e[0], b[1] + gl, e[1], g, y_in, c,
+                               s[0], s[1]);
 #pragma unroll
         for (int m = 1; m < 32; m <<= 1)
             if (m < g) {
@@ -410,6 +397,7 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaMinBlocks) k_rows_tma(IterArg
     c.hot = a.hot;
     c.hot_n = 0;
     c.hot_sm = nullptr;
+    c.lane_mode = a.lane_mode;
     Acc acc;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     bool timed_out = false;
@@ -624,6 +612,7 @@ IterArgs make_args(const pr_graph* g, bool uniform) {
     a.delay_ns = g->delay_ns;
     a.withhold = g->test_withhold;
     a.nnz = g->nnz;
+    a.lane_mode = g->lane_mode;
     return a;
 }
 

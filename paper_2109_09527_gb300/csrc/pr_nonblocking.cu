@@ -103,6 +103,7 @@ struct NbArgs {
     int32_t hub_n;               // ids [0, hub_n) are gathered from the block's snapshot
     int32_t l1_hubs;             // ids [hub_n, l1_hubs) are gathered with weak L1-cached loads
     int32_t fail_after;          // > 0: block 0 leaves after this many sweeps (a failing thread, Fig. 9)
+    int32_t lane_mode;           // lanes per light row (PR_OPT_LIGHT_LANES)
     uint8_t* frozen;             // loop perforation (Alg. 5): 1 = row frozen (perforated form only)
     float perf_eps;              // freeze bound: a nonzero change below it freezes the row
 };
@@ -160,7 +161,7 @@ __device__ __forceinline__ void nb_perf_zero_tile(const Tile& tile, const NbArgs
 template <typename IdxT, bool kUniform>
 __device__ __forceinline__ void nb_perf_light_tile(const Tile& tile, const NbArgs& a, const float* xr, float* xw,
                                                    const RowCtx& c, Acc& acc, int tid) {
-    const int lg = tile.kind;
+    const int lg = light_lanes_log2(tile, c.lane_mode);
     const int g = 1 << lg;
     const int rpp = kBlock >> lg;
     const int grp = tid >> lg;
@@ -190,16 +191,9 @@ __device__ __forceinline__ void nb_perf_light_tile(const Tile& tile, const NbArg
             }
         }
         float s[2] = {0.f, 0.f};
-        const int64_t len = max(e[0] - b[0], e[1] - b[1]);
-        for (int64_t k = gl; k < len; k += 2 * g) {
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int32_t c0 = b[q] + k < e[q] ? ld_stream(a.colidx + b[q] + k) : -1;
-                const int32_t c1 = b[q] + k + g < e[q] ? ld_stream(a.colidx + b[q] + k + g) : -1;
-                s[q] += (c0 >= 0 ? Mem<true>::gather(a.y, c0, c) : 0.f) +
-                        (c1 >= 0 ? Mem<true>::gather(a.y, c1, c) : 0.f);
-            }
-        }
+        const int32_t* colidx = a.colidx;
+        gather_row_pair<true, 2>([colidx](int64_t p) { return ld_stream(colidx + p); }, b[0] + gl, e[0], b[1] + gl,
+                              e[1], g, a.y, c, s[0], s[1]);
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1)
             if (o < g) {
@@ -344,6 +338,7 @@ __global__ void __launch_bounds__(kNbBlock, kNbMinBlocks) k_nonblocking(NbArgs a
         if (a.l1_hubs > 0 && threadIdx.x == 0) asm volatile("fence.acq_rel.gpu;" ::: "memory");
         c.hot_n = a.hub_n;
         c.hot_sm = hub_sm;
+        c.lane_mode = a.lane_mode;
         float r_sweep = 0.f;
         // Each warp publishes the mass change of its own rows since its last
         // publication (one FP64 atomic add by lane 0) and re-reads the running
@@ -728,6 +723,7 @@ pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_
     na.x = g->x[0];
     na.y = g->y[0];
     na.x_alt = g->x[1];
+    na.lane_mode = g->lane_mode;
     na.frozen = perf ? g->frozen : nullptr;
     na.perf_eps = perf ? (float)std::pow(10.0, -(double)g->perforation) : 0.f;
     if (perf) PRK_CHECK(cudaMemsetAsync(g->frozen, 0, (size_t)g->n, s));   // nothing frozen yet

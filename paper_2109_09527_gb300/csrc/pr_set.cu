@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(kBlock) k_set_rows(SetArgs a, const float* __r
     c.hot = a.it.hot;
     c.hot_n = 0;
     c.hot_sm = nullptr;
+    c.lane_mode = a.it.lane_mode;
     Acc acc;
     for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
         const Tile tile = a.tiles[t];

@@ -245,7 +245,33 @@ struct RowCtx {
     int32_t hot;      // L1 policy of the global gathers (see ld_gather)
     int32_t hot_n;    // binned ids [0, hot_n) are read from hot_sm (shared memory)
     const float* hot_sm;
+    int32_t lane_mode = kDefaultLaneMode;   // lanes per light row: see light_lanes_log2
 };
+
+// Lanes per row of a light tile (log2).  Mode 0: by degree class, 2^min(k, 5)
+// lanes for rows of degree in [2^k, 2^(k+1)) (tile.kind).  Mode 1: by the
+// tile's row count, the largest power of two g <= 32 with rows <= 2 kBlock / g,
+// so the block's groups cover the tile in one pass of two rows per group
+// where they can (a tile of more rows takes ceil(rows / 2 kBlock) passes with
+// g = 1), and each lane walks about edges / kBlock of the tile's edges.
+__device__ __forceinline__ int light_lanes_log2(const Tile& tile, int mode) {
+    if (mode == 0) return tile.kind;
+    const int rows = tile.row_end - tile.row_begin;
+    const int per = rows > 0 ? (2 * kBlock) / rows : 32;
+    if (per <= 1) return 0;
+    return 31 - __clz((unsigned)(per < 32 ? per : 32));
+}
+
+// This lane's share of the sums of two rows: edges b0, b0 + g, ... below e0
+// and b1, b1 + g, ... below e1 (b = the row's first edge + the lane's index
+// in its group), kU edges of each row per step, so that up to 2 kU gathers
+// are in flight; with kU = 4 each step adds ((v0 + v1) + (v2 + v3)) per row.
+// col(p) is the source id of edge p.  Every synchronous light-tile path sums
+// through this routine with kU = 4, so they agree bit for bit on a row's sum;
+// the barrier-free kernel, compiled for fewer registers, takes kU = 2.
+template <bool kInPlace, int kU = 4, typename OffT, typename ColAt>
+__device__ __forceinline__ void gather_row_pair(const ColAt& col, OffT b0, OffT e0, OffT b1, OffT e1, int g,
+                                                const float* y, const RowCtx& c, float& s0, float& s1);
 
 template <bool kInPlace>
 struct Mem;
@@ -271,6 +297,35 @@ struct Mem<true> {
     static __device__ __forceinline__ void store_x(float* p, float v) { st_relaxed_p<PRK_L2_STREAM>(p, v); }
     static __device__ __forceinline__ void store_y(float* p, float v) { st_relaxed_p<PRK_L2_GATHER>(p, v); }
 };
+
+template <bool kInPlace, int kU, typename OffT, typename ColAt>
+__device__ __forceinline__ void gather_row_pair(const ColAt& col, OffT b0, OffT e0, OffT b1, OffT e1, int g,
+                                                const float* y, const RowCtx& c, float& s0, float& s1) {
+    static_assert(kU == 2 || kU == 4, "two or four edges per row per step");
+    while (b0 < e0 || b1 < e1) {
+        int32_t c0[kU], c1[kU];
+#pragma unroll
+        for (int j = 0; j < kU; ++j) {
+            c0[j] = b0 + j * g < e0 ? col(b0 + j * g) : -1;
+            c1[j] = b1 + j * g < e1 ? col(b1 + j * g) : -1;
+        }
+        float v0[kU], v1[kU];
+#pragma unroll
+        for (int j = 0; j < kU; ++j) {
+            v0[j] = c0[j] >= 0 ? Mem<kInPlace>::gather(y, c0[j], c) : 0.f;
+            v1[j] = c1[j] >= 0 ? Mem<kInPlace>::gather(y, c1[j], c) : 0.f;
+        }
+        if constexpr (kU == 4) {
+            s0 += (v0[0] + v0[1]) + (v0[2] + v0[3]);
+            s1 += (v1[0] + v1[1]) + (v1[2] + v1[3]);
+        } else {
+            s0 += v0[0] + v0[1];
+            s1 += v1[0] + v1[1];
+        }
+        b0 += kU * g;
+        b1 += kU * g;
+    }
+}
 
 // Per-thread accumulators, both Kahan-compensated in FP32 (FP64 arithmetic
 // is a slow pipe on this GPU) and handed to the FP64 cross-thread reduction:
@@ -346,18 +401,18 @@ __device__ __forceinline__ void process_zero_tile(const Tile& tile, const float*
 // Tile functions run on a 256-thread (kBlock) group of whole warps; tid is
 // the thread's index in that group.
 //
-// Light rows of one degree class: groups of g = 2^tile.kind lanes gather one
-// row each, two rows per group at a time (rows r and r + 256/g), so that a lane
-// has up to four colidx loads and four gathers in flight; coalesced colidx
-// reads within the group; shuffle reduction; the group's first lane updates
-// both rows.
+// Light rows of one degree class: groups of g = 2^light_lanes_log2 lanes
+// gather one row each, two rows per group at a time (rows r and r + 256/g),
+// each lane up to four edges of each row per step (gather_row_pair);
+// coalesced colidx reads within the group; shuffle reduction; the group's
+// first lane updates both rows.
 template <typename IdxT, bool kUniform, bool kInPlace>
 __device__ __forceinline__ void process_light_tile(const Tile& tile, const void* rowptr,
                                                    const int32_t* colidx, const float* inv_out,
                                                    const float* teleport, const float* x_in,
                                                    const float* y_in, float* x_out, float* y_out,
                                                    const RowCtx& c, Acc& acc, int tid) {
-    const int lg = tile.kind;
+    const int lg = light_lanes_log2(tile, c.lane_mode);
     const int g = 1 << lg;
     const int rpp = kBlock >> lg;  // rows per pass of the whole group set
     const int grp = tid >> lg;
@@ -384,23 +439,8 @@ __device__ __forceinline__ void process_light_tile(const Tile& tile, const void*
             }
         }
         float s[2] = {0.f, 0.f};
-        const int64_t len = max(e[0] - b[0], e[1] - b[1]);
-        for (int64_t k = gl; k < len; k += 2 * g) {
-            int32_t cc[2][2];
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                cc[q][0] = b[q] + k < e[q] ? ld_stream(colidx + b[q] + k) : -1;
-                cc[q][1] = b[q] + k + g < e[q] ? ld_stream(colidx + b[q] + k + g) : -1;
-            }
-            float v[2][2];
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                v[q][0] = cc[q][0] >= 0 ? Mem<kInPlace>::gather(y_in, cc[q][0], c) : 0.f;
-                v[q][1] = cc[q][1] >= 0 ? Mem<kInPlace>::gather(y_in, cc[q][1], c) : 0.f;
-            }
-            s[0] += v[0][0] + v[0][1];
-            s[1] += v[1][0] + v[1][1];
-        }
+        gather_row_pair<kInPlace, kInPlace ? 2 : 4>([&](int64_t p) { return ld_stream(colidx + p); }, b[0] + gl,
+                                                    e[0], b[1] + gl, e[1], g, y_in, c, s[0], s[1]);
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1)
             if (o < g) {
@@ -467,7 +507,7 @@ __device__ __forceinline__ void perf_light_tile(const Tile& tile, const void* ro
                                                 const float* inv_out, const float* teleport, const float* x_in,
                                                 const float* y_in, float* x_out, float* y_out, const RowCtx& c,
                                                 const Perf& p, Acc& acc, int tid) {
-    const int lg = tile.kind;
+    const int lg = light_lanes_log2(tile, c.lane_mode);
     const int g = 1 << lg;
     const int rpp = kBlock >> lg;
     const int grp = tid >> lg;
@@ -497,16 +537,8 @@ __device__ __forceinline__ void perf_light_tile(const Tile& tile, const void* ro
             }
         }
         float s[2] = {0.f, 0.f};
-        const int64_t len = max(e[0] - b[0], e[1] - b[1]);
-        for (int64_t k = gl; k < len; k += 2 * g) {
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int32_t c0 = b[q] + k < e[q] ? ld_stream(colidx + b[q] + k) : -1;
-                const int32_t c1 = b[q] + k + g < e[q] ? ld_stream(colidx + b[q] + k + g) : -1;
-                s[q] += (c0 >= 0 ? Mem<false>::gather(y_in, c0, c) : 0.f) +
-                        (c1 >= 0 ? Mem<false>::gather(y_in, c1, c) : 0.f);
-            }
-        }
+        gather_row_pair<false>([&](int64_t q) { return ld_stream(colidx + q); }, b[0] + gl, e[0], b[1] + gl, e[1],
+                               g, y_in, c, s[0], s[1]);
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1)
             if (o < g) {

@@ -426,6 +426,43 @@ def test_pipelined_row_kernel_matches_row_kernel_and_oracle(build):
     assert info1.residual_l1 == pytest.approx(l1o, rel=1e-3, abs=1e-9)
 
 
+@pytest.mark.parametrize("build", ["rmat15", "er", "rmat12_heavy64"])
+def test_light_lane_mappings_match_the_oracle(build):
+    """Both lane mappings of the light-row tiles (PR_OPT_LIGHT_LANES: by degree class, or
+    by the tile's row count with four edges per lane and row in flight), on the pipelined
+    kernel, the row kernel and the barrier-free kernel: the synchronous solve in matching
+    mode against the oracle, the barrier-free solve against the fixed point.  The mapping
+    changes only the summation order."""
+    heavy = 64 if build == "rmat12_heavy64" else 256
+    if build == "rmat15":
+        rp, ci = gg.rmat(15, seed=15)
+    elif build == "er":
+        rp, ci = gg.er_dangling(30011, seed=12)
+    else:
+        rp, ci = gg.rmat(12, seed=8)
+    pr.set_heavy_degree(heavy)
+    try:
+        g = pr.Graph(rp, ci)
+    finally:
+        pr.set_heavy_degree(pr.DEFAULT_HEAVY_DEGREE)
+    xstar, _, _ = oracle.fixed_point(rp, ci, d=D)
+    with g:
+        for mode in (0, 1):
+            g.set_option(pr.PR_OPT_LIGHT_LANES, mode)
+            for tma in (1, 0):
+                g.set_option(pr.PR_OPT_TMA_TILES, tma)
+                x, info = g.solve(tol=1e-6, max_iter=200, variant="jacobi")
+                assert info.converged == 1
+                xo = matching(rp, ci, x, info)
+                assert l1(x, xo) <= 1e-6 and max_rel(x, xo) <= 1e-4, (mode, tma)
+            g.set_option(pr.PR_OPT_TMA_TILES, 1)
+            x, info = g.solve(tol=1e-6, max_iter=200, variant="nonblocking")
+            assert info.converged == 1
+            assert l1(x, xstar) <= info.residual_l1 / (1 - D) + 2e-7, mode
+        with pytest.raises(pr.PageRankError):
+            g.set_option(pr.PR_OPT_LIGHT_LANES, 2)
+
+
 @pytest.mark.parametrize("batch", range(4))
 def test_random_small_graphs_both_variants(batch):
     """Forty seeded random digraphs (1 to 600 vertices, 0 to 8 edges per vertex on average,
@@ -546,6 +583,8 @@ def test_loop_perforation(heavy):
         pr.set_heavy_degree(pr.DEFAULT_HEAVY_DEGREE)
     xstar, _, _ = oracle.fixed_point(rp, ci, d=D)
     with g:
+        # the perforated solve runs on the row kernel: compare with the same kernel
+        g.set_option(pr.PR_OPT_TMA_TILES, 0)
         x0, info0 = g.solve(tol=1e-7, max_iter=300)
         g.set_option(pr.PR_OPT_PERFORATION, 30)
         x1, info1 = g.solve(tol=1e-7, max_iter=300)
@@ -619,6 +658,9 @@ def test_dynamic_tiles_take_over_a_slow_block():
     rp, ci = gg.rmat(20, seed=23)     # several tiles per block
     with pr.Graph(rp, ci) as g:
         assert g.stats()["n_tiles"] > 3 * 608
+        # the reference is the row kernel the delayed runs use (the pipelined kernel's
+        # smaller tiles give its light rows other lane groups: other rounding)
+        g.set_option(pr.PR_OPT_TMA_TILES, 0)
         x_ref, info_ref = g.solve(tol=1e-6, max_iter=200)
         g.set_option(pr.PR_OPT_DELAY_NS, 100000)
         times, xs = {}, {}
