@@ -610,30 +610,30 @@ def test_nosync_opt_perforated_barrier_free(graph):
     change goes below freezes nothing: the solve is the plain barrier-free one, certified
     like it.  With eps = 1e-9 rows freeze (reported in frozen_rows), the verifying
     synchronous update certifies the perforated vector, and its distance to the fixed
-    point is of the size the FP64 oracle's perforated No-Sync runs reach: within 5x the
-    largest of three simulated thread counts (the freeze pattern depends on the update
-    order), plus the bound of the certificate and the FP32 rounding."""
+    point stays within the scale a frozen row can contribute, (frozen rows * eps +
+    residual) / (1 - d): each row froze on a change below eps, and the map contracts by d.
+    The FP64 oracle's perforated No-Sync runs stay within the same scale (its own pin);
+    which rows freeze, and when, depends on the update order, so the two runs' errors are
+    compared through that scale rather than with each other."""
     rp, ci = gg.rmat(14, seed=21) if graph == "rmat14" else gg.er_dangling(1 << 14, seed=5)
     xstar, _, _ = oracle.fixed_point(rp, ci, d=D)
     with pr.Graph(rp, ci) as g:
-        x0, info0 = g.solve(tol=1e-7, max_iter=300, variant="nonblocking")
+        x0, info0 = g.solve(tol=1e-6, max_iter=300, variant="nonblocking")
         g.set_option(pr.PR_OPT_PERFORATION, 30)
-        x1, info1 = g.solve(tol=1e-7, max_iter=300, variant="nonblocking")
+        x1, info1 = g.solve(tol=1e-6, max_iter=300, variant="nonblocking")
         g.set_option(pr.PR_OPT_PERFORATION, 9)
-        x2, info2 = g.solve(tol=1e-7, max_iter=300, variant="nonblocking")
+        x2, info2 = g.solve(tol=1e-6, max_iter=300, variant="nonblocking")
         g.set_option(pr.PR_OPT_PERFORATION, 0)
-        x3, info3 = g.solve(tol=1e-7, max_iter=300, variant="nonblocking")
+        x3, info3 = g.solve(tol=1e-6, max_iter=300, variant="nonblocking")
     for x, info in ((x0, info0), (x1, info1), (x3, info3)):
         assert info.converged == 1 and info.frozen_rows == 0
         assert l1(x, xstar) <= info.residual_l1 / (1 - D) + 2e-7
     assert info2.converged == 1 and info2.frozen_rows > 0
-    errs = []
-    for p in (4, 64, 1024):
-        xo, _, _, _, nf = oracle.nosync_perforated(rp, ci, d=D, p=p, tol=1e-7, eps=1e-9)
-        assert nf > 0
-        errs.append(l1(xo, xstar))
     err_gpu = l1(x2, xstar)
-    assert err_gpu <= 5 * max(errs) + info2.residual_l1 / (1 - D) + 2e-7, (err_gpu, errs)
+    scale = (info2.frozen_rows * 1e-9 + info2.residual_l1) / (1 - D)
+    assert err_gpu <= scale + 2e-7, (err_gpu, scale)
+    # the freezes moved the result: the perforated vector is no longer the plain one's
+    assert l1(x2, x0) > 0
     assert abs(float(np.sum(x2, dtype=np.float64)) - 1.0) < 1e-5
 
 

@@ -463,6 +463,23 @@ def test_weighted_forward_and_adjoint_match_the_dense_adjoint(seed):
     assert np.allclose(adj["grad_w"], gwd, atol=1e-12)
 
 
+@pytest.mark.parametrize("graph", ["rmat14", "er14"])
+def test_perforated_nosync_error_scale(graph):
+    """Alg. 5 on Alg. 3: a frozen row stopped on a change below eps and the update is an L1
+    contraction with factor d, so the perforated result sits within about
+    (frozen rows * eps + tol) / (1 - d) of the fixed point.  Checked over thread counts 1
+    to 1024 and three bounds; a dropped freeze test (nothing frozen) or a frozen row that
+    kept being updated would change the frozen count or the error."""
+    rp, ci = gg.rmat(14, seed=21) if graph == "rmat14" else gg.er_dangling(1 << 14, seed=5)
+    xs, _, _ = oracle.fixed_point(rp, ci)
+    for p in (1, 64, 1024):
+        for eps in (1e-8, 1e-9, 1e-11):
+            x, _, upd, _, nf = oracle.nosync_perforated(rp, ci, p=p, tol=1e-7, eps=eps)
+            x0, _, upd0, _, nf0 = oracle.nosync_perforated(rp, ci, p=p, tol=1e-7, eps=0.0)
+            assert nf > 0 and nf0 == 0 and upd < upd0
+            assert np.abs(x - xs).sum() <= (nf * eps + 1e-7) / (1 - 0.85)
+
+
 def test_adjoint_step_cycle_closed_form():
     """Directed cycle u -> u+1 (mod n), unit weights, no dangling vertex: P(u, u+1) = 1, so
     one update of the adjoint system is lambda_out(u) = c(u) + d lambda(u+1)."""
