@@ -40,6 +40,12 @@
 
 namespace prk {
 
+// 1: the segment kernel loads the next 256-edge chunk's indices while the
+// current chunk's gathers are in flight; 0: 512-edge chunks, loads then gathers.
+#ifndef PRK_SEG_PIPE
+#define PRK_SEG_PIPE 0
+#endif
+
 // --------------------------------------------------------- iteration kernels --
 
 // Copy y[0, hot_n) -- the sources of most edges in a power-law graph, which
@@ -70,6 +76,35 @@ __global__ void __launch_bounds__(kIterBlock, kGatherMinBlocks) k_heavy_segments
         const int64_t e1 = min(e0 + (int64_t)kSegEdges, re);
         const int64_t a0 = e0 & ~(int64_t)3;   // 16-byte aligned start
         float acc = 0.f;
+#if PRK_SEG_PIPE
+        // 256-edge chunks, the next chunk's indices loaded while this chunk's
+        // gathers are in flight
+        int4 cv[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int64_t p = a0 + 128 * j + 4 * lane;
+            cv[j] = p < e1 ? ld_stream4(a.colidx + p) : make_int4(0, 0, 0, 0);
+        }
+        for (int64_t base = a0; base < e1; base += 256) {
+            int4 nx[2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int64_t p = base + 256 + 128 * j + 4 * lane;
+                nx[j] = p < e1 ? ld_stream4(a.colidx + p) : make_int4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int64_t p = base + 128 * j + 4 * lane;
+                const float v0 = (p + 0 >= e0 && p + 0 < e1) ? Mem<false>::gather(y, cv[j].x, c) : 0.f;
+                const float v1 = (p + 1 >= e0 && p + 1 < e1) ? Mem<false>::gather(y, cv[j].y, c) : 0.f;
+                const float v2 = (p + 2 >= e0 && p + 2 < e1) ? Mem<false>::gather(y, cv[j].z, c) : 0.f;
+                const float v3 = (p + 3 >= e0 && p + 3 < e1) ? Mem<false>::gather(y, cv[j].w, c) : 0.f;
+                acc += (v0 + v1) + (v2 + v3);
+            }
+            cv[0] = nx[0];
+            cv[1] = nx[1];
+        }
+#else
         for (int64_t base = a0; base < e1; base += 512) {
             int4 cv[4];
 #pragma unroll
@@ -87,6 +122,7 @@ __global__ void __launch_bounds__(kIterBlock, kGatherMinBlocks) k_heavy_segments
                 acc += (v0 + v1) + (v2 + v3);
             }
         }
+#endif
         acc = warp_sum(acc);
         if (lane == 0) a.seg_sum[s] = acc;
     }
