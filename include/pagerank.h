@@ -247,6 +247,18 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
  *                         copy to the end.  X stays FP32 throughout, so the
  *                         result meets the same tol; BF16's 2^-9 rounding
  *                         limits how far the BF16 phase can go (m ~ 2..3).
+ *   PR_OPT_BATCH_DC       batched solver only: 0 (default) off; M in 1..32
+ *                         runs BF16 storage by defect correction instead:
+ *                         every FP32 step X' = F(X) (whose L1 change per
+ *                         column is the stopping test, as in the plain form)
+ *                         is followed by M sweeps delta <- r + A delta on the
+ *                         error equation, r = X' - X, gathering delta / outdeg
+ *                         from a BF16 copy (FP32 sums), and X <- X + delta.
+ *                         BF16 rounds the correction, not the ranks, so the
+ *                         columns reach the same tol.  info.iterations counts
+ *                         the FP32 steps; edge_visits counts both kinds of
+ *                         sweep.  Takes precedence over PR_OPT_BATCH_BF16; a
+ *                         host-driven loop (no CUDA graph).
  *   PR_OPT_PERFORATION    loop perforation (Alg. 5) in the synchronous solver
  *                         (PR_JACOBI, pr_iterate) and in the barrier-free one
  *                         (PR_NONBLOCKING: the paper's No-Sync-Opt, Section
@@ -326,6 +338,7 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
 #define PR_OPT_TEST_WITHHOLD_COPY 15
 #define PR_OPT_NB_FAIL_AFTER 16
 #define PR_OPT_LIGHT_LANES 17
+#define PR_OPT_BATCH_DC 18
 PR_API pr_status pr_set_option(pr_graph* g, int key, int64_t value);
 
 /* Batched personalised PageRank: k independent solves on one graph, one per

@@ -71,6 +71,9 @@ struct BatchState {
     const int32_t* tptr;             // teleport nonzeros of each binned row (CSR), when !uniform
     const int32_t* tcol;
     const float* tval;
+    int32_t dc_sweeps;               // defect correction: BF16 correction sweeps made
+    int32_t pad1;
+    double Ddc[kBK];                 // defect correction: dangling mass of each column of delta
     double D[kBK];                   // dangling mass of each column of the current input
     double T[kBK];                   // teleport sum of each column
     double resid[kBK];               // last L1 change of each column
@@ -373,6 +376,132 @@ __global__ void __launch_bounds__(kBlock) k_b_update(BatchArgs a, const float* _
     }
 }
 
+// ---- BF16 storage by defect correction (PR_OPT_BATCH_DC) -------------------
+//
+// The iteration x <- F(x) = b + A x of Eq. 1 (A = d (P^T + 1 a^T / n)) is
+// split into an outer FP32 step and an inner correction solve.  From the
+// current X, the FP32 step gives X' = F(X) and r = X' - X (its L1 norm per
+// column is the usual stopping test, on FP32 iterates).  The error e = x* - X
+// solves e = r + A e, which M sweeps approximate from delta_0 = r:
+//   delta_{m+1} = r + A delta_m,
+// gathering delta / outdeg from a BF16 copy (64-byte rows, FP32 sums).  Then
+// X <- X + delta_M.  BF16 rounds delta, not x, so its error shrinks with the
+// residual and the outer steps reach the FP32 tolerance.
+
+// R = X' - X and delta_0 = R for the active columns (0 for the others), the
+// BF16 quotient of delta_0 and its dangling mass per column; the gathers that
+// follow read BF16.
+__global__ void __launch_bounds__(kBlock) k_b_dc_prep(BatchArgs a, const float* __restrict__ Xprev,
+                                                      const float* __restrict__ Xcur, float* __restrict__ R,
+                                                      __nv_bfloat16* __restrict__ Yd16) {
+    BatchState* st = a.state;
+    if (batch_done(st)) return;
+    const int lane = threadIdx.x & 31;
+    const bool active = (st->active >> lane) & 1u;
+    KahanF dm;
+    const int64_t rows_per_pass = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < a.n; v += rows_per_pass) {
+        const size_t i = (size_t)v * kBK + lane;
+        const float r = active ? __ldcs(Xcur + i) - __ldcs(Xprev + i) : 0.f;
+        const float inv = __ldg(a.inv_out + v);
+        R[i] = r;
+        Yd16[i] = __float2bfloat16_rn(r * inv);
+        if (inv == 0.f) dm.add(r);
+    }
+    double Dd, unused;
+    if (batch_columns_to_grid(dm.value(), 0.0, a.slots, &st->ticket, &Dd, &unused) && threadIdx.x < 32) {
+        st->Ddc[lane] = Dd;
+        if (lane == 0) {
+            st->bf16 = 1;
+            st->ticket = 0;
+        }
+    }
+}
+
+// One correction sweep: delta'(v, j) = R(v, j) + d (S(v, j) + Ddc_j / n) from
+// the gathered sums of the BF16 quotient of delta; writes delta' (FP32) and
+// its BF16 quotient, and the new Ddc.
+__global__ void __launch_bounds__(kBlock) k_b_dc_update(BatchArgs a, const float* __restrict__ R,
+                                                        float* __restrict__ Dl, __nv_bfloat16* __restrict__ Yd16) {
+    BatchState* st = a.state;
+    if (batch_done(st)) return;
+    const int lane = threadIdx.x & 31;
+    const float d = (float)st->d;
+    const float share = (float)(st->d * st->Ddc[lane] * st->inv_n);
+    KahanF dm;
+    constexpr int kRows = 4;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t step = (((int64_t)gridDim.x * blockDim.x) >> 5) * kRows;
+    for (int64_t v0 = warp * kRows; v0 < a.n; v0 += step) {
+        float sv[kRows], rv[kRows], inv[kRows];
+#pragma unroll
+        for (int q = 0; q < kRows; ++q) {
+            const int64_t v = v0 + q;
+            sv[q] = rv[q] = inv[q] = 0.f;
+            if (v < a.n) {
+                if (v < a.n_heavy) {
+                    const int32_t q1 = a.seg_ptr[v + 1];
+                    for (int32_t j = a.seg_ptr[v]; j < q1; ++j) sv[q] += __ldcg(a.P + (size_t)j * kBK + lane);
+                } else if (v < a.zero_start) {
+                    sv[q] = __ldcs(a.S + (size_t)v * kBK + lane);
+                }
+                rv[q] = __ldcs(R + (size_t)v * kBK + lane);
+                inv[q] = __ldg(a.inv_out + v);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kRows; ++q) {
+            const int64_t v = v0 + q;
+            if (v >= a.n) break;
+            const float dn = rv[q] + d * (sv[q] + share);   // 0 for inactive columns (R = 0, S = 0)
+            Dl[(size_t)v * kBK + lane] = dn;
+            Yd16[(size_t)v * kBK + lane] = __float2bfloat16_rn(dn * inv[q]);
+            if (inv[q] == 0.f) dm.add(dn);
+        }
+    }
+    double Dd, unused;
+    if (batch_columns_to_grid(dm.value(), 0.0, a.slots, &st->ticket, &Dd, &unused) && threadIdx.x < 32) {
+        st->Ddc[lane] = Dd;
+        if (lane == 0) {
+            st->dc_sweeps += 1;
+            st->ticket = 0;
+        }
+    }
+}
+
+// X <- Xprev + delta for the active columns (the others keep the FP32 step's
+// copy), Y = X / outdeg, the dangling mass of every column; the gathers that
+// follow read FP32 again.
+__global__ void __launch_bounds__(kBlock) k_b_dc_apply(BatchArgs a, const float* __restrict__ Xprev,
+                                                       float* __restrict__ Xcur, const float* __restrict__ Dl,
+                                                       float* __restrict__ Ycur) {
+    BatchState* st = a.state;
+    if (batch_done(st)) return;
+    const int lane = threadIdx.x & 31;
+    const bool active = (st->active >> lane) & 1u;
+    KahanF dm;
+    const int64_t rows_per_pass = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < a.n; v += rows_per_pass) {
+        const size_t i = (size_t)v * kBK + lane;
+        const float inv = __ldg(a.inv_out + v);
+        float x = __ldcs(Xcur + i);
+        if (active) {
+            x = __ldcs(Xprev + i) + __ldcs(Dl + i);
+            Xcur[i] = x;
+            Ycur[i] = x * inv;
+        }
+        if (inv == 0.f) dm.add(x);
+    }
+    double Dn, unused;
+    if (batch_columns_to_grid(dm.value(), 0.0, a.slots, &st->ticket, &Dn, &unused) && threadIdx.x < 32) {
+        st->D[lane] = Dn;
+        if (lane == 0) {
+            st->bf16 = 0;
+            st->ticket = 0;
+        }
+    }
+}
+
 // X = T (binned order, 32 wide), Y = X / outdeg, per-column D and T; resets
 // the loop state.  t_dense: caller order, n x k, or NULL for uniform.
 __global__ void __launch_bounds__(kBlock) k_b_init(BatchArgs a, const float* __restrict__ t_dense,
@@ -484,6 +613,8 @@ struct BatchCtx {
     int graph_bf16 = -1;             // storage mode the captured loop graph was built for
     float* S = nullptr;
     float* P = nullptr;
+    float* R = nullptr;              // defect correction: residual X' - X of the FP32 step
+    float* Dl = nullptr;             // defect correction: latest correction delta (FP32)
     int32_t* tptr = nullptr;
     int32_t* tcol = nullptr;
     float* tval = nullptr;
@@ -556,6 +687,33 @@ cudaError_t enqueue_batch(const pr_graph* g, const BatchCtx* b, const BatchArgs&
                           cudaStream_t s) {
     return g->idx64 ? enqueue_batch_iteration<int64_t>(g, b, a, src, bf16, s)
                     : enqueue_batch_iteration<int32_t>(g, b, a, src, bf16, s);
+}
+
+// One outer step of the defect-correction form: the FP32 step X[src] ->
+// X[1-src], the residual, `sweeps` BF16 correction sweeps, the correction
+// applied to X[1-src].  Returns the kernels launched.
+template <typename IdxT>
+cudaError_t enqueue_dc_step(const pr_graph* g, const BatchCtx* b, const BatchArgs& a, int src, int sweeps,
+                            cudaStream_t s, int* launches) {
+    cudaError_t e = enqueue_batch_iteration<IdxT>(g, b, a, src, false, s);
+    if (e != cudaSuccess) return e;
+    *launches += g->n_seg > 0 ? 3 : 2;
+    const int ug = update_grid(g, b);
+    const int gs = batch_grid(g, g->n_seg, g_occ_bseg), gl = batch_grid(g, b->n_tasks, g_occ_blight);
+    k_b_dc_prep<<<ug, kBlock, 0, s>>>(a, b->X[src], b->X[1 - src], b->R, b->Y16[0]);
+    ++*launches;
+    for (int m = 0; m < sweeps; ++m) {
+        if (g->n_seg > 0) {
+            k_b_segments<IdxT, __nv_bfloat16><<<gs, kBlock, 0, s>>>(a, b->Y16[m & 1]);
+            ++*launches;
+        }
+        k_b_light<IdxT, __nv_bfloat16><<<gl, kBlock, 0, s>>>(a, b->Y16[m & 1]);
+        k_b_dc_update<<<ug, kBlock, 0, s>>>(a, b->R, b->Dl, b->Y16[(m + 1) & 1]);
+        *launches += 2;
+    }
+    k_b_dc_apply<<<ug, kBlock, 0, s>>>(a, b->X[src], b->X[1 - src], b->Dl, b->Y[1 - src]);
+    ++*launches;
+    return cudaGetLastError();
 }
 
 pr_status ensure_batch(pr_graph* g) {
@@ -671,7 +829,7 @@ void drop_batch_graph(pr_graph* g) {
 void destroy_batch(pr_graph* g) {
     BatchCtx* b = g->batch;
     if (!b) return;
-    void* dev[] = {b->X[0], b->X[1], b->Y[0], b->Y[1], b->Y16[0], b->Y16[1], b->S, b->P, b->tptr,
+    void* dev[] = {b->X[0], b->X[1], b->Y[0], b->Y[1], b->Y16[0], b->Y16[1], b->S, b->P, b->R, b->Dl, b->tptr,
                    b->tcol, b->tval, b->tcount, b->t_stage, b->out_stage, b->state, b->slots, b->tasks};
     for (void* p : dev)
         if (p) cudaFree(p);
@@ -719,11 +877,17 @@ extern "C" pr_status pr_solve_batched(pr_graph* g, float damping, double tol, in
         out = b->out_stage;
     }
 
-    const bool bf16 = g->batch_bf16 > 0;
-    if (bf16 && !b->Y16[0]) {
+    const bool dc = g->batch_dc > 0;                 // defect-correction form
+    const bool bf16 = !dc && g->batch_bf16 > 0;      // plain BF16 phase
+    if ((bf16 || dc) && !b->Y16[0]) {
         const size_t m16 = (size_t)(g->n + kPad) * kBK * sizeof(__nv_bfloat16);
         PRK_CHECK(dev_alloc(g, (void**)&b->Y16[0], m16));
         PRK_CHECK(dev_alloc(g, (void**)&b->Y16[1], m16));
+    }
+    if (dc && !b->R) {
+        const size_t mat = (size_t)(g->n + kPad) * kBK * sizeof(float);
+        PRK_CHECK(dev_alloc(g, (void**)&b->R, mat));
+        PRK_CHECK(dev_alloc(g, (void**)&b->Dl, mat));
     }
     BatchState* hs = b->host_state;
     memset(hs, 0, sizeof(BatchState));
@@ -747,7 +911,17 @@ extern "C" pr_status pr_solve_batched(pr_graph* g, float damping, double tol, in
     ++launches;
     PRK_CHECK(cudaGetLastError());
     PRK_CHECK(cudaEventRecord(g->ev_loop0, s));
-    if (g->use_graph) {
+    if (dc) {
+        // host-driven outer steps (one FP32 step + the correction sweeps
+        // each), the done flag read after every step
+        for (int32_t it = 0, src = 0; it < max_iter; ++it, src = 1 - src) {
+            PRK_CHECK(g->idx64 ? enqueue_dc_step<int64_t>(g, b, a, src, g->batch_dc, s, &launches)
+                               : enqueue_dc_step<int32_t>(g, b, a, src, g->batch_dc, s, &launches));
+            PRK_CHECK(cudaMemcpyAsync(hs, b->state, sizeof(BatchState), cudaMemcpyDeviceToHost, s));
+            PRK_CHECK(cudaStreamSynchronize(s));
+            if (hs->done) break;
+        }
+    } else if (g->use_graph) {
         if (b->loop_exec && b->graph_bf16 != (bf16 ? 1 : 0)) drop_batch_graph(g);
         if (!b->loop_exec && (rc = build_batch_graph(g, b, bf16)) != PR_OK) return rc;
         PRK_CHECK(cudaGraphLaunch(b->loop_exec, s));
@@ -799,7 +973,7 @@ extern "C" pr_status pr_solve_batched(pr_graph* g, float damping, double tol, in
         double dm = 0.0;
         for (int j = 0; j < k; ++j) dm += hs->D[j];
         info->dangling_mass = dm;
-        info->edge_visits = (double)hs->iter * (double)g->nnz;
+        info->edge_visits = (double)(hs->iter + hs->dc_sweeps) * (double)g->nnz;
         info->ms_device = ms;
         info->launches = launches;
         info->loop_edge_visits = info->edge_visits;

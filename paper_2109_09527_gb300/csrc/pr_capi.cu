@@ -208,6 +208,11 @@ static pr_status set_option_impl(pr_graph* g, int key, int64_t value) {
                 return fail(PR_ERR_INVALID_ARG, "PR_OPT_NB_FAIL_AFTER must be in [0, 1e6]");
             g->nb_fail_after = (int)value;
             return PR_OK;
+        case PR_OPT_BATCH_DC:
+            if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_BATCH_DC needs a graph");
+            if (value < 0 || value > 32) return fail(PR_ERR_INVALID_ARG, "PR_OPT_BATCH_DC must be in [0, 32]");
+            g->batch_dc = (int)value;
+            return PR_OK;
         case PR_OPT_LIGHT_LANES:
             if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_LIGHT_LANES needs a graph");
             if (value != 0 && value != 1) return fail(PR_ERR_INVALID_ARG, "PR_OPT_LIGHT_LANES is 0 or 1");

@@ -186,6 +186,7 @@ struct pr_graph {
     int64_t nb_hubs = prk::kDefaultNbHubs;    // hub snapshot of the barrier-free kernel (PR_OPT_NB_HUBS)
     int64_t nb_l1_hubs = prk::kDefaultNbL1Hubs;  // weak L1-cached hub gathers (PR_OPT_NB_L1_HUBS)
     int batch_bf16 = 0;                       // batched solver: BF16 Y until changes < 10^-value (0 = off)
+    int batch_dc = 0;                         // batched solver: BF16 correction sweeps per FP32 step (0 = off)
     int perforation = 0;                      // loop perforation eps = 10^-value (0 = off)
     int dynamic_tiles = 0;                    // PR_OPT_DYNAMIC_TILES
     int delay_ns = 0;                         // PR_OPT_DELAY_NS

@@ -206,3 +206,39 @@ def test_bf16_storage_phase_reaches_the_fixed_point(switch):
         err = np.abs(x[:, j].astype(np.float64) - xs).sum()
         assert err <= res[j] / (1 - D) + 2e-7, (j, err, res[j])
         assert np.max(np.abs(x[:, j] - xs) / xs) <= 1e-4
+
+
+@pytest.mark.parametrize("sweeps,index64", [(4, 0), (8, 0), (4, 1)])
+def test_bf16_defect_correction_reaches_the_fixed_point(sweeps, index64):
+    """BF16 storage by defect correction (PR_OPT_BATCH_DC): each FP32 step X' = F(X) is
+    followed by BF16 sweeps on the error equation delta = r + A delta (r = X' - X) and
+    X <- X + delta.  Every column meets tol on an FP32 step, and is within the contraction
+    bound of its residual of the oracle's fixed point for its teleport (all 32 columns),
+    with per-vertex relative error <= 1e-4; fewer FP32 steps than the plain solve's
+    iterations, and the BF16 sweeps counted in edge_visits."""
+    rp, ci = gg.rmat(13, 16, seed=33)
+    n = rp.size - 1
+    t = gg.seed_teleports(n, 32, 8, seed=33)
+    pr.pr_set_option(None, pr.PR_OPT_INDEX64, index64)
+    try:
+        g = pr.Graph(rp, ci)
+    finally:
+        pr.pr_set_option(None, pr.PR_OPT_INDEX64, 0)
+    with g:
+        x32, info32, res32, its32 = g.solve_batched(32, t, tol=1e-6)
+        g.set_option(pr.PR_OPT_BATCH_DC, sweeps)
+        x, info, res, its = g.solve_batched(32, t, tol=1e-6, max_iter=100)
+        g.set_option(pr.PR_OPT_BATCH_DC, 0)
+        x_again, _, _, _ = g.solve_batched(32, t, tol=1e-6)
+    assert np.array_equal(x_again, x32)                  # off again: the plain solve
+    assert info.converged == 1 and np.all(res < 1e-6)
+    assert info.iterations < info32.iterations
+    assert info.edge_visits > info.iterations * ci.size   # the BF16 sweeps gathered too
+    for j in range(32):
+        tj = t[:, j].astype(np.float64)
+        xs, _, _ = oracle.fixed_point(rp, ci, d=D, t=tj)
+        xj = x[:, j].astype(np.float64)
+        err = np.abs(xj - xs).sum()
+        assert err <= res[j] / (1 - D) + 2e-7, (j, err, res[j])
+        assert np.max(np.abs(xj - xs) / xs) <= 1e-4, j
+        assert abs(xj.sum() - tj.sum()) < 1e-5
