@@ -134,11 +134,19 @@ typedef struct pr_graph_stats {
  *   rowptr        host or device, n+1 offsets, int64 if rowptr_is_64 else
  *                 int32; rowptr[0] = 0, non-decreasing, rowptr[n] = nnz.
  *   colidx        host or device, nnz int32 vertex ids in [0, n).
- *   weights       must be NULL (edge weights are not supported by this
- *                 build: PR_ERR_UNSUPPORTED).
- *   layout        PR_IN_CSR (the CSR input of Alg. 1, "G = ConvertCsr(V,E)"
- *                 in Alg. 2/3, read as in-links).  PR_OUT_CSR returns
- *                 PR_ERR_UNSUPPORTED in this build.
+ *   weights       must be NULL: a weighted graph is its own object
+ *                 (pr_create_wgraph below), whose weighted forward and
+ *                 adjoint solvers keep both edge directions.  Non-NULL
+ *                 returns PR_ERR_UNSUPPORTED.
+ *   layout        PR_IN_CSR: row v lists the sources u of the edges u -> v
+ *                 (the CSR input of Alg. 1, "G = ConvertCsr(V,E)" in Alg.
+ *                 2/3, read as in-links).  PR_OUT_CSR: row u lists the
+ *                 targets v of the edges u -> v; the library transposes it
+ *                 on the device (a stable sort of the edges by target, so
+ *                 every in-row lists its sources in increasing order) and
+ *                 then proceeds as for PR_IN_CSR; needs nnz < 2^31
+ *                 (else PR_ERR_UNSUPPORTED) and about 21 bytes of device
+ *                 scratch per edge during the call.
  *   stream        CUDA stream for the copies and set-up kernels.
  *   out           receives the new graph; *out is NULL on failure.
  * The library copies the arrays into memory it owns; the caller may free or

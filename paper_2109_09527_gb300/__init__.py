@@ -298,14 +298,16 @@ def pr_last_error():
 class Graph:
     """Owns a pr_graph built from an in-edge CSR (row v lists the sources of v's in-edges)."""
 
-    def __init__(self, rowptr, colidx, stream=None):
+    def __init__(self, rowptr, colidx, stream=None, layout=PR_IN_CSR):
+        """layout PR_IN_CSR: row v lists the sources of v's in-edges; PR_OUT_CSR: row u
+        lists the targets of u's out-edges (transposed on the device at creation)."""
         n = (rowptr.shape[0] if hasattr(rowptr, "shape") else len(rowptr)) - 1
         nnz = colidx.shape[0] if hasattr(colidx, "shape") else len(colidx)
         is64 = str(getattr(rowptr, "dtype", "")) in ("int64", "torch.int64")
         if not is64 and str(getattr(rowptr, "dtype", "")) not in ("int32", "torch.int32"):
             raise TypeError("rowptr must be int32 or int64")
         self.n, self.nnz = int(n), int(nnz)
-        self.handle = pr_create_graph(n, nnz, rowptr, is64, colidx, stream=stream)
+        self.handle = pr_create_graph(n, nnz, rowptr, is64, colidx, layout=layout, stream=stream)
 
     def close(self):
         if getattr(self, "handle", None):

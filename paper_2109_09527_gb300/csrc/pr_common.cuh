@@ -178,6 +178,7 @@ struct pr_graph {
     int64_t n = 0;
     int64_t nnz = 0;
     bool idx64 = false;          // rowptr kept as int64
+    bool out_layout = false;     // created from an out-edge CSR (PR_OUT_CSR), transposed at set-up
     int heavy_degree = prk::kDefaultHeavy;
     int ctas_per_sm = 0;         // 0 = from occupancy
     bool use_graph = true;

@@ -444,6 +444,95 @@ pr_status build_layout(pr_graph* g, const RP* rp, const int32_t* ci, cudaStream_
     return PR_OK;
 }
 
+// ---- PR_OUT_CSR: the in-edge CSR from an out-edge CSR, on the device ------
+//
+// The out-edge CSR lists the edges grouped by source in increasing source
+// order.  Sorting them by target with a stable sort keeps that order within
+// every target, so each in-row lists its sources in increasing order, the
+// same for every run.  The sort is an LSD radix sort of edge positions on the
+// target id, four bits per pass, each pass the stable counting sort of the
+// binning step (k_bin_count, k_bin_scatter) on a 16-bucket digit.
+
+// src[e] = source u of edge e (warp per row of the out-edge CSR)
+template <typename RP>
+__global__ void k_edge_sources(const RP* __restrict__ rp, int64_t n, int32_t* __restrict__ src) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += nw) {
+        const int64_t e1 = (int64_t)rp[u + 1];
+        for (int64_t e = (int64_t)rp[u] + lane; e < e1; e += 32) src[e] = (int32_t)u;
+    }
+}
+
+__global__ void k_iota(int32_t* __restrict__ p, int64_t count) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) p[i] = (int32_t)i;
+}
+
+// digit of the target of the edge at sorted position i
+__global__ void k_target_digit(const int32_t* __restrict__ dst, const int32_t* __restrict__ perm, int64_t count,
+                               int shift, uint8_t* __restrict__ digit) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
+        digit[i] = (uint8_t)((dst[perm[i]] >> shift) & 15);
+}
+
+// out[i] = in[order[i]]
+__global__ void k_permute_i32(const int32_t* __restrict__ in, const int32_t* __restrict__ order, int64_t count,
+                              int32_t* __restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) out[i] = in[order[i]];
+}
+
+// in-degree of every target, 64-bit counts for the scan
+__global__ void k_target_counts(const int32_t* __restrict__ dst, int64_t nnz, unsigned long long* __restrict__ cnt) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride)
+        atomicAdd(cnt + dst[e], 1ull);
+}
+
+// The in-edge CSR (rp_in[n+1], ci_in[nnz], scratch-owned) of a validated
+// out-edge CSR (rp, ci); nnz < 2^31.
+template <typename RP>
+cudaError_t transpose_to_in_csr(const pr_graph* g, const RP* rp, const int32_t* ci, Scratch& s, cudaStream_t st,
+                                RP** rp_in, int32_t** ci_in) {
+    const int64_t n = g->n, nnz = g->nnz;
+    const int sm = g->sm_count;
+    unsigned long long* cnt = nullptr;
+    cudaError_t e = s.alloc((void**)&cnt, (size_t)n * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = s.alloc((void**)rp_in, (size_t)(n + 1) * sizeof(RP));
+    if (e == cudaSuccess) e = s.alloc((void**)ci_in, (size_t)(nnz + kPad) * sizeof(int32_t));
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(cnt, 0, (size_t)n * sizeof(unsigned long long), st)) != cudaSuccess) return e;
+    if (nnz > 0) k_target_counts<<<grid_for(nnz, sm), kBlock, 0, st>>>(ci, nnz, cnt);
+    if ((e = exclusive_scan<RP>(s, (const int64_t*)cnt, n, *rp_in, st)) != cudaSuccess) return e;
+    if (nnz == 0) return cudaGetLastError();
+    int32_t *src = nullptr, *perm = nullptr, *order = nullptr, *rank = nullptr, *next = nullptr;
+    uint8_t* digit = nullptr;
+    const int64_t nblk = (nnz + kChunk - 1) / kChunk;
+    int64_t *counts = nullptr, *offsets = nullptr;
+    for (auto pp : {&src, &perm, &order, &rank, &next})
+        if ((e = s.alloc((void**)pp, (size_t)nnz * sizeof(int32_t))) != cudaSuccess) return e;
+    if ((e = s.alloc((void**)&digit, (size_t)nnz)) != cudaSuccess) return e;
+    if ((e = s.alloc((void**)&counts, (size_t)(16 * nblk) * sizeof(int64_t))) != cudaSuccess) return e;
+    if ((e = s.alloc((void**)&offsets, (size_t)(16 * nblk + 1) * sizeof(int64_t))) != cudaSuccess) return e;
+    k_edge_sources<RP><<<grid_for(n * 32, sm), kBlock, 0, st>>>(rp, n, src);
+    k_iota<<<grid_for(nnz, sm), kBlock, 0, st>>>(perm, nnz);
+    int bits = 1;
+    while (bits < 31 && (1LL << bits) < n) ++bits;
+    for (int shift = 0; shift < bits; shift += 4) {
+        k_target_digit<<<grid_for(nnz, sm), kBlock, 0, st>>>(ci, perm, nnz, shift, digit);
+        k_bin_count<<<(unsigned)nblk, kBlock, 0, st>>>(digit, nnz, 16, nblk, counts);
+        if ((e = exclusive_scan<int64_t>(s, counts, 16 * nblk, offsets, st)) != cudaSuccess) return e;
+        k_bin_scatter<<<(unsigned)nblk, kBlock, (size_t)16 * kBlock * sizeof(int32_t), st>>>(digit, nnz, 16, nblk,
+                                                                                           offsets, order, rank);
+        k_permute_i32<<<grid_for(nnz, sm), kBlock, 0, st>>>(perm, order, nnz, next);
+        std::swap(perm, next);
+    }
+    k_permute_i32<<<grid_for(nnz, sm), kBlock, 0, st>>>(src, perm, nnz, *ci_in);
+    return cudaGetLastError();
+}
+
 template <typename RP>
 pr_status create_typed(pr_graph* g, const void* rowptr, const int32_t* colidx, cudaStream_t st) {
     const int64_t n = g->n, nnz = g->nnz;
@@ -470,6 +559,13 @@ pr_status create_typed(pr_graph* g, const void* rowptr, const int32_t* colidx, c
         if (herr & 4u) why += " rowptr decreases;";
         if (herr & 8u) why += " colidx out of [0, n);";
         return fail(PR_ERR_INVALID_GRAPH, "pr_create_graph: invalid CSR:" + why);
+    }
+    if (g->out_layout) {
+        RP* rp_in = nullptr;
+        int32_t* ci_in = nullptr;
+        PRK_CHECK(transpose_to_in_csr<RP>(g, rp, ci, s, st, &rp_in, &ci_in));
+        rp = rp_in;
+        ci = ci_in;
     }
     if (g->idx64) return build_layout<RP, int64_t>(g, rp, ci, st, s);
     return build_layout<RP, int32_t>(g, rp, ci, st, s);
@@ -508,8 +604,11 @@ extern "C" pr_status pr_create_graph(int64_t n, int64_t nnz, const void* rowptr,
         return fail(PR_ERR_INVALID_ARG, "pr_create_graph: nnz >= 2^31 needs int64 rowptr");
     if (layout != PR_IN_CSR && layout != PR_OUT_CSR)
         return fail(PR_ERR_INVALID_ARG, "pr_create_graph: layout must be PR_IN_CSR or PR_OUT_CSR");
-    if (layout == PR_OUT_CSR) return fail(PR_ERR_UNSUPPORTED, "pr_create_graph: PR_OUT_CSR is not supported by this build");
-    if (weights) return fail(PR_ERR_UNSUPPORTED, "pr_create_graph: edge weights are not supported by this build");
+    if (layout == PR_OUT_CSR && nnz > 0x7fffffffLL)
+        return fail(PR_ERR_UNSUPPORTED, "pr_create_graph: PR_OUT_CSR needs nnz < 2^31");
+    if (weights)
+        return fail(PR_ERR_UNSUPPORTED,
+                    "pr_create_graph: edge weights belong to the weighted graph object; use pr_create_wgraph");
 
     pr_graph* g = new (std::nothrow) pr_graph();
     if (!g) return fail(PR_ERR_OOM, "pr_create_graph: host allocation failed");
@@ -522,6 +621,7 @@ extern "C" pr_status pr_create_graph(int64_t n, int64_t nnz, const void* rowptr,
         if (e != cudaSuccess) { rc = cuda_fail(e, "cudaDeviceGetAttribute"); break; }
         g->n = n;
         g->nnz = nnz;
+        g->out_layout = layout == PR_OUT_CSR;
         g->idx64 = nnz > 0x7fffffffLL || thread_force_index64();
         g->heavy_degree = thread_heavy_degree();
         e = cudaEventCreate(&g->ev_start);

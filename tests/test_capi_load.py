@@ -57,7 +57,8 @@ def test_argument_errors_return_status_without_a_gpu():
     assert lib.pr_create_graph(2, 2, rp, 0, None, None, 0, None, ctypes.byref(out)) == pr.PR_ERR_INVALID_ARG
     ci = (ctypes.c_int32 * 2)(1, 0)
     assert lib.pr_create_graph(2, 2, rp, 0, ci, None, 7, None, ctypes.byref(out)) == pr.PR_ERR_INVALID_ARG
-    assert lib.pr_create_graph(2, 2, rp, 0, ci, None, pr.PR_OUT_CSR, None,
+    # an out-edge CSR is transposed on the device with 32-bit edge positions
+    assert lib.pr_create_graph(2, 1 << 31, rp, 1, ci, None, pr.PR_OUT_CSR, None,
                                ctypes.byref(out)) == pr.PR_ERR_UNSUPPORTED
     w = (ctypes.c_float * 2)(1.0, 1.0)
     assert lib.pr_create_graph(2, 2, rp, 0, ci, w, 0, None, ctypes.byref(out)) == pr.PR_ERR_UNSUPPORTED

@@ -675,3 +675,67 @@ def test_dynamic_tiles_take_over_a_slow_block():
     assert np.array_equal(xs[0], x_ref)
     assert max_rel(xs[1], x_ref) <= 1e-5
     assert times[1] < 0.7 * times[0], times
+
+
+# ------------------------------------------------------ out-edge CSR input --
+
+def out_csr(rp, ci, n):
+    """The out-edge CSR (row u lists the targets of u's edges) of an in-edge CSR."""
+    dst = np.repeat(np.arange(n, dtype=np.int64), np.diff(rp))
+    return gg.edges_to_in_csr(n, dst, ci.astype(np.int64), dedup=False, drop_self_loops=False)
+
+
+@pytest.mark.parametrize("build", ["rmat13", "er", "multi", "small", "index64"])
+def test_out_csr_layout_is_transposed_on_the_device(build):
+    """PR_OUT_CSR: the library sorts the edges by target on the device (stable, so every
+    in-row lists its sources in increasing order).  The in-edge CSR built from it is the
+    one the caller would have given, so both solves agree bit for bit, and the result
+    matches the oracle run on the in-edge CSR."""
+    index64 = 0
+    if build == "rmat13":
+        rp, ci = gg.rmat(13, seed=44)
+    elif build == "er":
+        rp, ci = gg.er_dangling(20011, seed=45)
+    elif build == "multi":
+        rp, ci = gg.random_digraph(700, 5000, seed=46, allow_multi=True, self_loops=True)
+    elif build == "small":
+        rp, ci = gg.random_digraph(3, 4, seed=47, allow_multi=True, self_loops=True)
+    else:
+        rp, ci = gg.rmat(12, seed=48)
+        index64 = 1
+    n = rp.size - 1
+    orp, oci = out_csr(rp, ci, n)
+    assert orp[-1] == ci.size
+    pr.pr_set_option(None, pr.PR_OPT_INDEX64, index64)
+    try:
+        g_in = pr.Graph(rp, ci)
+        g_out = pr.Graph(orp, oci, layout=pr.PR_OUT_CSR)
+    finally:
+        pr.pr_set_option(None, pr.PR_OPT_INDEX64, 0)
+    with g_in, g_out:
+        assert g_out.stats()["nnz"] == ci.size and g_out.stats()["max_indeg"] == g_in.stats()["max_indeg"]
+        for variant in ("jacobi", "nonblocking"):
+            x_in, info_in = g_in.solve(tol=1e-6, variant=variant)
+            x_out, info_out = g_out.solve(tol=1e-6, variant=variant)
+            if variant == "jacobi":
+                assert np.array_equal(x_in, x_out)
+                xo = matching(rp, ci, x_out, info_out)
+                assert l1(x_out, xo) <= 1e-6 and max_rel(x_out, xo) <= 1e-4
+            else:
+                xs, _, _ = oracle.fixed_point(rp, ci, d=D)
+                assert l1(x_out, xs) <= info_out.residual_l1 / (1 - D) + 2e-7
+
+
+def test_out_csr_validation_and_weights():
+    rp, ci = gg.rmat(8, seed=2)
+    n = rp.size - 1
+    orp, oci = out_csr(rp, ci, n)
+    bad = oci.copy()
+    bad[5] = n                                        # a target out of range
+    with pytest.raises(pr.PageRankError) as e:
+        pr.Graph(orp, bad, layout=pr.PR_OUT_CSR)
+    assert e.value.status == pr.PR_ERR_INVALID_GRAPH
+    with pytest.raises(pr.PageRankError) as e:
+        pr.pr_create_graph(n, ci.size, rp, 1, ci, weights=np.ones(ci.size, np.float32))
+    assert e.value.status == pr.PR_ERR_UNSUPPORTED
+    assert "pr_create_wgraph" in str(e.value)
