@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(kBlock) k_b_dc_update(BatchArgs a, const float
     if (batch_done(st)) return;
     const int lane = threadIdx.x & 31;
     const float d = (float)st->d;
-    const float share = (float)(st->d * st->Ddc[lane] * st->inv_n);
+    const float share = (float)(st->Ddc[lane] * st->inv_n);   // Ddc / n; d multiplies the sum below
     KahanF dm;
     constexpr int kRows = 4;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;

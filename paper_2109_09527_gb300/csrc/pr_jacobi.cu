@@ -45,6 +45,11 @@ namespace prk {
 #ifndef PRK_SEG_PIPE
 #define PRK_SEG_PIPE 0
 #endif
+// L2 eviction priority of the pipelined kernel's bulk copies (0 = no hint;
+// 1..3 as PRK_L2_STREAM).
+#ifndef PRK_L2_BULK
+#define PRK_L2_BULK 0
+#endif
 
 // --------------------------------------------------------- iteration kernels --
 
@@ -295,10 +300,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 // Bulk copy of `bytes` (a multiple of 16) from global to this block's shared
 // memory, both addresses 16-byte aligned, completing on `bar`.
 __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
+    if constexpr (PRK_L2_BULK == 0) {
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         smem_addr(dst)),
+                     "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                     : "memory");
+    } else {
+        // streamed once per iteration: an L2 eviction priority of class PRK_L2_BULK
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
+            "%4;" ::"r"(smem_addr(dst)),
+            "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(l2_policy<PRK_L2_BULK>())
+            : "memory");
+    }
 }
 
 // Shared-memory stage of one tile: colidx, then rowptr, x, 1/outdeg and

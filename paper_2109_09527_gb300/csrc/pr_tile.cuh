@@ -126,10 +126,13 @@ __device__ __forceinline__ void st_stream(float* p, float v) {
     asm volatile("st.global.cs.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
 }
 
-// Store of y' (read by the gathers of the next iteration).
+// Store of y' (read by the gathers of the next iteration): 0 streaming
+// (.cs), 1..3 with the L2 policy of that class, 4 a plain write-back store.
 __device__ __forceinline__ void st_y(float* p, float v) {
     if constexpr (PRK_L2_YSTORE == 0)
         asm volatile("st.global.cs.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+    else if constexpr (PRK_L2_YSTORE == 4)
+        asm volatile("st.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
     else
         asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v),
                      "l"(l2_policy<PRK_L2_YSTORE>()) : "memory");
