@@ -159,8 +159,16 @@ PR_API pr_status pr_create_graph(int64_t n, int64_t nnz, const void* rowptr, int
                                  const int32_t* colidx, const float* weights, int layout,
                                  void* stream, pr_graph** out);
 
-/* Free a graph and all device memory it owns.  NULL is accepted. */
+/* Free a graph and all device memory it owns.  NULL is accepted.  The call
+ * first waits for the device to finish all work (as cudaFree does); the
+ * memory goes back to the library's per-device pool, where the next
+ * pr_create_graph finds it without mapping new pages. */
 PR_API pr_status pr_destroy_graph(pr_graph* g);
+
+/* Return the device memory the library's pool on the current device keeps
+ * for reuse (memory freed by pr_destroy_graph and set-up scratch) to the
+ * system.  Graphs still alive keep theirs. */
+PR_API pr_status pr_trim_memory(void);
 
 /* Solve for the PageRank vector (Eq. 1 with the uniform dangling share).
  *   damping       d, 0 <= d < 1 (the paper uses 0.85, Section 1).

@@ -100,6 +100,7 @@ SIGNATURES = {
     "pr_create_graph": (ctypes.c_int, [_I64, _I64, _VP, ctypes.c_int, _VP, _VP, ctypes.c_int, _VP,
                                        ctypes.POINTER(_VP)]),
     "pr_destroy_graph": (ctypes.c_int, [_VP]),
+    "pr_trim_memory": (ctypes.c_int, []),
     "pr_solve": (ctypes.c_int, [_VP, _F, _D, _I32, ctypes.c_int, _VP, _VP, _VP,
                                 ctypes.POINTER(pr_info), _VP]),
     "pr_iterate": (ctypes.c_int, [_VP, _F, _VP, _VP, _I32, _VP, ctypes.POINTER(pr_info), _VP]),
@@ -206,6 +207,11 @@ def pr_create_graph(n, nnz, rowptr, rowptr_is_64, colidx, weights=None, layout=P
 
 def pr_destroy_graph(g):
     return _check(load().pr_destroy_graph(g))
+
+
+def pr_trim_memory():
+    """Return the device memory the library's pool keeps for reuse to the system."""
+    return _check(load().pr_trim_memory())
 
 
 def pr_solve(g, damping, tol, max_iter, variant, teleport, x0, x_out, stream=None):

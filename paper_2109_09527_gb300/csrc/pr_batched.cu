@@ -803,8 +803,9 @@ pr_status build_teleport_csr(pr_graph* g, BatchCtx* b, const float* t_dev, int k
     PRK_CHECK(cudaMemcpyAsync(&nnz, b->tptr + g->n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     PRK_CHECK(cudaStreamSynchronize(s));
     if (nnz > b->t_cap) {
-        if (b->tcol) cudaFree(b->tcol);
-        if (b->tval) cudaFree(b->tval);
+        PRK_CHECK(cudaStreamSynchronize(s));   // earlier solves on this stream are done with them
+        if (b->tcol) dev_free(b->tcol);
+        if (b->tval) dev_free(b->tval);
         b->tcol = nullptr;
         b->tval = nullptr;
         b->t_cap = 0;
@@ -829,10 +830,11 @@ void drop_batch_graph(pr_graph* g) {
 void destroy_batch(pr_graph* g) {
     BatchCtx* b = g->batch;
     if (!b) return;
+    cudaDeviceSynchronize();   // earlier solves may still use the memory (cudaFree waited the same way)
     void* dev[] = {b->X[0], b->X[1], b->Y[0], b->Y[1], b->Y16[0], b->Y16[1], b->S, b->P, b->R, b->Dl, b->tptr,
                    b->tcol, b->tval, b->tcount, b->t_stage, b->out_stage, b->state, b->slots, b->tasks};
     for (void* p : dev)
-        if (p) cudaFree(p);
+        if (p) dev_free(p);
     if (b->host_state) cudaFreeHost(b->host_state);
     if (b->loop_exec) cudaGraphExecDestroy(b->loop_exec);
     delete b;

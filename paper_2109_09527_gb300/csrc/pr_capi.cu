@@ -1,5 +1,6 @@
 // pr_capi.cu -- error reporting, options, statistics and teardown of the C ABI.
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "pr_common.cuh"
@@ -29,13 +30,90 @@ pr_status cuda_fail(cudaError_t e, const char* what) {
     return PR_ERR_CUDA;
 }
 
+// ---- device memory of graphs: one stream-ordered pool per device ----------
+//
+// Graph objects and their set-up scratch take memory from a pool the library
+// creates per device (cudaMemPoolCreate), with a release threshold that keeps
+// freed memory in the pool: a graph created after another was destroyed
+// reuses its memory instead of mapping new pages (which, for the gigabytes a
+// large graph holds, costs milliseconds per allocation).  The pool keeps at
+// most what the library held at its peak; pr_trim_memory returns it to the
+// system.  Allocation runs on a library stream that has no other work, and
+// that stream is synchronised before the memory is handed out, so any stream
+// may use it at once.
+#if PRK_POOL
+namespace {
+constexpr int kPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kPoolDevices] = {};
+cudaStream_t g_pool_stream[kPoolDevices] = {};
+}  // namespace
+
+cudaError_t lib_pool(cudaMemPool_t* pool, cudaStream_t* stream) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kPoolDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t mp = nullptr;
+        if ((e = cudaMemPoolCreate(&mp, &props)) != cudaSuccess) return e;
+        uint64_t keep = ~0ull;
+        if ((e = cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess ||
+            (e = cudaStreamCreateWithFlags(&g_pool_stream[dev], cudaStreamNonBlocking)) != cudaSuccess) {
+            cudaMemPoolDestroy(mp);
+            return e;
+        }
+        g_pool[dev] = mp;
+    }
+    *pool = g_pool[dev];
+    *stream = g_pool_stream[dev];
+    return cudaSuccess;
+}
+
+cudaError_t pool_alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    cudaMemPool_t pool;
+    cudaStream_t ps;
+    cudaError_t e = lib_pool(&pool, &ps);
+    if (e != cudaSuccess) return e;
+    e = cudaMallocFromPoolAsync(p, bytes ? bytes : 16, pool, ps);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ps);
+    if (e != cudaSuccess) *p = nullptr;
+    return e;
+}
+
+cudaError_t pool_free(void* p, cudaStream_t stream) {
+    if (!p) return cudaSuccess;
+    if (stream) return cudaFreeAsync(p, stream);
+    cudaMemPool_t pool;
+    cudaStream_t ps;
+    cudaError_t e = lib_pool(&pool, &ps);
+    if (e != cudaSuccess) return e;
+    return cudaFreeAsync(p, ps);
+}
+#else
+cudaError_t pool_alloc(void** p, size_t bytes) { return cudaMalloc(p, bytes ? bytes : 16); }
+cudaError_t pool_free(void* p, cudaStream_t) { return p ? cudaFree(p) : cudaSuccess; }
+#endif
+
 cudaError_t dev_alloc(pr_graph* g, void** p, size_t bytes) {
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = pool_alloc(p, bytes);
     if (e == cudaSuccess) g->device_bytes += (int64_t)bytes;
     else *p = nullptr;
     return e;
 }
+
+// Memory of a graph object: every kernel that may use it has finished (the
+// caller destroys a graph after its last call; the device is synchronised
+// first, as cudaFree would).
+cudaError_t dev_free(void* p) { return pool_free(p, nullptr); }
 
 bool is_device_pointer(const void* p) {
     cudaPointerAttributes at;
@@ -59,6 +137,9 @@ using namespace prk;
 
 extern "C" pr_status pr_destroy_graph(pr_graph* g) {
     if (!g) return PR_OK;
+    // every kernel that may still use the graph's memory finishes first (what
+    // cudaFree did implicitly; the memory goes back to the pool stream-ordered)
+    cudaError_t sync = cudaDeviceSynchronize();
     destroy_batch(g);
     destroy_set(g);
     void* dev[] = {g->rowptr, g->colidx, g->inv_out, g->order, g->rank, g->x[0], g->x[1],
@@ -67,9 +148,10 @@ extern "C" pr_status pr_destroy_graph(pr_graph* g) {
                    g->nb_items, g->nb_slots,
                    g->nb_scalars, g->nb_block_sweeps, g->frozen};
     cudaError_t first = cudaSuccess;
+    if (sync != cudaSuccess) first = sync;
     for (void* p : dev)
         if (p) {
-            cudaError_t e = cudaFree(p);
+            cudaError_t e = dev_free(p);
             if (first == cudaSuccess) first = e;
         }
     for (auto& ex : g->loop_exec)
@@ -82,7 +164,19 @@ extern "C" pr_status pr_destroy_graph(pr_graph* g) {
     if (g->ev_loop0) cudaEventDestroy(g->ev_loop0);
     if (g->ev_loop1) cudaEventDestroy(g->ev_loop1);
     delete g;
-    if (first != cudaSuccess) return cuda_fail(first, "pr_destroy_graph: cudaFree");
+    if (first != cudaSuccess) return cuda_fail(first, "pr_destroy_graph: freeing device memory");
+    return PR_OK;
+}
+
+extern "C" pr_status pr_trim_memory(void) {
+#if PRK_POOL
+    cudaMemPool_t pool;
+    cudaStream_t ps;
+    cudaError_t e = lib_pool(&pool, &ps);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ps);
+    if (e == cudaSuccess) e = cudaMemPoolTrimTo(pool, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "pr_trim_memory");
+#endif
     return PR_OK;
 }
 

@@ -59,6 +59,11 @@ constexpr int kPad = 64;                 // spare elements after every device ar
 constexpr int kTileHeavy = -1;           // tile kind: epilogue of heavy rows
 constexpr int kTileZero = -2;            // tile kind: rows without in-edges
 constexpr int kMaxBins = 42;
+// 1: graph memory and set-up scratch come from the library's stream-ordered
+// pool (pool_alloc); 0: plain cudaMalloc / cudaFree.
+#ifndef PRK_POOL
+#define PRK_POOL 1
+#endif
 // Lanes per row of light tiles (PR_OPT_LIGHT_LANES): 0 by degree class, 1 by
 // the tile's row count (see light_lanes_log2).
 #ifndef PRK_DEFAULT_LANE_MODE
@@ -270,6 +275,12 @@ int seg_grid(const pr_graph* g);
 
 // Device allocation recorded in g->device_bytes.
 cudaError_t dev_alloc(pr_graph* g, void** p, size_t bytes);
+cudaError_t dev_free(void* p);
+// Memory from the library's pool on the current device (see pr_capi.cu):
+// pool_free with a stream frees in that stream's order, without a stream on
+// the library's own stream (the caller has made sure nothing still uses it).
+cudaError_t pool_alloc(void** p, size_t bytes);
+cudaError_t pool_free(void* p, cudaStream_t stream);
 
 bool is_device_pointer(const void* p);
 

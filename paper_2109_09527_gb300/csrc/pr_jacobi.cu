@@ -46,9 +46,10 @@ namespace prk {
 #define PRK_SEG_PIPE 0
 #endif
 // L2 eviction priority of the pipelined kernel's bulk copies (0 = no hint;
-// 1..3 as PRK_L2_STREAM).
+// 1..3 as PRK_L2_STREAM): evict_first, so that the streamed column indices
+// do not push the gathered quotient vector out of L2.
 #ifndef PRK_L2_BULK
-#define PRK_L2_BULK 0
+#define PRK_L2_BULK 1
 #endif
 
 // --------------------------------------------------------- iteration kernels --

@@ -403,10 +403,11 @@ void drop_set_graph(pr_graph* g) {
 void destroy_set(pr_graph* g) {
     SetCtx* sc = g->set;
     if (!sc) return;
+    cudaDeviceSynchronize();   // earlier solves may still use the memory (cudaFree waited the same way)
     void* dev[] = {sc->d_offsets, sc->gid, sc->tiles, sc->gtile_ptr, sc->gtiles, sc->tile_part, sc->state,
                    sc->gr_block};
     for (void* p : dev)
-        if (p) cudaFree(p);
+        if (p) dev_free(p);
     if (sc->host_state) cudaFreeHost(sc->host_state);
     if (sc->loop_exec) cudaGraphExecDestroy(sc->loop_exec);
     delete sc;

@@ -268,13 +268,25 @@ int grid_for(int64_t work, int sm_count) {
 }
 
 // Scratch allocations freed when set-up returns.
+// With a stream, the scratch goes back to the pool in that stream's order
+// (after the set-up kernels that use it), without a device-wide wait.
 struct Scratch {
     std::vector<void*> ptrs;
+    cudaStream_t stream = nullptr;
+    Scratch() = default;
+    explicit Scratch(cudaStream_t s) : stream(s) {}
     ~Scratch() {
-        for (void* p : ptrs) cudaFree(p);
+        for (void* p : ptrs) {
+            if (stream) {
+                pool_free(p, stream);
+            } else {
+                cudaDeviceSynchronize();
+                pool_free(p, nullptr);
+            }
+        }
     }
     cudaError_t alloc(void** p, size_t bytes) {
-        cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+        cudaError_t e = pool_alloc(p, bytes ? bytes : 16);
         if (e == cudaSuccess) ptrs.push_back(*p);
         return e;
     }
@@ -536,7 +548,7 @@ cudaError_t transpose_to_in_csr(const pr_graph* g, const RP* rp, const int32_t* 
 template <typename RP>
 pr_status create_typed(pr_graph* g, const void* rowptr, const int32_t* colidx, cudaStream_t st) {
     const int64_t n = g->n, nnz = g->nnz;
-    Scratch s;
+    Scratch s(st);
     RP* rp = nullptr;
     int32_t* ci = nullptr;
     PRK_CHECK(s.alloc((void**)&rp, (size_t)(n + 1) * sizeof(RP)));
@@ -582,7 +594,7 @@ std::vector<Tile> tiles_with_threshold(const pr_graph* g, int heavy_degree, int6
 }
 
 cudaError_t scan_counts_i32(const int64_t* counts, int64_t count, int32_t* offsets, cudaStream_t st) {
-    Scratch s;
+    Scratch s(st);
     cudaError_t e = exclusive_scan<int32_t>(s, counts, count, offsets, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // before the temporaries are freed
     return e;

@@ -20,16 +20,22 @@
 // 2 = evict_last, 3 = evict_normal.  The stream class covers what an
 // iteration reads once (colidx, x, 1/outdeg, teleport); the gather class the
 // quotient vector y that every edge reads; the y-store class the writes of y'
-// (gathered by the next iteration).  Keeping y resident in L2 while colidx
-// streams past it is what these hints are for.
+// (gathered by the next iteration; 4 = a plain write-back store).  Keeping y
+// resident in L2 while colidx streams past it is what these hints are for:
+// on ER-24, where no hub keeps y's lines warm, a quarter of the gathers
+// missed L2 with the streamed loads and copies unhinted and y' stored with
+// .cs.  Streamed loads and bulk copies evict_first with y' stored plainly
+// measured fastest of seven combinations (ER-24 1.41 -> 1.26 ms per
+// synchronous iteration, 1.51 -> 1.43 ms per barrier-free sweep; R-MAT-24
+// 0.90 -> 0.88 and 0.906 -> 0.892 ms).
 #ifndef PRK_L2_STREAM
-#define PRK_L2_STREAM 0
+#define PRK_L2_STREAM 1
 #endif
 #ifndef PRK_L2_GATHER
 #define PRK_L2_GATHER 0
 #endif
 #ifndef PRK_L2_YSTORE
-#define PRK_L2_YSTORE 0
+#define PRK_L2_YSTORE 4
 #endif
 
 namespace prk {
