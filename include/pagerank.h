@@ -332,6 +332,15 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
  *                         rows' edges four at a time; 0 by degree class
  *                         (2^min(k,5) lanes for degrees in [2^k, 2^(k+1))).
  *                         Changes the summation order only.
+ *   PR_OPT_FUSED_SEGMENTS synchronous solver with the pipelined row kernel:
+ *                         1 (default) gathers the 2048-edge segments of the
+ *                         heavy rows as tiles of that same kernel,
+ *                         interleaved with the light-row tiles, so that one
+ *                         launch per iteration keeps both kinds of work in
+ *                         flight on every SM (the block that gathers a heavy
+ *                         row's last segment updates the row); 0 runs them
+ *                         as a separate kernel first.  Changes the summation
+ *                         order of a segment only.
  *   PR_OPT_INDEX64        1: keep 64-bit row offsets on the device even when
  *                         the edge count fits 32 bits (thread-local default
  *                         for the next pr_create_graph, set with g = NULL;
@@ -355,6 +364,7 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
 #define PR_OPT_NB_FAIL_AFTER 16
 #define PR_OPT_LIGHT_LANES 17
 #define PR_OPT_BATCH_DC 18
+#define PR_OPT_FUSED_SEGMENTS 19
 PR_API pr_status pr_set_option(pr_graph* g, int key, int64_t value);
 
 /* Batched personalised PageRank: k independent solves on one graph, one per

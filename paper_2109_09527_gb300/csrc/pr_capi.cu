@@ -144,7 +144,8 @@ extern "C" pr_status pr_destroy_graph(pr_graph* g) {
     destroy_set(g);
     void* dev[] = {g->rowptr, g->colidx, g->inv_out, g->order, g->rank, g->x[0], g->x[1],
                    g->y[0], g->y[1], g->teleport, g->stage, g->seg_row, g->seg_ptr, g->seg_sum,
-                   g->tiles, g->tma_tiles, g->out_src, g->out_pos, g->contrib, g->state, g->slots,
+                   g->tiles, g->tma_tiles, g->tma_fused, g->tma_fused_e1, g->row_cnt, g->hr_part,
+                   g->out_src, g->out_pos, g->contrib, g->state, g->slots,
                    g->nb_items, g->nb_slots,
                    g->nb_scalars, g->nb_block_sweeps, g->frozen};
     cudaError_t first = cudaSuccess;
@@ -306,6 +307,11 @@ static pr_status set_option_impl(pr_graph* g, int key, int64_t value) {
             if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_BATCH_DC needs a graph");
             if (value < 0 || value > 32) return fail(PR_ERR_INVALID_ARG, "PR_OPT_BATCH_DC must be in [0, 32]");
             g->batch_dc = (int)value;
+            return PR_OK;
+        case PR_OPT_FUSED_SEGMENTS:
+            if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_FUSED_SEGMENTS needs a graph");
+            if (value != 0 && value != 1) return fail(PR_ERR_INVALID_ARG, "PR_OPT_FUSED_SEGMENTS is 0 or 1");
+            g->fuse_segments = (int)value;
             return PR_OK;
         case PR_OPT_LIGHT_LANES:
             if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_LIGHT_LANES needs a graph");

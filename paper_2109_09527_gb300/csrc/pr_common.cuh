@@ -58,6 +58,8 @@ constexpr int kNbSegDegree = 1024;       // rows the barrier-free kernel gathers
 constexpr int kPad = 64;                 // spare elements after every device array
 constexpr int kTileHeavy = -1;           // tile kind: epilogue of heavy rows
 constexpr int kTileZero = -2;            // tile kind: rows without in-edges
+constexpr int kTileSeg = -3;             // tile kind (fused pipelined kernel): one 2048-edge segment of a
+                                         // heavy row; row_begin = the row, row_end = the segment's index
 constexpr int kMaxBins = 42;
 // 1: graph memory and set-up scratch come from the library's stream-ordered
 // pool (pool_alloc); 0: plain cudaMalloc / cudaFree.
@@ -172,6 +174,11 @@ struct IterArgs {
     int32_t lane_mode;           // lanes per light row (PR_OPT_LIGHT_LANES)
     const int32_t* out_src;      // edge-centric form: source of each out-edge, in out-edge order
     const int32_t* out_pos;      // edge-centric form: in-edge slot of each out-edge
+    const int32_t* tile_e1;      // fused pipelined kernel: one past the last edge of each tile
+    int32_t* row_cnt;            // fused: segments of each heavy row gathered so far this iteration
+    float2* hr_part;             // fused: (L1 change, dangling mass) of each heavy row's update
+    int32_t fused;               // 1: heavy-row segments are tiles of the pipelined kernel
+    int32_t n_heavy;             // rows [0, n_heavy) are gathered in segments
 };
 
 }  // namespace prk
@@ -221,6 +228,13 @@ struct pr_graph {
     int32_t* out_pos = nullptr;      // and the per-edge contribution array
     float* contrib = nullptr;
     int64_t n_tma_tiles = 0;         // 0: the layout cannot use k_rows_tma
+    prk::Tile* tma_fused = nullptr;  // fused tile list: light and empty-row tiles with every heavy-row
+                                     // segment as a tile of its own, interleaved (pad = first edge)
+    int32_t* tma_fused_e1 = nullptr; // one past the last edge of each fused tile
+    int64_t n_tma_fused = 0;         // 0: no fused list (no heavy rows, or the kernel does not apply)
+    int32_t* row_cnt = nullptr;      // per heavy row: its segments gathered so far in an iteration
+    float2* hr_part = nullptr;       // per heavy row: (L1 change, dangling mass) of its update
+    int fuse_segments = 1;           // PR_OPT_FUSED_SEGMENTS
     prk::SolveState* state = nullptr;
     double* slots = nullptr;
     int slot_capacity = 0;       // blocks the slot array can serve
@@ -315,6 +329,9 @@ pr_status ensure_stage(pr_graph* g);
 pr_status ensure_teleport(pr_graph* g);
 void launch_init(const pr_graph* g, const IterArgs& a, const float* t_dev, const float* x0_dev,
                  cudaStream_t s);
+// Edge ranges (pad, e1) and segment rows of the fused tile list of k_rows_tma.
+cudaError_t fill_fused_tiles(Tile* tiles, int32_t* e1, int64_t count, const int32_t* rowptr, const int32_t* seg_row,
+                             const int32_t* seg_ptr, cudaStream_t s);
 // Count the frozen rows of a perforated solve into SolveState::frozen.
 cudaError_t launch_count_frozen(const pr_graph* g, cudaStream_t s);
 void launch_finalize(const pr_graph* g, const IterArgs& a, float* out, bool renormalise,

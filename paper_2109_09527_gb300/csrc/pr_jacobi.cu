@@ -339,6 +339,19 @@ struct TmaStage {
 template <bool kUniform>
 __device__ __forceinline__ void tma_issue(const IterArgs& a, const Tile& tile, int64_t e0, int64_t e1,
                                           const float* x_in, TmaStage st, uint64_t* full) {
+    if (tile.kind == kTileSeg) {
+        // a heavy-row segment: its column indices only
+        const int64_t c0 = e0 & ~(int64_t)3;
+        const uint32_t col_bytes = (uint32_t)((((e1 + 3) & ~(int64_t)3) - c0) * 4);
+        if (col_bytes > kTmaColWords * 4u) {
+            atomicOr(&a.state->error, 4u);
+            mbar_arrive_expect_tx(full, 0);
+            return;
+        }
+        mbar_arrive_expect_tx(full, col_bytes);
+        if (col_bytes) bulk_copy_g2s(st.col, a.colidx + c0, col_bytes, full);
+        return;
+    }
     const int64_t r0 = tile.row_begin & ~3, r1 = (tile.row_end + 3) & ~3;
     const uint32_t vec_bytes = (uint32_t)(r1 - r0) * 4u;
     uint32_t bytes = (kUniform ? 2u : 3u) * vec_bytes;
@@ -415,6 +428,67 @@ __device__ __forceinline__ void tma_light_tile(const Tile& tile, const TmaStage&
     }
 }
 
+// Consumer side of a heavy-row segment (fused list): the 256 consumer threads
+// gather the segment's edges from the stage (thread i takes edges e0 + i,
+// e0 + i + 256, ..., four in flight), each warp sums its share, and the
+// warp that finishes last (a shared-memory counter per stage; no block
+// barrier, so a consumer warp whose bounded wait ran out cannot hold the
+// others) adds the eight warp sums in warp order and publishes the
+// segment's partial sum.  The block that publishes a heavy row's last
+// segment sums the row's partials in segment order and updates the row;
+// its L1 change and dangling mass go to hr_part, which the grid's last
+// block adds in row order, so the iteration stays deterministic.
+struct SegRed {
+    float part[kTmaStages][kWarps];
+    int32_t cnt[kTmaStages];
+};
+
+template <bool kUniform>
+__device__ __forceinline__ void tma_segment_tile(const IterArgs& a, const Tile& tile, int32_t e1, const TmaStage& st,
+                                                 int stage, SegRed& red, const float* x_in, const float* y_in,
+                                                 float* x_out, float* y_out, const RowCtx& c, int tid) {
+    const int32_t e0 = tile.pad;
+    const int32_t base = e0 & ~3;   // st.col[e - base] = colidx[e]
+    const int32_t* col = st.col;
+    float v = 0.f;
+    for (int32_t p = e0 + tid; p < e1; p += 4 * kBlock) {
+        float g[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int32_t q = p + j * kBlock;
+            g[j] = q < e1 ? Mem<false>::gather(y_in, col[q - base], c) : 0.f;
+        }
+        v += (g[0] + g[1]) + (g[2] + g[3]);
+    }
+    v = warp_sum(v);
+    if ((tid & 31) != 0) return;
+    red.part[stage][tid >> 5] = v;
+    __threadfence_block();
+    if (atomicAdd(&red.cnt[stage], 1) != kWarps - 1) return;
+    __threadfence_block();
+    red.cnt[stage] = 0;
+    float sum = 0.f;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) sum += red.part[stage][w];
+    const int32_t h = tile.row_begin;
+    a.seg_sum[tile.row_end] = sum;
+    __threadfence();
+    const int32_t j0 = a.seg_ptr[h], j1 = a.seg_ptr[h + 1];
+    if (atomicAdd(a.row_cnt + h, 1) != j1 - j0 - 1) return;
+    __threadfence();
+    a.row_cnt[h] = 0;   // ready for the next iteration
+    float rs = 0.f;
+    for (int32_t j = j0; j < j1; ++j) rs += __ldcg(a.seg_sum + j);
+    const float xo = ld_stream(x_in + h);
+    const float inv = ld_stream(a.inv_out + h);
+    const float tv = kUniform ? 0.f : ld_stream(a.teleport + h);
+    const float b = kUniform ? c.base : fmaf(c.one_m_d, tv, c.d_share);
+    const float xn = fmaf(c.d, rs, b);
+    st_stream(x_out + h, xn);
+    st_y(y_out + h, xn * inv);
+    a.hr_part[h] = make_float2(fabsf(xn - xo), inv == 0.f ? xn : 0.f);
+}
+
 template <bool kUniform>
 __global__ void __launch_bounds__(kTmaThreads, kTmaMinBlocks) k_rows_tma(IterArgs a, const float* __restrict__ x_in,
                                                                       const float* __restrict__ y_in,
@@ -430,10 +504,12 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaMinBlocks) k_rows_tma(IterArg
         if (a.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0);
         return;
     }
+    __shared__ SegRed seg_red;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kTmaStages; ++s) {
             mbar_init(full + s, 1);
             mbar_init(empty + s, kWarps);
+            seg_red.cnt[s] = 0;
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -470,7 +546,7 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaMinBlocks) k_rows_tma(IterArg
                     mbar_arrive_expect_tx(full + s, 16);
                     continue;
                 }
-                tma_issue<kUniform>(a, tile, a.tiles[t].pad, a.tiles[t + 1].pad, x_in,
+                tma_issue<kUniform>(a, tile, tile.pad, a.fused ? a.tile_e1[t] : a.tiles[t + 1].pad, x_in,
                                     TmaStage(stages, s), full + s);
             }
             // let every copy land before the block can exit
@@ -493,6 +569,8 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaMinBlocks) k_rows_tma(IterArg
             const TmaStage stg(stages, s);
             if (tile.kind >= 0) {
                 tma_light_tile<kUniform>(tile, stg, y_in, x_out, y_out, c, acc, tid);
+            } else if (tile.kind == kTileSeg) {
+                tma_segment_tile<kUniform>(a, tile, a.tile_e1[t], stg, s, seg_red, x_in, y_in, x_out, y_out, c, tid);
             } else {
                 const int o = tile.row_begin & 3;
                 for (int i = tid; i < tile.row_end - tile.row_begin; i += kBlock) {
@@ -513,7 +591,20 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaMinBlocks) k_rows_tma(IterArg
     if (timed_out) atomicOr(&st->error, 2u);
 
     double R, Dn;
-    if (block_pair_to_grid(acc.resid(), acc.mass(), a.slots, &st->ticket, &R, &Dn) && threadIdx.x == 0) {
+    const bool last_block = block_pair_to_grid(acc.resid(), acc.mass(), a.slots, &st->ticket, &R, &Dn);
+    if (last_block && a.fused) {
+        // the heavy rows' updates, in row order
+        double hr = 0.0, hd = 0.0;
+        for (int32_t h = threadIdx.x; h < a.n_heavy; h += blockDim.x) {
+            const float2 p = __ldcg(a.hr_part + h);
+            hr += (double)p.x;
+            hd += (double)p.y;
+        }
+        block_sum2(hr, hd);
+        R += hr;
+        Dn += hd;
+    }
+    if (last_block && threadIdx.x == 0) {
         st->resid = R;
         st->D = Dn;
         st->iter += 1;
@@ -534,6 +625,35 @@ __global__ void __launch_bounds__(kBlock) k_count_frozen(const uint8_t* __restri
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(&st->frozen, c);
+}
+
+// The fused list's edge ranges: light and empty-row tiles [rowptr[row_begin],
+// rowptr[row_end]); a segment tile (row_end = its index s) the row of s and
+// its 2048-edge range within that row.
+__global__ void k_fused_tile_edges(Tile* tiles, int32_t* e1, int64_t count, const int32_t* __restrict__ rowptr,
+                                   const int32_t* __restrict__ seg_row, const int32_t* __restrict__ seg_ptr) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        Tile t = tiles[i];
+        if (t.kind == kTileSeg) {
+            const int32_t h = seg_row[t.row_end];
+            const int32_t b = rowptr[h] + (t.row_end - seg_ptr[h]) * kSegEdges;
+            t.row_begin = h;
+            t.pad = b;
+            e1[i] = min(b + kSegEdges, rowptr[h + 1]);
+        } else {
+            t.pad = rowptr[t.row_begin];
+            e1[i] = rowptr[t.row_end];
+        }
+        tiles[i] = t;
+    }
+}
+
+cudaError_t fill_fused_tiles(Tile* tiles, int32_t* e1, int64_t count, const int32_t* rowptr, const int32_t* seg_row,
+                             const int32_t* seg_ptr, cudaStream_t s) {
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((count + kBlock - 1) / kBlock, 1024));
+    k_fused_tile_edges<<<grid, kBlock, 0, s>>>(tiles, e1, count, rowptr, seg_row, seg_ptr);
+    return cudaGetLastError();
 }
 
 // pad of every tile of the pipelined kernel (and of the sentinel after the
@@ -632,7 +752,7 @@ static bool tma_applies(const pr_graph* g, const IterArgs& a) {
 static int tma_grid(const pr_graph* g) {
     int per_sm = g->ctas_per_sm > 0 ? std::min(g->ctas_per_sm, g_occ_tma) : g_occ_tma;
     int64_t blocks = (int64_t)g->sm_count * std::max(1, per_sm);
-    blocks = std::min<int64_t>(blocks, std::max<int64_t>(1, g->n_tma_tiles));
+    blocks = std::min<int64_t>(blocks, std::max<int64_t>(1, std::max(g->n_tma_tiles, g->n_tma_fused)));
     return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)g->slot_capacity));
 }
 
@@ -686,7 +806,9 @@ cudaError_t enqueue_iteration_t(const pr_graph* g, const IterArgs& a, int src, b
     if (a.edge) return enqueue_edge_iteration(g, a, src, uniform, s, launches);
     const size_t hot = (size_t)a.hot_n * sizeof(float);
     const size_t rows_smem = hot + (a.staged ? (size_t)kStageFloats * sizeof(float) : 0);
-    if (g->n_seg > 0) {
+    // the pipelined kernel with the heavy-row segments as tiles of its own
+    const bool fused = sizeof(IdxT) == 4 && tma_applies(g, a) && g->fuse_segments && g->n_tma_fused > 0;
+    if (g->n_seg > 0 && !fused) {
         k_heavy_segments<IdxT><<<seg_grid(g), kIterBlock, hot, s>>>(a, g->y[src]);
         ++*launches;
     }
@@ -697,8 +819,13 @@ cudaError_t enqueue_iteration_t(const pr_graph* g, const IterArgs& a, int src, b
     float* yo = g->y[1 - src];
     if (sizeof(IdxT) == 4 && tma_applies(g, a)) {
         IterArgs at = a;
-        at.tiles = g->tma_tiles;
-        at.n_tiles = (int32_t)g->n_tma_tiles;
+        at.tiles = fused ? g->tma_fused : g->tma_tiles;
+        at.n_tiles = (int32_t)(fused ? g->n_tma_fused : g->n_tma_tiles);
+        at.fused = fused ? 1 : 0;
+        at.tile_e1 = g->tma_fused_e1;
+        at.row_cnt = g->row_cnt;
+        at.hr_part = g->hr_part;
+        at.n_heavy = (int32_t)g->n_heavy;
         const int tg = tma_grid(g);
         if (uniform) k_rows_tma<true><<<tg, kTmaThreads, kTmaSmemBytes, s>>>(at, xi, yi, xo, yo);
         else k_rows_tma<false><<<tg, kTmaThreads, kTmaSmemBytes, s>>>(at, xi, yi, xo, yo);
@@ -799,6 +926,9 @@ pr_status ensure_teleport(pr_graph* g) {
 
 void launch_init(const pr_graph* g, const IterArgs& a, const float* t_dev, const float* x0_dev,
                  cudaStream_t s) {
+    // the fused kernel's per-row segment counters return to 0 after every
+    // iteration; an iteration cut short (a wait that ran out) may leave some set
+    if (g->row_cnt) cudaMemsetAsync(g->row_cnt, 0, (size_t)g->n_heavy * sizeof(int32_t), s);
     k_init<<<small_grid(g), kBlock, 0, s>>>(a, t_dev, x0_dev, g->order, g->teleport, g->x[0], g->y[0]);
 }
 

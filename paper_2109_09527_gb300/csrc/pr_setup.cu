@@ -447,6 +447,31 @@ pr_status build_layout(pr_graph* g, const RP* rp, const int32_t* ci, cudaStream_
         PRK_CHECK(cudaMemcpyAsync(g->tma_tiles, tt.data(), tt.size() * sizeof(Tile), cudaMemcpyHostToDevice, st));
         PRK_CHECK(fill_tile_edges(g->tma_tiles, (int64_t)tt.size() - 1, (const int32_t*)g->rowptr, st));
         g->n_tma_tiles = (int64_t)tt.size() - 1;
+
+        // The fused list: the light and empty-row tiles in the same order, with
+        // every heavy-row segment a tile of its own, spread evenly among them,
+        // so that each block's round-robin share mixes the two kinds of work.
+        if (g->n_seg > 0 && kTmaEdges >= kSegEdges) {
+            std::vector<Tile> lt;
+            for (size_t i = 0; i + 1 < tt.size(); ++i)
+                if (tt[i].kind != kTileHeavy) lt.push_back(tt[i]);
+            const int64_t L = (int64_t)lt.size(), S = g->n_seg;
+            std::vector<Tile> ft;
+            ft.reserve((size_t)(L + S));
+            for (int64_t li = 0, si = 0; li < L || si < S;) {
+                if (si < S && (li >= L || si * L <= li * S)) ft.push_back(Tile{0, (int32_t)si++, kTileSeg, 0});
+                else ft.push_back(lt[(size_t)li++]);
+            }
+            PRK_CHECK(dev_alloc(g, (void**)&g->tma_fused, ft.size() * sizeof(Tile)));
+            PRK_CHECK(dev_alloc(g, (void**)&g->tma_fused_e1, ft.size() * sizeof(int32_t)));
+            PRK_CHECK(cudaMemcpyAsync(g->tma_fused, ft.data(), ft.size() * sizeof(Tile), cudaMemcpyHostToDevice, st));
+            PRK_CHECK(fill_fused_tiles(g->tma_fused, g->tma_fused_e1, (int64_t)ft.size(), (const int32_t*)g->rowptr,
+                                       g->seg_row, g->seg_ptr, st));
+            PRK_CHECK(dev_alloc(g, (void**)&g->row_cnt, (size_t)g->n_heavy * sizeof(int32_t)));
+            PRK_CHECK(cudaMemsetAsync(g->row_cnt, 0, (size_t)g->n_heavy * sizeof(int32_t), st));
+            PRK_CHECK(dev_alloc(g, (void**)&g->hr_part, (size_t)g->n_heavy * sizeof(float2)));
+            g->n_tma_fused = (int64_t)ft.size();
+        }
     }
 
     unsigned long long ndang = 0;

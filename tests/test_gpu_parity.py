@@ -426,6 +426,61 @@ def test_pipelined_row_kernel_matches_row_kernel_and_oracle(build):
     assert info1.residual_l1 == pytest.approx(l1o, rel=1e-3, abs=1e-9)
 
 
+@pytest.mark.parametrize("build", ["rmat15", "rmat13_heavy64", "rmat14_heavy2048", "bistar"])
+def test_fused_segments_match_the_separate_kernel_and_oracle(build):
+    """Heavy-row segments as tiles of the pipelined kernel (PR_OPT_FUSED_SEGMENTS = 1, the
+    default), interleaved with the light tiles, the block that gathers a row's last segment
+    updating the row: against the separate segment kernel (0) and the oracle -- the solve
+    in matching mode, one update with a personalised teleport, bitwise reproducible runs
+    (the heavy rows' L1 change and dangling mass are added in row order).  The layouts cover
+    heavy thresholds 64, 256 and 2048 and a hub with 40,000 in-edges (20 segments)."""
+    heavy = 256
+    if build == "rmat15":
+        rp, ci = gg.rmat(15, seed=61)
+    elif build == "rmat13_heavy64":
+        rp, ci = gg.rmat(13, seed=62)
+        heavy = 64
+    elif build == "rmat14_heavy2048":
+        rp, ci = gg.rmat(14, seed=63)
+        heavy = 2048
+    else:
+        rp, ci = gg.bi_star(40001)
+    n = rp.size - 1
+    pr.set_heavy_degree(heavy)
+    try:
+        g = pr.Graph(rp, ci)
+    finally:
+        pr.set_heavy_degree(pr.DEFAULT_HEAVY_DEGREE)
+    t = (gg.uniform(5, 7, n) + 0.05).astype(np.float32)
+    t /= t.sum()
+    x_in = (gg.uniform(6, 7, n) + 0.1).astype(np.float32)
+    x_in /= x_in.sum()
+    with g:
+        assert g.stats()["n_segments"] > 0 and g.stats()["n_tma_tiles"] > 0
+        res = {}
+        for fused in (1, 0):
+            g.set_option(pr.PR_OPT_FUSED_SEGMENTS, fused)
+            x, info = g.solve(tol=1e-6, max_iter=200, variant="jacobi")
+            x1, info1 = g.iterate(x_in, n_iter=1, teleport=t)
+            res[fused] = (x, info, x1, info1)
+        g.set_option(pr.PR_OPT_FUSED_SEGMENTS, 1)
+        x_again, _ = g.solve(tol=1e-6, max_iter=200, variant="jacobi")
+        xb, infob = g.solve(tol=1e-6, max_iter=200, variant="nonblocking")
+    x, info, x1, info1 = res[1]
+    xr, infor, x1r, info1r = res[0]
+    assert np.array_equal(x, x_again)
+    assert info.converged == 1 and abs(info.iterations - infor.iterations) <= 1
+    assert max_rel(x, xr) <= 1e-5 and max_rel(x1, x1r) <= 1e-5
+    xo = matching(rp, ci, x, info)
+    assert l1(x, xo) <= 1e-6 and max_rel(x, xo) <= 1e-4
+    xo1, d_in, l1o, _ = oracle.jacobi_step(rp, ci, x_in.astype(np.float64), d=D, t=t.astype(np.float64))
+    assert l1(x1, xo1) <= 1e-6 and max_rel(x1, xo1) <= 1e-4
+    assert info1.residual_l1 == pytest.approx(l1o, rel=1e-3, abs=1e-9)
+    assert info1.dangling_mass == pytest.approx(oracle.dangling_mass(rp, ci, xo1), rel=1e-5, abs=1e-12)
+    xs, _, _ = oracle.fixed_point(rp, ci, d=D)
+    assert infob.converged == 1 and l1(xb, xs) <= infob.residual_l1 / (1 - D) + 2e-7
+
+
 @pytest.mark.parametrize("build", ["rmat15", "er", "rmat12_heavy64"])
 def test_light_lane_mappings_match_the_oracle(build):
     """Both lane mappings of the light-row tiles (PR_OPT_LIGHT_LANES: by degree class, or
