@@ -234,7 +234,7 @@ struct pr_graph {
     int64_t n_tma_fused = 0;         // 0: no fused list (no heavy rows, or the kernel does not apply)
     int32_t* row_cnt = nullptr;      // per heavy row: its segments gathered so far in an iteration
     float2* hr_part = nullptr;       // per heavy row: (L1 change, dangling mass) of its update
-    int fuse_segments = 1;           // PR_OPT_FUSED_SEGMENTS
+    int fuse_segments = 0;           // PR_OPT_FUSED_SEGMENTS (off: measured 2.5x slower, see the option)
     prk::SolveState* state = nullptr;
     double* slots = nullptr;
     int slot_capacity = 0;       // blocks the slot array can serve
