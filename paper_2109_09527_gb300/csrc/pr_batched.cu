@@ -388,9 +388,24 @@ __global__ void __launch_bounds__(kBlock) k_b_update(BatchArgs a, const float* _
 // X <- X + delta_M.  BF16 rounds delta, not x, so its error shrinks with the
 // residual and the outer steps reach the FP32 tolerance.
 
+// Rounding a quotient delta(u)/outdeg(u) to BF16 changes the mass the
+// gathers pass on by outdeg(u) times the rounding error -- for a hub, ten
+// thousand times a 2^-9 relative error.  Left alone this mass error is what
+// the corrections stall on (an FP32 emulation of R-MAT-16 with 8 seed-set
+// columns: 10 outer steps instead of 4, the iterates' mass 1e-3 off).  So the
+// mass each row loses to rounding, delta(u) - outdeg(u) bf16(delta(u)/outdeg(u)),
+// is summed per column and spread uniformly with the dangling mass: every
+// sweep then conserves mass exactly (up to FP32 rounding).
+__device__ __forceinline__ __nv_bfloat16 dc_quotient(float dv, float inv, KahanF& dm) {
+    const __nv_bfloat16 q = __float2bfloat16_rn(dv * inv);
+    if (inv == 0.f) dm.add(dv);                                   // dangling: all of it
+    else dm.add(dv - __bfloat162float(q) / inv);                 // what rounding lost
+    return q;
+}
+
 // R = X' - X and delta_0 = R for the active columns (0 for the others), the
-// BF16 quotient of delta_0 and its dangling mass per column; the gathers that
-// follow read BF16.
+// BF16 quotient of delta_0 and the mass it does not pass on per column (its
+// dangling mass and the rounding loss); the gathers that follow read BF16.
 __global__ void __launch_bounds__(kBlock) k_b_dc_prep(BatchArgs a, const float* __restrict__ Xprev,
                                                       const float* __restrict__ Xcur, float* __restrict__ R,
                                                       __nv_bfloat16* __restrict__ Yd16) {
@@ -405,8 +420,7 @@ __global__ void __launch_bounds__(kBlock) k_b_dc_prep(BatchArgs a, const float* 
         const float r = active ? __ldcs(Xcur + i) - __ldcs(Xprev + i) : 0.f;
         const float inv = __ldg(a.inv_out + v);
         R[i] = r;
-        Yd16[i] = __float2bfloat16_rn(r * inv);
-        if (inv == 0.f) dm.add(r);
+        Yd16[i] = dc_quotient(r, inv, dm);
     }
     double Dd, unused;
     if (batch_columns_to_grid(dm.value(), 0.0, a.slots, &st->ticket, &Dd, &unused) && threadIdx.x < 32) {
@@ -419,8 +433,9 @@ __global__ void __launch_bounds__(kBlock) k_b_dc_prep(BatchArgs a, const float* 
 }
 
 // One correction sweep: delta'(v, j) = R(v, j) + d (S(v, j) + Ddc_j / n) from
-// the gathered sums of the BF16 quotient of delta; writes delta' (FP32) and
-// its BF16 quotient, and the new Ddc.
+// the gathered sums of the BF16 quotient of delta, Ddc the mass those sums do
+// not carry (dangling mass and rounding loss); writes delta' (FP32) and its
+// BF16 quotient, and the new Ddc.
 __global__ void __launch_bounds__(kBlock) k_b_dc_update(BatchArgs a, const float* __restrict__ R,
                                                         float* __restrict__ Dl, __nv_bfloat16* __restrict__ Yd16) {
     BatchState* st = a.state;
@@ -455,8 +470,7 @@ __global__ void __launch_bounds__(kBlock) k_b_dc_update(BatchArgs a, const float
             if (v >= a.n) break;
             const float dn = rv[q] + d * (sv[q] + share);   // 0 for inactive columns (R = 0, S = 0)
             Dl[(size_t)v * kBK + lane] = dn;
-            Yd16[(size_t)v * kBK + lane] = __float2bfloat16_rn(dn * inv[q]);
-            if (inv[q] == 0.f) dm.add(dn);
+            Yd16[(size_t)v * kBK + lane] = dc_quotient(dn, inv[q], dm);
         }
     }
     double Dd, unused;
