@@ -275,6 +275,11 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
  *                         the FP32 steps; edge_visits counts both kinds of
  *                         sweep.  Takes precedence over PR_OPT_BATCH_BF16; a
  *                         host-driven loop (no CUDA graph).
+ *   PR_OPT_BATCH_ASYNC    batched solver: 1 (default) gathers the rows of a
+ *                         32-edge window into shared memory with asynchronous
+ *                         copies while the previous window is summed (64 rows
+ *                         in flight per warp); 0 loads them into registers
+ *                         (16 or 32 rows per warp).  Same sums, same order.
  *   PR_OPT_PERFORATION    loop perforation (Alg. 5) in the synchronous solver
  *                         (PR_JACOBI, pr_iterate) and in the barrier-free one
  *                         (PR_NONBLOCKING: the paper's No-Sync-Opt, Section
@@ -367,6 +372,7 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
 #define PR_OPT_LIGHT_LANES 17
 #define PR_OPT_BATCH_DC 18
 #define PR_OPT_FUSED_SEGMENTS 19
+#define PR_OPT_BATCH_ASYNC 20
 PR_API pr_status pr_set_option(pr_graph* g, int key, int64_t value);
 
 /* Batched personalised PageRank: k independent solves on one graph, one per

@@ -58,6 +58,7 @@ PR_OPT_NB_FAIL_AFTER = 16
 PR_OPT_LIGHT_LANES = 17
 PR_OPT_BATCH_DC = 18
 PR_OPT_FUSED_SEGMENTS = 19
+PR_OPT_BATCH_ASYNC = 20
 
 LIB_PATH = _build.LIB_PATH
 

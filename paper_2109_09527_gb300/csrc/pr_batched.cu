@@ -220,6 +220,134 @@ __global__ void __launch_bounds__(kBlock, 4) k_b_light(BatchArgs a, const T* __r
     }
 }
 
+// ---- gathers with asynchronous copies (PR_OPT_BATCH_ASYNC) ----------------
+//
+// The gathers above hold each row they load in registers until it is summed,
+// which caps a warp at 16 (light) or 32 (segments) rows in flight and makes
+// them latency-bound (ncu: L1->L2 request path 14-15% busy, DRAM 12-13%).
+// These copy the rows of a 32-edge window into a per-warp shared-memory
+// buffer with cp.async (16-byte pieces, no register dependency) while the
+// previous window is summed from the other buffer, so each warp keeps 64
+// rows in flight and needs few registers.  Lane j still sums column j.
+constexpr int kAW = 32;   // edges per window
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Copy the source rows of edges [wb, min(wb + kAW, ee)) into buf (row e of
+// the window at buf + e * kBK elements); rows past ee are not copied.
+template <typename T>
+__device__ __forceinline__ void issue_window(const int32_t* __restrict__ colidx, const T* __restrict__ Y, int64_t wb,
+                                             int64_t ee, T* buf, int lane) {
+    constexpr int kPieces = kBK * (int)sizeof(T) / 16;   // 16-byte pieces of a row: 8 (FP32) or 4 (BF16)
+    const int32_t u_l = wb + lane < ee ? __ldg(colidx + wb + lane) : -1;
+#pragma unroll
+    for (int k = 0; k < kPieces; ++k) {
+        const int c = lane + 32 * k;          // piece c: row c / kPieces, part c % kPieces
+        const int r = c / kPieces, part = c % kPieces;
+        const int32_t u = __shfl_sync(0xffffffffu, u_l, r);
+        if (u >= 0)
+            cp_async16(reinterpret_cast<char*>(buf + (size_t)r * kBK) + 16 * part,
+                       reinterpret_cast<const char*>(Y + (size_t)u * kBK) + 16 * part);
+    }
+    cp_async_commit();
+}
+
+__device__ __forceinline__ float ld_sm(const float* p) { return *p; }
+__device__ __forceinline__ float ld_sm(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+// Heavy rows: a warp per segment, windows double-buffered in shared memory.
+template <typename IdxT, typename T>
+__global__ void __launch_bounds__(kBlock) k_b_segments_async(BatchArgs a, const T* __restrict__ Y) {
+    extern __shared__ __align__(16) unsigned char b_smem[];
+    if (batch_skip<T>(a.state)) return;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    T* buf0 = reinterpret_cast<T*>(b_smem) + (size_t)wib * 2 * kAW * kBK;
+    T* buf1 = buf0 + kAW * kBK;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t s = warp; s < a.n_seg; s += nwarp) {
+        const int32_t h = a.seg_row[s];
+        const int64_t re = row_at<IdxT>(a.rowptr, h + 1);
+        const int64_t e0 = row_at<IdxT>(a.rowptr, h) + (s - a.seg_ptr[h]) * (int64_t)kSegEdges;
+        const int64_t e1 = min(e0 + (int64_t)kSegEdges, re);
+        float acc = 0.f;
+        issue_window<T>(a.colidx, Y, e0, e1, buf0, lane);
+        int w = 0;
+        for (int64_t wb = e0; wb < e1; wb += kAW, ++w) {
+            T* cur = (w & 1) ? buf1 : buf0;
+            T* nxt = (w & 1) ? buf0 : buf1;
+            if (wb + kAW < e1) issue_window<T>(a.colidx, Y, wb + kAW, e1, nxt, lane);
+            else cp_async_commit();   // an empty group keeps the count of groups in flight fixed
+            cp_async_wait<1>();
+            __syncwarp();
+            const int cnt = (int)min((int64_t)kAW, e1 - wb);
+#pragma unroll 8
+            for (int e = 0; e < kAW; ++e)
+                if (e < cnt) acc += ld_sm(cur + e * kBK + lane);
+            __syncwarp();   // the buffer is refilled two windows on
+        }
+        cp_async_wait<0>();
+        __syncwarp();
+        a.P[s * kBK + lane] = acc;
+    }
+}
+
+// Light rows: a warp per task, windows double-buffered in shared memory, the
+// row ends of a window from one warp-wide OR (the lanes hold the end offsets
+// of the 32 rows from the first row the window touches).
+template <typename IdxT, typename T>
+__global__ void __launch_bounds__(kBlock) k_b_light_async(BatchArgs a, const T* __restrict__ Y) {
+    extern __shared__ __align__(16) unsigned char b_smem[];
+    if (batch_skip<T>(a.state)) return;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    T* buf0 = reinterpret_cast<T*>(b_smem) + (size_t)wib * 2 * kAW * kBK;
+    T* buf1 = buf0 + kAW * kBK;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = warp; t < a.n_tiles; t += nwarp) {
+        const Tile tile = a.tiles[t];
+        if (tile.kind < 0) continue;
+        const int64_t r1 = tile.row_end;
+        const int64_t eb = row_at<IdxT>(a.rowptr, tile.row_begin), eend = row_at<IdxT>(a.rowptr, r1);
+        int64_t row = tile.row_begin;
+        float acc = 0.f;
+        issue_window<T>(a.colidx, Y, eb, eend, buf0, lane);
+        int w = 0;
+        for (int64_t wb = eb; wb < eend; wb += kAW, ++w) {
+            T* cur = (w & 1) ? buf1 : buf0;
+            T* nxt = (w & 1) ? buf0 : buf1;
+            if (wb + kAW < eend) issue_window<T>(a.colidx, Y, wb + kAW, eend, nxt, lane);
+            else cp_async_commit();
+            // the ends of the rows this window may close: rows row .. row + 31
+            const int64_t rend = row + 1 + lane <= r1 ? row_at<IdxT>(a.rowptr, row + 1 + lane) : INT64_MAX;
+            const int64_t pos = rend - 1 - wb;
+            const unsigned ends = __reduce_or_sync(0xffffffffu, (pos >= 0 && pos < kAW) ? (1u << pos) : 0u);
+            const int cnt = (int)min((int64_t)kAW, eend - wb);
+            cp_async_wait<1>();
+            __syncwarp();
+#pragma unroll 8
+            for (int e = 0; e < kAW; ++e) {
+                if (e < cnt) acc += ld_sm(cur + e * kBK + lane);
+                if ((ends >> e) & 1u) {
+                    a.S[row * kBK + lane] = acc;
+                    acc = 0.f;
+                    ++row;
+                }
+            }
+            __syncwarp();
+        }
+        cp_async_wait<0>();
+        __syncwarp();
+    }
+}
+
 // Per-column block partials of (a, b) -> slots; the last block gets the grid
 // totals of its own column in every lane-j thread of warp 0 (fixed order).
 __device__ __forceinline__ bool batch_columns_to_grid(double a, double b, double* slots, uint32_t* ticket,
@@ -680,18 +808,67 @@ int update_grid(const pr_graph* g, const BatchCtx* b) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)b->slot_blocks));
 }
 
+// Dynamic shared memory of the asynchronous gathers: two windows per warp.
+template <typename T>
+constexpr size_t async_smem() {
+    return (size_t)kWarps * 2 * kAW * kBK * sizeof(T);
+}
+
+// Blocks per SM of an asynchronous gather kernel (shared memory bounds it),
+// set up once per kernel.
+template <typename K>
+int async_occupancy(K kernel, size_t smem) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernel, kBlock, smem) != cudaSuccess) {
+        cudaGetLastError();
+        o = 1;
+    }
+    return std::max(1, o);
+}
+
+// The segment and light-row gathers of one sweep over the quotient matrix Y
+// (FP32 or BF16), with register loads or, with PR_OPT_BATCH_ASYNC, with
+// asynchronous copies into shared memory.  Returns the kernels launched.
+// Blocks per SM of the asynchronous gathers, [segments, light][IdxT 32/64][FP32, BF16];
+// set by ensure_batch (outside any stream capture).
+int g_occ_async[2][2][2] = {};
+
+template <typename IdxT, typename T>
+void init_async_occupancy() {
+    const int i = sizeof(IdxT) == 8 ? 1 : 0, j = sizeof(T) == 2 ? 1 : 0;
+    g_occ_async[0][i][j] = async_occupancy(k_b_segments_async<IdxT, T>, async_smem<T>());
+    g_occ_async[1][i][j] = async_occupancy(k_b_light_async<IdxT, T>, async_smem<T>());
+}
+
+template <typename IdxT, typename T>
+int launch_gathers(const pr_graph* g, const BatchCtx* b, const BatchArgs& a, const T* Y, cudaStream_t s) {
+    int n = 0;
+    if (g->batch_async) {
+        const int i = sizeof(IdxT) == 8 ? 1 : 0, j = sizeof(T) == 2 ? 1 : 0;
+        const int occ_s = g_occ_async[0][i][j], occ_l = g_occ_async[1][i][j];
+        if (g->n_seg > 0) {
+            k_b_segments_async<IdxT, T><<<batch_grid(g, g->n_seg, occ_s), kBlock, async_smem<T>(), s>>>(a, Y);
+            ++n;
+        }
+        k_b_light_async<IdxT, T><<<batch_grid(g, b->n_tasks, occ_l), kBlock, async_smem<T>(), s>>>(a, Y);
+        return n + 1;
+    }
+    if (g->n_seg > 0) {
+        k_b_segments<IdxT, T><<<batch_grid(g, g->n_seg, g_occ_bseg), kBlock, 0, s>>>(a, Y);
+        ++n;
+    }
+    k_b_light<IdxT, T><<<batch_grid(g, b->n_tasks, g_occ_blight), kBlock, 0, s>>>(a, Y);
+    return n + 1;
+}
+
 // One iteration.  With BF16 storage both gather versions are enqueued and the
 // one that does not match the current phase returns at once.
 template <typename IdxT>
 cudaError_t enqueue_batch_iteration(const pr_graph* g, const BatchCtx* b, const BatchArgs& a, int src,
                                     bool bf16, cudaStream_t s) {
-    const int gs = batch_grid(g, g->n_seg, g_occ_bseg), gl = batch_grid(g, b->n_tasks, g_occ_blight);
-    if (bf16) {
-        if (g->n_seg > 0) k_b_segments<IdxT, __nv_bfloat16><<<gs, kBlock, 0, s>>>(a, b->Y16[src]);
-        k_b_light<IdxT, __nv_bfloat16><<<gl, kBlock, 0, s>>>(a, b->Y16[src]);
-    }
-    if (g->n_seg > 0) k_b_segments<IdxT, float><<<gs, kBlock, 0, s>>>(a, b->Y[src]);
-    k_b_light<IdxT, float><<<gl, kBlock, 0, s>>>(a, b->Y[src]);
+    if (bf16) launch_gathers<IdxT, __nv_bfloat16>(g, b, a, b->Y16[src], s);
+    launch_gathers<IdxT, float>(g, b, a, b->Y[src], s);
     k_b_update<<<update_grid(g, b), kBlock, 0, s>>>(a, b->X[src], b->X[1 - src], b->Y[1 - src],
                                                    bf16 ? b->Y16[1 - src] : nullptr);
     return cudaGetLastError();
@@ -713,17 +890,12 @@ cudaError_t enqueue_dc_step(const pr_graph* g, const BatchCtx* b, const BatchArg
     if (e != cudaSuccess) return e;
     *launches += g->n_seg > 0 ? 3 : 2;
     const int ug = update_grid(g, b);
-    const int gs = batch_grid(g, g->n_seg, g_occ_bseg), gl = batch_grid(g, b->n_tasks, g_occ_blight);
     k_b_dc_prep<<<ug, kBlock, 0, s>>>(a, b->X[src], b->X[1 - src], b->R, b->Y16[0]);
     ++*launches;
     for (int m = 0; m < sweeps; ++m) {
-        if (g->n_seg > 0) {
-            k_b_segments<IdxT, __nv_bfloat16><<<gs, kBlock, 0, s>>>(a, b->Y16[m & 1]);
-            ++*launches;
-        }
-        k_b_light<IdxT, __nv_bfloat16><<<gl, kBlock, 0, s>>>(a, b->Y16[m & 1]);
+        *launches += launch_gathers<IdxT, __nv_bfloat16>(g, b, a, b->Y16[m & 1], s);
         k_b_dc_update<<<ug, kBlock, 0, s>>>(a, b->R, b->Dl, b->Y16[(m + 1) & 1]);
-        *launches += 2;
+        ++*launches;
     }
     k_b_dc_apply<<<ug, kBlock, 0, s>>>(a, b->X[src], b->X[1 - src], b->Dl, b->Y[1 - src]);
     ++*launches;
@@ -761,6 +933,12 @@ pr_status ensure_batch(pr_graph* g) {
         PRK_CHECK(dev_alloc(g, (void**)&b->tasks, (tasks.size() + 1) * sizeof(Tile)));
         if (!tasks.empty())
             PRK_CHECK(cudaMemcpy(b->tasks, tasks.data(), tasks.size() * sizeof(Tile), cudaMemcpyHostToDevice));
+    }
+    if (g_occ_async[1][0][0] == 0) {
+        init_async_occupancy<int32_t, float>();
+        init_async_occupancy<int32_t, __nv_bfloat16>();
+        init_async_occupancy<int64_t, float>();
+        init_async_occupancy<int64_t, __nv_bfloat16>();
     }
     if (g_occ_bseg == 0) {
         int o = 0;

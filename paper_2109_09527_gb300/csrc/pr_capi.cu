@@ -308,6 +308,11 @@ static pr_status set_option_impl(pr_graph* g, int key, int64_t value) {
             if (value < 0 || value > 32) return fail(PR_ERR_INVALID_ARG, "PR_OPT_BATCH_DC must be in [0, 32]");
             g->batch_dc = (int)value;
             return PR_OK;
+        case PR_OPT_BATCH_ASYNC:
+            if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_BATCH_ASYNC needs a graph");
+            if (value != 0 && value != 1) return fail(PR_ERR_INVALID_ARG, "PR_OPT_BATCH_ASYNC is 0 or 1");
+            g->batch_async = (int)value;
+            return PR_OK;
         case PR_OPT_FUSED_SEGMENTS:
             if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_FUSED_SEGMENTS needs a graph");
             if (value != 0 && value != 1) return fail(PR_ERR_INVALID_ARG, "PR_OPT_FUSED_SEGMENTS is 0 or 1");

@@ -72,6 +72,10 @@ constexpr int kMaxBins = 42;
 #define PRK_DEFAULT_LANE_MODE 1
 #endif
 constexpr int kDefaultLaneMode = PRK_DEFAULT_LANE_MODE;
+#ifndef PRK_DEFAULT_BATCH_ASYNC
+#define PRK_DEFAULT_BATCH_ASYNC 1
+#endif
+constexpr int kDefaultBatchAsync = PRK_DEFAULT_BATCH_ASYNC;
 
 // Pipelined synchronous row kernel (k_rows_tma): a producer warp copies each
 // tile's offsets, column indices and per-row vectors into shared memory with
@@ -200,6 +204,7 @@ struct pr_graph {
     int64_t nb_l1_hubs = prk::kDefaultNbL1Hubs;  // weak L1-cached hub gathers (PR_OPT_NB_L1_HUBS)
     int batch_bf16 = 0;                       // batched solver: BF16 Y until changes < 10^-value (0 = off)
     int batch_dc = 0;                         // batched solver: BF16 correction sweeps per FP32 step (0 = off)
+    int batch_async = prk::kDefaultBatchAsync; // batched gathers with asynchronous copies (PR_OPT_BATCH_ASYNC)
     int perforation = 0;                      // loop perforation eps = 10^-value (0 = off)
     int dynamic_tiles = 0;                    // PR_OPT_DYNAMIC_TILES
     int delay_ns = 0;                         // PR_OPT_DELAY_NS

@@ -242,3 +242,37 @@ def test_bf16_defect_correction_reaches_the_fixed_point(sweeps, index64):
         assert err <= res[j] / (1 - D) + 2e-7, (j, err, res[j])
         assert np.max(np.abs(xj - xs) / xs) <= 1e-4, j
         assert abs(xj.sum() - tj.sum()) < 1e-5
+
+
+@pytest.mark.parametrize("scale,heavy,index64", [(13, 256, 0), (12, 64, 1)])
+def test_async_gathers_match_register_gathers_bit_for_bit(scale, heavy, index64):
+    """PR_OPT_BATCH_ASYNC: the rows of each 32-edge window copied into shared memory while
+    the previous window is summed, against loads into registers -- the same sums in the
+    same edge order, so the solves agree bit for bit; in the FP32 form, the BF16 phase and
+    the defect-correction form."""
+    rp, ci = gg.rmat(scale, 16, seed=70 + scale)
+    n = rp.size - 1
+    t = gg.seed_teleports(n, 32, 8, seed=scale)
+    pr.set_heavy_degree(heavy)
+    pr.pr_set_option(None, pr.PR_OPT_INDEX64, index64)
+    try:
+        g = pr.Graph(rp, ci)
+    finally:
+        pr.set_heavy_degree(pr.DEFAULT_HEAVY_DEGREE)
+        pr.pr_set_option(None, pr.PR_OPT_INDEX64, 0)
+    with g:
+        assert g.stats()["n_segments"] > 0
+        for opt, val in ((None, 0), (pr.PR_OPT_BATCH_BF16, 2), (pr.PR_OPT_BATCH_DC, 4)):
+            if opt is not None:
+                g.set_option(opt, val)
+            res = {}
+            for asy in (1, 0):
+                g.set_option(pr.PR_OPT_BATCH_ASYNC, asy)
+                res[asy] = g.solve_batched(32, t, tol=1e-6, max_iter=200)
+            assert np.array_equal(res[0][0], res[1][0]), opt
+            assert np.array_equal(res[0][3], res[1][3]), opt
+            if opt is not None:
+                g.set_option(opt, 0)
+        g.set_option(pr.PR_OPT_BATCH_ASYNC, 1)
+        x, info, res_, its = g.solve_batched(32, t, tol=1e-6)
+    check_columns(rp, ci, t, x, its, res_, 1e-6)
