@@ -51,6 +51,14 @@ constexpr int kBK = 32;              // row width of the batched matrices (float
 #endif
 constexpr int kBTaskEdges = PRK_BATCH_TASK_EDGES;
 constexpr int kBUpdateBlocksPerSM = 4;
+// Rows a warp of the update kernels has in flight per pass (each lane loads
+// its column of S or the segment partials, and of X).  The update streams
+// 4 n k floats per iteration and is latency-bound: at 4 rows a warp it ran at
+// about half the DRAM bandwidth.
+#ifndef PRK_BATCH_UPDATE_ROWS
+#define PRK_BATCH_UPDATE_ROWS 4
+#endif
+constexpr int kBUpdateRows = PRK_BATCH_UPDATE_ROWS;
 
 // Device state of a batched solve.
 struct BatchState {
@@ -426,7 +434,7 @@ __global__ void __launch_bounds__(kBlock) k_b_update(BatchArgs a, const float* _
     Acc acc;
     // four rows per warp per pass: their loads are independent, so a warp has
     // four 128-byte rows of S, X (and the segment partials of heavy rows) in flight
-    constexpr int kRows = 4;
+    constexpr int kRows = kBUpdateRows;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t step = (((int64_t)gridDim.x * blockDim.x) >> 5) * kRows;
     for (int64_t v0 = warp * kRows; v0 < a.n; v0 += step) {
@@ -572,7 +580,7 @@ __global__ void __launch_bounds__(kBlock) k_b_dc_update(BatchArgs a, const float
     const float d = (float)st->d;
     const float share = (float)(st->Ddc[lane] * st->inv_n);   // Ddc / n; d multiplies the sum below
     KahanF dm;
-    constexpr int kRows = 4;
+    constexpr int kRows = kBUpdateRows;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t step = (((int64_t)gridDim.x * blockDim.x) >> 5) * kRows;
     for (int64_t v0 = warp * kRows; v0 < a.n; v0 += step) {
