@@ -202,9 +202,10 @@ def kernel_sources_sha(family):
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(family):
-    """DRAM bytes per gathered edge of a kernel family on R-MAT-24, from the committed
-    ncu summary (`key: value` lines), if it was taken on the current sources."""
+def recorded_traffic(family, graph="rmat24"):
+    """DRAM bytes per gathered edge of a kernel family on a graph of the default step
+    (rmat24, er24), from the committed ncu summary (`key: value` lines), if it was taken on
+    the current sources."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
     rec = {}
@@ -215,11 +216,24 @@ def recorded_traffic(family):
                 rec[k.strip()] = v.strip()
     if rec.get(f"{family}_sources_sha") != kernel_sources_sha(family):
         return None
-    v = rec.get(f"{family}_dram_bytes_per_edge_visit")
+    v = rec.get(f"{family}_dram_bytes_per_edge_visit_{graph}")
+    if v is None and graph == "rmat24":
+        v = rec.get(f"{family}_dram_bytes_per_edge_visit")
     return float(v) if v else None
 
 
-def rooflines(records, resident):
+def gather_ceiling(pr, stream):
+    """Random 4-byte loads per second from an L2-resident 64 MB vector bypassing L1, 16 in
+    flight per lane, 4 blocks per SM (pr_measure_gather_rate): the rate at which an SM can
+    send L1 misses to L2, measured on this GPU now.  Median of three launches."""
+    rates = []
+    for _ in range(4):
+        r = pr.pr_measure_gather_rate(1 << 24, 1 << 27, 0, 4, 2048, seed=1, stream=stream)
+        rates.append(r["gathers_per_s"])
+    return statistics.median(rates[1:])
+
+
+def rooflines(records, resident, loads_per_s=None):
     """Roofline of the dominant kernel of the step, and of every (graph, variant) pair.
 
     A launch of the synchronous variant is one iteration (k_heavy_segments + k_rows_tma, or
@@ -244,9 +258,16 @@ def rooflines(records, resident):
         visits = sum(r["loop_edge_visits"] for r in rs)
         alg_bytes = b_sweep * visits / st["nnz"]
         achieved = alg_bytes / (loop_ms * 1e-3) / 1e9
-        per_visit = recorded_traffic(vname) if gname.startswith("rmat") else None
+        per_visit = recorded_traffic(vname, gname)
         traffic = per_visit * visits / launches if per_visit else None
-        rows.append({"graph": gname, "variant": vname,
+        ceiling = None
+        if loads_per_s:
+            # every gather whose source is outside the L1 hub prefix is one L2 request
+            missing = st["nnz"] - st.get("hub_prefix_edges", 0)
+            c_ms = missing * (visits / st["nnz"]) / launches / loads_per_s * 1e3
+            ceiling = {"l1_missing_gathers_per_sweep": missing, "loads_per_s": loads_per_s,
+                       "ms_per_launch": c_ms, "frac_of_ceiling": c_ms / (loop_ms / launches)}
+        rows.append({"graph": gname, "variant": vname, "gather_ceiling": ceiling,
                      "kernel": ((f"jacobi iteration (k_heavy_segments + "
                                  f"{'k_rows_tma' if st.get('n_tma_tiles', 0) > 0 else 'k_rows'})")
                                 if vname == "jacobi"
@@ -262,6 +283,12 @@ def rooflines(records, resident):
     dominant = max(share, key=share.get)
     head = [r for r in rows if r["variant"] == dominant and r["graph"].startswith("rmat")][0]
     roofline = {k: head[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
+    if head.get("gather_ceiling"):
+        roofline["frac_of_ceiling"] = head["gather_ceiling"]["frac_of_ceiling"]
+        roofline["gather_ceiling"] = {**head["gather_ceiling"],
+                                      "how": "L1-missing gathers per launch (edges whose source is outside "
+                                             "the 49,152-vertex hub prefix) / random-gather rate measured "
+                                             "live by pr_measure_gather_rate (L2-resident 64 MB vector)"}
     roofline.update({"kernel": f"{head['kernel']} on {head['graph']}",
                      "share_of_step": share[dominant] / total,
                      "peak_source": f"{peak_kind} hbm_gbs (of measured)" if peak_kind == "measured"
@@ -1320,7 +1347,8 @@ def main():
     ms, visits = combine_ranks(dist, dev, ev0.elapsed_time(ev1), visits)
     value = visits / (ms * 1e-3) / 1e9
 
-    roofline, roofline_all = rooflines(records, resident)
+    loads_per_s = gather_ceiling(pr, stream)
+    roofline, roofline_all = rooflines(records, resident, loads_per_s)
 
     cases = {}
     for r in records:

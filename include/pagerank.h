@@ -127,6 +127,10 @@ typedef struct pr_graph_stats {
     float setup_ms;        /* device time of pr_create_graph's kernels         */
     int64_t n_tma_tiles;   /* tiles of the pipelined synchronous row kernel (0:
                               the layout cannot use it; see PR_OPT_TMA_TILES)   */
+    int64_t hub_prefix_edges; /* edges whose source is among the first 49,152
+                              vertices of the binned order, the hub prefix the
+                              synchronous gathers read through L1 by default
+                              (the other gathers are L1 misses)             */
 } pr_graph_stats;
 
 /* Build a graph on the current device.

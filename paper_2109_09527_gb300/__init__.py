@@ -87,7 +87,8 @@ class pr_graph_stats(ctypes.Structure):
                 ("n_segments", ctypes.c_int64), ("n_tiles", ctypes.c_int64),
                 ("max_indeg", ctypes.c_int64), ("rowptr_bytes", ctypes.c_int32),
                 ("sm_count", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
-                ("setup_ms", ctypes.c_float), ("n_tma_tiles", ctypes.c_int64)]
+                ("setup_ms", ctypes.c_float), ("n_tma_tiles", ctypes.c_int64),
+                ("hub_prefix_edges", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

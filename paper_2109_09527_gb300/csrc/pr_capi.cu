@@ -197,6 +197,7 @@ extern "C" pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* s) {
     s->device_bytes = g->device_bytes;
     s->setup_ms = g->setup_ms;
     s->n_tma_tiles = g->n_tma_tiles;
+    s->hub_prefix_edges = g->hub_prefix_edges;
     return PR_OK;
 }
 

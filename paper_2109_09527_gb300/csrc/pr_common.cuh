@@ -233,6 +233,7 @@ struct pr_graph {
     int32_t* out_pos = nullptr;      // and the per-edge contribution array
     float* contrib = nullptr;
     int64_t n_tma_tiles = 0;         // 0: the layout cannot use k_rows_tma
+    int64_t hub_prefix_edges = 0;    // edges whose source is among the default L1 hub prefix
     prk::Tile* tma_fused = nullptr;  // fused tile list: light and empty-row tiles with every heavy-row
                                      // segment as a tile of its own, interleaved (pad = first edge)
     int32_t* tma_fused_e1 = nullptr; // one past the last edge of each fused tile

@@ -236,6 +236,17 @@ __global__ void k_relabel_block(const RP* __restrict__ rp, const int32_t* __rest
     }
 }
 
+// Edges whose (binned) source id is below `limit`.
+__global__ void k_count_below(const int32_t* __restrict__ ci, int64_t nnz, int32_t limit,
+                              unsigned long long* __restrict__ count) {
+    unsigned long long c = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += stride) c += ci[k] < limit;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
 __global__ void k_inv_outdeg(const uint32_t* __restrict__ outdeg, const int32_t* __restrict__ order,
                              int64_t n, float* __restrict__ inv, unsigned long long* n_dangling) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -474,10 +485,19 @@ pr_status build_layout(pr_graph* g, const RP* rp, const int32_t* ci, cudaStream_
         }
     }
 
-    unsigned long long ndang = 0;
+    // edges whose source is in the hub prefix the gathers read through L1
+    unsigned long long* hub_edges = nullptr;
+    PRK_CHECK(s.alloc((void**)&hub_edges, sizeof(unsigned long long)));
+    PRK_CHECK(cudaMemsetAsync(hub_edges, 0, sizeof(unsigned long long), st));
+    if (nnz > 0)
+        k_count_below<<<grid_for(nnz, sm), kBlock, 0, st>>>(g->colidx, nnz, (int32_t)(kDefaultHot & 0x0fffffff),
+                                                             hub_edges);
+    unsigned long long ndang = 0, nhub = 0;
     PRK_CHECK(cudaMemcpyAsync(&ndang, dmax + 1, sizeof(ndang), cudaMemcpyDeviceToHost, st));
+    PRK_CHECK(cudaMemcpyAsync(&nhub, hub_edges, sizeof(nhub), cudaMemcpyDeviceToHost, st));
     PRK_CHECK(cudaStreamSynchronize(st));
     g->n_dangling = (int64_t)ndang;
+    g->hub_prefix_edges = (int64_t)nhub;
     return PR_OK;
 }
 

@@ -133,7 +133,7 @@ def test_roofline_arithmetic_on_synthetic_records():
     assert nb["bytes_per_launch"] == pytest.approx(15.5 * B)
     assert nb["achieved"] == pytest.approx(15.5 * B / 14e-3 / 1e9)
     for (g, v), r in by.items():
-        per_edge = bench.recorded_traffic(v) if g.startswith("rmat") else None
+        per_edge = bench.recorded_traffic(v, g)
         if per_edge is None:
             assert r["traffic"] is None
         else:
@@ -162,3 +162,27 @@ def test_clock_samples_summary():
     c = bench.ClockSampler.summarise(hot)
     assert c["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"] and c["sm_mhz"] == 1785.0
     assert bench.ClockSampler.summarise([])["reasons"] == ["no samples"]
+
+
+def test_gather_ceiling_arithmetic_on_synthetic_records():
+    """frac_of_ceiling = (gathers outside the L1 hub prefix per launch / the measured random
+    gather rate) / the launch's time: 0.57 ms of requests in a 0.9 ms iteration is 0.633."""
+    sys.path.insert(0, ROOT)
+    import bench
+    n, nnz = 1 << 24, 263_429_870
+    hub = int(0.43 * nnz)
+    st = {"n": n, "nnz": nnz, "rowptr_bytes": 4, "n_tma_tiles": 10, "hub_prefix_edges": hub}
+    resident = [("rmat24", None, st)]
+    recs = [{"graph": "rmat24", "variant": "jacobi", "iterations": 19, "loop_ms": 19 * 0.9,
+             "loop_edge_visits": 19.0 * nnz, "time_to_tol_ms": 17.0},
+            {"graph": "rmat24", "variant": "nonblocking", "iterations": 17, "loop_ms": 14.0,
+             "loop_edge_visits": 15.5 * nnz, "time_to_tol_ms": 16.0}]
+    rate = 303e9
+    roof, rows = bench.rooflines(recs, resident, rate)
+    by = {r["variant"]: r for r in rows}
+    c_ms = (nnz - hub) / rate * 1e3
+    assert by["jacobi"]["gather_ceiling"]["ms_per_launch"] == pytest.approx(c_ms)
+    assert by["jacobi"]["gather_ceiling"]["frac_of_ceiling"] == pytest.approx(c_ms / 0.9)
+    assert by["nonblocking"]["gather_ceiling"]["ms_per_launch"] == pytest.approx(15.5 * c_ms)
+    assert roof["frac_of_ceiling"] == pytest.approx(c_ms / 0.9)
+    assert bench.rooflines(recs, resident)[0].get("frac_of_ceiling") is None
