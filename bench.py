@@ -164,7 +164,7 @@ KERNEL_SOURCES = {
     "jacobi": ["pr_common.cuh", "pr_tile.cuh", "pr_jacobi.cu"],
     "nonblocking": ["pr_common.cuh", "pr_tile.cuh", "pr_nonblocking.cu"],
 }
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_rmat24.txt")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_rmat24_er24.txt")
 
 
 def _code_only(src):
@@ -763,9 +763,13 @@ def measure_set(args, dev, dist, rank, local_rank, world):
         time.sleep(0.3)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
+    t_host = time.perf_counter()
     runs = [g.solve_set(tol=TOL, max_iter=MAX_ITER, out=out) for _ in range(args.steps)]
     ev1.record(stream)
     torch.cuda.synchronize()
+    t_host = time.perf_counter() - t_host
+    log(f"[bench] set: {args.steps} solves, events {ev0.elapsed_time(ev1):.2f} ms, host {1e3 * t_host:.2f} ms, "
+        f"per-solve device {[round(r[1].ms_device, 2) for r in runs]} ms")
     if dist:
         dist.barrier()
     clocks = sampler.stop() if sampler else None
