@@ -131,6 +131,8 @@ typedef struct pr_graph_stats {
                               vertices of the binned order, the hub prefix the
                               synchronous gathers read through L1 by default
                               (the other gathers are L1 misses)             */
+    int64_t n_isolated;    /* vertices without in- and out-edges (the last
+                              rows of the binned order)                       */
 } pr_graph_stats;
 
 /* Build a graph on the current device.
@@ -284,6 +286,19 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
  *                         copies while the previous window is summed (64 rows
  *                         in flight per warp); 0 loads them into registers
  *                         (16 or 32 rows per warp).  Same sums, same order.
+ *   PR_OPT_IMPLICIT_ZERO_ROWS batched solver, FP32 form: 1 (default) keeps
+ *                         the ranks of rows without in-edges implicit after
+ *                         the first iteration.  By Eq. 1 such a row's rank is
+ *                         (1-d) t_v + d D/n, where D is the column's dangling
+ *                         mass, so the update writes only the quotient rank /
+ *                         outdeg of those with out-edges and nothing for
+ *                         isolated vertices; their L1 change, n_z d |D - D'|/n
+ *                         over the n_z such rows, and the isolated vertices'
+ *                         share of the next dangling mass are added in FP64,
+ *                         and their ranks are written once after the loop.
+ *                         Same iterates, same quotients; 0 updates every row
+ *                         every iteration.  Not used by PR_OPT_BATCH_BF16 or
+ *                         PR_OPT_BATCH_DC.
  *   PR_OPT_PERFORATION    loop perforation (Alg. 5) in the synchronous solver
  *                         (PR_JACOBI, pr_iterate) and in the barrier-free one
  *                         (PR_NONBLOCKING: the paper's No-Sync-Opt, Section
@@ -377,6 +392,7 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
 #define PR_OPT_BATCH_DC 18
 #define PR_OPT_FUSED_SEGMENTS 19
 #define PR_OPT_BATCH_ASYNC 20
+#define PR_OPT_IMPLICIT_ZERO_ROWS 21
 PR_API pr_status pr_set_option(pr_graph* g, int key, int64_t value);
 
 /* Batched personalised PageRank: k independent solves on one graph, one per

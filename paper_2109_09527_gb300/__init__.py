@@ -59,6 +59,7 @@ PR_OPT_LIGHT_LANES = 17
 PR_OPT_BATCH_DC = 18
 PR_OPT_FUSED_SEGMENTS = 19
 PR_OPT_BATCH_ASYNC = 20
+PR_OPT_IMPLICIT_ZERO_ROWS = 21
 
 LIB_PATH = _build.LIB_PATH
 
@@ -88,7 +89,7 @@ class pr_graph_stats(ctypes.Structure):
                 ("max_indeg", ctypes.c_int64), ("rowptr_bytes", ctypes.c_int32),
                 ("sm_count", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
                 ("setup_ms", ctypes.c_float), ("n_tma_tiles", ctypes.c_int64),
-                ("hub_prefix_edges", ctypes.c_int64)]
+                ("hub_prefix_edges", ctypes.c_int64), ("n_isolated", ctypes.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

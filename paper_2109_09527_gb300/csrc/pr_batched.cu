@@ -80,8 +80,10 @@ struct BatchState {
     const int32_t* tcol;
     const float* tval;
     int32_t dc_sweeps;               // defect correction: BF16 correction sweeps made
-    int32_t pad1;
+    int32_t implicit_zero;           // 1: rows without in-edges implicit after the first update
     double Ddc[kBK];                 // defect correction: dangling mass of each column of delta
+    double Dz[kBK];                  // implicit rows: dangling mass of each column's latest update
+    double Tiso[kBK];                // teleport sum of each column over the isolated vertices
     double D[kBK];                   // dangling mass of each column of the current input
     double T[kBK];                   // teleport sum of each column
     double resid[kBK];               // last L1 change of each column
@@ -100,6 +102,7 @@ struct BatchArgs {
     int64_t n;
     int64_t n_heavy;                 // rows [0, n_heavy) are gathered in segments
     int64_t zero_start;              // rows [zero_start, n) have no in-edges
+    int64_t iso_start;               // rows [iso_start, n) have no in- and no out-edges
     int32_t n_seg;
     int32_t n_tiles;
     BatchState* state;
@@ -356,24 +359,27 @@ __global__ void __launch_bounds__(kBlock) k_b_light_async(BatchArgs a, const T* 
     }
 }
 
-// Per-column block partials of (a, b) -> slots; the last block gets the grid
-// totals of its own column in every lane-j thread of warp 0 (fixed order).
-__device__ __forceinline__ bool batch_columns_to_grid(double a, double b, double* slots, uint32_t* ticket,
-                                                      double* ta, double* tb) {
-    __shared__ double sa[kBlock / 32][32], sb[kBlock / 32][32];
+// Per-column block partials of N values -> slots (N doubles per block and
+// column; the buffer holds kSlotValues); the last block gets the grid totals
+// of its own column in every lane-j thread of warp 0 (fixed order).
+constexpr int kSlotValues = 3;
+template <int N>
+__device__ __forceinline__ bool batch_columns_to_grid_n(const double (&v)[N], double* slots, uint32_t* ticket,
+                                                        double (&t)[N]) {
+    static_assert(N <= kSlotValues, "slot values");
+    __shared__ double sv[N][kBlock / 32][32];
     __shared__ int last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    sa[warp][lane] = a;
-    sb[warp][lane] = b;
+#pragma unroll
+    for (int i = 0; i < N; ++i) sv[i][warp][lane] = v[i];
     __syncthreads();
     if (warp == 0) {
-        double A = 0.0, B = 0.0;
-        for (int w = 0; w < kBlock / 32; ++w) {
-            A += sa[w][lane];
-            B += sb[w][lane];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            double A = 0.0;
+            for (int w = 0; w < kBlock / 32; ++w) A += sv[i][w][lane];
+            slots[((size_t)blockIdx.x * kBK + lane) * N + i] = A;
         }
-        slots[((size_t)blockIdx.x * kBK + lane) * 2] = A;
-        slots[((size_t)blockIdx.x * kBK + lane) * 2 + 1] = B;
         __threadfence();
     }
     __syncthreads();
@@ -382,21 +388,41 @@ __device__ __forceinline__ bool batch_columns_to_grid(double a, double b, double
     if (!last) return false;
     __threadfence();
     if (warp == 0) {
-        double A = 0.0, B = 0.0;
-        for (unsigned blk = 0; blk < gridDim.x; ++blk) {
-            A += __ldcg(slots + ((size_t)blk * kBK + lane) * 2);
-            B += __ldcg(slots + ((size_t)blk * kBK + lane) * 2 + 1);
-        }
-        *ta = A;
-        *tb = B;
+#pragma unroll
+        for (int i = 0; i < N; ++i) t[i] = 0.0;
+        for (unsigned blk = 0; blk < gridDim.x; ++blk)
+#pragma unroll
+            for (int i = 0; i < N; ++i) t[i] += __ldcg(slots + ((size_t)blk * kBK + lane) * N + i);
     }
     return true;
 }
 
+__device__ __forceinline__ bool batch_columns_to_grid(double a, double b, double* slots, uint32_t* ticket,
+                                                      double* ta, double* tb) {
+    const double v[2] = {a, b};
+    double t[2] = {0.0, 0.0};
+    const bool last = batch_columns_to_grid_n<2>(v, slots, ticket, t);
+    *ta = t[0];
+    *tb = t[1];
+    return last;
+}
+
 // X' from S / P, per-column dangling mass and L1 change; lane j = column j.
+//
+// Rows without in-edges (binned rows [zero_start, n)) gather nothing, so by
+// Eq. 1 a column's rank there is (1-d) t_v + d D/n, D its dangling mass.
+// With implicit_zero, after the first update such a row's rank is not read
+// or written: the update writes only the quotient of those with out-edges
+// (rows up to iso_start) and nothing for the isolated vertices after them;
+// for each active column the rows' L1 change, n_z d |D - Dz| / n with Dz
+// the dangling mass of the column's previous update, and the isolated
+// vertices' ranks, (1-d) Tiso + n_iso d D / n, as part of the next dangling
+// mass, are added in FP64 by the last block.  k_b_zero_fill writes the ranks
+// after the loop.  The quotients are those the full update would store.
 __global__ void __launch_bounds__(kBlock) k_b_update(BatchArgs a, const float* __restrict__ Xin,
                                                      float* __restrict__ Xout, float* __restrict__ Yout,
                                                      __nv_bfloat16* __restrict__ Yout16) {
+    __shared__ int32_t s_implicit;
     __shared__ int32_t s_bf16;
     __shared__ float s_dshare[kBK];
     __shared__ float s_base[kBK];
@@ -415,6 +441,7 @@ __global__ void __launch_bounds__(kBlock) k_b_update(BatchArgs a, const float* _
         if (lane == 0) {
             s_active = st->active;
             s_bf16 = st->bf16;
+            s_implicit = st->implicit_zero && st->iter > 0;
             s_done = *(const volatile int32_t*)&st->done;
             s_tptr = st->uniform ? nullptr : st->tptr;
             s_tcol = st->tcol;
@@ -437,7 +464,9 @@ __global__ void __launch_bounds__(kBlock) k_b_update(BatchArgs a, const float* _
     constexpr int kRows = kBUpdateRows;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t step = (((int64_t)gridDim.x * blockDim.x) >> 5) * kRows;
-    for (int64_t v0 = warp * kRows; v0 < a.n; v0 += step) {
+    const bool implicit = s_implicit != 0;
+    const int64_t hi = implicit ? a.zero_start : a.n;   // rows updated in full
+    for (int64_t v0 = warp * kRows; v0 < hi; v0 += step) {
         float sv[kRows], xo[kRows], inv[kRows];
 #pragma unroll
         for (int q = 0; q < kRows; ++q) {
@@ -445,7 +474,7 @@ __global__ void __launch_bounds__(kBlock) k_b_update(BatchArgs a, const float* _
             sv[q] = 0.f;
             xo[q] = 0.f;
             inv[q] = 0.f;
-            if (v < a.n) {
+            if (v < hi) {
                 if (v < a.n_heavy) {
                     const int32_t q1 = a.seg_ptr[v + 1];
                     for (int32_t j = a.seg_ptr[v]; j < q1; ++j) sv[q] += __ldcg(a.P + (size_t)j * kBK + lane);
@@ -459,7 +488,7 @@ __global__ void __launch_bounds__(kBlock) k_b_update(BatchArgs a, const float* _
 #pragma unroll
         for (int q = 0; q < kRows; ++q) {
             const int64_t v = v0 + q;
-            if (v >= a.n) break;
+            if (v >= hi) break;
             float xn = xo[q];
             if (active) {
                 if (tptr) {
@@ -479,10 +508,40 @@ __global__ void __launch_bounds__(kBlock) k_b_update(BatchArgs a, const float* _
             if (inv[q] == 0.f) acc.kahan(xn);
         }
     }
+    if (implicit) {
+        // rows without in-edges that have out-edges: the quotient only (the
+        // same value as the full update's, which adds d * 0)
+        const int64_t wstep = (((int64_t)gridDim.x * blockDim.x) >> 5) * kRows;
+        for (int64_t v0 = a.zero_start + warp * kRows; v0 < a.iso_start; v0 += wstep) {
+            float inv[kRows];
+#pragma unroll
+            for (int q = 0; q < kRows; ++q) inv[q] = v0 + q < a.iso_start ? __ldg(a.inv_out + v0 + q) : 0.f;
+#pragma unroll
+            for (int q = 0; q < kRows; ++q) {
+                const int64_t v = v0 + q;
+                if (v >= a.iso_start) break;
+                float xn = base;
+                if (tptr) {
+                    float tv = 0.f;
+                    const int32_t p1 = tptr[v + 1];
+                    for (int32_t p = tptr[v]; p < p1; ++p)
+                        if (s_tcol[p] == lane) tv = s_tval[p];
+                    xn = fmaf(omd, tv, dshare);
+                }
+                __stcs(Yout + (size_t)v * kBK + lane, xn * inv[q]);
+            }
+        }
+    }
     double R, Dn;
     if (batch_columns_to_grid(acc.resid(), acc.mass(), a.slots, &st->ticket, &R, &Dn) && threadIdx.x < 32) {
         const bool was_active = (s_active >> lane) & 1u;
         const double prev = st->resid[lane];
+        if (implicit) {
+            const double dd = st->d, Du = st->D[lane], Dz = st->Dz[lane];
+            if (was_active) R += (double)(a.n - a.zero_start) * dd * fabs(Du - Dz) * st->inv_n;
+            Dn += (1.0 - dd) * st->Tiso[lane] + (double)(a.n - a.iso_start) * dd * (was_active ? Du : Dz) * st->inv_n;
+        }
+        if (was_active) st->Dz[lane] = st->D[lane];   // the mass this update's zero-row ranks use
         st->D[lane] = Dn;
         const int32_t it = st->iter + 1;
         if (was_active) {
@@ -661,7 +720,7 @@ __global__ void __launch_bounds__(kBlock) k_b_init(BatchArgs a, const float* __r
     const int lane = threadIdx.x & 31;
     const int k = st->k;
     const float tu = (float)st->inv_n;
-    double dsum = 0.0, tsum = 0.0;
+    double dsum = 0.0, tsum = 0.0, tiso = 0.0;
     bool bad = false;
     const int64_t rows_per_pass = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < a.n; v += rows_per_pass) {
@@ -675,13 +734,17 @@ __global__ void __launch_bounds__(kBlock) k_b_init(BatchArgs a, const float* __r
         Y[(size_t)v * kBK + lane] = tv * inv;
         if (Y16) Y16[(size_t)v * kBK + lane] = __float2bfloat16_rn(tv * inv);
         if (inv == 0.f) dsum += (double)tv;
+        if (v >= a.iso_start) tiso += (double)tv;
         tsum += (double)tv;
     }
     if (bad) atomicOr(&st->error, 1u);
-    double D, T;
-    if (batch_columns_to_grid(dsum, tsum, a.slots, &st->ticket, &D, &T) && threadIdx.x < 32) {
+    const double part[3] = {dsum, tsum, tiso};
+    double tot[3];
+    if (batch_columns_to_grid_n<3>(part, a.slots, &st->ticket, tot) && threadIdx.x < 32) {
+        const double D = tot[0], T = tot[1];
         st->D[lane] = D;
         st->T[lane] = T;
+        st->Tiso[lane] = tot[2];
         st->resid[lane] = INFINITY;
         st->col_iter[lane] = 0;
         if (lane < k && !(T > 0.0)) atomicOr(&st->error, 1u);
@@ -691,6 +754,37 @@ __global__ void __launch_bounds__(kBlock) k_b_init(BatchArgs a, const float* __r
             st->active = k == 32 ? 0xffffffffu : ((1u << k) - 1u);
             st->ticket = 0;
         }
+    }
+}
+
+// The ranks of the rows without in-edges after a loop that kept them implicit
+// (k_b_update): (1-d) t_v + d Dz/n for each of the k columns, Dz the dangling
+// mass of the column's last update, in the same FP32 arithmetic as the update.
+__global__ void __launch_bounds__(kBlock) k_b_zero_fill(BatchArgs a, float* __restrict__ X0, float* __restrict__ X1) {
+    const BatchState* st = a.state;
+    if (!st->implicit_zero || st->iter < 2) return;   // after one update the rows were written in full
+    float* X = (st->iter & 1) ? X1 : X0;
+    const int lane = threadIdx.x & 31;
+    if (lane >= st->k) return;
+    const double d = st->d;
+    const float omd = (float)(1.0 - d);
+    const float dshare = (float)(d * st->Dz[lane] * st->inv_n);
+    const float base = (float)((1.0 - d) * st->inv_n + d * st->Dz[lane] * st->inv_n);
+    const int32_t* tptr = st->uniform ? nullptr : st->tptr;
+    const int32_t* tcol = st->tcol;
+    const float* tval = st->tval;
+    const int64_t rows_per_pass = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = a.zero_start + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); v < a.n;
+         v += rows_per_pass) {
+        float xn = base;
+        if (tptr) {
+            float tv = 0.f;
+            const int32_t p1 = tptr[v + 1];
+            for (int32_t p = tptr[v]; p < p1; ++p)
+                if (tcol[p] == lane) tv = tval[p];
+            xn = fmaf(omd, tv, dshare);
+        }
+        X[(size_t)v * kBK + lane] = xn;
     }
 }
 
@@ -802,6 +896,7 @@ BatchArgs batch_args(const pr_graph* g, const BatchCtx* b) {
     a.n = g->n;
     a.n_heavy = g->n_heavy;
     a.zero_start = b->zero_start;
+    a.iso_start = g->n - g->n_isolated;
     a.n_seg = (int32_t)g->n_seg;
     a.n_tiles = (int32_t)b->n_tasks;
     a.state = b->state;
@@ -926,7 +1021,7 @@ pr_status ensure_batch(pr_graph* g) {
     PRK_CHECK(dev_alloc(g, (void**)&b->state, sizeof(BatchState)));
     PRK_CHECK(cudaMallocHost((void**)&b->host_state, sizeof(BatchState)));
     b->slot_blocks = g->sm_count * kBUpdateBlocksPerSM;
-    PRK_CHECK(dev_alloc(g, (void**)&b->slots, (size_t)b->slot_blocks * kBK * 2 * sizeof(double)));
+    PRK_CHECK(dev_alloc(g, (void**)&b->slots, (size_t)b->slot_blocks * kBK * kSlotValues * sizeof(double)));
     b->zero_start = g->n;
     for (const Tile& t : g->host_tiles)
         if (t.kind == kTileZero) {
@@ -1104,6 +1199,7 @@ extern "C" pr_status pr_solve_batched(pr_graph* g, float damping, double tol, in
     hs->tptr = b->tptr;
     hs->tcol = b->tcol;
     hs->tval = b->tval;
+    hs->implicit_zero = (!dc && !bf16 && g->implicit_zero) ? 1 : 0;
     PRK_CHECK(cudaEventRecord(g->ev_start, s));
     PRK_CHECK(cudaMemcpyAsync(b->state, hs, sizeof(BatchState), cudaMemcpyHostToDevice, s));
     BatchArgs a = batch_args(g, b);
@@ -1144,9 +1240,10 @@ extern "C" pr_status pr_solve_batched(pr_graph* g, float damping, double tol, in
         }
     }
     PRK_CHECK(cudaEventRecord(g->ev_loop1, s));
+    k_b_zero_fill<<<update_grid(g, b), kBlock, 0, s>>>(a, b->X[0], b->X[1]);
     k_b_sum<<<update_grid(g, b), kBlock, 0, s>>>(a, b->X[0], b->X[1]);
     k_b_unpermute<<<small_grid(g), kBlock, 0, s>>>(a, b->X[0], b->X[1], g->rank, out, k);
-    launches += 2;
+    launches += 3;
     PRK_CHECK(cudaGetLastError());
     PRK_CHECK(cudaEventRecord(g->ev_stop, s));
     if (!out_dev) PRK_CHECK(cudaMemcpyAsync(x_out, out, nk * sizeof(float), cudaMemcpyDeviceToHost, s));

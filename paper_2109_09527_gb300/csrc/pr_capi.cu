@@ -198,6 +198,7 @@ extern "C" pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* s) {
     s->setup_ms = g->setup_ms;
     s->n_tma_tiles = g->n_tma_tiles;
     s->hub_prefix_edges = g->hub_prefix_edges;
+    s->n_isolated = g->n_isolated;
     return PR_OK;
 }
 
@@ -313,6 +314,11 @@ static pr_status set_option_impl(pr_graph* g, int key, int64_t value) {
             if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_BATCH_ASYNC needs a graph");
             if (value != 0 && value != 1) return fail(PR_ERR_INVALID_ARG, "PR_OPT_BATCH_ASYNC is 0 or 1");
             g->batch_async = (int)value;
+            return PR_OK;
+        case PR_OPT_IMPLICIT_ZERO_ROWS:
+            if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_IMPLICIT_ZERO_ROWS needs a graph");
+            if (value != 0 && value != 1) return fail(PR_ERR_INVALID_ARG, "PR_OPT_IMPLICIT_ZERO_ROWS is 0 or 1");
+            g->implicit_zero = (int)value;
             return PR_OK;
         case PR_OPT_FUSED_SEGMENTS:
             if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_FUSED_SEGMENTS needs a graph");

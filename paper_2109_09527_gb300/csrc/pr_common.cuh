@@ -60,7 +60,7 @@ constexpr int kTileHeavy = -1;           // tile kind: epilogue of heavy rows
 constexpr int kTileZero = -2;            // tile kind: rows without in-edges
 constexpr int kTileSeg = -3;             // tile kind (fused pipelined kernel): one 2048-edge segment of a
                                          // heavy row; row_begin = the row, row_end = the segment's index
-constexpr int kMaxBins = 42;
+constexpr int kMaxBins = 43;
 // 1: graph memory and set-up scratch come from the library's stream-ordered
 // pool (pool_alloc); 0: plain cudaMalloc / cudaFree.
 #ifndef PRK_POOL
@@ -205,6 +205,8 @@ struct pr_graph {
     int batch_bf16 = 0;                       // batched solver: BF16 Y until changes < 10^-value (0 = off)
     int batch_dc = 0;                         // batched solver: BF16 correction sweeps per FP32 step (0 = off)
     int batch_async = prk::kDefaultBatchAsync; // batched gathers with asynchronous copies (PR_OPT_BATCH_ASYNC)
+    int implicit_zero = 1;                    // batched solver: ranks of rows without in-edges kept implicit
+                                              // (PR_OPT_IMPLICIT_ZERO_ROWS)
     int perforation = 0;                      // loop perforation eps = 10^-value (0 = off)
     int dynamic_tiles = 0;                    // PR_OPT_DYNAMIC_TILES
     int delay_ns = 0;                         // PR_OPT_DELAY_NS
@@ -266,6 +268,7 @@ struct pr_graph {
     int64_t n_tiles = 0;
     int64_t n_dangling = 0;
     int64_t n_zero_indeg = 0;
+    int64_t n_isolated = 0;             // no in- and no out-edges: the last rows of the binned order
     int64_t max_indeg = 0;
     int64_t device_bytes = 0;
     float setup_ms = 0.f;

@@ -132,22 +132,25 @@ __global__ void k_outdeg(const int32_t* __restrict__ ci, int64_t nnz, uint32_t* 
 }
 
 // Bin of a row by in-degree: bin 40 - floor(log2 deg) for deg >= 1 (so bins
-// 1..40 hold decreasing power-of-two degree classes) and bin kZeroBin for rows
-// without in-edges.  With a power-of-two heavy threshold the heavy rows are
-// the prefix of bins up to 40 - log2(heavy).
+// 1..40 hold decreasing power-of-two degree classes), bin kZeroBin for rows
+// without in-edges that have out-edges, and bin kIsoBin, the last, for
+// isolated vertices (no in- and no out-edges).  With a power-of-two heavy
+// threshold the heavy rows are the prefix of bins up to 40 - log2(heavy).
 constexpr int kTopClass = 40;
 constexpr int kZeroBin = kTopClass + 1;
-constexpr int kNumBins = kTopClass + 2;
+constexpr int kIsoBin = kTopClass + 2;
+constexpr int kNumBins = kTopClass + 3;
 static_assert(kNumBins <= kMaxBins, "bin count");
 
 template <typename RP>
-__global__ void k_bins(const RP* __restrict__ rp, int64_t n, uint8_t* __restrict__ bin,
-                       int64_t* __restrict__ deg_out, unsigned long long* max_deg) {
+__global__ void k_bins(const RP* __restrict__ rp, int64_t n, const uint32_t* __restrict__ outdeg,
+                       uint8_t* __restrict__ bin, int64_t* __restrict__ deg_out, unsigned long long* max_deg) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     unsigned long long mx = 0;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
         int64_t deg = (int64_t)rp[v + 1] - (int64_t)rp[v];
-        int b = deg == 0 ? kZeroBin : kTopClass - (63 - __clzll((unsigned long long)deg));
+        int b = deg != 0 ? kTopClass - (63 - __clzll((unsigned long long)deg))
+                         : (outdeg[v] == 0 ? kIsoBin : kZeroBin);
         bin[v] = (uint8_t)b;
         deg_out[v] = deg;
         if ((unsigned long long)deg > mx) mx = (unsigned long long)deg;
@@ -367,7 +370,7 @@ pr_status build_layout(pr_graph* g, const RP* rp, const int32_t* ci, cudaStream_
     PRK_CHECK(s.alloc((void**)&deg, (size_t)n * sizeof(int64_t)));
     PRK_CHECK(s.alloc((void**)&dmax, 2 * sizeof(unsigned long long)));
     PRK_CHECK(cudaMemsetAsync(dmax, 0, 2 * sizeof(unsigned long long), st));
-    k_bins<RP><<<grid_for(n, sm), kBlock, 0, st>>>(rp, n, bin, deg, dmax);
+    k_bins<RP><<<grid_for(n, sm), kBlock, 0, st>>>(rp, n, outdeg, bin, deg, dmax);
 
     // stable counting sort by bin
     const int64_t nblk = (n + kChunk - 1) / kChunk;
@@ -401,6 +404,7 @@ pr_status build_layout(pr_graph* g, const RP* rp, const int32_t* ci, cudaStream_
     g->max_indeg = (int64_t)hmax;
     g->n_heavy = bin_start[kTopClass + 1 - lh];
     g->n_zero_indeg = n - bin_start[kZeroBin];
+    g->n_isolated = n - bin_start[kIsoBin];
     g->bin_start = bin_start;
 
     // binned colidx

@@ -276,3 +276,65 @@ def test_async_gathers_match_register_gathers_bit_for_bit(scale, heavy, index64)
         g.set_option(pr.PR_OPT_BATCH_ASYNC, 1)
         x, info, res_, its = g.solve_batched(32, t, tol=1e-6)
     check_columns(rp, ci, t, x, its, res_, 1e-6)
+
+
+def _zero_row_graph():
+    """R-MAT-12 (18% isolated vertices, 13% more without in-edges) with the seeds of some
+    columns placed on rows without in-edges, isolated or not."""
+    rp, ci = gg.rmat(12, 16, seed=21)
+    n = rp.size - 1
+    indeg = np.diff(rp)
+    outdeg = np.bincount(ci, minlength=n)
+    iso = np.flatnonzero((indeg == 0) & (outdeg == 0))
+    src_only = np.flatnonzero((indeg == 0) & (outdeg > 0))
+    assert iso.size > n // 8 and src_only.size > n // 16
+    t = gg.seed_teleports(n, 7, 6, seed=4)
+    t[:, 1] = 0.0
+    t[iso[:3], 1] = 1.0 / 3          # column 1: seeds on isolated vertices only
+    t[:, 2] = 0.0
+    t[src_only[:4], 2] = 0.25        # column 2: seeds on rows without in-edges
+    t[iso[5], 3] += 0.5              # column 3: a mixed seed set
+    t[:, 3] /= t[:, 3].sum()
+    return rp, ci, t
+
+
+@pytest.mark.parametrize("max_iter", [1, 2, 3, 400])
+@pytest.mark.parametrize("uniform", [False, True])
+def test_implicit_zero_rows_match_the_full_update(max_iter, uniform):
+    """PR_OPT_IMPLICIT_ZERO_ROWS: after the first update the ranks of rows without
+    in-edges are (1-d) t_v + d D/n (Eq. 1 with no gathered term), so they are neither read
+    nor written until the loop ends.  The iterates equal the full update's up to the
+    rounding of the dangling mass (FP64 instead of FP32 sums), at every iteration count
+    including the budget-cut ones, and match the oracle; isolated vertices end at
+    (1-d) t_v + d D/n exactly as the full update leaves them."""
+    rp, ci, t = _zero_row_graph()
+    n = rp.size - 1
+    tt = None if uniform else t
+    k = 7
+    outs = {}
+    with pr.Graph(rp, ci) as g:
+        st = g.stats()
+        assert st["n_isolated"] == int(((np.diff(rp) == 0) & (np.bincount(ci, minlength=n) == 0)).sum())
+        for implicit in (1, 0):
+            g.set_option(pr.PR_OPT_IMPLICIT_ZERO_ROWS, implicit)
+            x = np.empty((n, k), np.float32)
+            status, info, res, its = pr.pr_solve_batched(g.handle, D, 1e-6, max_iter, k, tt, x)
+            outs[implicit] = (x, info, res, its, status)
+        g.set_option(pr.PR_OPT_IMPLICIT_ZERO_ROWS, 1)
+    (x1, i1, r1, it1, s1), (x0, i0, r0, it0, s0) = outs[1], outs[0]
+    assert s1 == s0
+    assert np.all(np.abs(it1.astype(int) - it0.astype(int)) <= 1)
+    np.testing.assert_allclose(r1, r0, rtol=1e-4, atol=1e-12)
+    np.testing.assert_allclose(i1.dangling_mass, i0.dangling_mass, rtol=1e-6)
+    if np.array_equal(it1, it0):
+        np.testing.assert_allclose(x1, x0, rtol=2e-6, atol=1e-12)
+    if max_iter == 400:
+        assert i1.converged == 1
+        check_columns(rp, ci, tt, x1, it1, r1, 1e-6)
+    else:
+        # budget-cut: each column equals max_iter oracle updates (then rescaled)
+        for j in range(k):
+            tj = None if tt is None else tt[:, j].astype(np.float64)
+            xo, _, _ = oracle.pagerank_jacobi(rp, ci, d=D, tol=0, max_iter=max_iter, t=tj)
+            xo = xo * ((1.0 if tj is None else tj.sum()) / xo.sum())
+            assert np.abs(x1[:, j] - xo).sum() <= 1e-6, j
