@@ -286,9 +286,12 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
  *                         copies while the previous window is summed (64 rows
  *                         in flight per warp); 0 loads them into registers
  *                         (16 or 32 rows per warp).  Same sums, same order.
- *   PR_OPT_IMPLICIT_ZERO_ROWS batched solver, FP32 form: 1 (default) keeps
- *                         the ranks of rows without in-edges implicit after
- *                         the first iteration.  By Eq. 1 such a row's rank is
+ *   PR_OPT_IMPLICIT_ZERO_ROWS the batched solver's FP32 form and the
+ *                         synchronous solver's pipelined row kernel (PR_JACOBI,
+ *                         pr_iterate; PR_OPT_TMA_TILES, not with
+ *                         PR_OPT_FUSED_SEGMENTS): 1 (default) keeps the ranks
+ *                         of rows without in-edges implicit after the first
+ *                         iteration.  By Eq. 1 such a row's rank is
  *                         (1-d) t_v + d D/n, where D is the column's dangling
  *                         mass, so the update writes only the quotient rank /
  *                         outdeg of those with out-edges and nothing for
@@ -296,8 +299,9 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
  *                         over the n_z such rows, and the isolated vertices'
  *                         share of the next dangling mass are added in FP64,
  *                         and their ranks are written once after the loop.
- *                         Same iterates, same quotients; 0 updates every row
- *                         every iteration.  Not used by PR_OPT_BATCH_BF16 or
+ *                         Same iterates and quotients up to the rounding of
+ *                         the dangling mass; 0 updates every row every
+ *                         iteration.  Not used by PR_OPT_BATCH_BF16 or
  *                         PR_OPT_BATCH_DC.
  *   PR_OPT_PERFORATION    loop perforation (Alg. 5) in the synchronous solver
  *                         (PR_JACOBI, pr_iterate) and in the barrier-free one

@@ -145,7 +145,9 @@ struct SolveState {
     int32_t sweeps_max;
     uint32_t tile_next;  // next tile to hand out (dynamic tile assignment)
     uint32_t frozen;     // rows frozen by loop perforation (counted after the solve)
-    uint32_t pad_;
+    int32_t implicit;    // 1: ranks of rows without in-edges implicit after the first update
+    double Dz;           // implicit rows: the dangling mass their current ranks use
+    double t_iso;        // implicit rows: teleport sum over the isolated vertices
 };
 
 // Arguments of the per-iteration kernels (passed by value).
@@ -183,6 +185,9 @@ struct IterArgs {
     float2* hr_part;             // fused: (L1 change, dangling mass) of each heavy row's update
     int32_t fused;               // 1: heavy-row segments are tiles of the pipelined kernel
     int32_t n_heavy;             // rows [0, n_heavy) are gathered in segments
+    int32_t n_tiles_live;        // pipelined kernel: tiles before those of the isolated vertices
+    int64_t zero_start;          // rows [zero_start, n) have no in-edges
+    int64_t iso_start;           // rows [iso_start, n) have no in- and no out-edges
 };
 
 }  // namespace prk
@@ -205,7 +210,8 @@ struct pr_graph {
     int batch_bf16 = 0;                       // batched solver: BF16 Y until changes < 10^-value (0 = off)
     int batch_dc = 0;                         // batched solver: BF16 correction sweeps per FP32 step (0 = off)
     int batch_async = prk::kDefaultBatchAsync; // batched gathers with asynchronous copies (PR_OPT_BATCH_ASYNC)
-    int implicit_zero = 1;                    // batched solver: ranks of rows without in-edges kept implicit
+    int implicit_zero = 1;                    // ranks of rows without in-edges kept implicit in the
+                                              // batched solver and the pipelined synchronous iteration
                                               // (PR_OPT_IMPLICIT_ZERO_ROWS)
     int perforation = 0;                      // loop perforation eps = 10^-value (0 = off)
     int dynamic_tiles = 0;                    // PR_OPT_DYNAMIC_TILES
@@ -269,6 +275,7 @@ struct pr_graph {
     int64_t n_dangling = 0;
     int64_t n_zero_indeg = 0;
     int64_t n_isolated = 0;             // no in- and no out-edges: the last rows of the binned order
+    int64_t n_tma_live = 0;             // pipelined-kernel tiles before those of the isolated vertices
     int64_t max_indeg = 0;
     int64_t device_bytes = 0;
     float setup_ms = 0.f;
@@ -344,7 +351,7 @@ cudaError_t fill_fused_tiles(Tile* tiles, int32_t* e1, int64_t count, const int3
 // Count the frozen rows of a perforated solve into SolveState::frozen.
 cudaError_t launch_count_frozen(const pr_graph* g, cudaStream_t s);
 void launch_finalize(const pr_graph* g, const IterArgs& a, float* out, bool renormalise,
-                     cudaStream_t s, int* launches);
+                     cudaStream_t s, int* launches, bool implicit = false);
 
 // Exclusive scan of count int64 values into int32 offsets[count + 1] (device
 // arrays); synchronises the stream before its temporaries are freed.

@@ -241,7 +241,10 @@ __global__ void __launch_bounds__(kIterBlock, kGatherMinBlocks) k_rows(IterArgs 
 //
 // k_rows_tma computes exactly what k_rows computes, for the configuration
 // the solver runs by default (32-bit offsets, tiles in a fixed round-robin
-// order, no perforation, no shared-memory copy of y).  In k_rows a row group
+// order, no perforation, no shared-memory copy of y), except that by default
+// (PR_OPT_IMPLICIT_ZERO_ROWS) it keeps the ranks of rows without in-edges
+// implicit after the first update: the same iterates, with the dangling mass
+// and the L1 change of those rows summed in FP64.  In k_rows a row group
 // waits on three memory latencies per pair of rows: the row offsets, then the
 // column indices, then the gathers.  Here a producer warp moves every tile's
 // offsets, column indices and per-row vectors (x, 1/outdeg, teleport) into
@@ -526,13 +529,21 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaMinBlocks) k_rows_tma(IterArg
     c.hot_sm = nullptr;
     c.lane_mode = a.lane_mode;
     Acc acc;
+    // Rows without in-edges gather nothing: by Eq. 1 their rank is
+    // (1-d) t_v + d D/n.  After the first update (implicit) their ranks are
+    // neither read nor written: the tiles of isolated vertices are skipped and
+    // the other such rows store their quotient only; the last block adds their
+    // L1 change and the isolated vertices' dangling mass, and k_zero_fill
+    // writes the ranks after the loop.
+    const bool implicit = sv.implicit && sv.iter > 0 && !a.fused;
+    const int n_tiles = implicit ? a.n_tiles_live : a.n_tiles;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     bool timed_out = false;
     if (warp == kWarps) {
         // producer: lane 0 issues the copies of the block's tiles in order
         if (lane == 0) {
             int k = 0;
-            for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x, ++k) {
+            for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++k) {
                 const int s = k % kTmaStages;
                 const int use = k / kTmaStages;
                 if (use > 0 && !mbar_wait(empty + s, (uint32_t)(use - 1) & 1u)) {
@@ -559,7 +570,7 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaMinBlocks) k_rows_tma(IterArg
     } else {
         const int tid = threadIdx.x;
         int k = 0;
-        for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x, ++k) {
+        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++k) {
             const int s = k % kTmaStages;
             if (!mbar_wait(full + s, (uint32_t)(k / kTmaStages) & 1u)) {
                 timed_out = true;
@@ -571,6 +582,13 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaMinBlocks) k_rows_tma(IterArg
                 tma_light_tile<kUniform>(tile, stg, y_in, x_out, y_out, c, acc, tid);
             } else if (tile.kind == kTileSeg) {
                 tma_segment_tile<kUniform>(a, tile, a.tile_e1[t], stg, s, seg_red, x_in, y_in, x_out, y_out, c, tid);
+            } else if (implicit && tile.kind == kTileZero) {
+                // the quotient of the implicit rank (what row_update stores for s = 0)
+                const int o = tile.row_begin & 3;
+                for (int i = tid; i < tile.row_end - tile.row_begin; i += kBlock) {
+                    const float b = kUniform ? c.base : fmaf(c.one_m_d, stg.tel[o + i], c.d_share);
+                    st_y(y_out + tile.row_begin + i, b * stg.inv[o + i]);
+                }
             } else {
                 const int o = tile.row_begin & 3;
                 for (int i = tid; i < tile.row_end - tile.row_begin; i += kBlock) {
@@ -605,6 +623,13 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaMinBlocks) k_rows_tma(IterArg
         Dn += hd;
     }
     if (last_block && threadIdx.x == 0) {
+        if (implicit) {
+            // every row without in-edges changed by d |D - Dz| / n; the
+            // isolated ones are dangling: (1-d) t_iso + n_iso d D / n
+            R += (double)(a.n - a.zero_start) * d * fabs(sv.D - st->Dz) * sv.inv_n;
+            Dn += (1.0 - d) * st->t_iso + (double)(a.n - a.iso_start) * d * sv.D * sv.inv_n;
+        }
+        st->Dz = sv.D;
         st->resid = R;
         st->D = Dn;
         st->iter += 1;
@@ -614,6 +639,34 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaMinBlocks) k_rows_tma(IterArg
         st->tile_next = 0;
         if (done && a.use_cond) cudaGraphSetConditional(a.cond, 0);
     }
+}
+
+// Teleport sum over the isolated vertices (binned rows [iso_start, n)).
+__global__ void __launch_bounds__(kBlock) k_t_iso(IterArgs a, const float* __restrict__ t_bin) {
+    SolveState* st = a.state;
+    KahanF s;
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
+    for (int64_t i = a.iso_start + (int64_t)blockIdx.x * kBlock + threadIdx.x; i < a.n; i += stride) s.add(t_bin[i]);
+    double T, unused;
+    if (block_pair_to_grid(s.value(), 0.0, a.slots, &st->ticket, &T, &unused) && threadIdx.x == 0) {
+        st->t_iso = T;
+        st->ticket = 0;
+    }
+}
+
+// The ranks of the rows without in-edges after a loop that kept them implicit
+// (k_rows_tma): (1-d) t_v + d Dz/n, in the arithmetic of the row kernel.
+__global__ void __launch_bounds__(kBlock) k_zero_fill(IterArgs a, float* __restrict__ x0, float* __restrict__ x1) {
+    const SolveState* st = a.state;
+    if (!st->implicit || st->iter < 2) return;   // after one update the rows were written in full
+    float* x = (st->iter & 1) ? x1 : x0;
+    const double d = st->d;
+    const double share = st->Dz * st->inv_n;
+    const float base = (float)((1.0 - d) * st->inv_n + d * share);
+    const float one_m_d = (float)(1.0 - d), d_share = (float)(d * share);
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
+    for (int64_t i = a.zero_start + (int64_t)blockIdx.x * kBlock + threadIdx.x; i < a.n; i += stride)
+        x[i] = a.teleport ? fmaf(one_m_d, a.teleport[i], d_share) : base;
 }
 
 // Rows frozen by loop perforation, added into the solve state.
@@ -784,6 +837,9 @@ IterArgs make_args(const pr_graph* g, bool uniform) {
     a.withhold = g->test_withhold;
     a.nnz = g->nnz;
     a.lane_mode = g->lane_mode;
+    a.n_tiles_live = (int32_t)g->n_tma_live;
+    a.zero_start = g->n - g->n_zero_indeg;
+    a.iso_start = g->n - g->n_isolated;
     return a;
 }
 
@@ -933,7 +989,11 @@ void launch_init(const pr_graph* g, const IterArgs& a, const float* t_dev, const
 }
 
 void launch_finalize(const pr_graph* g, const IterArgs& a, float* out, bool renormalise, cudaStream_t s,
-                     int* launches) {
+                     int* launches, bool implicit) {
+    if (implicit && a.zero_start < a.n) {
+        k_zero_fill<<<small_grid(g), kBlock, 0, s>>>(a, g->x[0], g->x[1]);
+        ++*launches;
+    }
     if (renormalise) {
         k_sum_x<<<small_grid(g), kBlock, 0, s>>>(a, g->x[0], g->x[1]);
         ++*launches;
@@ -1067,18 +1127,28 @@ pr_status run_jacobi(pr_graph* g, float damping, double tol, int32_t max_iter, c
     hs->t_sum = 1.0;
     hs->max_iter = max_iter;
     hs->uniform_t = uniform ? 1 : 0;
-    PRK_CHECK(cudaEventRecord(g->ev_start, s));
-    PRK_CHECK(cudaMemcpyAsync(g->state, hs, sizeof(SolveState), cudaMemcpyHostToDevice, s));
-
     IterArgs a = make_args(g, uniform);
     if (edge) {
         a.edge = 1;
         a.out_src = g->out_src;
         a.out_pos = g->out_pos;
     }
+    // implicit ranks of rows without in-edges: the pipelined kernel with the
+    // heavy-row segments in a kernel of their own
+    const bool tma = !edge && !g->idx64 && tma_applies(g, a);
+    const bool implicit = g->implicit_zero && tma && !(g->fuse_segments && g->n_tma_fused > 0);
+    hs->implicit = implicit ? 1 : 0;
+    hs->t_iso = (double)g->n_isolated * hs->inv_n;   // uniform teleport; else summed on the device
+    PRK_CHECK(cudaEventRecord(g->ev_start, s));
+    PRK_CHECK(cudaMemcpyAsync(g->state, hs, sizeof(SolveState), cudaMemcpyHostToDevice, s));
+
     int launches = 0;
     launch_init(g, a, t_dev, x0_dev, s);
     ++launches;
+    if (implicit && !uniform) {
+        k_t_iso<<<small_grid(g), kBlock, 0, s>>>(a, g->teleport);
+        ++launches;
+    }
     PRK_CHECK(cudaGetLastError());
     if (a.frozen) PRK_CHECK(cudaMemsetAsync(g->frozen, 0, (size_t)g->n, s));   // nothing frozen yet
     PRK_CHECK(cudaEventRecord(g->ev_loop0, s));
@@ -1126,7 +1196,7 @@ pr_status run_jacobi(pr_graph* g, float damping, double tol, int32_t max_iter, c
     }
     PRK_CHECK(cudaEventRecord(g->ev_loop1, s));
 
-    launch_finalize(g, a, out, renormalise, s, &launches);
+    launch_finalize(g, a, out, renormalise, s, &launches, implicit);
     PRK_CHECK(cudaGetLastError());
     if (a.frozen) {
         PRK_CHECK(launch_count_frozen(g, s));

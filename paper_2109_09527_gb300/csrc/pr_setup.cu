@@ -344,7 +344,8 @@ std::vector<Tile> make_tiles(const std::vector<int64_t>& bin_start, int lh, int6
         const int64_t rows = std::max<int64_t>(1, std::min<int64_t>(max_rows, max_edges / ((1LL << (k + 1)) - 1)));
         add(bin_start[b], bin_start[b + 1], rows, lg);
     }
-    add(bin_start[kZeroBin], bin_start[kNumBins], zero_rows, kTileZero);
+    add(bin_start[kZeroBin], bin_start[kIsoBin], zero_rows, kTileZero);
+    add(bin_start[kIsoBin], bin_start[kNumBins], zero_rows, kTileZero);   // isolated vertices: the last tiles
     return tiles;
 }
 
@@ -462,6 +463,9 @@ pr_status build_layout(pr_graph* g, const RP* rp, const int32_t* ci, cudaStream_
         PRK_CHECK(cudaMemcpyAsync(g->tma_tiles, tt.data(), tt.size() * sizeof(Tile), cudaMemcpyHostToDevice, st));
         PRK_CHECK(fill_tile_edges(g->tma_tiles, (int64_t)tt.size() - 1, (const int32_t*)g->rowptr, st));
         g->n_tma_tiles = (int64_t)tt.size() - 1;
+        g->n_tma_live = 0;
+        while (g->n_tma_live < g->n_tma_tiles && tt[(size_t)g->n_tma_live].row_begin < bin_start[kIsoBin])
+            ++g->n_tma_live;
 
         // The fused list: the light and empty-row tiles in the same order, with
         // every heavy-row segment a tile of its own, spread evenly among them,

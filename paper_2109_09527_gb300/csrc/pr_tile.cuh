@@ -219,7 +219,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 // every block would queue hundreds of thousands of requests on one L2 slice.
 struct StateView {
     double d, D, inv_n, t_sum, scale;
-    int32_t done, iter;
+    int32_t done, iter, implicit;
 };
 
 __device__ __forceinline__ StateView block_state(const SolveState* st) {
@@ -227,6 +227,7 @@ __device__ __forceinline__ StateView block_state(const SolveState* st) {
     if (threadIdx.x == 0) {
         sv.done = *(const volatile int32_t*)&st->done;
         sv.iter = *(const volatile int32_t*)&st->iter;
+        sv.implicit = st->implicit;
         sv.d = st->d;
         sv.D = st->D;
         sv.inv_n = st->inv_n;

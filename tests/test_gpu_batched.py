@@ -324,7 +324,10 @@ def test_implicit_zero_rows_match_the_full_update(max_iter, uniform):
     (x1, i1, r1, it1, s1), (x0, i0, r0, it0, s0) = outs[1], outs[0]
     assert s1 == s0
     assert np.all(np.abs(it1.astype(int) - it0.astype(int)) <= 1)
-    np.testing.assert_allclose(r1, r0, rtol=1e-4, atol=1e-12)
+    # near convergence a column's L1 change is a few FP32 units of each rank, which the
+    # analytic change of the implicit rows (exact, not rounded to FP32) does not
+    # reproduce: there the two agree to a tenth of the tolerance 1e-6
+    np.testing.assert_allclose(r1, r0, rtol=1e-4, atol=1e-7)
     np.testing.assert_allclose(i1.dangling_mass, i0.dangling_mass, rtol=1e-6)
     if np.array_equal(it1, it0):
         np.testing.assert_allclose(x1, x0, rtol=2e-6, atol=1e-12)

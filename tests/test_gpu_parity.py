@@ -795,3 +795,71 @@ def test_out_csr_validation_and_weights():
         pr.pr_create_graph(n, ci.size, rp, 1, ci, weights=np.ones(ci.size, np.float32))
     assert e.value.status == pr.PR_ERR_UNSUPPORTED
     assert "pr_create_wgraph" in str(e.value)
+
+
+@pytest.mark.parametrize("build", ["rmat12", "er_isolated", "all_isolated", "rmat14_heavy64"])
+def test_implicit_zero_rows_in_the_synchronous_iteration(build):
+    """PR_OPT_IMPLICIT_ZERO_ROWS in the pipelined row kernel: after the first update the
+    ranks of rows without in-edges are (1-d) t_v + d D/n (Eq. 1 with nothing gathered), so
+    the tiles of isolated vertices are skipped, the other such rows store their quotient
+    only, and the ranks are written after the loop.  Against the full update (option 0)
+    and the oracle: the converged solve in matching mode, a personalised teleport, and
+    exactly 1, 2 and 5 updates from a given vector (pr_iterate), whose last L1 change
+    includes the analytic part."""
+    heavy = 64 if build == "rmat14_heavy64" else 256
+    if build == "rmat12":
+        rp, ci = gg.rmat(12, seed=31)
+    elif build == "rmat14_heavy64":
+        rp, ci = gg.rmat(14, seed=32)
+    elif build == "er_isolated":
+        # ER on the first 3000 vertices, 2001 isolated vertices after them
+        rp0, ci0 = gg.er_dangling(3000, 6.0, 0.2, seed=33)
+        rp = np.concatenate([rp0, np.full(2001, rp0[-1], rp0.dtype)])
+        ci = ci0
+    else:
+        rp, ci = np.zeros(1001, np.int64), np.zeros(0, np.int32)
+    n = rp.size - 1
+    iso = int(((np.diff(rp) == 0) & (np.bincount(ci, minlength=n) == 0)).sum())
+    t = (gg.uniform(5, 9, n) + 0.05).astype(np.float32)
+    t /= t.sum()
+    x_in = (gg.uniform(6, 9, n) + 0.1).astype(np.float32)
+    x_in /= x_in.sum()
+    pr.set_heavy_degree(heavy)
+    try:
+        g = pr.Graph(rp, ci)
+    finally:
+        pr.set_heavy_degree(pr.DEFAULT_HEAVY_DEGREE)
+    with g:
+        assert g.stats()["n_isolated"] == iso and g.stats()["n_tma_tiles"] > 0
+        res = {}
+        for imp in (1, 0):
+            g.set_option(pr.PR_OPT_IMPLICIT_ZERO_ROWS, imp)
+            r = [g.solve(tol=1e-6, max_iter=200), g.solve(tol=1e-6, max_iter=200, teleport=t)]
+            for k in (1, 2, 5):
+                r.append(g.iterate(x_in, n_iter=k, teleport=t))
+            res[imp] = r
+        g.set_option(pr.PR_OPT_IMPLICIT_ZERO_ROWS, 1)
+    for (x1, i1), (x0, i0) in zip(res[1], res[0]):
+        assert abs(i1.iterations - i0.iterations) <= 1
+        assert max_rel(x1, x0) <= 1e-5
+        # near convergence the L1 change is a few FP32 units of each rank, which the
+        # analytic change of the implicit rows (exact, not rounded to FP32) does not
+        # reproduce: there the two agree to a tenth of the tolerance 1e-6
+        assert i1.residual_l1 == pytest.approx(i0.residual_l1, rel=1e-4, abs=1e-7)
+        assert i1.dangling_mass == pytest.approx(i0.dangling_mass, rel=1e-6, abs=1e-12)
+    (x, info), (xt, infot) = res[1][0], res[1][1]
+    assert info.converged == 1 and infot.converged == 1
+    xo = matching(rp, ci, x, info)
+    assert l1(x, xo) <= 1e-6 and max_rel(x, xo) <= 1e-4
+    xo = matching(rp, ci, xt, infot, t=t.astype(np.float64))
+    assert l1(xt, xo) <= 1e-6 and max_rel(xt, xo) <= 1e-4
+    for (xk, ik), k in zip(res[1][2:], (1, 2, 5)):
+        xo, _, _ = oracle.pagerank_jacobi(rp, ci, d=D, tol=0, max_iter=k, t=t.astype(np.float64),
+                                          x0=x_in.astype(np.float64))
+        assert l1(xk, xo) <= 1e-6 and max_rel(xk, xo) <= 1e-4, k
+        xp, _, _ = oracle.pagerank_jacobi(rp, ci, d=D, tol=0, max_iter=k - 1, t=t.astype(np.float64),
+                                          x0=x_in.astype(np.float64)) if k > 1 else (x_in, 0, 0)
+        assert ik.residual_l1 == pytest.approx(l1(xo, xp), rel=1e-3, abs=1e-7), k
+    if build == "all_isolated":
+        np.testing.assert_allclose(x, 1.0 / n, rtol=1e-6)
+        assert info.iterations == 1
