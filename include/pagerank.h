@@ -286,6 +286,20 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
  *                         copies while the previous window is summed (64 rows
  *                         in flight per warp); 0 loads them into registers
  *                         (16 or 32 rows per warp).  Same sums, same order.
+ *   PR_OPT_SYNC_DC        synchronous solver (PR_JACOBI): BF16 storage of the
+ *                         quotient vector by defect correction.  0 (default)
+ *                         off; M in 1..32: after each FP32 step x' = F(x)
+ *                         (Eq. 1; its L1 change is the stopping test, so the
+ *                         result is an FP32 iterate) the error e = x* - x is
+ *                         approximated by M sweeps delta <- r + d (P^T delta +
+ *                         L/n) from delta = r = x' - x, each gathering
+ *                         delta/outdeg from a BF16 copy (FP32 sums); L, the
+ *                         mass the rounded quotients do not pass on (dangling
+ *                         rows and rounding), keeps every sweep mass-
+ *                         conserving; then x <- x + delta.  iterations counts
+ *                         the FP32 steps, edge_visits both kinds of sweep.
+ *                         A host-driven loop (no CUDA graph); not with
+ *                         PR_OPT_PERFORATION or PR_EDGE.
  *   PR_OPT_IMPLICIT_ZERO_ROWS the batched solver's FP32 form and the
  *                         synchronous solver's pipelined row kernel (PR_JACOBI,
  *                         pr_iterate; PR_OPT_TMA_TILES, not with
@@ -397,6 +411,7 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
 #define PR_OPT_FUSED_SEGMENTS 19
 #define PR_OPT_BATCH_ASYNC 20
 #define PR_OPT_IMPLICIT_ZERO_ROWS 21
+#define PR_OPT_SYNC_DC 22
 PR_API pr_status pr_set_option(pr_graph* g, int key, int64_t value);
 
 /* Batched personalised PageRank: k independent solves on one graph, one per

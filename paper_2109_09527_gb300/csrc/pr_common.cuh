@@ -148,6 +148,7 @@ struct SolveState {
     int32_t implicit;    // 1: ranks of rows without in-edges implicit after the first update
     double Dz;           // implicit rows: the dangling mass their current ranks use
     double t_iso;        // implicit rows: teleport sum over the isolated vertices
+    double Ldc;          // correction sweeps: mass the BF16 quotients of delta do not pass on
 };
 
 // Arguments of the per-iteration kernels (passed by value).
@@ -231,6 +232,10 @@ struct pr_graph {
     float* x[2] = {nullptr, nullptr};
     float* y[2] = {nullptr, nullptr};
     float* teleport = nullptr;   // binned teleport (allocated on first use)
+    int sync_dc = 0;             // BF16 correction sweeps per FP32 step of the synchronous solver (PR_OPT_SYNC_DC)
+    float* dc_r = nullptr;       // correction sweeps: residual F(x) - x of the FP32 step
+    float* dc_delta = nullptr;   // correction sweeps: the latest correction (FP32)
+    void* dc_q[2] = {nullptr, nullptr};   // correction sweeps: BF16 quotients delta / outdeg
     float* stage = nullptr;      // staging for host inputs/outputs (first use)
     int32_t* seg_row = nullptr;
     int32_t* seg_ptr = nullptr;
@@ -352,6 +357,11 @@ cudaError_t fill_fused_tiles(Tile* tiles, int32_t* e1, int64_t count, const int3
 cudaError_t launch_count_frozen(const pr_graph* g, cudaStream_t s);
 void launch_finalize(const pr_graph* g, const IterArgs& a, float* out, bool renormalise,
                      cudaStream_t s, int* launches, bool implicit = false);
+// Defect correction with BF16 quotients after the FP32 step x[src] -> x[1-src]
+// of the synchronous solver (PR_OPT_SYNC_DC, pr_dc.cu).
+pr_status ensure_sync_dc(pr_graph* g);
+cudaError_t enqueue_sync_dc(const pr_graph* g, const IterArgs& a, int src, int sweeps, cudaStream_t s,
+                            int* launches);
 
 // Exclusive scan of count int64 values into int32 offsets[count + 1] (device
 // arrays); synchronises the stream before its temporaries are freed.

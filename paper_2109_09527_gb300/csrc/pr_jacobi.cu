@@ -63,11 +63,13 @@ __device__ __forceinline__ void load_hot(const float* __restrict__ y, int32_t ho
     __syncthreads();
 }
 
-template <typename IdxT>
-__global__ void __launch_bounds__(kIterBlock, kGatherMinBlocks) k_heavy_segments(IterArgs a, const float* __restrict__ y) {
+// YT: FP32 quotients, or BF16 ones (the correction sweeps of PR_OPT_SYNC_DC,
+// no shared-memory hub copy).
+template <typename IdxT, typename YT = float>
+__global__ void __launch_bounds__(kIterBlock, kGatherMinBlocks) k_heavy_segments(IterArgs a, const YT* __restrict__ y) {
     extern __shared__ __align__(16) float hot_sm[];
     if (block_state(a.state).done) return;
-    load_hot(y, a.hot_n, hot_sm);
+    if constexpr (std::is_same<YT, float>::value) load_hot(y, a.hot_n, hot_sm);
     RowCtx c{};
     c.hot = a.hot;
     c.hot_n = a.hot_n;
@@ -899,6 +901,18 @@ cudaError_t enqueue_iteration_t(const pr_graph* g, const IterArgs& a, int src, b
     return cudaGetLastError();
 }
 
+// k_heavy_segments over BF16 quotients (the correction sweeps of PR_OPT_SYNC_DC).
+cudaError_t launch_segments_q16(const pr_graph* g, const IterArgs& a, const __nv_bfloat16* q, cudaStream_t s,
+                                int* launches) {
+    if (a.n_seg == 0) return cudaSuccess;
+    IterArgs b = a;
+    b.hot_n = 0;
+    if (g->idx64) k_heavy_segments<int64_t, __nv_bfloat16><<<seg_grid(g), kIterBlock, 0, s>>>(b, q);
+    else k_heavy_segments<int32_t, __nv_bfloat16><<<seg_grid(g), kIterBlock, 0, s>>>(b, q);
+    ++*launches;
+    return cudaGetLastError();
+}
+
 // k_heavy_segments over segments [0, a.n_seg) alone.
 cudaError_t launch_segments(const pr_graph* g, const IterArgs& a, int src, cudaStream_t s, int* launches) {
     if (a.n_seg == 0) return cudaSuccess;
@@ -1043,8 +1057,10 @@ pr_status alloc_solver(pr_graph* g) {
             (const void*)k_rows<int64_t, true, true, false>,  (const void*)k_rows<int64_t, false, true, false>,
             (const void*)k_rows<int32_t, true, false, true>,  (const void*)k_rows<int32_t, false, false, true>,
             (const void*)k_rows<int64_t, true, false, true>,  (const void*)k_rows<int64_t, false, false, true>};
-        const void* seg_kernels[] = {(const void*)k_heavy_segments<int32_t>,
-                                     (const void*)k_heavy_segments<int64_t>};
+        const void* seg_kernels[] = {(const void*)k_heavy_segments<int32_t, float>,
+                                     (const void*)k_heavy_segments<int64_t, float>,
+                                     (const void*)k_heavy_segments<int32_t, __nv_bfloat16>,
+                                     (const void*)k_heavy_segments<int64_t, __nv_bfloat16>};
         // These kernels need little shared memory: the preferred carveout 0
         // gives the rest of the SRAM to L1, which caches the hub ranks.
         // The staged kernels (entries 4..7) hold a 24.6 KB staging area per
@@ -1078,7 +1094,7 @@ pr_status alloc_solver(pr_graph* g) {
         PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_tma, k_rows_tma<false>, kTmaThreads, kTmaSmemBytes));
         g_occ_tma = std::max(1, occ_tma);
         int occ_seg = 0;
-        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_seg, k_heavy_segments<int32_t>, kIterBlock, 0));
+        PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_seg, k_heavy_segments<int32_t, float>, kIterBlock, 0));
         g_occ_seg = std::max(1, occ_seg);
         g_occ_rows = std::max(1, occ);   // last: marks the block as done
     }
@@ -1133,10 +1149,13 @@ pr_status run_jacobi(pr_graph* g, float damping, double tol, int32_t max_iter, c
         a.out_src = g->out_src;
         a.out_pos = g->out_pos;
     }
+    // BF16 correction sweeps after each FP32 step (PR_OPT_SYNC_DC; the solve only)
+    const bool dc = g->sync_dc > 0 && renormalise && !edge && !a.frozen;
+    if (dc && (rc = ensure_sync_dc(g)) != PR_OK) return rc;
     // implicit ranks of rows without in-edges: the pipelined kernel with the
     // heavy-row segments in a kernel of their own
     const bool tma = !edge && !g->idx64 && tma_applies(g, a);
-    const bool implicit = g->implicit_zero && tma && !(g->fuse_segments && g->n_tma_fused > 0);
+    const bool implicit = !dc && g->implicit_zero && tma && !(g->fuse_segments && g->n_tma_fused > 0);
     hs->implicit = implicit ? 1 : 0;
     hs->t_iso = (double)g->n_isolated * hs->inv_n;   // uniform teleport; else summed on the device
     PRK_CHECK(cudaEventRecord(g->ev_start, s));
@@ -1153,7 +1172,20 @@ pr_status run_jacobi(pr_graph* g, float damping, double tol, int32_t max_iter, c
     if (a.frozen) PRK_CHECK(cudaMemsetAsync(g->frozen, 0, (size_t)g->n, s));   // nothing frozen yet
     PRK_CHECK(cudaEventRecord(g->ev_loop0, s));
 
-    if (allow_graph && g->use_graph) {
+    if (dc) {
+        // host-driven outer steps: the FP32 step, then (unless it met the
+        // stopping test) the correction; the done flag read after each step
+        for (int32_t it = 0; it < max_iter; ++it) {
+            const int src = it & 1;
+            cudaError_t e = enqueue_iteration(g, a, src, uniform, s, &launches);
+            if (e == cudaSuccess) e = enqueue_sync_dc(g, a, src, g->sync_dc, s, &launches);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(&g->host_flag[0], &g->state->done, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return cuda_fail(e, "correction step");
+            if (*(volatile int32_t*)&g->host_flag[0]) break;
+        }
+    } else if (allow_graph && g->use_graph) {
         const int kind = uniform ? 0 : 1;
         if (!g->loop_exec[kind] && (rc = build_loop_graph(g, uniform)) != PR_OK) return rc;
         PRK_CHECK(cudaGraphLaunch(g->loop_exec[kind], s));
@@ -1221,7 +1253,9 @@ pr_status run_jacobi(pr_graph* g, float damping, double tol, int32_t max_iter, c
         info->residual_l1 = hs->resid;
         info->sum_x = renormalise ? hs->sum_x : 0.0;
         info->dangling_mass = hs->D;
-        info->edge_visits = (double)hs->iter * (double)g->nnz;
+        // correction sweeps ran after every FP32 step but the last
+        const double sweeps = dc ? (double)g->sync_dc * (double)std::max(0, hs->iter - 1) : 0.0;
+        info->edge_visits = ((double)hs->iter + sweeps) * (double)g->nnz;
         info->ms_device = ms;
         info->launches = launches;
         info->loop_edge_visits = info->edge_visits;

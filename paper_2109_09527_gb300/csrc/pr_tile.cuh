@@ -13,6 +13,10 @@
 //     relaxed accesses (one per row per sweep), so no cached copy can be stale.
 #pragma once
 
+#include <cuda_bf16.h>
+
+#include <type_traits>
+
 #include "pr_common.cuh"
 
 // L2 eviction priority of each access class, as an L2 cache policy made by
@@ -279,9 +283,9 @@ __device__ __forceinline__ int light_lanes_log2(const Tile& tile, int mode) {
 // col(p) is the source id of edge p.  Every synchronous light-tile path sums
 // through this routine with kU = 4, so they agree bit for bit on a row's sum;
 // the barrier-free kernel, compiled for fewer registers, takes kU = 2.
-template <bool kInPlace, int kU = 4, typename OffT, typename ColAt>
+template <bool kInPlace, int kU = 4, typename OffT, typename ColAt, typename YT>
 __device__ __forceinline__ void gather_row_pair(const ColAt& col, OffT b0, OffT e0, OffT b1, OffT e1, int g,
-                                                const float* y, const RowCtx& c, float& s0, float& s1);
+                                                const YT* y, const RowCtx& c, float& s0, float& s1);
 
 template <bool kInPlace>
 struct Mem;
@@ -290,6 +294,14 @@ template <>
 struct Mem<false> {
     static __device__ __forceinline__ float gather(const float* y, int32_t c, const RowCtx& x) {
         return c < x.hot_n ? x.hot_sm[c] : ld_gather(y, c, x.hot);
+    }
+    // BF16 quotients (the correction sweeps of the synchronous solver): the hub
+    // prefix through L1, the rest from L2, as ld_gather's default policy
+    static __device__ __forceinline__ float gather(const __nv_bfloat16* y, int32_t c, const RowCtx& x) {
+        const int32_t count = x.hot & 0x0fffffff;
+        const unsigned short* p = reinterpret_cast<const unsigned short*>(y) + c;
+        const unsigned short h = c < count ? __ldg(p) : __ldcg(p);
+        return __uint_as_float((uint32_t)h << 16);
     }
     static __device__ __forceinline__ float load_x(const float* p) { return ld_stream(p); }
     static __device__ __forceinline__ void store_x(float* p, float v) { st_stream(p, v); }
@@ -308,9 +320,9 @@ struct Mem<true> {
     static __device__ __forceinline__ void store_y(float* p, float v) { st_relaxed_p<PRK_L2_GATHER>(p, v); }
 };
 
-template <bool kInPlace, int kU, typename OffT, typename ColAt>
+template <bool kInPlace, int kU, typename OffT, typename ColAt, typename YT>
 __device__ __forceinline__ void gather_row_pair(const ColAt& col, OffT b0, OffT e0, OffT b1, OffT e1, int g,
-                                                const float* y, const RowCtx& c, float& s0, float& s1) {
+                                                const YT* y, const RowCtx& c, float& s0, float& s1) {
     static_assert(kU == 2 || kU == 4, "two or four edges per row per step");
     while (b0 < e0 || b1 < e1) {
         int32_t c0[kU], c1[kU];

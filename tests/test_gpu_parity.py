@@ -863,3 +863,54 @@ def test_implicit_zero_rows_in_the_synchronous_iteration(build):
     if build == "all_isolated":
         np.testing.assert_allclose(x, 1.0 / n, rtol=1e-6)
         assert info.iterations == 1
+
+
+@pytest.mark.parametrize("build,sweeps", [("rmat14", 4), ("rmat13_heavy64", 2), ("er", 4), ("er", 1),
+                                          ("rmat12_idx64", 3)])
+def test_sync_bf16_defect_correction_reaches_the_fixed_point(build, sweeps):
+    """PR_OPT_SYNC_DC: BF16 storage of the quotient vector in the synchronous solver by
+    defect correction.  Each FP32 step x' = F(x) (Eq. 1) is followed by `sweeps` sweeps
+    delta <- r + d (P^T delta + L/n) gathering BF16 quotients (heavy rows through the
+    segment kernel), then x <- x + delta.  The stopping test is the FP32 step's L1 change,
+    so the result is an FP32 iterate: against the FP64 fixed point it is within the L1 bound
+    r/(1-d) its residual gives, one oracle update of it changes it by less than 2e-6, and it
+    takes fewer FP32 steps than the plain solve, for the uniform and a personalised
+    teleport."""
+    heavy, idx64 = 256, 0
+    if build == "rmat14":
+        rp, ci = gg.rmat(14, seed=41)
+    elif build == "rmat13_heavy64":
+        rp, ci = gg.rmat(13, seed=42)
+        heavy = 64
+    elif build == "rmat12_idx64":
+        rp, ci = gg.rmat(12, seed=43)
+        idx64 = 1
+    else:
+        rp, ci = gg.er_dangling(30011, 8.0, 0.2, seed=44)
+    n = rp.size - 1
+    t = (gg.uniform(8, 3, n) + 0.05).astype(np.float32)
+    t /= t.sum()
+    pr.set_heavy_degree(heavy)
+    pr.pr_set_option(None, pr.PR_OPT_INDEX64, idx64)
+    try:
+        g = pr.Graph(rp, ci)
+    finally:
+        pr.set_heavy_degree(pr.DEFAULT_HEAVY_DEGREE)
+        pr.pr_set_option(None, pr.PR_OPT_INDEX64, 0)
+    with g:
+        plain = [g.solve(tol=1e-6, max_iter=200), g.solve(tol=1e-6, max_iter=200, teleport=t)]
+        g.set_option(pr.PR_OPT_SYNC_DC, sweeps)
+        dcs = [g.solve(tol=1e-6, max_iter=200), g.solve(tol=1e-6, max_iter=200, teleport=t)]
+        g.set_option(pr.PR_OPT_SYNC_DC, 0)
+        again, _ = g.solve(tol=1e-6, max_iter=200)
+    assert np.array_equal(again, plain[0][0])            # off again: the plain solve
+    for (x, info), (xp, infop), tt in zip(dcs, plain, (None, t)):
+        t64 = None if tt is None else tt.astype(np.float64)
+        assert info.converged == 1 and info.residual_l1 < 1e-6
+        assert info.iterations < infop.iterations
+        assert info.edge_visits == (info.iterations + sweeps * (info.iterations - 1)) * ci.size
+        assert x.astype(np.float64).sum() == pytest.approx(1.0, abs=1e-6)
+        xstar, _, _ = oracle.fixed_point(rp, ci, d=D, t=t64)
+        assert l1(x, xstar) <= info.residual_l1 / (1 - D) + 2e-7
+        _, _, r_or, _ = oracle.jacobi_step(rp, ci, x.astype(np.float64), d=D, t=t64)
+        assert r_or < 2e-6
