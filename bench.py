@@ -17,6 +17,11 @@ L1 change below 1e-6 (damping 0.85, budget 200 iterations).  Four solves per ste
             made) over its CUDA-event duration; roofline_all has every graph/variant
   cpu_baseline  the FP64 oracle (single thread, as it stands) on a bounded sample:
             a few synchronous iterations of the same R-MAT-24 graph
+  barrier_free_race_free, bf16_defect_correction  the barrier-free solve with every
+            gather a relaxed load, and the synchronous solve with BF16 quotient
+            storage by defect correction, each beside the default on both graphs
+  forms, massive  the batched, graph-set and weighted forms, and the R-MAT-26 int64
+            barrier-free solve, each with FP64 oracle certificates
 
 ``--impl reference`` times the oracle alone (the reference arm for this build).
 Multi-GPU (torchrun): every rank solves its own replica (weak scaling, no collective
@@ -47,6 +52,7 @@ SEED_RMAT = 24
 SEED_ER = 1024
 FORM_STEPS = 3                # timed solves of each form under `forms` and `massive`
 NB_L1_HUBS_DEFAULT = 49152    # the library's default PR_OPT_NB_L1_HUBS
+SYNC_DC_SWEEPS = 4            # BF16 correction sweeps per FP32 step in the measured PR_OPT_SYNC_DC solve
 
 
 def log(*a):
@@ -1440,6 +1446,33 @@ def main():
         row["weak_hub_gain"] = row["race_free"]["time_to_tol_ms"] / row["default_weak_l1_hubs"]["time_to_tol_ms"]
         race_free[name] = row
 
+    # BF16 storage of the quotient vector by defect correction (PR_OPT_SYNC_DC) beside
+    # the plain FP32 Jacobi solve of the same graph, with its own oracle certificate
+    sync_dc = {}
+    plain_ms = {cl["graph"]: cl["time_to_tol_ms"] for cl in case_lines if cl["variant"] == "jacobi"}
+    for name, g, st in resident:
+        g.set_option(pr.PR_OPT_SYNC_DC, SYNC_DC_SWEEPS)
+        for _ in range(2):
+            pr.pr_solve(g.handle, DAMPING, TOL, MAX_ITER, pr.PR_JACOBI, None, None, outs[name])
+        torch.cuda.synchronize()
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record(stream)
+        infos = [pr.pr_solve(g.handle, DAMPING, TOL, MAX_ITER, pr.PR_JACOBI, None, None, outs[name])[1]
+                 for _ in range(3)]
+        r1.record(stream)
+        torch.cuda.synchronize()
+        g.set_option(pr.PR_OPT_SYNC_DC, 0)
+        ms_dc = r0.elapsed_time(r1) / 3
+        sweeps = infos[-1].edge_visits / st["nnz"]
+        sync_dc[name] = {"sweeps_per_fp32_step": SYNC_DC_SWEEPS, "time_to_tol_ms": ms_dc,
+                         "fp32_steps": infos[-1].iterations, "sweeps": sweeps,
+                         "ms_per_sweep": ms_dc / sweeps, "residual_l1": infos[-1].residual_l1,
+                         "converged": all(bool(i.converged) for i in infos),
+                         "fp32_jacobi_time_to_tol_ms": plain_ms.get(name),
+                         "speedup_vs_fp32": plain_ms[name] / ms_dc if name in plain_ms else None}
+        rp_h, ci_h = host_graphs[name]
+        jobs.append((f"sync_dc {name}", certificate_job(rp_h, ci_h, outs[name].cpu().numpy())))
+
     graph_info = [{"name": n, "n": st["n"], "nnz": st["nnz"]} for n, _, st in resident]
     for _, g, _ in resident:
         g.close()
@@ -1462,6 +1495,8 @@ def main():
     certs = run_certificates(jobs) if rank == 0 else {}
     for cl in case_lines:
         cl["oracle_certificate"] = certs.get(f"{cl['graph']} {cl['variant']}")
+    for name, row in sync_dc.items():
+        row["oracle_certificate"] = certs.get(f"sync_dc {name}")
     if forms and rank == 0:
         for key in forms:
             sub = {k[len(key) + 2:]: v for k, v in certs.items() if k.startswith(key + ": ")}
@@ -1487,7 +1522,8 @@ def main():
                 "roofline": roofline, "roofline_all": roofline_all, "cpu_baseline": cpu,
                 "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks, "cases": case_lines,
-                "barrier_free_race_free": race_free, "forms": forms, "massive": massive}
+                "barrier_free_race_free": race_free, "bf16_defect_correction": sync_dc,
+                "forms": forms, "massive": massive}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

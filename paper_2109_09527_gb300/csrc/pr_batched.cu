@@ -59,6 +59,12 @@ constexpr int kBUpdateBlocksPerSM = 4;
 #define PRK_BATCH_UPDATE_ROWS 4
 #endif
 constexpr int kBUpdateRows = PRK_BATCH_UPDATE_ROWS;
+// Quads of four rows a warp of k_b_update has in flight (each lane one float4
+// of S or the segment partials, and of X, per quad).
+#ifndef PRK_BATCH_UPDATE_QUADS
+#define PRK_BATCH_UPDATE_QUADS 4
+#endif
+constexpr int kBUpdateQuads = PRK_BATCH_UPDATE_QUADS;
 
 // Device state of a batched solve.
 struct BatchState {
@@ -455,85 +461,142 @@ __global__ void __launch_bounds__(kBlock) k_b_update(BatchArgs a, const float* _
         if (a.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0);
         return;
     }
-    const bool active = (s_active >> lane) & 1u;
-    const float dshare = s_dshare[lane], base = s_base[lane], d = s_d, omd = s_omd;
+    // Rows in quads of four consecutive rows: lane l holds columns c0 .. c0+3
+    // (c0 = 4 (l % 8)) of row l / 8 of the quad, so every load of S, P, X and
+    // every store of X', Y' is one float4 per lane and a warp instruction moves
+    // 512 contiguous bytes; kQuads quads (4 kQuads rows) per warp in flight.
+    const int c0 = (lane & 7) * 4;
+    const int sub = lane >> 3;
+    float dsh[4], bas[4];
+    bool act[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        dsh[k] = s_dshare[c0 + k];
+        bas[k] = s_base[c0 + k];
+        act[k] = (s_active >> (c0 + k)) & 1u;
+    }
+    const float d = s_d, omd = s_omd;
     const int32_t* tptr = s_tptr;
-    Acc acc;
-    // four rows per warp per pass: their loads are independent, so a warp has
-    // four 128-byte rows of S, X (and the segment partials of heavy rows) in flight
-    constexpr int kRows = kBUpdateRows;
+    // this lane's four teleport values of row v (the CSR of the nonzeros)
+    auto teleports = [&](int64_t v, float (&tv)[4]) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) tv[k] = 0.f;
+        const int32_t p1 = tptr[v + 1];
+        for (int32_t p = tptr[v]; p < p1; ++p) {
+            const int j = s_tcol[p] - c0;
+            const float val = s_tval[p];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (j == k) tv[k] = val;
+        }
+    };
+    Acc acc[4];
+    constexpr int kQuads = kBUpdateQuads;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t step = (((int64_t)gridDim.x * blockDim.x) >> 5) * kRows;
+    const int64_t step = (((int64_t)gridDim.x * blockDim.x) >> 5) * kQuads * 4;
     const bool implicit = s_implicit != 0;
     const int64_t hi = implicit ? a.zero_start : a.n;   // rows updated in full
-    for (int64_t v0 = warp * kRows; v0 < hi; v0 += step) {
-        float sv[kRows], xo[kRows], inv[kRows];
+    for (int64_t q0 = warp * kQuads * 4; q0 < hi; q0 += step) {
+        float4 sv[kQuads], xo[kQuads];
+        float inv[kQuads];
 #pragma unroll
-        for (int q = 0; q < kRows; ++q) {
-            const int64_t v = v0 + q;
-            sv[q] = 0.f;
-            xo[q] = 0.f;
+        for (int q = 0; q < kQuads; ++q) {
+            const int64_t v = q0 + 4 * q + sub;
+            sv[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            xo[q] = make_float4(0.f, 0.f, 0.f, 0.f);
             inv[q] = 0.f;
             if (v < hi) {
                 if (v < a.n_heavy) {
-                    const int32_t q1 = a.seg_ptr[v + 1];
-                    for (int32_t j = a.seg_ptr[v]; j < q1; ++j) sv[q] += __ldcg(a.P + (size_t)j * kBK + lane);
+                    const int32_t j1 = a.seg_ptr[v + 1];
+                    for (int32_t j = a.seg_ptr[v]; j < j1; ++j) {
+                        const float4 p = __ldcg(reinterpret_cast<const float4*>(a.P + (size_t)j * kBK + c0));
+                        sv[q].x += p.x;
+                        sv[q].y += p.y;
+                        sv[q].z += p.z;
+                        sv[q].w += p.w;
+                    }
                 } else if (v < a.zero_start) {
-                    sv[q] = __ldcs(a.S + (size_t)v * kBK + lane);
+                    sv[q] = __ldcs(reinterpret_cast<const float4*>(a.S + (size_t)v * kBK + c0));
                 }
-                xo[q] = __ldcs(Xin + (size_t)v * kBK + lane);
+                xo[q] = __ldcs(reinterpret_cast<const float4*>(Xin + (size_t)v * kBK + c0));
                 inv[q] = __ldg(a.inv_out + v);
             }
         }
 #pragma unroll
-        for (int q = 0; q < kRows; ++q) {
-            const int64_t v = v0 + q;
-            if (v >= hi) break;
-            float xn = xo[q];
-            if (active) {
-                if (tptr) {
-                    float tv = 0.f;
-                    const int32_t p1 = tptr[v + 1];
-                    for (int32_t p = tptr[v]; p < p1; ++p)
-                        if (s_tcol[p] == lane) tv = s_tval[p];
-                    xn = fmaf(d, sv[q], fmaf(omd, tv, dshare));
-                } else {
-                    xn = fmaf(d, sv[q], base);
-                }
+        for (int q = 0; q < kQuads; ++q) {
+            const int64_t v = q0 + 4 * q + sub;
+            if (v >= hi) continue;
+            const float s4[4] = {sv[q].x, sv[q].y, sv[q].z, sv[q].w};
+            const float x4[4] = {xo[q].x, xo[q].y, xo[q].z, xo[q].w};
+            float tv[4] = {0.f, 0.f, 0.f, 0.f};
+            if (tptr) teleports(v, tv);
+            float xn[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                xn[k] = x4[k];
+                if (act[k]) xn[k] = tptr ? fmaf(d, s4[k], fmaf(omd, tv[k], dsh[k])) : fmaf(d, s4[k], bas[k]);
             }
-            __stcs(Xout + (size_t)v * kBK + lane, xn);
-            __stcs(Yout + (size_t)v * kBK + lane, xn * inv[q]);
-            if (s_bf16) Yout16[(size_t)v * kBK + lane] = __float2bfloat16_rn(xn * inv[q]);
-            acc.add_r(fabsf(xn - xo[q]));
-            if (inv[q] == 0.f) acc.kahan(xn);
+            const float iv = inv[q];
+            __stcs(reinterpret_cast<float4*>(Xout + (size_t)v * kBK + c0), make_float4(xn[0], xn[1], xn[2], xn[3]));
+            __stcs(reinterpret_cast<float4*>(Yout + (size_t)v * kBK + c0),
+                   make_float4(xn[0] * iv, xn[1] * iv, xn[2] * iv, xn[3] * iv));
+            if (s_bf16) {
+                __nv_bfloat162* y16 = reinterpret_cast<__nv_bfloat162*>(Yout16 + (size_t)v * kBK + c0);
+                y16[0] = __floats2bfloat162_rn(xn[0] * iv, xn[1] * iv);
+                y16[1] = __floats2bfloat162_rn(xn[2] * iv, xn[3] * iv);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                acc[k].add_r(fabsf(xn[k] - x4[k]));
+                if (iv == 0.f) acc[k].kahan(xn[k]);
+            }
         }
     }
     if (implicit) {
         // rows without in-edges that have out-edges: the quotient only (the
         // same value as the full update's, which adds d * 0)
-        const int64_t wstep = (((int64_t)gridDim.x * blockDim.x) >> 5) * kRows;
-        for (int64_t v0 = a.zero_start + warp * kRows; v0 < a.iso_start; v0 += wstep) {
-            float inv[kRows];
+        for (int64_t q0 = a.zero_start + warp * kQuads * 4; q0 < a.iso_start; q0 += step) {
+            float inv[kQuads];
 #pragma unroll
-            for (int q = 0; q < kRows; ++q) inv[q] = v0 + q < a.iso_start ? __ldg(a.inv_out + v0 + q) : 0.f;
+            for (int q = 0; q < kQuads; ++q) {
+                const int64_t v = q0 + 4 * q + sub;
+                inv[q] = v < a.iso_start ? __ldg(a.inv_out + v) : 0.f;
+            }
 #pragma unroll
-            for (int q = 0; q < kRows; ++q) {
-                const int64_t v = v0 + q;
-                if (v >= a.iso_start) break;
-                float xn = base;
-                if (tptr) {
-                    float tv = 0.f;
-                    const int32_t p1 = tptr[v + 1];
-                    for (int32_t p = tptr[v]; p < p1; ++p)
-                        if (s_tcol[p] == lane) tv = s_tval[p];
-                    xn = fmaf(omd, tv, dshare);
-                }
-                __stcs(Yout + (size_t)v * kBK + lane, xn * inv[q]);
+            for (int q = 0; q < kQuads; ++q) {
+                const int64_t v = q0 + 4 * q + sub;
+                if (v >= a.iso_start) continue;
+                float xn[4];
+                float tv[4] = {0.f, 0.f, 0.f, 0.f};
+                if (tptr) teleports(v, tv);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) xn[k] = tptr ? fmaf(omd, tv[k], dsh[k]) : bas[k];
+                const float iv = inv[q];
+                __stcs(reinterpret_cast<float4*>(Yout + (size_t)v * kBK + c0),
+                       make_float4(xn[0] * iv, xn[1] * iv, xn[2] * iv, xn[3] * iv));
             }
         }
     }
+    // the warp's per-column totals in lane order: the lanes with the same c0
+    // hold the same columns; lane j then takes column j = c0 + k of lane j / 4
+    double rj = 0.0, mj = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        double rk = acc[k].resid(), mk = acc[k].mass();
+#pragma unroll
+        for (int o = 8; o < 32; o <<= 1) {
+            rk += __shfl_xor_sync(0xffffffffu, rk, o);
+            mk += __shfl_xor_sync(0xffffffffu, mk, o);
+        }
+        rk = __shfl_sync(0xffffffffu, rk, lane >> 2);
+        mk = __shfl_sync(0xffffffffu, mk, lane >> 2);
+        if ((lane & 3) == k) {
+            rj = rk;
+            mj = mk;
+        }
+    }
     double R, Dn;
-    if (batch_columns_to_grid(acc.resid(), acc.mass(), a.slots, &st->ticket, &R, &Dn) && threadIdx.x < 32) {
+    if (batch_columns_to_grid(rj, mj, a.slots, &st->ticket, &R, &Dn) && threadIdx.x < 32) {
         const bool was_active = (s_active >> lane) & 1u;
         const double prev = st->resid[lane];
         if (implicit) {
