@@ -305,9 +305,13 @@ __global__ void __launch_bounds__(kBlock) k_b_segments_async(BatchArgs a, const 
             cp_async_wait<1>();
             __syncwarp();
             const int cnt = (int)min((int64_t)kAW, e1 - wb);
-#pragma unroll 8
-            for (int e = 0; e < kAW; ++e)
-                if (e < cnt) acc += ld_sm(cur + e * kBK + lane);
+            if (cnt == kAW) {
+                // a full window: straight-line loads and adds, edge order
+#pragma unroll
+                for (int e = 0; e < kAW; ++e) acc += ld_sm(cur + e * kBK + lane);
+            } else {
+                for (int e = 0; e < cnt; ++e) acc += ld_sm(cur + e * kBK + lane);
+            }
             __syncwarp();   // the buffer is refilled two windows on
         }
         cp_async_wait<0>();
@@ -349,14 +353,22 @@ __global__ void __launch_bounds__(kBlock) k_b_light_async(BatchArgs a, const T* 
             const int cnt = (int)min((int64_t)kAW, eend - wb);
             cp_async_wait<1>();
             __syncwarp();
-#pragma unroll 8
-            for (int e = 0; e < kAW; ++e) {
-                if (e < cnt) acc += ld_sm(cur + e * kBK + lane);
-                if ((ends >> e) & 1u) {
+            if (ends == 0u && cnt == kAW) {
+                // no row ends in a full window: straight-line loads and adds
+#pragma unroll
+                for (int e = 0; e < kAW; ++e) acc += ld_sm(cur + e * kBK + lane);
+            } else {
+                // the edges up to each row end (bit k: a row ends at edge k), then
+                // the rest; the same order of adds as edge by edge
+                int e = 0;
+                for (unsigned m = ends; m != 0u; m &= m - 1u) {
+                    const int k = __ffs((int)m) - 1;
+                    for (; e <= k; ++e) acc += ld_sm(cur + e * kBK + lane);
                     a.S[row * kBK + lane] = acc;
                     acc = 0.f;
                     ++row;
                 }
+                for (; e < cnt; ++e) acc += ld_sm(cur + e * kBK + lane);
             }
             __syncwarp();
         }
