@@ -1247,7 +1247,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--scale", type=int, default=24)
     ap.add_argument("--er-log2", type=int, default=24)
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched, graph-set, adjoint and massive-graph cases that the "
@@ -1384,14 +1384,23 @@ def main():
                 for name, (rp, ci) in graphs}
     d2h = sum(2 * 4 * (rp.size - 1) for _, (rp, ci) in graphs)
 
+    phases = []
+
     def e2e_step():
         v = 0.0
+        ph = []
         for name, prp, pci in pinned:
+            t_a = time.perf_counter()
             with pr.Graph(prp, pci) as g:
+                t_b = time.perf_counter()
                 for vid, _ in variants:
                     _, info = pr.pr_solve(g.handle, DAMPING, TOL, MAX_ITER, vid, None, None,
                                           host_out[name])
                     v += info.edge_visits
+                t_c = time.perf_counter()
+            ph.append(f"{name}: create {1e3 * (t_b - t_a):.1f} solves {1e3 * (t_c - t_b):.1f} "
+                      f"destroy {1e3 * (time.perf_counter() - t_c):.1f} ms")
+        phases.append("; ".join(ph))
         return v
 
     e2e_step()
@@ -1403,6 +1412,8 @@ def main():
     for _ in range(args.e2e_steps):
         ev += e2e_step()
     torch.cuda.synchronize()
+    for i, p in enumerate(phases):
+        log(f"[bench] e2e step {i} (0: untimed): {p}")
     e2e_s, ev = combine_ranks(dist, dev, time.perf_counter() - t0, ev)
     e2e = {"value": ev / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
