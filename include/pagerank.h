@@ -229,6 +229,11 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
  *                         no L1 allocation; 4 (default, with 49152 hubs) the
  *                         hubs are plain cached loads and all others are read
  *                         from L2 only, so they cannot evict the hubs.
+ *   PR_OPT_TMA_HOT_VERTICES the hub count of the pipelined row kernel
+ *                         (PR_OPT_TMA_TILES), at most PR_OPT_HOT_VERTICES' own:
+ *                         its two stages take 132 KB of each SM's SRAM, so its
+ *                         L1 holds fewer hub ranks than the other kernels'
+ *                         (default 6144; 0 = PR_OPT_HOT_VERTICES' count).
  *   PR_OPT_HOT_CACHE      vertices at the front of the library's degree
  *                         order whose quotient values each block of the
  *                         synchronous kernels copies into shared memory and
@@ -412,6 +417,7 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
 #define PR_OPT_BATCH_ASYNC 20
 #define PR_OPT_IMPLICIT_ZERO_ROWS 21
 #define PR_OPT_SYNC_DC 22
+#define PR_OPT_TMA_HOT_VERTICES 23
 PR_API pr_status pr_set_option(pr_graph* g, int key, int64_t value);
 
 /* Batched personalised PageRank: k independent solves on one graph, one per

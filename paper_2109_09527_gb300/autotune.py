@@ -22,11 +22,13 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import (DEFAULT_HEAVY_DEGREE, PR_OPT_CTAS_PER_SM, PR_OPT_HOT_VERTICES, Graph, pr_iterate,
-               set_heavy_degree)
+from . import (DEFAULT_HEAVY_DEGREE, PR_OPT_CTAS_PER_SM, PR_OPT_HOT_VERTICES,
+               PR_OPT_TMA_HOT_VERTICES, Graph, pr_iterate, set_heavy_degree)
 
 HEAVY_CANDIDATES = (128, 256, 512, 1024, 2048, 4096)
 HOT_CANDIDATES = (16384, 49152, 131072)
+TMA_HOT_CANDIDATES = (2048, 6144, 16384)   # the pipelined row kernel's own hub count
+DEFAULT_TMA_HOT = 6144
 CTAS_CANDIDATES = (0, 2, 3)
 POLICY_L1_HUBS = 4   # see PR_OPT_HOT_VERTICES: hubs through L1, the rest L2-only
 
@@ -38,11 +40,13 @@ def _time(g: Graph, x, out, iterations: int, damping: float) -> float:
 
 
 def tune(rowptr, colidx, iterations: int = 6, damping: float = 0.85,
-         heavy=HEAVY_CANDIDATES, hot=HOT_CANDIDATES, ctas=CTAS_CANDIDATES) -> dict:
+         heavy=HEAVY_CANDIDATES, hot=HOT_CANDIDATES, ctas=CTAS_CANDIDATES,
+         tma_hot=TMA_HOT_CANDIDATES) -> dict:
     """Time candidate options on this graph (rowptr/colidx as for Graph: host arrays or CUDA
     tensors).  The search is coordinate-wise: the heavy threshold first (with default launch
-    options), then the hub count, then blocks per SM, each with the best of the previous.
-    Returns {"heavy_degree", "hot_vertices", "ctas_per_sm", "ms_per_iteration", "trials"}."""
+    options), then the hub count, then the pipelined row kernel's own hub count, then blocks
+    per SM, each with the best of the previous.  Returns {"heavy_degree", "hot_vertices",
+    "tma_hot_vertices", "ctas_per_sm", "ms_per_iteration", "trials"}."""
     n = (rowptr.shape[0] if hasattr(rowptr, "shape") else len(rowptr)) - 1
     try:
         import torch
@@ -56,7 +60,8 @@ def tune(rowptr, colidx, iterations: int = 6, damping: float = 0.85,
         x = np.full(n, 1.0 / n, dtype=np.float32)
         out = np.empty(n, dtype=np.float32)
     trials = []
-    best = {"heavy_degree": DEFAULT_HEAVY_DEGREE, "hot_vertices": 49152, "ctas_per_sm": 0, "ms_per_iteration": float("inf")}
+    best = {"heavy_degree": DEFAULT_HEAVY_DEGREE, "hot_vertices": 49152, "tma_hot_vertices": DEFAULT_TMA_HOT,
+            "ctas_per_sm": 0, "ms_per_iteration": float("inf")}
     graphs = {}
     try:
         for h in heavy:
@@ -77,6 +82,14 @@ def tune(rowptr, colidx, iterations: int = 6, damping: float = 0.85,
             if ms < best["ms_per_iteration"]:
                 best.update(hot_vertices=hv, ms_per_iteration=ms)
         g.set_option(PR_OPT_HOT_VERTICES, (POLICY_L1_HUBS << 28) | best["hot_vertices"])
+        for th in tma_hot:
+            g.set_option(PR_OPT_TMA_HOT_VERTICES, th)
+            ms = _time(g, x, out, iterations, damping)
+            trials.append({"heavy_degree": best["heavy_degree"], "hot_vertices": best["hot_vertices"],
+                           "tma_hot_vertices": th, "ctas_per_sm": 0, "ms": ms})
+            if ms < best["ms_per_iteration"]:
+                best.update(tma_hot_vertices=th, ms_per_iteration=ms)
+        g.set_option(PR_OPT_TMA_HOT_VERTICES, best["tma_hot_vertices"])
         for c in ctas:
             g.set_option(PR_OPT_CTAS_PER_SM, c)
             ms = _time(g, x, out, iterations, damping)
@@ -124,6 +137,7 @@ def tune_batched(rowptr, colidx, teleport, k: int, damping: float = 0.85, tol: f
 def apply(g: Graph, result: dict) -> Graph:
     """Set a tuning result's launch options on a graph built with its heavy threshold."""
     g.set_option(PR_OPT_HOT_VERTICES, (POLICY_L1_HUBS << 28) | int(result["hot_vertices"]))
+    g.set_option(PR_OPT_TMA_HOT_VERTICES, int(result.get("tma_hot_vertices", DEFAULT_TMA_HOT)))
     g.set_option(PR_OPT_CTAS_PER_SM, int(result["ctas_per_sm"]))
     return g
 

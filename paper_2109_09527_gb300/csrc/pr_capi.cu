@@ -241,6 +241,12 @@ static pr_status set_option_impl(pr_graph* g, int key, int64_t value) {
             if ((value >> 28) > 4) return fail(PR_ERR_INVALID_ARG, "PR_OPT_HOT_VERTICES: policy (bits 28..31) must be 0..4");
             g->hot_vertices = value;
             return PR_OK;
+        case PR_OPT_TMA_HOT_VERTICES:
+            if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_TMA_HOT_VERTICES needs a graph");
+            if (value < 0 || value > 0x0fffffffLL)
+                return fail(PR_ERR_INVALID_ARG, "PR_OPT_TMA_HOT_VERTICES must be in [0, 2^28)");
+            g->tma_hot = value;
+            return PR_OK;
         case PR_OPT_HOT_CACHE:
             if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_HOT_CACHE needs a graph");
             if (value < 0 || value > kHotCacheMax)

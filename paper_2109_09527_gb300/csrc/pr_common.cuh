@@ -112,6 +112,7 @@ constexpr int kNbHubsMax = 8192;         // largest hub snapshot of the barrier-
 #endif
 constexpr int kDefaultNbHubs = PRK_DEFAULT_NB_HUBS;
 constexpr int64_t kDefaultNbL1Hubs = 49152;   // barrier-free hub gathers through L1  // light-tile mode per variant (PR_OPT_STAGED_TILES)
+constexpr int64_t kDefaultTmaHot = 6144;   // the pipelined row kernel's hub count (its L1 is small)
 constexpr int64_t kDefaultHot = (4LL << 28) | 49152;  // gather L1 policy 4, 48K hot ids (see ld_gather)   // degree bins: 40 power-of-two classes + zero + spare
 
 // A tile of the row kernel: rows [row_begin, row_end) of one bin.  kind >= 0
@@ -187,6 +188,7 @@ struct IterArgs {
     int32_t fused;               // 1: heavy-row segments are tiles of the pipelined kernel
     int32_t n_heavy;             // rows [0, n_heavy) are gathered in segments
     int32_t n_tiles_live;        // pipelined kernel: tiles before those of the isolated vertices
+    int32_t hot_tma;             // pipelined kernel: L1 policy and hub count of its gathers (as hot)
     int64_t zero_start;          // rows [zero_start, n) have no in-edges
     int64_t iso_start;           // rows [iso_start, n) have no in- and no out-edges
 };
@@ -205,6 +207,7 @@ struct pr_graph {
     int ctas_per_sm = 0;         // 0 = from occupancy
     bool use_graph = true;
     int64_t hot_vertices = prk::kDefaultHot;  // see ld_gather
+    int64_t tma_hot = prk::kDefaultTmaHot;    // hub count of the pipelined row kernel (PR_OPT_TMA_HOT_VERTICES)
     int64_t hot_cache = 0;                    // size of the shared-memory copy of y's prefix (off)
     int64_t nb_hubs = prk::kDefaultNbHubs;    // hub snapshot of the barrier-free kernel (PR_OPT_NB_HUBS)
     int64_t nb_l1_hubs = prk::kDefaultNbL1Hubs;  // weak L1-cached hub gathers (PR_OPT_NB_L1_HUBS)

@@ -526,7 +526,7 @@ __global__ void __launch_bounds__(kTmaThreads, kTmaMinBlocks) k_rows_tma(IterArg
     c.one_m_d = (float)(1.0 - d);
     c.d_share = (float)(d * share);
     c.base = (float)((1.0 - d) * sv.inv_n + d * share);
-    c.hot = a.hot;
+    c.hot = a.hot_tma;
     c.hot_n = 0;
     c.hot_sm = nullptr;
     c.lane_mode = a.lane_mode;
@@ -840,6 +840,11 @@ IterArgs make_args(const pr_graph* g, bool uniform) {
     a.nnz = g->nnz;
     a.lane_mode = g->lane_mode;
     a.n_tiles_live = (int32_t)g->n_tma_live;
+    {
+        const int32_t count = a.hot & 0x0fffffff;
+        const int32_t cap = g->tma_hot > 0 ? (int32_t)std::min<int64_t>(g->tma_hot, count) : count;
+        a.hot_tma = (int32_t)(((uint32_t)a.hot & 0xf0000000u) | (uint32_t)cap);
+    }
     a.zero_start = g->n - g->n_zero_indeg;
     a.iso_start = g->n - g->n_isolated;
     return a;
