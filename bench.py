@@ -1393,13 +1393,14 @@ def main():
             t_a = time.perf_counter()
             with pr.Graph(prp, pci) as g:
                 t_b = time.perf_counter()
+                dev_setup = g.stats()["setup_ms"]
                 for vid, _ in variants:
                     _, info = pr.pr_solve(g.handle, DAMPING, TOL, MAX_ITER, vid, None, None,
                                           host_out[name])
                     v += info.edge_visits
                 t_c = time.perf_counter()
-            ph.append(f"{name}: create {1e3 * (t_b - t_a):.1f} solves {1e3 * (t_c - t_b):.1f} "
-                      f"destroy {1e3 * (time.perf_counter() - t_c):.1f} ms")
+            ph.append(f"{name}: create {1e3 * (t_b - t_a):.1f} (device {dev_setup:.1f}) solves "
+                      f"{1e3 * (t_c - t_b):.1f} destroy {1e3 * (time.perf_counter() - t_c):.1f} ms")
         phases.append("; ".join(ph))
         return v
 

@@ -231,9 +231,10 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
  *                         from L2 only, so they cannot evict the hubs.
  *   PR_OPT_TMA_HOT_VERTICES the hub count of the pipelined row kernel
  *                         (PR_OPT_TMA_TILES), at most PR_OPT_HOT_VERTICES' own:
- *                         its two stages take 132 KB of each SM's SRAM, so its
- *                         L1 holds fewer hub ranks than the other kernels'
- *                         (default 6144; 0 = PR_OPT_HOT_VERTICES' count).
+ *                         the shared-memory stages of its three blocks per SM
+ *                         take 132 KB of the SM's SRAM, so its L1 holds fewer
+ *                         hub ranks than the other kernels' (default 16384;
+ *                         0 = PR_OPT_HOT_VERTICES' count).
  *   PR_OPT_HOT_CACHE      vertices at the front of the library's degree
  *                         order whose quotient values each block of the
  *                         synchronous kernels copies into shared memory and

@@ -27,8 +27,8 @@ from . import (DEFAULT_HEAVY_DEGREE, PR_OPT_CTAS_PER_SM, PR_OPT_HOT_VERTICES,
 
 HEAVY_CANDIDATES = (128, 256, 512, 1024, 2048, 4096)
 HOT_CANDIDATES = (16384, 49152, 131072)
-TMA_HOT_CANDIDATES = (2048, 6144, 16384)   # the pipelined row kernel's own hub count
-DEFAULT_TMA_HOT = 6144
+TMA_HOT_CANDIDATES = (4096, 16384, 32768)   # the pipelined row kernel's own hub count
+DEFAULT_TMA_HOT = 16384
 CTAS_CANDIDATES = (0, 2, 3)
 POLICY_L1_HUBS = 4   # see PR_OPT_HOT_VERTICES: hubs through L1, the rest L2-only
 

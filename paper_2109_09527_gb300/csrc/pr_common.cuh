@@ -85,13 +85,13 @@ constexpr int kDefaultBatchAsync = PRK_DEFAULT_BATCH_ASYNC;
 #define PRK_TMA_STAGES 2
 #endif
 #ifndef PRK_TMA_EDGES
-#define PRK_TMA_EDGES 2048
+#define PRK_TMA_EDGES 3072
 #endif
 #ifndef PRK_TMA_ROWS
 #define PRK_TMA_ROWS 512
 #endif
 #ifndef PRK_TMA_MIN_BLOCKS
-#define PRK_TMA_MIN_BLOCKS 4
+#define PRK_TMA_MIN_BLOCKS 3
 #endif
 constexpr int kTmaStages = PRK_TMA_STAGES;
 constexpr int kTmaEdges = PRK_TMA_EDGES;
@@ -112,7 +112,7 @@ constexpr int kNbHubsMax = 8192;         // largest hub snapshot of the barrier-
 #endif
 constexpr int kDefaultNbHubs = PRK_DEFAULT_NB_HUBS;
 constexpr int64_t kDefaultNbL1Hubs = 49152;   // barrier-free hub gathers through L1  // light-tile mode per variant (PR_OPT_STAGED_TILES)
-constexpr int64_t kDefaultTmaHot = 6144;   // the pipelined row kernel's hub count (its L1 is small)
+constexpr int64_t kDefaultTmaHot = 16384;  // the pipelined row kernel's hub count (its L1 is smaller)
 constexpr int64_t kDefaultHot = (4LL << 28) | 49152;  // gather L1 policy 4, 48K hot ids (see ld_gather)   // degree bins: 40 power-of-two classes + zero + spare
 
 // A tile of the row kernel: rows [row_begin, row_end) of one bin.  kind >= 0

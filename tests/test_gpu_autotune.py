@@ -24,13 +24,13 @@ def test_tune_picks_a_timed_candidate_and_the_tuned_graph_is_correct():
     from paper_2109_09527_gb300 import autotune
     rp, ci = gg.rmat(15, 16, seed=15)
     res = autotune.tune(rp, ci, iterations=4, heavy=(256, 1024), hot=(16384, 49152), ctas=(0, 2),
-                        tma_hot=(2048, 6144))
+                        tma_hot=(4096, 16384))
     trials = res["trials"]
     assert len(trials) == 2 + 2 + 2 + 2
     assert all(t["ms"] > 0 for t in trials)
     assert res["ms_per_iteration"] == min(t["ms"] for t in trials)
     assert res["heavy_degree"] in (256, 1024) and res["hot_vertices"] in (16384, 49152)
-    assert res["tma_hot_vertices"] in (2048, 6144)
+    assert res["tma_hot_vertices"] in (4096, 16384)
     xstar, _, _ = oracle.fixed_point(rp, ci, d=0.85)
     with autotune.build_tuned(rp, ci, res) as g:
         x, info = g.solve(tol=1e-6)
