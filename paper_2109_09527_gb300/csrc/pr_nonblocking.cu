@@ -499,6 +499,24 @@ __global__ void __launch_bounds__(kBlock) k_mass_split(IterArgs a, const float* 
     }
 }
 
+// Ranks of the isolated vertices (binned rows [iso_start, n)), which the
+// barrier-free kernel does not sweep: such a vertex gathers nothing and passes
+// nothing on, and with the complement form of the dangling share its rank
+// enters no other row's update, so its converged rank is (1-d) t_v + d (sum(t)
+// - S)/n with S (scalars[0]) the final mass of the vertices with out-edges.
+// Written before the verifying synchronous update, which recomputes them.
+__global__ void __launch_bounds__(kBlock) k_nb_iso_fill(IterArgs a, float* __restrict__ x,
+                                                        const double* __restrict__ scalars) {
+    const SolveState* st = a.state;
+    const double d = st->d;
+    const double share = (st->t_sum - scalars[0]) * st->inv_n;
+    const float base = (float)((1.0 - d) * st->inv_n + d * share);
+    const float one_m_d = (float)(1.0 - d), d_share = (float)(d * share);
+    const int64_t stride = (int64_t)gridDim.x * kBlock;
+    for (int64_t i = a.iso_start + (int64_t)blockIdx.x * kBlock + threadIdx.x; i < a.n; i += stride)
+        x[i] = a.teleport ? fmaf(one_m_d, a.teleport[i], d_share) : base;
+}
+
 template <typename IdxT>
 __global__ void k_item_edges(const void* rowptr, const Tile* items, int64_t count, int64_t* edges) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -580,9 +598,12 @@ pr_status build_items(pr_graph* g, cudaStream_t s) {
         }
     }
     g->nb_n_seg = nb_heavy_rows > 0 ? seg_ptr[(size_t)nb_heavy_rows] : 0;
+    // the isolated vertices' tiles (the last ones) are not swept: k_nb_iso_fill
+    const int64_t iso_start = g->n - g->n_isolated;
     std::vector<Tile> items;
     for (const Tile& t : tiles)
-        if (kNbHeavyTiles || t.kind != kTileHeavy) items.push_back(t);
+        if ((kNbHeavyTiles || t.kind != kTileHeavy) && !(t.kind == kTileZero && t.row_begin >= iso_start))
+            items.push_back(t);
     const int64_t count = (int64_t)items.size();
 
     Tile* d_items = nullptr;
@@ -777,6 +798,12 @@ pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_
         // verify with one synchronous update x[0] -> x[1]
         k_mass_split<<<small_grid(g), kBlock, 0, s>>>(a, g->x[0], g->nb_scalars + 4);
         ++launches;
+        if (g->n_isolated > 0) {
+            // the isolated vertices' ranks from the final mass S, then D again
+            k_nb_iso_fill<<<small_grid(g), kBlock, 0, s>>>(a, g->x[0], g->nb_scalars + 4);
+            k_mass_split<<<small_grid(g), kBlock, 0, s>>>(a, g->x[0], g->nb_scalars + 4);
+            launches += 2;
+        }
         PRK_CHECK(cudaGetLastError());
         PRK_CHECK(enqueue_iteration(g, a, 0, uniform, s, &launches));
         PRK_CHECK(cudaMemcpyAsync(h_counts, g->nb_scalars + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -914,3 +914,37 @@ def test_sync_bf16_defect_correction_reaches_the_fixed_point(build, sweeps):
         assert l1(x, xstar) <= info.residual_l1 / (1 - D) + 2e-7
         _, _, r_or, _ = oracle.jacobi_step(rp, ci, x.astype(np.float64), d=D, t=t64)
         assert r_or < 2e-6
+
+
+@pytest.mark.parametrize("build", ["er_isolated", "rmat13", "all_isolated"])
+def test_nonblocking_leaves_isolated_vertices_to_the_end(build):
+    """The barrier-free kernel does not sweep isolated vertices (no in- and no out-edges):
+    with the complement form of the dangling share their ranks enter no other row's update,
+    so they are written once from the final mass of the other vertices, before the
+    verifying synchronous update.  The solve still reaches the FP64 fixed point within the
+    bound its certified residual gives, for the uniform and a personalised teleport (seeds
+    on isolated vertices included)."""
+    if build == "er_isolated":
+        rp0, ci0 = gg.er_dangling(3000, 6.0, 0.2, seed=51)
+        rp = np.concatenate([rp0, np.full(2001, rp0[-1], rp0.dtype)])
+        ci = ci0
+    elif build == "rmat13":
+        rp, ci = gg.rmat(13, seed=52)
+    else:
+        rp, ci = np.zeros(1001, np.int64), np.zeros(0, np.int32)
+    n = rp.size - 1
+    iso = np.flatnonzero((np.diff(rp) == 0) & (np.bincount(ci, minlength=n) == 0))
+    assert iso.size > 0
+    t = (gg.uniform(9, 4, n) + 0.05).astype(np.float32)
+    t[iso[: max(1, iso.size // 10)]] += 1.0          # heavier teleport on some isolated vertices
+    t /= t.sum()
+    with pr.Graph(rp, ci) as g:
+        assert g.stats()["n_isolated"] == iso.size
+        for tt in (None, t):
+            x, info = g.solve(tol=1e-6, max_iter=200, variant="nonblocking", teleport=tt)
+            assert info.converged == 1 and info.residual_l1 < 1e-6
+            t64 = None if tt is None else tt.astype(np.float64)
+            xstar, _, _ = oracle.fixed_point(rp, ci, d=D, t=t64)
+            assert l1(x, xstar) <= info.residual_l1 / (1 - D) + 2e-7
+            _, _, r_or, _ = oracle.jacobi_step(rp, ci, x.astype(np.float64), d=D, t=t64)
+            assert r_or < 2e-6
