@@ -65,10 +65,6 @@ constexpr int kBUpdateRows = PRK_BATCH_UPDATE_ROWS;
 #define PRK_BATCH_UPDATE_QUADS 4
 #endif
 constexpr int kBUpdateQuads = PRK_BATCH_UPDATE_QUADS;
-#ifndef PRK_BATCH_UPDATE_MINB
-#define PRK_BATCH_UPDATE_MINB 1
-#endif
-constexpr int kBUpdateMinBlocks = PRK_BATCH_UPDATE_MINB;
 
 // Device state of a batched solve.
 struct BatchState {
@@ -441,7 +437,7 @@ __device__ __forceinline__ bool batch_columns_to_grid(double a, double b, double
 // vertices' ranks, (1-d) Tiso + n_iso d D / n, as part of the next dangling
 // mass, are added in FP64 by the last block.  k_b_zero_fill writes the ranks
 // after the loop.  The quotients are those the full update would store.
-__global__ void __launch_bounds__(kBlock, kBUpdateMinBlocks) k_b_update(BatchArgs a, const float* __restrict__ Xin,
+__global__ void __launch_bounds__(kBlock) k_b_update(BatchArgs a, const float* __restrict__ Xin,
                                                      float* __restrict__ Xout, float* __restrict__ Yout,
                                                      __nv_bfloat16* __restrict__ Yout16) {
     __shared__ int32_t s_implicit;
