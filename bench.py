@@ -167,8 +167,8 @@ class ClockSampler:
 # Sources each timed kernel family is compiled from: a recorded ncu traffic figure is
 # used only while the code in these files (comments aside) is unchanged.
 KERNEL_SOURCES = {
-    "jacobi": ["pr_common.cuh", "pr_tile.cuh", "pr_jacobi.cu"],
-    "nonblocking": ["pr_common.cuh", "pr_tile.cuh", "pr_nonblocking.cu"],
+    "jacobi": ["pr_common.cuh", "pr_tile.cuh", "pr_tma.cuh", "pr_jacobi.cu"],
+    "nonblocking": ["pr_common.cuh", "pr_tile.cuh", "pr_tma.cuh", "pr_nonblocking.cu"],
 }
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_rmat24_er24.txt")
 

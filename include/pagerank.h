@@ -229,6 +229,17 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
  *                         no L1 allocation; 4 (default, with 49152 hubs) the
  *                         hubs are plain cached loads and all others are read
  *                         from L2 only, so they cannot evict the hubs.
+ *   PR_OPT_NB_PIPELINE    barrier-free solver (PR_NONBLOCKING): 1 feeds its
+ *                         light-row tiles through shared memory
+ *                         like the pipelined synchronous kernel (a producer
+ *                         warp bulk-copies each tile's row offsets, column
+ *                         indices, 1/outdeg and teleport ahead of the
+ *                         gathering warps; x and y are read in place as
+ *                         before); 0 (default; measured faster): every
+ *                         gathering warp loads them itself.
+ *                         Needs 32-bit offsets and PR_OPT_TMA_TILES; not used
+ *                         with PR_OPT_PERFORATION, PR_OPT_NB_HUBS, the staged
+ *                         tiles or the diagnostics form.
  *   PR_OPT_TMA_HOT_VERTICES the hub count of the pipelined row kernel
  *                         (PR_OPT_TMA_TILES), at most PR_OPT_HOT_VERTICES' own:
  *                         the shared-memory stages of its three blocks per SM
@@ -419,6 +430,7 @@ PR_API pr_status pr_graph_get_stats(const pr_graph* g, pr_graph_stats* stats);
 #define PR_OPT_IMPLICIT_ZERO_ROWS 21
 #define PR_OPT_SYNC_DC 22
 #define PR_OPT_TMA_HOT_VERTICES 23
+#define PR_OPT_NB_PIPELINE 24
 PR_API pr_status pr_set_option(pr_graph* g, int key, int64_t value);
 
 /* Batched personalised PageRank: k independent solves on one graph, one per

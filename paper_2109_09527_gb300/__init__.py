@@ -62,6 +62,7 @@ PR_OPT_BATCH_ASYNC = 20
 PR_OPT_IMPLICIT_ZERO_ROWS = 21
 PR_OPT_SYNC_DC = 22
 PR_OPT_TMA_HOT_VERTICES = 23
+PR_OPT_NB_PIPELINE = 24
 
 LIB_PATH = _build.LIB_PATH
 

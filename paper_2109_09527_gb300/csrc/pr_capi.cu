@@ -146,7 +146,7 @@ extern "C" pr_status pr_destroy_graph(pr_graph* g) {
                    g->y[0], g->y[1], g->teleport, g->stage, g->seg_row, g->seg_ptr, g->seg_sum,
                    g->tiles, g->tma_tiles, g->tma_fused, g->tma_fused_e1, g->row_cnt, g->hr_part,
                    g->out_src, g->out_pos, g->contrib, g->state, g->slots,
-                   g->nb_items, g->nb_slots,
+                   g->nb_items, g->nb_slots, g->nbp_items, g->nbp_e1,
                    g->nb_scalars, g->nb_block_sweeps, g->frozen,
                    g->dc_r, g->dc_delta, g->dc_q[0], g->dc_q[1]};
     cudaError_t first = cudaSuccess;
@@ -321,6 +321,11 @@ static pr_status set_option_impl(pr_graph* g, int key, int64_t value) {
             if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_BATCH_ASYNC needs a graph");
             if (value != 0 && value != 1) return fail(PR_ERR_INVALID_ARG, "PR_OPT_BATCH_ASYNC is 0 or 1");
             g->batch_async = (int)value;
+            return PR_OK;
+        case PR_OPT_NB_PIPELINE:
+            if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_NB_PIPELINE needs a graph");
+            if (value != 0 && value != 1) return fail(PR_ERR_INVALID_ARG, "PR_OPT_NB_PIPELINE is 0 or 1");
+            g->nb_pipeline = (int)value;
             return PR_OK;
         case PR_OPT_SYNC_DC:
             if (!g) return fail(PR_ERR_INVALID_ARG, "PR_OPT_SYNC_DC needs a graph");

@@ -274,6 +274,11 @@ struct pr_graph {
     std::vector<int64_t> nb_cta_edges;  // edges owned by each block (items dealt round-robin)
     std::vector<int64_t> nb_item_edges; // edges of each work item
     std::vector<int64_t> nb_seg_edges;  // edges of each heavy-row segment
+    int32_t* nbp_items = nullptr;       // Tile[]: light and empty-row tiles of the pipelined kernel (pad = first edge)
+    int32_t* nbp_e1 = nullptr;          // one past the last edge of each of those tiles
+    int64_t nbp_items_count = 0;
+    std::vector<int64_t> nbp_item_edges;
+    int nb_pipeline = 0;                // PR_OPT_NB_PIPELINE (measured slower: off)
     std::vector<int64_t> bin_start;     // first binned row of each degree bin (+ n)
     std::vector<prk::Tile> host_tiles;  // copy of tiles
 

@@ -42,6 +42,7 @@
 #include <vector>
 
 #include "pr_tile.cuh"
+#include "pr_tma.cuh"
 
 namespace prk {
 
@@ -106,6 +107,7 @@ struct NbArgs {
     int32_t lane_mode;           // lanes per light row (PR_OPT_LIGHT_LANES)
     uint8_t* frozen;             // loop perforation (Alg. 5): 1 = row frozen (perforated form only)
     float perf_eps;              // freeze bound: a nonzero change below it freezes the row
+    const int32_t* item_e1;      // pipelined form: one past the last edge of each item (pad: its first)
 };
 
 // ---- loop perforation (Alg. 5) in the barrier-free kernel ------------------
@@ -474,6 +476,268 @@ __global__ void __launch_bounds__(kNbBlock, kNbMinBlocks) k_nonblocking(NbArgs a
     }
 }
 
+// ---- the pipelined barrier-free kernel (PR_OPT_NB_PIPELINE) ---------------
+//
+// The same sweeps as k_nonblocking (in-place y, x in two parity copies, the
+// heavy-row segments by warps, the complement dangling share, the per-block
+// stopping test), with the light-row tiles fed the way k_rows_tma feeds its
+// own: a producer warp copies each tile's row offsets, column indices,
+// 1/outdeg and teleport into a shared-memory stage with bulk asynchronous
+// copies, kTmaStages tiles ahead of the 8 gathering warps.  Those arrays never
+// change, so copying them ahead is safe across the in-place updates; x is
+// read by the owning block itself and y is gathered in place, as before.  The
+// tiles are the pipelined kernel's (at most kTmaEdges edges and kTmaRows
+// rows); the pipeline drains at the end of every sweep, where the block
+// reduces its L1 change.  Every wait is bounded: one that runs out sets error
+// bit 2 and the block leaves.
+#ifndef PRK_NBP_MIN_BLOCKS
+#define PRK_NBP_MIN_BLOCKS 3
+#endif
+constexpr int kNbpMinBlocks = PRK_NBP_MIN_BLOCKS;
+constexpr int kNbpThreads = kBlock + 32;                                   // 8 gathering warps + 1 producer
+constexpr int kNbpStageWords = kTmaColWords + 3 * kTmaRowWords;            // colidx, rowptr, 1/outdeg, teleport
+constexpr size_t kNbpSmem = 2 * kTmaStages * sizeof(uint64_t) + (size_t)kTmaStages * kNbpStageWords * 4;
+#ifndef PRK_NBP_UNROLL
+#define PRK_NBP_UNROLL 4
+#endif
+
+struct NbpStage {
+    int32_t* col;
+    int32_t* rp;
+    float* inv;
+    float* tel;
+    __device__ __forceinline__ NbpStage(uint32_t* base, int s) {
+        uint32_t* p = base + (size_t)s * kNbpStageWords;
+        col = (int32_t*)p;
+        rp = (int32_t*)(p + kTmaColWords);
+        inv = (float*)(p + kTmaColWords + kTmaRowWords);
+        tel = (float*)(p + kTmaColWords + 2 * kTmaRowWords);
+    }
+};
+
+// Producer side: the copies of light tile `tile` (edges [e0, e1)) into stage st.
+template <bool kUniform>
+__device__ __forceinline__ void nbp_issue(const NbArgs& a, const Tile& tile, int64_t e0, int64_t e1,
+                                          const NbpStage& st, uint64_t* full) {
+    const int64_t r0 = tile.row_begin & ~3, r1 = (tile.row_end + 3) & ~3, p1 = (tile.row_end + 1 + 3) & ~3;
+    const int64_t c0 = e0 & ~(int64_t)3;
+    const uint32_t vec_bytes = (uint32_t)(r1 - r0) * 4u;
+    const uint32_t rp_bytes = (uint32_t)(p1 - r0) * 4u;
+    const uint32_t col_bytes = (uint32_t)((((e1 + 3) & ~(int64_t)3) - c0) * 4);
+    if (vec_bytes > kTmaRowWords * 4u || rp_bytes > kTmaRowWords * 4u || col_bytes > kTmaColWords * 4u) {
+        // larger than a stage (the tiling rules this out): copy nothing, flag the solve
+        atomicOr(&a.state->error, 4u);
+        mbar_arrive_expect_tx(full, 0);
+        return;
+    }
+    mbar_arrive_expect_tx(full, (kUniform ? 1u : 2u) * vec_bytes + rp_bytes + col_bytes);
+    if (col_bytes) bulk_copy_g2s(st.col, a.colidx + c0, col_bytes, full);
+    bulk_copy_g2s(st.rp, (const int32_t*)a.rowptr + r0, rp_bytes, full);
+    bulk_copy_g2s(st.inv, a.inv_out + r0, vec_bytes, full);
+    if (!kUniform) bulk_copy_g2s(st.tel, a.teleport + r0, vec_bytes, full);
+}
+
+// Consumer side: one light tile from its stage, in place (as process_light_tile
+// with kInPlace: lane groups by the tile's row count, two rows per group; the
+// rows' ranks are loaded before their gathers).
+template <bool kUniform>
+__device__ __forceinline__ void nbp_light_tile(const Tile& tile, const NbpStage& st, const NbArgs& a,
+                                               const float* xr, float* xw, const RowCtx& c, Acc& acc, int tid) {
+    const int lg = light_lanes_log2(tile, c.lane_mode);
+    const int g = 1 << lg;
+    const int rpp = kBlock >> lg;
+    const int grp = tid >> lg;
+    const int gl = tid & (g - 1);
+    const int o = tile.row_begin & 3;                 // row i of the tile is element o + i
+    const int32_t* rp = st.rp + o;
+    const int32_t base = rp[0] & ~3;                  // st.col[e - base] = colidx[e]
+    const int nrows = tile.row_end - tile.row_begin;
+    const int32_t* col = st.col;
+    for (int i0 = 0; i0 < nrows; i0 += 2 * rpp) {
+        int ii[2];
+        bool act[2];
+        int32_t b[2], e[2];
+        float xo[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            ii[q] = i0 + q * rpp + grp;
+            act[q] = ii[q] < nrows;
+            b[q] = act[q] ? rp[ii[q]] - base : 0;
+            e[q] = act[q] ? rp[ii[q] + 1] - base : 0;
+            xo[q] = (act[q] && gl == 0) ? Mem<true>::load_x(xr + tile.row_begin + ii[q]) : 0.f;
+        }
+        float s[2] = {0.f, 0.f};
+        gather_row_pair<true, PRK_NBP_UNROLL>([col](int32_t p) { return col[p]; }, b[0] + gl, e[0], b[1] + gl, e[1],
+                                              g, a.y, c, s[0], s[1]);
+#pragma unroll
+        for (int m = 1; m < 32; m <<= 1)
+            if (m < g) {
+                s[0] += __shfl_xor_sync(0xffffffffu, s[0], m);
+                s[1] += __shfl_xor_sync(0xffffffffu, s[1], m);
+            }
+        if (gl == 0) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+                if (act[q]) {
+                    const int i = o + ii[q];
+                    row_update<kUniform, true>(tile.row_begin + ii[q], s[q], xo[q], st.inv[i],
+                                               kUniform ? 0.f : st.tel[i], c, xw, a.y, acc);
+                }
+        }
+    }
+}
+
+template <bool kUniform>
+__global__ void __launch_bounds__(kNbpThreads, kNbpMinBlocks) k_nonblocking_pipe(NbArgs a) {
+    extern __shared__ __align__(128) uint64_t nbp_smem[];
+    uint64_t* full = nbp_smem;
+    uint64_t* empty = nbp_smem + kTmaStages;
+    uint32_t* stages = (uint32_t*)(nbp_smem + 2 * kTmaStages);
+    __shared__ int s_fail;
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < kTmaStages; ++st) {
+            mbar_init(full + st, 1);
+            mbar_init(empty + st, kWarps);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    __syncthreads();
+    const StateView sv = block_state(a.state);
+    const double d = sv.d, inv_n = sv.inv_n, T = sv.t_sum;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool producer = warp == kWarps;
+    const int tid = threadIdx.x;   // < kBlock for the gathering warps
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t wstep = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int32_t sweeps = 0;
+    uint32_t kq = 0;   // light tiles staged (producer) or taken (gathering warps) so far
+    Acc acc;
+    while (sweeps < a.max_sweeps) {
+        const float* xr = (sweeps & 1) ? a.x_alt : a.x;
+        float* xw = (sweeps & 1) ? a.x : a.x_alt;
+        RowCtx c;
+        c.d = (float)d;
+        c.one_m_d = (float)(1.0 - d);
+        c.hot = a.l1_hubs;
+        if (a.l1_hubs > 0 && threadIdx.x == 0) asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        c.hot_n = 0;
+        c.hot_sm = nullptr;
+        c.lane_mode = a.lane_mode;
+        float r_sweep = 0.f;
+        auto warp_publish = [&](bool publish_mass) {
+            double dS = warp_sum(acc.mass());
+            double m = 0.0;
+            if (lane == 0) {
+                if (publish_mass && dS != 0.0) atomicAdd(a.scalars, dS);
+                m = ld_relaxed(a.scalars);
+            }
+            m = __shfl_sync(0xffffffffu, m, 0);
+            r_sweep += (float)acc.resid();
+            acc = Acc();
+            const double share = (T - m) * inv_n;
+            c.d_share = (float)(d * share);
+            c.base = (float)((1.0 - d) * inv_n + d * share);
+        };
+        warp_publish(false);
+        // heavy-row segments: every warp of the grid, the producers' too
+        const int64_t rounds = (a.n_seg + wstep - 1) / wstep;
+        for (int64_t rd = 0; rd < rounds; ++rd) {
+            const int64_t sid = wid + rd * wstep;
+            if (sid < a.n_seg) warp_segment<int32_t, kUniform, false>(sid, a, xr, xw, c, acc);
+            if ((rd % kSegPublish) == kSegPublish - 1) warp_publish(true);
+        }
+        warp_publish(true);
+        if (producer) {
+            if (lane == 0) {
+                for (int32_t t = blockIdx.x; t < a.n_items; t += gridDim.x) {
+                    const Tile item = a.items[t];
+                    if (item.kind < 0) continue;
+                    const int st = (int)(kq % kTmaStages);
+                    const uint32_t use = kq / kTmaStages;
+                    if (use > 0 && !mbar_wait(empty + st, (use - 1) & 1u)) {
+                        atomicExch(&s_fail, 1);
+                        break;
+                    }
+                    nbp_issue<kUniform>(a, item, item.pad, a.item_e1[t], NbpStage(stages, st), full + st);
+                    ++kq;
+                }
+            }
+            kq = __shfl_sync(0xffffffffu, kq, 0);
+        } else {
+            int since = 0;
+            for (int32_t t = blockIdx.x; t < a.n_items; t += gridDim.x) {
+                const Tile item = a.items[t];
+                if (item.kind >= 0) {
+                    const int st = (int)(kq % kTmaStages);
+                    if (*(volatile int*)&s_fail || !mbar_wait(full + st, (kq / kTmaStages) & 1u)) {
+                        atomicExch(&s_fail, 1);
+                        break;
+                    }
+                    nbp_light_tile<kUniform>(item, NbpStage(stages, st), a, xr, xw, c, acc, tid);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(empty + st);
+                    ++kq;
+                } else if (item.kind == kTileHeavy) {
+                    for (int64_t r = item.row_begin + tid; r < item.row_end; r += kBlock) {
+                        const int32_t j1 = a.seg_ptr[r + 1];
+                        float p = 0.f;
+                        for (int32_t j = a.seg_ptr[r]; j < j1; ++j) p += ld_relaxed(a.seg_sum + j);
+                        const float tv = kUniform ? 0.f : ld_stream(a.teleport + r);
+                        row_update<kUniform, true>(r, p, Mem<true>::load_x(xr + r), ld_stream(a.inv_out + r), tv, c,
+                                                   xw, a.y, acc);
+                    }
+                } else {
+                    process_zero_tile<kUniform, true>(item, a.inv_out, a.teleport, xr, xw, a.y, c, acc, tid);
+                }
+                if (++since == kPublishEvery) {
+                    warp_publish(true);
+                    since = 0;
+                }
+            }
+        }
+        warp_publish(true);
+        ++sweeps;
+        double R = (double)r_sweep, unused1 = 0.0;
+        block_sum2(R, unused1);
+        if (s_fail) {
+            if (threadIdx.x == 0) atomicOr(&a.state->error, 2u);
+            break;
+        }
+        if (threadIdx.x == 0) st_relaxed(a.slots + blockIdx.x, R);
+        double est = 0.0, unused = 0.0;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) est += ld_relaxed(a.slots + i);
+        block_sum2(est, unused);
+        if (est < a.tol_int) break;
+    }
+    // every copy issued has landed before the block can exit (they all have,
+    // unless a wait ran out): the last use of each stage, bounded
+    if (producer && lane == 0)
+        for (uint32_t st = 0; st < (uint32_t)kTmaStages && st < kq; ++st) {
+            const uint32_t last = (kq - 1 - st) / kTmaStages;   // last use of stage (kq - 1 - st) % kTmaStages
+            const uint32_t stage = (kq - 1 - st) % kTmaStages;
+            mbar_wait(full + stage, last & 1u);
+        }
+    // after an odd number of sweeps the block's latest ranks are in x_alt
+    if (sweeps & 1) {
+        if (!producer)
+            for (int32_t t = blockIdx.x; t < a.n_items; t += gridDim.x) {
+                const Tile item = a.items[t];
+                for (int64_t r = item.row_begin + tid; r < item.row_end; r += kBlock)
+                    st_relaxed(a.x + r, ld_relaxed(a.x_alt + r));
+            }
+        if (lane == 0)
+            for (int64_t sid = wid; sid < a.n_seg; sid += wstep) {
+                const int32_t h = a.seg_row[sid];
+                if (sid + 1 == a.seg_ptr[h + 1]) st_relaxed(a.x + h, ld_relaxed(a.x_alt + h));
+            }
+    }
+    if (threadIdx.x == 0) {
+        a.block_sweeps[blockIdx.x] = sweeps;
+        atomicMax(a.sweeps_max, sweeps);
+    }
+}
+
 // Mass of x split by dangling status: writes S (non-dangling) to scalars[0],
 // and D (dangling) to the solve state, and resets the iteration counters for
 // the synchronous update that follows.
@@ -517,6 +781,16 @@ __global__ void __launch_bounds__(kBlock) k_nb_iso_fill(IterArgs a, float* __res
         x[i] = a.teleport ? fmaf(one_m_d, a.teleport[i], d_share) : base;
 }
 
+// First edge (into pad) and one past the last edge of each item of the
+// pipelined kernel's list (32-bit offsets).
+__global__ void k_nbp_item_range(const int32_t* __restrict__ rowptr, Tile* items, int64_t count, int32_t* e1) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        items[i].pad = rowptr[items[i].row_begin];
+        e1[i] = rowptr[items[i].row_end];
+    }
+}
+
 template <typename IdxT>
 __global__ void k_item_edges(const void* rowptr, const Tile* items, int64_t count, int64_t* edges) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -550,7 +824,7 @@ void* pick_kernel(const pr_graph* g, bool uniform, bool staged, bool trace, bool
 // memory (cached per kernel and size).  The carveout is left to the CUDA driver:
 // asking for a small shared-memory carveout measured slower (the offsets and
 // tile metadata the kernel reads live in L1).
-pr_status nb_occupancy(const void* kernel, size_t smem, int* occ) {
+pr_status nb_occupancy(const void* kernel, size_t smem, int* occ, int threads = kNbBlock) {
     struct Entry {
         const void* kernel;
         size_t smem;
@@ -566,8 +840,15 @@ pr_status nb_occupancy(const void* kernel, size_t smem, int* occ) {
         }
     PRK_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)((kNbHubsMax + kStageFloats) * sizeof(float))));
+    if (threads != kNbBlock) {
+        // the pipelined kernel: shared memory for kNbpMinBlocks blocks' stages
+        // (plus the 1 KB the CUDA driver reserves per block), the rest to L1
+        const int carve = (int)std::min<int64_t>(
+            100, (int64_t)(kNbpMinBlocks * (smem + 1024) * 100 + 228 * 1024 - 1) / (228 * 1024));
+        PRK_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, carve));
+    }
     int o = 0;
-    PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernel, kNbBlock, smem));
+    PRK_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernel, threads, smem));
     if (o < 1) return fail(PR_ERR_UNSUPPORTED, "barrier-free kernel: no block fits on an SM");
     cache.push_back({kernel, smem, o});
     *occ = o;
@@ -632,6 +913,33 @@ pr_status build_items(pr_graph* g, cudaStream_t s) {
             const int64_t e0 = heavy_rp[h] + (int64_t)(sg - seg_ptr[h]) * kSegEdges;
             g->nb_seg_edges[sg] = std::min<int64_t>(kSegEdges, heavy_rp[h + 1] - e0);
         }
+    // the pipelined kernel's list: the same rows in tiles that fit its
+    // shared-memory stages (32-bit offsets only)
+    if (!g->idx64 && kTmaEdges + 1 >= std::max(g->heavy_degree, kNbSegDegree)) {
+        int64_t rows_p = 0;
+        const std::vector<Tile> tp =
+            tiles_with_threshold(g, std::max(g->heavy_degree, kNbSegDegree), &rows_p, kTmaEdges, kTmaRows);
+        std::vector<Tile> pitems;
+        for (const Tile& t : tp)
+            if (t.kind != kTileHeavy && !(t.kind == kTileZero && t.row_begin >= iso_start)) pitems.push_back(t);
+        const int64_t pc = (int64_t)pitems.size();
+        PRK_CHECK(dev_alloc(g, (void**)&g->nbp_items, (size_t)(pc + 1) * sizeof(Tile)));
+        PRK_CHECK(dev_alloc(g, (void**)&g->nbp_e1, (size_t)(pc + 1) * sizeof(int32_t)));
+        if (pc > 0) {
+            PRK_CHECK(cudaMemcpyAsync(g->nbp_items, pitems.data(), (size_t)pc * sizeof(Tile), cudaMemcpyHostToDevice, s));
+            const int pg = (int)std::max<int64_t>(1, std::min<int64_t>((pc + kBlock - 1) / kBlock, 4096));
+            k_nbp_item_range<<<pg, kBlock, 0, s>>>((const int32_t*)g->rowptr, (Tile*)g->nbp_items, pc, g->nbp_e1);
+            PRK_CHECK(cudaGetLastError());
+            std::vector<Tile> back((size_t)pc);
+            std::vector<int32_t> e1((size_t)pc);
+            PRK_CHECK(cudaMemcpyAsync(back.data(), g->nbp_items, (size_t)pc * sizeof(Tile), cudaMemcpyDeviceToHost, s));
+            PRK_CHECK(cudaMemcpyAsync(e1.data(), g->nbp_e1, (size_t)pc * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            PRK_CHECK(cudaStreamSynchronize(s));
+            g->nbp_item_edges.assign((size_t)pc, 0);
+            for (int64_t i = 0; i < pc; ++i) g->nbp_item_edges[(size_t)i] = (int64_t)e1[(size_t)i] - back[(size_t)i].pad;
+        }
+        g->nbp_items_count = pc;
+    }
     // slots and counters for the largest grid any kernel variant can have
     const int64_t max_grid = (int64_t)g->sm_count * 8;
     PRK_CHECK(dev_alloc(g, (void**)&g->nb_slots, (size_t)max_grid * sizeof(double)));
@@ -644,16 +952,15 @@ pr_status build_items(pr_graph* g, cudaStream_t s) {
 // Grid of the persistent kernel for `per_sm` co-resident blocks per SM, and the
 // edges each block owns.  Tiles are dealt round-robin to the 256-thread groups
 // and segments to the warps of the grid, so every block owns the same mix.
-void nb_partition(pr_graph* g, int per_sm) {
+void nb_partition(pr_graph* g, int per_sm, int threads, const std::vector<int64_t>& item_edges) {
     if (g->ctas_per_sm > 0) per_sm = std::min(g->ctas_per_sm, per_sm);
     per_sm = std::min(per_sm, 8);
-    const int groups = kNbBlock / kBlock, warps = kNbBlock / 32;
-    const int64_t count = g->nb_items_count;
+    const int groups = 1, warps = threads / 32;
+    const int64_t count = (int64_t)item_edges.size();
     const int64_t work = std::max<int64_t>((count + groups - 1) / groups, (g->nb_n_seg + warps - 1) / warps);
     const int G = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)g->sm_count * per_sm, work));
-    if (G == g->nb_grid) return;
     g->nb_cta_edges.assign((size_t)G, 0);
-    for (int64_t i = 0; i < count; ++i) g->nb_cta_edges[(i % ((int64_t)G * groups)) / groups] += g->nb_item_edges[i];
+    for (int64_t i = 0; i < count; ++i) g->nb_cta_edges[(i % ((int64_t)G * groups)) / groups] += item_edges[i];
     for (int64_t sg = 0; sg < g->nb_n_seg; ++sg) g->nb_cta_edges[(sg % ((int64_t)G * warps)) / warps] += g->nb_seg_edges[sg];
     g->nb_grid = G;
 }
@@ -687,10 +994,18 @@ pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_
     const bool staged = !diag && !perf && ((g->staged_tiles >> 1) & 1);
     const int32_t hub_n = (int32_t)(std::min<int64_t>(g->nb_hubs, g->n) & ~(int64_t)3);
     const size_t nb_smem = ((size_t)hub_n + (staged ? (size_t)kStageFloats : 0)) * sizeof(float);
-    void* kernel = pick_kernel(g, uniform, staged, diag, perf);
+    const char* form_env = getenv("PR_NB_DANGLING_FORM");
+    const int dangling_form = (form_env && form_env[0] == '0') ? 0 : 1;
+    // the pipelined form (PR_OPT_NB_PIPELINE) where it applies
+    const bool pipe = g->nb_pipeline && g->use_tma && !g->idx64 && !diag && !perf && !staged && hub_n == 0 &&
+                      dangling_form == 1 && g->nbp_items != nullptr;
+    void* kernel = pipe ? (uniform ? (void*)k_nonblocking_pipe<true> : (void*)k_nonblocking_pipe<false>)
+                        : pick_kernel(g, uniform, staged, diag, perf);
+    const int threads = pipe ? kNbpThreads : kNbBlock;
+    const size_t launch_smem = pipe ? kNbpSmem : nb_smem;
     int per_sm = 1;
-    if ((rc = nb_occupancy(kernel, nb_smem, &per_sm)) != PR_OK) return rc;
-    nb_partition(g, per_sm);
+    if ((rc = nb_occupancy(kernel, launch_smem, &per_sm, threads)) != PR_OK) return rc;
+    nb_partition(g, per_sm, threads, pipe ? g->nbp_item_edges : g->nb_item_edges);
     const int G = g->nb_grid;
 
     SolveState* hs = g->host_state;
@@ -726,8 +1041,9 @@ pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_
     na.colidx = g->colidx;
     na.inv_out = g->inv_out;
     na.teleport = uniform ? nullptr : g->teleport;
-    na.items = (const Tile*)g->nb_items;
-    na.n_items = (int32_t)g->nb_items_count;
+    na.items = (const Tile*)(pipe ? g->nbp_items : g->nb_items);
+    na.n_items = (int32_t)(pipe ? g->nbp_items_count : g->nb_items_count);
+    na.item_e1 = g->nbp_e1;
     na.seg_ptr = g->seg_ptr;
     na.seg_row = g->seg_row;
     na.n_seg = g->nb_n_seg;
@@ -736,8 +1052,7 @@ pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_
     na.scalars = g->nb_scalars;
     na.block_sweeps = g->nb_block_sweeps;
     na.sweeps_max = (int32_t*)(g->nb_scalars + 3);
-    const char* form_env = getenv("PR_NB_DANGLING_FORM");
-    na.dangling_form = (form_env && form_env[0] == '0') ? 0 : 1;
+    na.dangling_form = dangling_form;
     na.hub_n = hub_n;
     na.l1_hubs = (int32_t)std::min<int64_t>(g->nb_l1_hubs, g->n);
     na.state = g->state;
@@ -792,7 +1107,7 @@ pr_status solve_nonblocking(pr_graph* g, float damping, double tol, int32_t max_
         na.fail_after = launch_no == 0 ? g->nb_fail_after : 0;
         void* args[] = {&na};
         PRK_CHECK(cudaEventRecord(g->ev_loop0, s));
-        PRK_CHECK(cudaLaunchCooperativeKernel(kernel, dim3(G), dim3(kNbBlock), args, nb_smem, s));
+        PRK_CHECK(cudaLaunchCooperativeKernel(kernel, dim3(G), dim3(threads), args, launch_smem, s));
         PRK_CHECK(cudaEventRecord(g->ev_loop1, s));
         ++launches;
         // verify with one synchronous update x[0] -> x[1]

@@ -103,7 +103,8 @@ def test_options_validate_host_side():
                 pr.PR_OPT_HOT_VERTICES, pr.PR_OPT_HOT_CACHE, pr.PR_OPT_CTAS_PER_SM,
                 pr.PR_OPT_TMA_TILES, pr.PR_OPT_TEST_WITHHOLD_COPY, pr.PR_OPT_LIGHT_LANES,
                 pr.PR_OPT_FUSED_SEGMENTS, pr.PR_OPT_BATCH_DC, pr.PR_OPT_BATCH_ASYNC,
-                pr.PR_OPT_IMPLICIT_ZERO_ROWS, pr.PR_OPT_SYNC_DC, pr.PR_OPT_TMA_HOT_VERTICES):
+                pr.PR_OPT_IMPLICIT_ZERO_ROWS, pr.PR_OPT_SYNC_DC, pr.PR_OPT_TMA_HOT_VERTICES,
+                pr.PR_OPT_NB_PIPELINE):
         with pytest.raises(pr.PageRankError):
             pr.pr_set_option(None, key, 1)               # needs a graph
     pr.pr_set_option(None, pr.PR_OPT_INDEX64, 0)

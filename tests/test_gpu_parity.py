@@ -948,3 +948,30 @@ def test_nonblocking_leaves_isolated_vertices_to_the_end(build):
             assert l1(x, xstar) <= info.residual_l1 / (1 - D) + 2e-7
             _, _, r_or, _ = oracle.jacobi_step(rp, ci, x.astype(np.float64), d=D, t=t64)
             assert r_or < 2e-6
+
+
+@pytest.mark.parametrize("build", ["rmat14", "er", "rmat13_teleport"])
+def test_pipelined_nonblocking_reaches_the_fixed_point(build):
+    """PR_OPT_NB_PIPELINE: the barrier-free sweeps with the light-row tiles' offsets,
+    column indices, 1/outdeg and teleport staged in shared memory by a producer warp (bulk
+    asynchronous copies) reach the FP64 fixed point within the bound of their certified
+    residual, as the default form does."""
+    if build == "rmat14":
+        rp, ci = gg.rmat(14, seed=61)
+    elif build == "er":
+        rp, ci = gg.er_dangling(40000, 8.0, 0.2, seed=62)
+    else:
+        rp, ci = gg.rmat(13, seed=63)
+    n = rp.size - 1
+    t = None
+    if build == "rmat13_teleport":
+        t = (gg.uniform(11, 5, n) + 0.05).astype(np.float32)
+        t /= t.sum()
+    with pr.Graph(rp, ci) as g:
+        g.set_option(pr.PR_OPT_NB_PIPELINE, 1)
+        x, info = g.solve(tol=1e-6, max_iter=200, variant="nonblocking", teleport=t)
+        g.set_option(pr.PR_OPT_NB_PIPELINE, 0)
+    assert info.converged == 1 and info.residual_l1 < 1e-6
+    t64 = None if t is None else t.astype(np.float64)
+    xstar, _, _ = oracle.fixed_point(rp, ci, d=D, t=t64)
+    assert l1(x, xstar) <= info.residual_l1 / (1 - D) + 2e-7
