@@ -340,14 +340,21 @@ __global__ void __launch_bounds__(kBlock) k_b_light_async(BatchArgs a, const T* 
         int64_t row = tile.row_begin;
         float acc = 0.f;
         issue_window<T>(a.colidx, Y, eb, eend, buf0, lane);
+        // the lanes hold the end offsets of rows rbase + 1 .. rbase + 32; a
+        // window closes at most 32 rows from `row`, so they are reloaded only
+        // when a row has closed since (rows longer than a window skip it)
+        int64_t rbase = row;
+        int64_t rend = rbase + 1 + lane <= r1 ? row_at<IdxT>(a.rowptr, rbase + 1 + lane) : INT64_MAX;
         int w = 0;
         for (int64_t wb = eb; wb < eend; wb += kAW, ++w) {
             T* cur = (w & 1) ? buf1 : buf0;
             T* nxt = (w & 1) ? buf0 : buf1;
             if (wb + kAW < eend) issue_window<T>(a.colidx, Y, wb + kAW, eend, nxt, lane);
             else cp_async_commit();
-            // the ends of the rows this window may close: rows row .. row + 31
-            const int64_t rend = row + 1 + lane <= r1 ? row_at<IdxT>(a.rowptr, row + 1 + lane) : INT64_MAX;
+            if (row != rbase) {
+                rbase = row;
+                rend = rbase + 1 + lane <= r1 ? row_at<IdxT>(a.rowptr, rbase + 1 + lane) : INT64_MAX;
+            }
             const int64_t pos = rend - 1 - wb;
             const unsigned ends = __reduce_or_sync(0xffffffffu, (pos >= 0 && pos < kAW) ? (1u << pos) : 0u);
             const int cnt = (int)min((int64_t)kAW, eend - wb);
