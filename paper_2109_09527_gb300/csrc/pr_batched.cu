@@ -257,13 +257,19 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Copy the source rows of edges [wb, min(wb + kAW, ee)) into buf (row e of
-// the window at buf + e * kBK elements); rows past ee are not copied.
+// This lane's column index of the window of edges [wb, min(wb + kAW, ee))
+// (-1 past ee): loaded a window ahead of its copies, so that issuing them
+// does not wait on it.
+__device__ __forceinline__ int32_t window_col(const int32_t* __restrict__ colidx, int64_t wb, int64_t ee, int lane) {
+    return wb + lane < ee ? __ldg(colidx + wb + lane) : -1;
+}
+
+// Copy the source rows of a window (lane l holds the column index u_l of its
+// edge l, -1 for none) into buf (row e of the window at buf + e * kBK
+// elements).
 template <typename T>
-__device__ __forceinline__ void issue_window(const int32_t* __restrict__ colidx, const T* __restrict__ Y, int64_t wb,
-                                             int64_t ee, T* buf, int lane) {
+__device__ __forceinline__ void issue_window(int32_t u_l, const T* __restrict__ Y, T* buf, int lane) {
     constexpr int kPieces = kBK * (int)sizeof(T) / 16;   // 16-byte pieces of a row: 8 (FP32) or 4 (BF16)
-    const int32_t u_l = wb + lane < ee ? __ldg(colidx + wb + lane) : -1;
 #pragma unroll
     for (int k = 0; k < kPieces; ++k) {
         const int c = lane + 32 * k;          // piece c: row c / kPieces, part c % kPieces
@@ -295,13 +301,15 @@ __global__ void __launch_bounds__(kBlock) k_b_segments_async(BatchArgs a, const 
         const int64_t e0 = row_at<IdxT>(a.rowptr, h) + (s - a.seg_ptr[h]) * (int64_t)kSegEdges;
         const int64_t e1 = min(e0 + (int64_t)kSegEdges, re);
         float acc = 0.f;
-        issue_window<T>(a.colidx, Y, e0, e1, buf0, lane);
+        issue_window<T>(window_col(a.colidx, e0, e1, lane), Y, buf0, lane);
+        int32_t u_next = window_col(a.colidx, e0 + kAW, e1, lane);
         int w = 0;
         for (int64_t wb = e0; wb < e1; wb += kAW, ++w) {
             T* cur = (w & 1) ? buf1 : buf0;
             T* nxt = (w & 1) ? buf0 : buf1;
-            if (wb + kAW < e1) issue_window<T>(a.colidx, Y, wb + kAW, e1, nxt, lane);
+            if (wb + kAW < e1) issue_window<T>(u_next, Y, nxt, lane);
             else cp_async_commit();   // an empty group keeps the count of groups in flight fixed
+            u_next = window_col(a.colidx, wb + 2 * kAW, e1, lane);
             cp_async_wait<1>();
             __syncwarp();
             const int cnt = (int)min((int64_t)kAW, e1 - wb);
@@ -339,7 +347,8 @@ __global__ void __launch_bounds__(kBlock) k_b_light_async(BatchArgs a, const T* 
         const int64_t eb = row_at<IdxT>(a.rowptr, tile.row_begin), eend = row_at<IdxT>(a.rowptr, r1);
         int64_t row = tile.row_begin;
         float acc = 0.f;
-        issue_window<T>(a.colidx, Y, eb, eend, buf0, lane);
+        issue_window<T>(window_col(a.colidx, eb, eend, lane), Y, buf0, lane);
+        int32_t u_next = window_col(a.colidx, eb + kAW, eend, lane);
         // the lanes hold the end offsets of rows rbase + 1 .. rbase + 32; a
         // window closes at most 32 rows from `row`, so they are reloaded only
         // when a row has closed since (rows longer than a window skip it)
@@ -349,8 +358,9 @@ __global__ void __launch_bounds__(kBlock) k_b_light_async(BatchArgs a, const T* 
         for (int64_t wb = eb; wb < eend; wb += kAW, ++w) {
             T* cur = (w & 1) ? buf1 : buf0;
             T* nxt = (w & 1) ? buf0 : buf1;
-            if (wb + kAW < eend) issue_window<T>(a.colidx, Y, wb + kAW, eend, nxt, lane);
+            if (wb + kAW < eend) issue_window<T>(u_next, Y, nxt, lane);
             else cp_async_commit();
+            u_next = window_col(a.colidx, wb + 2 * kAW, eend, lane);
             if (row != rbase) {
                 rbase = row;
                 rend = rbase + 1 + lane <= r1 ? row_at<IdxT>(a.rowptr, rbase + 1 + lane) : INT64_MAX;
