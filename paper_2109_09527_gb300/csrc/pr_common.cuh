@@ -42,11 +42,19 @@ constexpr int kIterBlock = 256;          // threads per block of the Jacobi iter
 #define PRK_GATHER_MIN_BLOCKS 4
 #endif
 constexpr int kGatherMinBlocks = PRK_GATHER_MIN_BLOCKS;
-// The barrier-free kernel is latency-bound: six blocks per SM (40 registers a
-// thread, a few spilled) measured faster than four (ER-24: 2.15 -> 1.77 ms
-// per sweep-equivalent), while the synchronous kernels are best at four.
+// The barrier-free kernel is latency-bound.  With two edges of each row in
+// flight per lane, six blocks per SM (40 registers a thread, a few spilled)
+// measured faster than four (ER-24: 2.15 -> 1.77 ms per sweep-equivalent).
+// With the next step's column indices loaded while a step's gathers are in
+// flight, four blocks of four edges per row and lane (61 registers) measured
+// best (R-MAT-24 + ER-24 solves: 24.05 ms, against 24.18 at five blocks of
+// four edges, 24.42 at five of two, 24.98 at six of two).
 #ifndef PRK_NB_MIN_BLOCKS
-#define PRK_NB_MIN_BLOCKS 6
+#define PRK_NB_MIN_BLOCKS 4
+#endif
+// Edges of each of its two rows a lane of the barrier-free kernel gathers per step.
+#ifndef PRK_NB_UNROLL
+#define PRK_NB_UNROLL 4
 #endif
 constexpr int kNbMinBlocks = PRK_NB_MIN_BLOCKS;
 constexpr int kHotCacheMax = 40960;      // largest shared-memory copy of y's hot prefix (160 KB)

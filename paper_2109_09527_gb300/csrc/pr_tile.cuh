@@ -324,6 +324,39 @@ template <bool kInPlace, int kU, typename OffT, typename ColAt, typename YT>
 __device__ __forceinline__ void gather_row_pair(const ColAt& col, OffT b0, OffT e0, OffT b1, OffT e1, int g,
                                                 const YT* y, const RowCtx& c, float& s0, float& s1) {
     static_assert(kU == 2 || kU == 4, "two or four edges per row per step");
+    if constexpr (kInPlace) {
+        // the barrier-free kernel reads the column indices from global memory:
+        // the next step's are loaded while this step's gathers are in flight
+        int32_t c0[kU], c1[kU];
+#pragma unroll
+        for (int j = 0; j < kU; ++j) {
+            c0[j] = b0 + j * g < e0 ? col(b0 + j * g) : -1;
+            c1[j] = b1 + j * g < e1 ? col(b1 + j * g) : -1;
+        }
+        while (b0 < e0 || b1 < e1) {
+            float v0[kU], v1[kU];
+#pragma unroll
+            for (int j = 0; j < kU; ++j) {
+                v0[j] = c0[j] >= 0 ? Mem<kInPlace>::gather(y, c0[j], c) : 0.f;
+                v1[j] = c1[j] >= 0 ? Mem<kInPlace>::gather(y, c1[j], c) : 0.f;
+            }
+            b0 += kU * g;
+            b1 += kU * g;
+#pragma unroll
+            for (int j = 0; j < kU; ++j) {
+                c0[j] = b0 + j * g < e0 ? col(b0 + j * g) : -1;
+                c1[j] = b1 + j * g < e1 ? col(b1 + j * g) : -1;
+            }
+            if constexpr (kU == 4) {
+                s0 += (v0[0] + v0[1]) + (v0[2] + v0[3]);
+                s1 += (v1[0] + v1[1]) + (v1[2] + v1[3]);
+            } else {
+                s0 += v0[0] + v0[1];
+                s1 += v1[0] + v1[1];
+            }
+        }
+        return;
+    }
     while (b0 < e0 || b1 < e1) {
         int32_t c0[kU], c1[kU];
 #pragma unroll
@@ -461,7 +494,7 @@ __device__ __forceinline__ void process_light_tile(const Tile& tile, const void*
             }
         }
         float s[2] = {0.f, 0.f};
-        gather_row_pair<kInPlace, kInPlace ? 2 : 4>([&](int64_t p) { return ld_stream(colidx + p); }, b[0] + gl,
+        gather_row_pair<kInPlace, kInPlace ? PRK_NB_UNROLL : 4>([&](int64_t p) { return ld_stream(colidx + p); }, b[0] + gl,
                                                     e[0], b[1] + gl, e[1], g, y_in, c, s[0], s[1]);
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1)
