@@ -567,7 +567,7 @@ __device__ __forceinline__ void nbp_light_tile(const Tile& tile, const NbpStage&
             xo[q] = (act[q] && gl == 0) ? Mem<true>::load_x(xr + tile.row_begin + ii[q]) : 0.f;
         }
         float s[2] = {0.f, 0.f};
-        gather_row_pair<true, PRK_NBP_UNROLL>([col](int32_t p) { return col[p]; }, b[0] + gl, e[0], b[1] + gl, e[1],
+        gather_row_pair<true, PRK_NBP_UNROLL, false>([col](int32_t p) { return col[p]; }, b[0] + gl, e[0], b[1] + gl, e[1],
                                               g, a.y, c, s[0], s[1]);
 #pragma unroll
         for (int m = 1; m < 32; m <<= 1)

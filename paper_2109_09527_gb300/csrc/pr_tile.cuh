@@ -283,7 +283,7 @@ __device__ __forceinline__ int light_lanes_log2(const Tile& tile, int mode) {
 // col(p) is the source id of edge p.  Every synchronous light-tile path sums
 // through this routine with kU = 4, so they agree bit for bit on a row's sum;
 // the barrier-free kernel, compiled for fewer registers, takes kU = 2.
-template <bool kInPlace, int kU = 4, typename OffT, typename ColAt, typename YT>
+template <bool kInPlace, int kU = 4, bool kPrefetch = kInPlace, typename OffT, typename ColAt, typename YT>
 __device__ __forceinline__ void gather_row_pair(const ColAt& col, OffT b0, OffT e0, OffT b1, OffT e1, int g,
                                                 const YT* y, const RowCtx& c, float& s0, float& s1);
 
@@ -320,13 +320,13 @@ struct Mem<true> {
     static __device__ __forceinline__ void store_y(float* p, float v) { st_relaxed_p<PRK_L2_GATHER>(p, v); }
 };
 
-template <bool kInPlace, int kU, typename OffT, typename ColAt, typename YT>
+template <bool kInPlace, int kU, bool kPrefetch, typename OffT, typename ColAt, typename YT>
 __device__ __forceinline__ void gather_row_pair(const ColAt& col, OffT b0, OffT e0, OffT b1, OffT e1, int g,
                                                 const YT* y, const RowCtx& c, float& s0, float& s1) {
     static_assert(kU == 2 || kU == 4, "two or four edges per row per step");
-    if constexpr (kInPlace) {
-        // the barrier-free kernel reads the column indices from global memory:
-        // the next step's are loaded while this step's gathers are in flight
+    if constexpr (kPrefetch) {
+        // column indices read from global memory: the next step's are loaded
+        // while this step's gathers are in flight
         int32_t c0[kU], c1[kU];
 #pragma unroll
         for (int j = 0; j < kU; ++j) {
@@ -494,7 +494,7 @@ __device__ __forceinline__ void process_light_tile(const Tile& tile, const void*
             }
         }
         float s[2] = {0.f, 0.f};
-        gather_row_pair<kInPlace, kInPlace ? PRK_NB_UNROLL : 4>([&](int64_t p) { return ld_stream(colidx + p); }, b[0] + gl,
+        gather_row_pair<kInPlace, kInPlace ? PRK_NB_UNROLL : 4, true>([&](int64_t p) { return ld_stream(colidx + p); }, b[0] + gl,
                                                     e[0], b[1] + gl, e[1], g, y_in, c, s[0], s[1]);
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1)
@@ -592,7 +592,7 @@ __device__ __forceinline__ void perf_light_tile(const Tile& tile, const void* ro
             }
         }
         float s[2] = {0.f, 0.f};
-        gather_row_pair<false>([&](int64_t q) { return ld_stream(colidx + q); }, b[0] + gl, e[0], b[1] + gl, e[1],
+        gather_row_pair<false, 4, true>([&](int64_t q) { return ld_stream(colidx + q); }, b[0] + gl, e[0], b[1] + gl, e[1],
                                g, y_in, c, s[0], s[1]);
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1)
