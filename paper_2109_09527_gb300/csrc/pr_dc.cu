@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kBlock) k_dc_rows(IterArgs a, const float* __r
                 }
                 float s[2] = {0.f, 0.f};
                 const int32_t* colidx = a.colidx;
-                gather_row_pair<false, 4, true>([&](int64_t p) { return ld_stream(colidx + p); }, b[0] + gl, e[0],
+                gather_row_pair<false, 4, true>([&](int64_t p) { return ld_col<PRK_SYNC_COL_L1>(colidx + p); }, b[0] + gl, e[0],
                                           b[1] + gl, e[1], g, q_in, c, s[0], s[1]);
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1)

@@ -86,6 +86,35 @@ __device__ __forceinline__ int4 ld_stream4(const int32_t* p) {
     return v;
 }
 
+// Column index of a light row gathered by lane groups (gather_row_pair from
+// global memory).  The lanes of a warp read one stretch of g indices from each
+// of 32/g rows per instruction, and the next instructions of the step read the
+// following stretches of the same lines: through L1 (kMode 1: evict_first,
+// 2: evict_normal) those lines are requested from L2 once; kMode 0 does not
+// allocate in L1.  PRK_NB_COL_L1 is the barrier-free kernel's mode,
+// PRK_SYNC_COL_L1 that of the synchronous light-row gathers.
+#ifndef PRK_NB_COL_L1
+#define PRK_NB_COL_L1 2
+#endif
+#ifndef PRK_SYNC_COL_L1
+#define PRK_SYNC_COL_L1 2
+#endif
+template <int kMode>
+__device__ __forceinline__ int32_t ld_col(const int32_t* p) {
+    if constexpr (kMode == 0) {
+        return ld_stream(p);
+    } else {
+        int32_t v;
+        if constexpr (kMode == 1)
+            asm("ld.global.nc.L1::evict_first.L2::cache_hint.s32 %0, [%1], %2;"
+                : "=r"(v) : "l"(p), "l"(l2_policy<PRK_L2_STREAM>()));
+        else
+            asm("ld.global.nc.L1::evict_normal.L2::cache_hint.s32 %0, [%1], %2;"
+                : "=r"(v) : "l"(p), "l"(l2_policy<PRK_L2_STREAM>()));
+        return v;
+    }
+}
+
 // Gathers of y with the gather-class L2 policy: through L1 (ldg) or L2 only (cg).
 __device__ __forceinline__ float ld_y_ldg(const float* p) {
     if constexpr (PRK_L2_GATHER == 0) {
@@ -494,8 +523,9 @@ __device__ __forceinline__ void process_light_tile(const Tile& tile, const void*
             }
         }
         float s[2] = {0.f, 0.f};
-        gather_row_pair<kInPlace, kInPlace ? PRK_NB_UNROLL : 4, true>([&](int64_t p) { return ld_stream(colidx + p); }, b[0] + gl,
-                                                    e[0], b[1] + gl, e[1], g, y_in, c, s[0], s[1]);
+        gather_row_pair<kInPlace, kInPlace ? PRK_NB_UNROLL : 4, true>(
+            [&](int64_t p) { return ld_col<kInPlace ? PRK_NB_COL_L1 : PRK_SYNC_COL_L1>(colidx + p); }, b[0] + gl, e[0],
+            b[1] + gl, e[1], g, y_in, c, s[0], s[1]);
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1)
             if (o < g) {
@@ -592,7 +622,7 @@ __device__ __forceinline__ void perf_light_tile(const Tile& tile, const void* ro
             }
         }
         float s[2] = {0.f, 0.f};
-        gather_row_pair<false, 4, true>([&](int64_t q) { return ld_stream(colidx + q); }, b[0] + gl, e[0], b[1] + gl, e[1],
+        gather_row_pair<false, 4, true>([&](int64_t q) { return ld_col<PRK_SYNC_COL_L1>(colidx + q); }, b[0] + gl, e[0], b[1] + gl, e[1],
                                g, y_in, c, s[0], s[1]);
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1)
