@@ -53,6 +53,17 @@ struct WState {
     int32_t pad;
 };
 
+// Ends of the row classes in a class order (rows listed class by class, in
+// caller order within a class): [0, giant) rows with >= kWGiantEdges edges,
+// [giant, heavy) those with >= 32, [heavy, mid) 8..31 edges, [mid, small)
+// 1..7 edges, [small, n) rows without edges.
+struct WClasses {
+    int64_t giant;
+    int64_t heavy;
+    int64_t mid;
+    int64_t small;
+};
+
 struct WArgs {
     int64_t n;
     int64_t nnz;
@@ -63,56 +74,74 @@ struct WArgs {
     const int32_t* out_dst;
     const float* out_p;         // P(u, v) of each out-edge
     const float* inv_w;         // 1/W(u), 0 for dangling u
-    const int32_t* in_order;    // rows by in-degree: the n_in_giant rows with >= kWGiantEdges in-edges,
-    int64_t n_in_giant;         // then up to n_in_heavy those with >= 32, then the rest
-    int64_t n_in_heavy;
+    const int32_t* in_order;    // rows by in-degree class (WClasses)
+    WClasses in_cls;
     const int32_t* out_order;   // the same classes by out-degree
-    int64_t n_out_giant;
-    int64_t n_out_heavy;
+    WClasses out_cls;
     WState* state;
     double* slots;
 };
 
-// Rows are visited in three passes: rows with at least kWGiantEdges edges a
+// Rows are visited class by class: rows with at least kWGiantEdges edges a
 // block each (a power-law hub has tens of thousands: one warp walking it
 // would set the length of the whole launch), rows with at least 32 edges a
-// warp each, then the rest by groups of 8 lanes (four rows per warp at a
-// time).  The row body gather(row, lane_in_group, group_size) returns this
-// lane's share of the row's sum; the group's total reaches the group's first
-// thread, where `epilogue(row, sum)` runs.
+// warp each, rows of 8..31 edges by groups of 8 lanes and rows of 1..7 by
+// groups of 4 (four or eight rows per warp at a time), rows without edges a
+// thread each.  The row body gather(row, lane_in_group, group_size) returns
+// this lane's share of the row's sum; the group's total reaches the group's
+// first thread, where `epilogue(row, sum)` runs (with sum 0 for a row without
+// edges).  With PRK_W_CLASSES = 0 the set-up lists every row below 32 edges in
+// one class of 8-lane groups.
+#ifndef PRK_W_CLASSES
+#define PRK_W_CLASSES 1
+#endif
 constexpr int kWLightLanes = 8;
+constexpr int kWSmallLanes = 4;
+constexpr int kWSmallEdges = 8;
 #ifndef PRK_W_GIANT_EDGES
 #define PRK_W_GIANT_EDGES 2048
 #endif
 constexpr int64_t kWGiantEdges = PRK_W_GIANT_EDGES;
 
+// Rows [begin, end) of the order by groups of G lanes; the loop bound is
+// uniform per warp, so every lane reaches the shuffles.
+template <int G, typename Gather, typename Epilogue>
+__device__ __forceinline__ void w_groups(const int32_t* order, int64_t begin, int64_t end, int64_t warp,
+                                         int64_t nwarp, int lane, Gather& gather, Epilogue& epilogue) {
+    constexpr int per = 32 / G;
+    const int sub = lane / G, sl = lane % G;
+    for (int64_t i0 = begin + warp * per; i0 < end; i0 += nwarp * per) {
+        const int64_t i = i0 + sub;
+        const bool act = i < end;
+        const int32_t r = act ? order[i] : 0;
+        float s = act ? gather(r, sl, G) : 0.f;
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (act && sl == 0) epilogue(r, s);
+    }
+}
+
 template <typename Gather, typename Epilogue>
-__device__ __forceinline__ void w_rows(const int32_t* order, int64_t n, int64_t n_giant, int64_t n_heavy,
-                                       Gather gather, Epilogue epilogue) {
+__device__ __forceinline__ void w_rows(const int32_t* order, int64_t n, const WClasses& cls, Gather gather,
+                                       Epilogue epilogue) {
     const int lane = threadIdx.x & 31;
-    for (int64_t i = blockIdx.x; i < n_giant; i += gridDim.x) {   // uniform per block
+    for (int64_t i = blockIdx.x; i < cls.giant; i += gridDim.x) {   // uniform per block
         const int32_t r = order[i];
         const float s = block_sum(gather(r, (int)threadIdx.x, (int)blockDim.x));
         if (threadIdx.x == 0) epilogue(r, s);
     }
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = n_giant + warp; i < n_heavy; i += nwarp) {
+    for (int64_t i = cls.giant + warp; i < cls.heavy; i += nwarp) {
         const int32_t r = order[i];
         float s = warp_sum(gather(r, lane, 32));
         if (lane == 0) epilogue(r, s);
     }
-    constexpr int per = 32 / kWLightLanes;
-    const int sub = lane / kWLightLanes, sl = lane % kWLightLanes;
-    for (int64_t i0 = n_heavy + warp * per; i0 < n; i0 += nwarp * per) {
-        const int64_t i = i0 + sub;
-        const bool act = i < n;
-        const int32_t r = act ? order[i] : 0;
-        float s = act ? gather(r, sl, kWLightLanes) : 0.f;
-#pragma unroll
-        for (int o = kWLightLanes / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (act && sl == 0) epilogue(r, s);
-    }
+    w_groups<kWLightLanes>(order, cls.heavy, cls.mid, warp, nwarp, lane, gather, epilogue);
+    w_groups<kWSmallLanes>(order, cls.mid, cls.small, warp, nwarp, lane, gather, epilogue);
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = cls.small + tid; i < n; i += nthreads) epilogue(order[i], 0.f);
 }
 
 // sum over the edges k of row r of p[k] * vec[idx[k]], this lane's share
@@ -158,7 +187,7 @@ __global__ void __launch_bounds__(kBlock) k_w_forward(WArgs a, const float* __re
     const float share = (float)(s_D * s_inv_n);
     const float tu = (float)s_inv_n;
     Acc acc;
-    w_rows(a.in_order, a.n, a.n_in_giant, a.n_in_heavy,
+    w_rows(a.in_order, a.n, a.in_cls,
            [&](int32_t v, int l, int g) { return w_gather(a.rowptr, a.colidx, a.in_p, x, v, l, g); },
            [&](int32_t v, float s) {
                const float tv = t ? t[v] : tu;
@@ -196,7 +225,7 @@ __global__ void __launch_bounds__(kBlock) k_w_adjoint(WArgs a, const float* __re
     const float d = (float)s_d;
     const float lshare = (float)(s_L * s_inv_n);
     double r = 0.0, L = 0.0;
-    w_rows(a.out_order, a.n, a.n_out_giant, a.n_out_heavy,
+    w_rows(a.out_order, a.n, a.out_cls,
            [&](int32_t u, int l, int g) { return w_gather(a.out_rowptr, a.out_dst, a.out_p, lam, u, l, g); },
            [&](int32_t u, float m) {
                if (final) {
@@ -229,7 +258,7 @@ __global__ void __launch_bounds__(kBlock) k_w_grads(WArgs a, const float* __rest
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < a.n; u += stride)
         if (grad_t) grad_t[u] = (1.f - d) * lam[u];
     if (!grad_w) return;
-    w_rows(a.in_order, a.n, a.n_in_giant, a.n_in_heavy,
+    w_rows(a.in_order, a.n, a.in_cls,
            [&](int32_t v, int l, int g) {
                const float lv = lam[v];
                for (int64_t e = a.rowptr[v] + l; e < a.rowptr[v + 1]; e += g) {
@@ -347,10 +376,8 @@ struct pr_wgraph {
     double* W = nullptr;
     int32_t* in_order = nullptr;
     int32_t* out_order = nullptr;
-    int64_t n_in_giant = 0;
-    int64_t n_in_heavy = 0;
-    int64_t n_out_giant = 0;
-    int64_t n_out_heavy = 0;
+    prk::WClasses in_cls{};
+    prk::WClasses out_cls{};
     float* vec[4] = {nullptr, nullptr, nullptr, nullptr};   // iterate buffers, mu
     float* stage = nullptr;                                 // host inputs / outputs
     prk::WState* state = nullptr;
@@ -382,11 +409,9 @@ WArgs w_args(const pr_wgraph* g) {
     a.out_p = g->out_p;
     a.inv_w = g->inv_w;
     a.in_order = g->in_order;
-    a.n_in_giant = g->n_in_giant;
-    a.n_in_heavy = g->n_in_heavy;
+    a.in_cls = g->in_cls;
     a.out_order = g->out_order;
-    a.n_out_giant = g->n_out_giant;
-    a.n_out_heavy = g->n_out_heavy;
+    a.out_cls = g->out_cls;
     a.state = g->state;
     a.slots = g->slots;
     return a;
@@ -494,34 +519,35 @@ extern "C" pr_status pr_create_wgraph(int64_t n, int64_t nnz, const int64_t* row
                 oeid[slot] = k;
             }
     }
-    // rows with >= kWGiantEdges edges first (a block each), then those with
-    // >= 32 (a warp each), then the rest (groups of 8 lanes); caller order
-    // within each class
-    auto split = [&](const std::vector<int64_t>& ptr, std::vector<int32_t>& order, int64_t& n_giant,
-                     int64_t& n_heavy) {
+    // the row classes of w_rows, each in caller order
+    auto split = [&](const std::vector<int64_t>& ptr, std::vector<int32_t>& order, WClasses& cls) {
         order.clear();
         order.reserve((size_t)n);
-        for (int64_t v = 0; v < n; ++v)
-            if (ptr[v + 1] - ptr[v] >= kWGiantEdges) order.push_back((int32_t)v);
-        n_giant = (int64_t)order.size();
-        for (int64_t v = 0; v < n; ++v) {
-            const int64_t dv = ptr[v + 1] - ptr[v];
-            if (dv >= 32 && dv < kWGiantEdges) order.push_back((int32_t)v);
+        auto take = [&](int64_t lo, int64_t hi) {   // rows with lo <= edges < hi
+            for (int64_t v = 0; v < n; ++v) {
+                const int64_t dv = ptr[v + 1] - ptr[v];
+                if (dv >= lo && dv < hi) order.push_back((int32_t)v);
+            }
+            return (int64_t)order.size();
+        };
+        cls.giant = take(kWGiantEdges, INT64_MAX);
+        cls.heavy = take(32, kWGiantEdges);
+        if (PRK_W_CLASSES) {
+            cls.mid = take(kWSmallEdges, 32);
+            cls.small = take(1, kWSmallEdges);
+            take(0, 1);
+        } else {
+            cls.mid = cls.small = take(0, 32);
         }
-        n_heavy = (int64_t)order.size();
-        for (int64_t v = 0; v < n; ++v)
-            if (ptr[v + 1] - ptr[v] < 32) order.push_back((int32_t)v);
     };
     std::vector<int32_t> in_order, out_order;
-    int64_t n_in_giant = 0, n_in_heavy = 0, n_out_giant = 0, n_out_heavy = 0;
-    split(rp, in_order, n_in_giant, n_in_heavy);
-    split(orp, out_order, n_out_giant, n_out_heavy);
+    WClasses in_cls{}, out_cls{};
+    split(rp, in_order, in_cls);
+    split(orp, out_order, out_cls);
     pr_wgraph* g = new (std::nothrow) pr_wgraph();
     if (!g) return fail(PR_ERR_OOM, "pr_create_wgraph: host allocation failed");
-    g->n_in_giant = n_in_giant;
-    g->n_in_heavy = n_in_heavy;
-    g->n_out_giant = n_out_giant;
-    g->n_out_heavy = n_out_heavy;
+    g->in_cls = in_cls;
+    g->out_cls = out_cls;
     g->n = n;
     g->nnz = nnz;
     pr_status rc = PR_OK;
