@@ -1404,7 +1404,9 @@ def main():
         phases.append("; ".join(ph))
         return v
 
-    e2e_step()
+    e2e_warmup = max(1, args.warmup)   # untimed, as the device-resident steps
+    for _ in range(e2e_warmup):
+        e2e_step()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -1414,10 +1416,10 @@ def main():
         ev += e2e_step()
     torch.cuda.synchronize()
     for i, p in enumerate(phases):
-        log(f"[bench] e2e step {i} (0: untimed): {p}")
+        log(f"[bench] e2e step {i} ({'untimed' if i < e2e_warmup else 'timed'}): {p}")
     e2e_s, ev = combine_ranks(dist, dev, time.perf_counter() - t0, ev)
     e2e = {"value": ev / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
+           "d2h_bytes_per_step": d2h, "steps": args.e2e_steps, "warmup": e2e_warmup,
            "ms_per_step": e2e_s * 1e3 / args.e2e_steps,
            "includes": "pr_create_graph from pinned host CSR (H2D + set-up), Jacobi and "
                        "barrier-free solves, D2H of each result, pr_destroy_graph"}

@@ -97,9 +97,42 @@ cudaError_t pool_free(void* p, cudaStream_t stream) {
     if (e != cudaSuccess) return e;
     return cudaFreeAsync(p, ps);
 }
+
+// Blocks last used by work on `stream` go back to the pool on the pool's own
+// stream, which first waits for `stream` to reach this point.  Freed there,
+// they are reusable in stream order by the next allocation (which runs on
+// the pool stream), so a set-up that frees its scratch and then allocates
+// does not make the pool grow while the scratch's kernels are still queued.
+cudaError_t pool_free_after(void* const* ptrs, size_t count, cudaStream_t stream) {
+    if (count == 0) return cudaSuccess;
+    cudaMemPool_t pool;
+    cudaStream_t ps;
+    cudaError_t e = lib_pool(&pool, &ps);
+    cudaEvent_t ev = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ps, ev, 0);
+    if (ev) cudaEventDestroy(ev);   // released once the wait has been satisfied
+    cudaError_t first = e;
+    for (size_t i = 0; i < count; ++i)
+        if (ptrs[i]) {
+            const cudaError_t f = e == cudaSuccess ? cudaFreeAsync(ptrs[i], ps) : cudaFreeAsync(ptrs[i], stream);
+            if (first == cudaSuccess) first = f;
+        }
+    return first;
+}
 #else
 cudaError_t pool_alloc(void** p, size_t bytes) { return cudaMalloc(p, bytes ? bytes : 16); }
 cudaError_t pool_free(void* p, cudaStream_t) { return p ? cudaFree(p) : cudaSuccess; }
+cudaError_t pool_free_after(void* const* ptrs, size_t count, cudaStream_t) {
+    cudaError_t first = cudaSuccess;
+    for (size_t i = 0; i < count; ++i)
+        if (ptrs[i]) {
+            const cudaError_t f = cudaFree(ptrs[i]);
+            if (first == cudaSuccess) first = f;
+        }
+    return first;
+}
 #endif
 
 cudaError_t dev_alloc(pr_graph* g, void** p, size_t bytes) {

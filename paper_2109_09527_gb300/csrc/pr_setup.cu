@@ -282,21 +282,22 @@ int grid_for(int64_t work, int sm_count) {
 }
 
 // Scratch allocations freed when set-up returns.
-// With a stream, the scratch goes back to the pool in that stream's order
-// (after the set-up kernels that use it), without a device-wide wait.
+// With a stream, the scratch goes back to the pool once that stream has
+// reached the end of the set-up kernels that use it (pool_free_after),
+// without a device-wide wait.
 struct Scratch {
     std::vector<void*> ptrs;
     cudaStream_t stream = nullptr;
     Scratch() = default;
     explicit Scratch(cudaStream_t s) : stream(s) {}
     ~Scratch() {
+        if (stream) {
+            pool_free_after(ptrs.data(), ptrs.size(), stream);
+            return;
+        }
         for (void* p : ptrs) {
-            if (stream) {
-                pool_free(p, stream);
-            } else {
-                cudaDeviceSynchronize();
-                pool_free(p, nullptr);
-            }
+            cudaDeviceSynchronize();
+            pool_free(p, nullptr);
         }
     }
     cudaError_t alloc(void** p, size_t bytes) {
