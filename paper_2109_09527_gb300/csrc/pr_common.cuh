@@ -332,9 +332,6 @@ cudaError_t dev_free(void* p);
 // the library's own stream (the caller has made sure nothing still uses it).
 cudaError_t pool_alloc(void** p, size_t bytes);
 cudaError_t pool_free(void* p, cudaStream_t stream);
-// pool_free of every pointer once `stream` has reached this point, returned
-// on the pool's own stream (reusable in stream order by the next pool_alloc).
-cudaError_t pool_free_after(void* const* ptrs, size_t count, cudaStream_t stream);
 
 bool is_device_pointer(const void* p);
 

@@ -281,6 +281,11 @@ int grid_for(int64_t work, int sm_count) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, cap));
 }
 
+// pool_free of every pointer once `stream` has reached this point, returned
+// on the pool's own stream (reusable in stream order by the next pool_alloc);
+// defined beside the pool in pr_capi.cu.
+cudaError_t pool_free_after(void* const* ptrs, size_t count, cudaStream_t stream);
+
 // Scratch allocations freed when set-up returns.
 // With a stream, the scratch goes back to the pool once that stream has
 // reached the end of the set-up kernels that use it (pool_free_after),
