@@ -17,6 +17,12 @@
 #include "pr_common.cuh"
 
 namespace prk {
+
+// pool_free of every pointer once `stream` has reached this point, returned
+// on the pool's own stream (reusable in stream order by the next pool_alloc);
+// defined beside the pool in pr_capi.cu.
+cudaError_t pool_free_after(void* const* ptrs, size_t count, cudaStream_t stream);
+
 namespace {
 
 constexpr int kChunk = 4096;  // elements per block in the scan and sort kernels (256 x 16)
@@ -280,11 +286,6 @@ int grid_for(int64_t work, int sm_count) {
     int64_t cap = (int64_t)sm_count * 16;
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, cap));
 }
-
-// pool_free of every pointer once `stream` has reached this point, returned
-// on the pool's own stream (reusable in stream order by the next pool_alloc);
-// defined beside the pool in pr_capi.cu.
-cudaError_t pool_free_after(void* const* ptrs, size_t count, cudaStream_t stream);
 
 // Scratch allocations freed when set-up returns.
 // With a stream, the scratch goes back to the pool once that stream has
